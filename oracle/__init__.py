@@ -1,0 +1,187 @@
+"""FP64 CPU oracle of the RFA bioheat explicit scheme -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its Python binding) never imports, links or runs it; the two share no code.
+
+The numeric work is in ``oracle.c`` (plain C, FP64, OpenMP over z so the result
+does not depend on the thread count); this module only marshals numpy arrays.
+``brute.py`` holds an independent dense-matrix formulation used to pin it.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+_P_D = ctypes.POINTER(ctypes.c_double)
+_P_U8 = ctypes.POINTER(ctypes.c_uint8)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        i, d, i64 = ctypes.c_int, ctypes.c_double, ctypes.c_int64
+        L.or_round_bf16.argtypes = [d]
+        L.or_round_bf16.restype = d
+        L.or_setup.argtypes = [i, i, i, d, d, i, d, i, _P_U8, i, _P_D,
+                               _P_D, _P_D, _P_D, _P_D, _P_U8, _P_D]
+        L.or_source.argtypes = [i, i, i, d, d, _P_D, _P_D, _P_U8, _P_D, _P_D, _P_D]
+        L.or_run.argtypes = [i, i, i, i64, _P_D, _P_D, _P_D, _P_D, _P_U8, _P_D, _P_U8, d, d,
+                             i, d, d, d, d, _P_D, _P_D, i]
+        L.or_adjoint.argtypes = [i, i, i, i64, d, d, _P_D, _P_D, _P_D, _P_D, _P_U8, _P_U8, i,
+                                 _P_D, _P_D, _P_D, _P_D, _P_D, _P_D, _P_D, i]
+        L.or_source_grad.argtypes = [i, i, i, d, d, _P_D, _P_D, _P_U8, _P_D, _P_D]
+        for f in ("or_setup", "or_source", "or_run", "or_adjoint", "or_source_grad"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _pd(a):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_P_D)
+
+
+def _pu8(a):
+    assert a.dtype == np.uint8 and a.flags.c_contiguous
+    return a.ctypes.data_as(_P_U8)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+def round_bf16(x: float) -> float:
+    return lib().or_round_bf16(float(x))
+
+
+def table_array(table) -> np.ndarray:
+    return np.ascontiguousarray(np.array([t.as_tuple() for t in table], dtype=np.float64))
+
+
+def needle_array(nd) -> np.ndarray:
+    ax = list(nd.axis)
+    return np.ascontiguousarray(np.array(
+        [nd.kind, nd.tip[0], nd.tip[1], nd.tip[2], ax[0], ax[1], ax[2], nd.active_len,
+         nd.tine_len, nd.tine_polar_deg, nd.n_tines, nd.tine_axial, nd.power, nd.r_clamp],
+        dtype=np.float64))
+
+
+PARAM_MODE = {"f64": 0, "f32": 1, "bf16": 2}
+
+
+@dataclasses.dataclass
+class Model:
+    """Per-voxel coefficients of one problem (all [nz, ny, nx] float64)."""
+    nx: int
+    ny: int
+    nz: int
+    h: float
+    dt: float
+    a: np.ndarray
+    b: np.ndarray
+    qm: np.ndarray
+    rhoc: np.ndarray
+    isfixed: np.ndarray
+    theta0: np.ndarray
+    s: np.ndarray
+    dist: np.ndarray
+    W: float
+    labels: np.ndarray
+    tab: np.ndarray
+    needle: np.ndarray
+    T_a: float
+
+
+def setup(case, param_mode: str = "f64") -> Model:
+    """Coefficients, fixed set, initial state and RF source of ``case``."""
+    nx, ny, nz = case.nx, case.ny, case.nz
+    shape = (nz, ny, nx)
+    labels = np.ascontiguousarray(case.labels.astype(np.uint8).reshape(shape))
+    tab = table_array(case.table)
+    a, b, qm, rhoc, th0 = (np.zeros(shape) for _ in range(5))
+    fx = np.zeros(shape, dtype=np.uint8)
+    _check(lib().or_setup(nx, ny, nz, case.h, case.dt, case.face_bc, case.T_a_C,
+                          PARAM_MODE[param_mode], _pu8(labels), len(case.table), _pd(tab),
+                          _pd(a), _pd(b), _pd(qm), _pd(rhoc), _pu8(fx), _pd(th0)), "setup")
+    nd = needle_array(case.needle)
+    s, dist = np.zeros(shape), np.zeros(shape)
+    W = ctypes.c_double(0.0)
+    _check(lib().or_source(nx, ny, nz, case.h, case.dt, _pd(nd), _pd(rhoc), _pu8(fx), _pd(s),
+                           _pd(dist), ctypes.byref(W)), "source")
+    return Model(nx, ny, nz, case.h, case.dt, a, b, qm, rhoc, fx, th0, s, dist, W.value,
+                 labels, tab, nd, case.T_a_C)
+
+
+@dataclasses.dataclass
+class State:
+    theta: np.ndarray
+    latch: np.ndarray
+    omega: np.ndarray
+    omega_c: np.ndarray
+    steps: int = 0
+
+
+def initial_state(m: Model) -> State:
+    shape = m.a.shape
+    return State(m.theta0.copy(), np.zeros(shape, dtype=np.uint8), np.zeros(shape),
+                 np.zeros(shape), 0)
+
+
+def run(m: Model, st: State, nsteps: int, damage=None, T_thr_C: float = 60.0,
+        nthreads: int = 0) -> State:
+    """Advance ``st`` in place by ``nsteps`` explicit steps."""
+    dmg = damage
+    en = int(bool(dmg is not None and dmg.enable))
+    A = dmg.A if en else 0.0
+    Ea = dmg.Ea if en else 0.0
+    R = dmg.R if en else 1.0
+    thr = dmg.T_thr_C if dmg is not None else T_thr_C
+    _check(lib().or_run(m.nx, m.ny, m.nz, int(nsteps), _pd(m.a), _pd(m.b), _pd(m.s), _pd(m.qm),
+                        _pu8(m.isfixed), _pd(st.theta), _pu8(st.latch), m.T_a, thr, en, m.dt,
+                        A, Ea, R, _pd(st.omega), _pd(st.omega_c), int(nthreads)), "run")
+    st.steps += int(nsteps)
+    return st
+
+
+def adjoint(m: Model, nsteps: int, lam_N: np.ndarray, nthreads: int = 0):
+    """Discrete adjoint of ``nsteps`` steps from m.theta0.  Returns
+    (lambda_0, Lambda, g_k[L], g_wb[L], g_P, g_tip[3])."""
+    lam = np.ascontiguousarray(lam_N.astype(np.float64).reshape(m.a.shape)).copy()
+    Lam = np.zeros(m.a.shape)
+    nl = m.tab.shape[0]
+    gk, gw = np.zeros(nl), np.zeros(nl)
+    _check(lib().or_adjoint(m.nx, m.ny, m.nz, int(nsteps), m.h, m.dt, _pd(m.a), _pd(m.b),
+                            _pd(m.s), _pd(m.qm), _pu8(m.isfixed), _pu8(m.labels), nl, _pd(m.tab),
+                            _pd(m.rhoc), _pd(m.theta0), _pd(lam), _pd(Lam), _pd(gk), _pd(gw),
+                            int(nthreads)), "adjoint")
+    g = np.zeros(4)
+    _check(lib().or_source_grad(m.nx, m.ny, m.nz, m.h, m.dt, _pd(m.needle), _pd(m.rhoc),
+                                _pu8(m.isfixed), _pd(Lam), _pd(g)), "source_grad")
+    return lam, Lam, gk, gw, float(g[0]), g[1:].copy()
+
+
+def necrosis(m: Model, st: State, T_a: Optional[float] = None, width_K: float = 1.0,
+             thr_C: float = 60.0):
+    """Mask bits (bit0 thermal latch, bit1 Arrhenius Omega >= 1), counts,
+    volumes h^3*count and the smoothed volume h^3 sum sigmoid((T - thr)/width)."""
+    Ta = m.T_a if T_a is None else T_a
+    mask = (st.latch != 0).astype(np.uint8) | ((st.omega >= 1.0).astype(np.uint8) << 1)
+    h3 = m.h ** 3
+    n_th = int(np.count_nonzero(mask & 1))
+    n_ar = int(np.count_nonzero(mask & 2))
+    T = st.theta + Ta
+    vs = h3 * float(np.sum(1.0 / (1.0 + np.exp(-(T - thr_C) / width_K))))
+    return mask, (n_th, n_ar), (h3 * n_th, h3 * n_ar), vs
