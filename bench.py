@@ -1,0 +1,398 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the RFA bioheat hot path on B300.
+
+One bench "step" is one pass of the whole hot path over one synthetic
+phantom: tissue set-up (labels -> coefficients), needle placement (RF
+source), N explicit time steps fused with the 60 C latch and the FP64
+Arrhenius integral, and the necrosis reduction.  Default workload: 256^3
+voxels, h = 0.5 mm, 1-3 tumours and 2-4 vessels, 4-tine umbrella at 30 W,
+dt = 0.05 s, 12000 steps, BF16 coefficient fields, compensated FP32 state.
+
+The metric is voxel-steps per second (GVox-steps/s); ``value`` times the
+device-resident path (labels already in HBM), ``e2e`` the same work through
+the C ABI from host buffers including the host<->device copies.  Multi-GPU
+runs (torchrun) simulate independent phantoms per rank (weak scaling, no
+collective on the data path).
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
+same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import phantoms as ph  # noqa: E402
+
+METRIC = "bioheat GVox-steps/s and % HBM roofline; batched+adjoint vs plain @1e-3 K"
+UNIT = "GVox-steps/s"
+
+
+def workload(name: str, seed: int, sim_steps):
+    if name == "umbrella256":
+        c = ph.umbrella_case_256(seed=seed)
+    elif name == "homogeneous64":
+        c = ph.homogeneous_case()
+    elif name == "adjoint128":
+        c = ph.adjoint_case_128(seed=seed)
+    elif name == "large512":
+        c = ph.large_case_512(seed=seed)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    if sim_steps:
+        c.nsteps = int(sim_steps)
+    return c
+
+
+def workload_config(c, name):
+    return {"workload": name, "grid": [c.nx, c.ny, c.nz], "h_mm": c.h * 1e3, "dt_s": c.dt,
+            "time_steps": c.nsteps, "needle": {0: "straight", 1: "umbrella"}[c.needle.kind],
+            "n_tines": c.needle.n_tines if c.needle.kind == 1 else 0,
+            "power_W": c.needle.power, "arrhenius": bool(c.damage.enable),
+            "state": "fp32 hi+lo compensated", "coefficients": "bf16",
+            "l2": "inputs larger than L2 (working set ~42 B/voxel)"}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.uuid:
+                cmd[1:1] = ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 10:
+                continue
+            try:
+                sm.append(float(p[2]))
+                smax.append(float(p[3]))
+                power.append(float(p[4]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[6:10]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ roofline
+def algorithmic_bytes_per_voxel(arrhenius: bool) -> int:
+    """Compulsory HBM bytes per voxel for one launch of the step kernel
+    (compensated FP32 state, BF16 coefficients): theta hi+lo read and written
+    (16), packed a/b (4), source (4), latch read+write (2), and with the damage
+    integral Omega (FP64) and its FP32 Kahan term read and written (24)."""
+    return 16 + 4 + 4 + 2 + (24 if arrhenius else 0)
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1907_05709_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel: str, nvox: int):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_sha") != kernel_source_sha():
+        return None
+    return e["bytes_per_voxel_per_launch"] * nvox
+
+
+def measured_peak_hbm():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(case, target_s=15.0, min_steps=2, max_steps=2000):
+    """Time the FP64 oracle on the full grid for a bounded number of steps."""
+    import oracle
+    t0 = time.perf_counter()
+    m = oracle.setup(case, "bf16")
+    t_setup = time.perf_counter() - t0
+    st = oracle.initial_state(m)
+    dmg = case.damage if case.damage.enable else None
+    t0 = time.perf_counter()
+    oracle.run(m, st, min_steps, damage=dmg)
+    t_cal = (time.perf_counter() - t0) / min_steps
+    n = int(max(min_steps, min(max_steps, target_s / max(t_cal, 1e-9))))
+    t0 = time.perf_counter()
+    oracle.run(m, st, n, damage=dmg)
+    t = time.perf_counter() - t0
+    return n, t, t_setup
+
+
+def cpu_baseline(case, target_s=15.0):
+    n, t, _ = oracle_sample(case, target_s)
+    return {"value": case.nvox * n / t / 1e9, "unit": UNIT, "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"FP64 oracle (C, OpenMP over z, {os.cpu_count()} threads), full "
+                      f"{case.nx}x{case.ny}x{case.nz} phantom, {n} of {case.nsteps} time steps"
+                      f"{' with Arrhenius' if case.damage.enable else ''}, set-up excluded"}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    case = workload(args.workload, 0, args.sim_steps)
+    import oracle
+    # one step = oracle set-up + a bounded sample of time steps on the full grid
+    n, t_cal, t_setup = oracle_sample(case, target_s=4.0, min_steps=2)
+    per_step_target = 12.0
+    n = max(2, int(n * per_step_target / max(4.0, 1e-9)))
+    dmg = case.damage if case.damage.enable else None
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        m = oracle.setup(case, "bf16")
+        st = oracle.initial_state(m)
+        oracle.run(m, st, n, damage=dmg)
+        oracle.necrosis(m, st)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = case.nvox * n * len(times) / tot / 1e9
+    sample = (f"FP64 oracle (C, OpenMP over z, {os.cpu_count()} threads) on the full "
+              f"{case.nx}x{case.ny}x{case.nz} phantom: set-up + {n} of {case.nsteps} time steps"
+              f"{' with Arrhenius' if case.damage.enable else ''} + necrosis per step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(case, args.workload),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    import paper_1907_05709_b300 as rfa
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    case = workload(args.workload, rank, args.sim_steps)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(case, target_s=args.cpu_seconds)
+
+    stream = torch.cuda.current_stream()
+    g = rfa.Grid(case.nx, case.ny, case.nz, case.h, case.dt, rfa.STATE_F32C, rfa.PARAM_BF16,
+                 case.face_bc, case.T_a_C, stream.cuda_stream)
+    labels_dev = torch.from_numpy(np.ascontiguousarray(case.labels)).to(dev)
+    labels_pin = torch.from_numpy(np.ascontiguousarray(case.labels)).pin_memory()
+    T_host = torch.empty(case.nvox, dtype=torch.float32).pin_memory()
+    d = case.damage
+    g.set_tissue(labels_dev, case.table)
+    g.place_needle(case.needle)
+    g.set_damage(int(d.enable), d.A, d.Ea, d.R, d.T_thr_C)
+    depth, variant = 1, 0
+    if args.schedule == "auto":
+        try:
+            rfa.rfa_autotune(g.handle, os.path.join(ROOT, "gpurun_out", "autotune.json")
+                             if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+        except rfa.RfaError:
+            pass
+    elif args.schedule.startswith("tb"):
+        g.set_schedule(int(args.schedule[2:]), 0)
+    depth, variant = rfa.rfa_get_schedule(g.handle)
+
+    step_ms = []
+
+    def one_step(host: bool):
+        lab = labels_pin if host else labels_dev
+        g.set_tissue(lab, case.table)
+        g.place_needle(case.needle)
+        g.set_damage(int(d.enable), d.A, d.Ea, d.R, d.T_thr_C)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step(case.nsteps)
+        e1.record(stream)
+        _, counts, vols, sv = g.necrosis(want_mask=False)
+        if host:
+            rfa.rfa_get_temperature(g.handle, T_host, False, False)
+        step_ms.append((e0, e1))
+        return counts
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        one_step(False)
+    barrier()
+    step_ms.clear()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clk = ClockSampler(uuid)
+    clk.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        counts = one_step(False)
+    t_end.record(stream)
+    barrier()
+    clocks = clk.stop()
+    ms = t_start.elapsed_time(t_end)
+    kern_ms = sum(a.elapsed_time(b) for a, b in step_ms)
+    ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    vox_steps = case.nvox * case.nsteps * args.steps * world
+    value = vox_steps / (ms_max * 1e-3) / 1e9
+
+    # end to end from host buffers (labels in, temperature field out)
+    e2e = None
+    if not args.no_e2e:
+        one_step(True)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            one_step(True)
+        barrier()
+        wall = time.perf_counter() - t0
+        w_t = torch.tensor([wall], device=dev, dtype=torch.float64)
+        if dist is not None:
+            dist.all_reduce(w_t, op=dist.ReduceOp.MAX)
+        e2e = {"value": vox_steps / float(w_t.item()) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(case.nvox + 256 * 9 * 8 + 104),
+               "d2h_bytes_per_step": int(case.nvox * 4 + 32 + 4)}
+
+    # roofline of the dominant kernel (the step kernel)
+    launches_per_step = (case.nsteps // depth + case.nsteps % depth) if depth > 1 else case.nsteps
+    avg_launch_ms = kern_ms / (args.steps * launches_per_step)
+    nbytes = algorithmic_bytes_per_voxel(bool(d.enable)) * case.nvox
+    peak, peak_kind = measured_peak_hbm()
+    achieved = nbytes / (avg_launch_ms * 1e-3) / 1e9
+    kname = "k_step_tb" if depth > 1 else "k_step_plain"
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": load_traffic(kname, case.nvox),
+            "kernel": kname, "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+            "algorithmic_bytes_per_launch": nbytes, "avg_launch_us": avg_launch_ms * 1e3,
+            "steps_per_launch": depth}
+    kernels_per_step = 1 + 3 + launches_per_step + 2
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic (seeded tumour/vessel phantom per rank)",
+                "config": dict(workload_config(case, args.workload),
+                               parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                               schedule={"tb_depth": depth, "tile_variant": variant}),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": kernels_per_step * args.steps,
+                "necrosis_voxels": [int(counts[0]), int(counts[1])]}
+        print(json.dumps(line), flush=True)
+    g.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="umbrella256")
+    ap.add_argument("--sim-steps", type=int, default=None, help="override time steps per bench step")
+    ap.add_argument("--schedule", default="auto", help="auto | plain | tbN")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.schedule == "plain":
+        args.schedule = "tb1"
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,240 @@
+/*
+ * rfa.h -- C ABI of the B300 (sm_103a) radio-frequency-ablation bioheat library.
+ *
+ * The library advances the simplified bioheat equation of Kath, Handels and
+ * Mastmeyer (arXiv 1907.05709, Eq. 2675-eq1_Kath, discretised as Eq.
+ * CUDAbioheat3d) on a 3D voxel grid by explicit Euler steps, with
+ *   - a 7-point central-difference diffusion stencil (Eq. 2675-eq3),
+ *   - the blood-perfusion sink toward arterial temperature T_a,
+ *   - an RF heat source placed by the needle geometry (straight or umbrella),
+ *   - voxels held at a fixed temperature (vessels, Eq. 2675-eq6 and the
+ *     else-branch of Alg. 1),
+ *   - a 60 C necrosis latch (Sec. "Introduction") and the Arrhenius damage
+ *     integral of Eq. eq-tissState, accumulated in FP64,
+ *   - a hand-written discrete adjoint for gradients (the paper has none).
+ *
+ * Conventions shared by every call:
+ *   - Units are SI (metres, seconds, watts, W/m/K, kg/m^3, J/kg/K) and
+ *     temperatures at the ABI are degrees Celsius.
+ *   - Voxel (i, j, k) has its centre at (i*h, j*h, k*h) metres; host volumes
+ *     are dense [nz][ny][nx] arrays with x fastest.
+ *   - The library owns all device memory of a grid.  Host pointers are borrowed
+ *     for the duration of the call only; device pointers passed in stay owned
+ *     by the caller.
+ *   - Work is enqueued on the CUDA stream given at creation and runs
+ *     asynchronously; a fault in asynchronous work is reported by the next call
+ *     that synchronises (rfa_synchronize, rfa_get_*, rfa_necrosis_mask,
+ *     rfa_backward).
+ *   - No call throws across the ABI.  On failure a call returns a non-zero
+ *     rfa_status and rfa_last_error() gives a message (thread-local).
+ *   - A grid is not thread-safe; distinct grids may be used from distinct threads.
+ */
+#ifndef RFA_H
+#define RFA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rfa_grid rfa_grid;    /* opaque, library-owned */
+typedef struct rfa_batch rfa_batch;  /* opaque, library-owned */
+
+typedef enum {
+    RFA_OK = 0,
+    RFA_E_INVALID = 1,      /* bad argument (null pointer, size, enum value) */
+    RFA_E_OOM = 2,          /* device or host allocation failed */
+    RFA_E_CUDA = 3,         /* a CUDA runtime/driver call failed */
+    RFA_E_UNSTABLE = 4,     /* 1 - 6a - b < 0 for some free voxel (scheme not positive) */
+    RFA_E_STATE = 5,        /* call out of order (e.g. step before set_tissue) */
+    RFA_E_NONFINITE = 6,    /* a step produced a non-finite temperature */
+    RFA_E_TIMEOUT = 7,      /* a bounded device-side wait gave up */
+    RFA_E_UNSUPPORTED = 8   /* valid request this build does not provide */
+} rfa_status;
+
+/* State precision: FP32, FP32 hi + FP32 lo compensated pair, FP64. */
+enum { RFA_STATE_F32 = 0, RFA_STATE_F32C = 1, RFA_STATE_F64 = 2 };
+/* Storage of the static per-voxel coefficients a = K dt/(rho c h^2) and
+ * b = w_b rho_b c_b dt/(rho c): BF16 (rounded to nearest even), FP32, FP64. */
+enum { RFA_PARAM_BF16 = 0, RFA_PARAM_F32 = 1, RFA_PARAM_F64 = 2 };
+/* Outer faces: Dirichlet = the outer voxel layer is held at T_a; insulated =
+ * zero flux (a neighbour outside the grid contributes nothing). */
+enum { RFA_FACE_DIRICHLET = 0, RFA_FACE_INSULATED = 1 };
+enum { RFA_NEEDLE_STRAIGHT = 0, RFA_NEEDLE_UMBRELLA = 1 };
+/* Field ids for rfa_get_field. */
+enum { RFA_FIELD_THETA = 0, RFA_FIELD_A = 1, RFA_FIELD_B = 2, RFA_FIELD_S = 3,
+       RFA_FIELD_LATCH = 4, RFA_FIELD_OMEGA = 5, RFA_FIELD_THETA_LO = 6 };
+
+/* Per-label tissue parameters (Eq. 2675-eq1_Kath symbols), SI units.
+ * Perfusion enters as beta = w_b * rho_b * c_b [W/m^3/K]; the paper's
+ * per-volume blood flow (kg/m^3/s) corresponds to rho_b = 1.
+ * fixed != 0 holds every voxel of the label at T_fixed_C (vessels). */
+typedef struct {
+    double k, rho, c, w_b, rho_b, c_b, Q_m;
+    int fixed;
+    double T_fixed_C;
+} rfa_tissue;
+
+/* Needle.  STRAIGHT: the active segment is [tip - active_len*axis, tip].
+ * UMBRELLA: n_tines tines of length tine_len leave the tip at tine_polar_deg
+ * off the axis, at azimuths 2*pi*j/n_tines measured from e1, where
+ * (e1, e2, axis) is right-handed and e1 is the unit projection onto the plane
+ * normal to the axis of +x if |axis_z| >= 0.9, else of +z (for axis +z:
+ * e1 = +x, e2 = +y); tine_axial adds one tine along
+ * the axis.  Source: q_i = P w_i / (h^3 sum_free w), w_i = max(d_i, r_clamp)^-4
+ * with d_i the distance from the voxel centre to the nearest active segment
+ * (the 1/r^4 fall-off of the resistive term sigma|grad V|^2 of Eq.
+ * 2675-eq1_Linte around a point electrode). */
+typedef struct {
+    int kind;
+    double tip_m[3];
+    double axis[3];
+    double active_len_m;
+    double tine_len_m;
+    double tine_polar_deg;
+    int n_tines;
+    int tine_axial;
+    double power_W;
+    double r_clamp_m;
+} rfa_needle;
+
+/*
+ * Create a grid of nx*ny*nz voxels of edge h_m, time step dt_s, ambient
+ * (arterial) temperature T_a_C.  state_prec / param_prec / face_bc take the
+ * enum values above.  cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream) on which all work of this grid is enqueued.  Allocates the device
+ * fields; the state starts at T_a everywhere until rfa_set_tissue.
+ * Errors: RFA_E_INVALID (size < 1, h or dt <= 0, bad enum), RFA_E_OOM, RFA_E_CUDA.
+ */
+rfa_status rfa_create_grid(int nx, int ny, int nz, double h_m, double dt_s, int state_prec,
+                           int param_prec, int face_bc, double T_a_C, void *cuda_stream,
+                           rfa_grid **out);
+
+/* Free every device and host resource of the grid (synchronises its stream). */
+rfa_status rfa_destroy_grid(rfa_grid *g);
+
+/*
+ * Tissue set-up (Sec. "Implementation": the label image becomes the start
+ * temperature image).  labels: nx*ny*nz uint8, x fastest, every value
+ * < n_labels, in host or device memory (the library detects which; a device
+ * array stays owned by the caller).  table: host, n_labels entries
+ * (1 <= n_labels <= 256).  Synchronous.
+ * Builds the per-voxel coefficients on the device, resets the state to T_a
+ * (T_fixed for fixed voxels), the latch and the damage integral to zero, the
+ * step counter to zero and clears any recording for rfa_backward.
+ * A needle placed earlier is placed again (the source depends on rho c).
+ * Errors: RFA_E_INVALID (also a label >= n_labels, detected on the device),
+ * RFA_E_UNSTABLE (1 - 6a - b < 0 for a free label).
+ */
+rfa_status rfa_set_tissue(rfa_grid *g, const uint8_t *labels, const rfa_tissue *table,
+                          int n_labels);
+
+/*
+ * Place the needle: builds the per-voxel source term
+ * s_i = (q_i + Q_m,i) dt / (rho c)_i on the device (FP64 geometry and
+ * normalisation sum, stored in the state precision).  Fixed voxels get no
+ * source.  Does not reset the state.  Errors: RFA_E_STATE (no tissue yet),
+ * RFA_E_INVALID (zero axis, n_tines outside 0..16, negative lengths).
+ */
+rfa_status rfa_place_needle(rfa_grid *g, const rfa_needle *needle);
+
+/*
+ * Damage model.  enable != 0 accumulates, after every step,
+ * Omega_i += dt * A * exp(-Ea / (R * T_K)) with T_K = T + 273.15 (Eq.
+ * eq-tissState's integral, right-rectangle rule), in FP64 with Kahan
+ * compensation.  T_thr_C is the necrosis-latch threshold used whether or not
+ * the integral is enabled (default 60 C).  Defaults: disabled, A = 7.39e39,
+ * Ea = 2.577e5, R = 8.31 (the paper's printed gas constant).
+ */
+rfa_status rfa_set_damage(rfa_grid *g, int enable, double A, double Ea, double R,
+                          double T_thr_C);
+
+/*
+ * Advance nsteps explicit steps (Eq. CUDAbioheat3d, Jacobi double buffer as
+ * in Alg. 2), updating the 60 C latch and, if enabled, the damage integral
+ * after every step.  Asynchronous on the grid's stream.
+ * record_for_backward != 0 stores sqrt(N) checkpoints so that rfa_backward can
+ * differentiate the state after this call; recording is only valid when
+ * every step since rfa_set_tissue was recorded.
+ * Errors: RFA_E_STATE (no tissue or needle), RFA_E_INVALID (nsteps < 0).
+ */
+rfa_status rfa_step(rfa_grid *g, int64_t nsteps, int record_for_backward);
+
+/*
+ * Copy the temperature T = theta + T_a in Celsius to dst (nx*ny*nz, x fastest)
+ * as float (as_f64 = 0) or double (as_f64 = 1).  dst_is_device selects a
+ * device (stream-ordered, asynchronous) or host (synchronous) destination.
+ * Reports RFA_E_NONFINITE if a previous step produced a non-finite value.
+ */
+rfa_status rfa_get_temperature(rfa_grid *g, void *dst, int dst_is_device, int as_f64);
+
+/* Diagnostic copy of one field (RFA_FIELD_*) to host doubles, nx*ny*nz.
+ * THETA is theta = T - T_a (hi + lo for the compensated state). */
+rfa_status rfa_get_field(rfa_grid *g, int field, double *dst_host);
+
+/*
+ * Necrosis: mask bit0 = thermal latch (T ever >= T_thr), bit1 = Arrhenius
+ * (Omega >= 1).  mask_or_null: host nx*ny*nz bytes or NULL.  counts[2] and
+ * volumes_m3[2] (h^3 * count) for the two criteria; smooth_volume_m3 =
+ * h^3 * sum_i sigmoid((T_i - T_thr) / smooth_width_K) on the current state.
+ * Any output pointer may be NULL.  Deterministic two-pass reduction on device.
+ */
+rfa_status rfa_necrosis_mask(rfa_grid *g, uint8_t *mask_or_null, int64_t *counts,
+                             double *volumes_m3, double *smooth_volume_m3,
+                             double smooth_width_K);
+
+/*
+ * Discrete adjoint of every recorded step (the paper has no adjoint).
+ * dLdT_final_dev: device float array nx*ny*nz (x fastest), dL/dT of the final
+ * state.  grads (host, 4 + 2*n_labels doubles) receives
+ *   [dL/dP, dL/dtip_x, dL/dtip_y, dL/dtip_z, dL/dk[0..L-1], dL/dw_b[0..L-1]].
+ * Recomputes the trajectory from the sqrt(N) checkpoints.  Synchronous.
+ * Errors: RFA_E_STATE (nothing recorded, or unrecorded steps since set-up),
+ * RFA_E_UNSUPPORTED (FP64 state).
+ */
+rfa_status rfa_backward(rfa_grid *g, const float *dLdT_final_dev, double *grads);
+
+/*
+ * Serialise the evolving state (theta, lo, latch, Omega and its compensation,
+ * step counter) to blob.  With blob == NULL, *n receives the required size.
+ * rfa_set_state restores a blob made by a grid of the same shape/precision.
+ */
+rfa_status rfa_get_state(rfa_grid *g, void *blob, size_t *n);
+rfa_status rfa_set_state(rfa_grid *g, const void *blob, size_t n);
+
+/*
+ * Temporal blocking: advance tb_depth steps per launch (1 = one step per
+ * launch); tile_variant selects the xy tile of the blocked kernel (0 = default).
+ * rfa_autotune times the candidates on a scratch copy of the grid's state and
+ * keeps the fastest; cache_path (may be NULL) is a JSON file read and updated.
+ */
+rfa_status rfa_set_schedule(rfa_grid *g, int tb_depth, int tile_variant);
+rfa_status rfa_get_schedule(rfa_grid *g, int *tb_depth, int *tile_variant);
+rfa_status rfa_autotune(rfa_grid *g, const char *cache_path);
+
+/*
+ * Batched stepping of several grids in one persistent launch per call
+ * (independent needle configurations on grids of uneven size).  Members must
+ * be F32C grids with tissue and needle set, all on the same stream; they stay
+ * owned by the caller and must outlive the batch.  rfa_batch_step advances
+ * every member by nsteps, capturing the launch in a CUDA graph.
+ */
+rfa_status rfa_batch_create(rfa_grid *const *members, int n, rfa_batch **out);
+rfa_status rfa_batch_step(rfa_batch *b, int64_t nsteps);
+rfa_status rfa_batch_destroy(rfa_batch *b);
+
+/* Wait for the grid's stream and report deferred device errors. */
+rfa_status rfa_synchronize(rfa_grid *g);
+
+/* Number of steps taken since the last rfa_set_tissue. */
+int64_t rfa_steps_done(const rfa_grid *g);
+
+/* Message of the last failure on this thread ("" if none). */
+const char *rfa_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RFA_H */

@@ -1,0 +1,216 @@
+// kernels_reduce.cu -- necrosis mask and volumes, and conversions of the
+// padded device state to dense host-layout arrays.
+//
+// Necrosis (Sec. "Introduction": instantaneous death above 60 C; Eq.
+// eq-tissState for the Arrhenius criterion Omega >= 1) is reduced in two
+// passes: a fixed grid of kReduceBlocks blocks writes per-block partials
+// (warp shuffles, then shared memory), and one block sums the partials in a
+// fixed order, so the counts and the FP64 smoothed volume are bit-reproducible.
+#include "rfa_internal.cuh"
+
+namespace rfa {
+
+namespace {
+
+struct NecroPartial {
+    unsigned long long n_thermal, n_arrh;
+    double smooth;
+    double pad;
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int SP>
+__global__ void __launch_bounds__(256) k_necrosis(const void *th, const float *lo,
+                                                  const uint8_t *latch, const double *omega,
+                                                  int nx, int ny, int nz, int pitch, double T_a,
+                                                  double T_thr, double inv_width,
+                                                  uint8_t *mask_dense, NecroPartial *part)
+{
+    using T = typename std::conditional<SP == RFA_STATE_F64, double, float>::type;
+    size_t nvp = (size_t)pitch * ny * nz;
+    unsigned long long c0 = 0, c1 = 0;
+    double sm = 0.0;
+    const double off = T_thr - T_a;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nvp;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int x = (int)(i % pitch);
+        if (x >= nx) continue;
+        uint8_t m = (latch[i] ? 1 : 0) | (omega[i] >= 1.0 ? 2 : 0);
+        c0 += m & 1;
+        c1 += (m >> 1) & 1;
+        if (SP == RFA_STATE_F64) {
+            double u = (((const double *)th)[i] - off) * inv_width;
+            sm += 1.0 / (1.0 + exp(-u));
+        } else {
+            float v = ((const float *)th)[i];
+            if (SP == RFA_STATE_F32C) v += lo[i];
+            float u = (v - (float)off) * (float)inv_width;
+            sm += (double)(1.0f / (1.0f + __expf(-u)));
+        }
+        if (mask_dense) {
+            size_t r = i / pitch;
+            mask_dense[r * nx + x] = m;
+        }
+    }
+    __shared__ unsigned long long s0[8], s1[8];
+    __shared__ double s2[8];
+    c0 = warp_sum(c0);
+    c1 = warp_sum(c1);
+    sm = warp_sum(sm);
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s0[w] = c0;
+        s1[w] = c1;
+        s2[w] = sm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        NecroPartial p{0, 0, 0.0, 0.0};
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            p.n_thermal += s0[k];
+            p.n_arrh += s1[k];
+            p.smooth += s2[k];
+        }
+        part[blockIdx.x] = p;
+    }
+}
+
+__global__ void k_necrosis_final(const NecroPartial *part, int n, NecroPartial *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    NecroPartial p{0, 0, 0.0, 0.0};
+    for (int k = 0; k < n; ++k) {
+        p.n_thermal += part[k].n_thermal;
+        p.n_arrh += part[k].n_arrh;
+        p.smooth += part[k].smooth;
+    }
+    *out = p;
+}
+
+template <int SP>
+__global__ void k_to_temperature(const void *th, const float *lo, int nx, int ny, int nz,
+                                 int pitch, double T_a, void *dst, int as_f64)
+{
+    size_t n = (size_t)nx * ny * nz;
+    for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < n;
+         j += (size_t)gridDim.x * blockDim.x) {
+        int x = (int)(j % nx);
+        size_t r = j / nx;
+        size_t i = r * pitch + x;
+        double v;
+        if (SP == RFA_STATE_F64) v = ((const double *)th)[i];
+        else v = (double)((const float *)th)[i] + (SP == RFA_STATE_F32C ? (double)lo[i] : 0.0);
+        v += T_a;
+        if (as_f64) ((double *)dst)[j] = v;
+        else ((float *)dst)[j] = (float)v;
+    }
+}
+
+struct FieldView {
+    int nx, ny, nz, pitch, sp, pp;
+    const void *ab, *s;
+    const uint8_t *latch;
+    const double *omega;
+};
+
+__global__ void k_get_field(const FieldView G, const void *th, const float *lo, int field,
+                            double *dst)
+{
+    size_t n = (size_t)G.nx * G.ny * G.nz;
+    for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < n;
+         j += (size_t)gridDim.x * blockDim.x) {
+        int x = (int)(j % G.nx);
+        size_t r = j / G.nx;
+        size_t i = r * G.pitch + x;
+        double v = 0.0;
+        switch (field) {
+        case RFA_FIELD_THETA:
+            if (G.sp == RFA_STATE_F64) v = ((const double *)th)[i];
+            else v = (double)((const float *)th)[i] + (G.sp == RFA_STATE_F32C ? (double)lo[i] : 0.0);
+            break;
+        case RFA_FIELD_THETA_LO:
+            v = G.sp == RFA_STATE_F32C ? (double)lo[i] : 0.0;
+            break;
+        case RFA_FIELD_A:
+        case RFA_FIELD_B: {
+            int k = field == RFA_FIELD_A ? 0 : 1;
+            if (G.pp == RFA_PARAM_BF16) {
+                uint32_t u = ((const uint32_t *)G.ab)[i];
+                v = bf16_to_float(k == 0 ? (u & 0xffffu) : (u >> 16));
+            } else if (G.pp == RFA_PARAM_F32) {
+                float2 t = ((const float2 *)G.ab)[i];
+                v = k == 0 ? t.x : t.y;
+            } else {
+                double2 t = ((const double2 *)G.ab)[i];
+                v = k == 0 ? t.x : t.y;
+            }
+            break;
+        }
+        case RFA_FIELD_S:
+            v = G.sp == RFA_STATE_F64 ? ((const double *)G.s)[i] : (double)((const float *)G.s)[i];
+            break;
+        case RFA_FIELD_LATCH:
+            v = G.latch[i];
+            break;
+        case RFA_FIELD_OMEGA:
+            v = G.omega[i];
+            break;
+        default:
+            break;
+        }
+        dst[j] = v;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_necrosis(rfa_grid *g, uint8_t *mask_dense_dev, double width_K, void *result_dev)
+{
+    NecroPartial *part = (NecroPartial *)g->red;
+    const void *th = g->th[g->cur];
+    const float *lo = (const float *)g->lo[g->cur];
+    double iw = 1.0 / width_K;
+    if (g->sp == RFA_STATE_F64)
+        k_necrosis<RFA_STATE_F64><<<kReduceBlocks, 256, 0, g->stream>>>(
+            th, lo, g->latch, g->omega, g->nx, g->ny, g->nz, g->pitch, g->T_a, g->T_thr, iw,
+            mask_dense_dev, part);
+    else if (g->sp == RFA_STATE_F32C)
+        k_necrosis<RFA_STATE_F32C><<<kReduceBlocks, 256, 0, g->stream>>>(
+            th, lo, g->latch, g->omega, g->nx, g->ny, g->nz, g->pitch, g->T_a, g->T_thr, iw,
+            mask_dense_dev, part);
+    else
+        k_necrosis<RFA_STATE_F32><<<kReduceBlocks, 256, 0, g->stream>>>(
+            th, lo, g->latch, g->omega, g->nx, g->ny, g->nz, g->pitch, g->T_a, g->T_thr, iw,
+            mask_dense_dev, part);
+    k_necrosis_final<<<1, 32, 0, g->stream>>>(part, kReduceBlocks, (NecroPartial *)result_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_temperature(rfa_grid *g, void *dst, int as_f64)
+{
+    const void *th = g->th[g->cur];
+    const float *lo = (const float *)g->lo[g->cur];
+    if (g->sp == RFA_STATE_F64)
+        k_to_temperature<RFA_STATE_F64><<<148 * 8, 256, 0, g->stream>>>(th, lo, g->nx, g->ny, g->nz, g->pitch, g->T_a, dst, as_f64);
+    else if (g->sp == RFA_STATE_F32C)
+        k_to_temperature<RFA_STATE_F32C><<<148 * 8, 256, 0, g->stream>>>(th, lo, g->nx, g->ny, g->nz, g->pitch, g->T_a, dst, as_f64);
+    else
+        k_to_temperature<RFA_STATE_F32><<<148 * 8, 256, 0, g->stream>>>(th, lo, g->nx, g->ny, g->nz, g->pitch, g->T_a, dst, as_f64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_field(rfa_grid *g, int field, double *dst)
+{
+    FieldView G{g->nx, g->ny, g->nz, g->pitch, g->sp, g->pp, g->ab, g->s, g->latch, g->omega};
+    k_get_field<<<148 * 8, 256, 0, g->stream>>>(G, g->th[g->cur], (const float *)g->lo[g->cur],
+                                                field, dst);
+    return cudaGetLastError();
+}
+
+}  // namespace rfa

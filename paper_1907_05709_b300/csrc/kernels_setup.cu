@@ -1,0 +1,221 @@
+// kernels_setup.cu -- tissue set-up and RF source placement (run once per
+// set-up / needle placement).
+//
+// Tissue set-up follows Sec. "Implementation": the segmented label image is
+// turned into the start temperature image; vessel (fixed) labels keep their
+// temperature (Eq. 2675-eq6 and Alg. 1's else-branch).  Per voxel the update
+// coefficients of Eq. CUDAbioheat3d divided by rho c_p are formed in FP64 and
+// rounded once to the storage precision.
+//
+// The RF source: the paper gives the resistive heating sigma |grad V|^2 of Eq.
+// 2675-eq1_Linte only symbolically; around an electrode |grad V|^2 falls off as
+// 1/r^4, so q_i ~ max(d_i, r0)^-4 with d_i the distance to the nearest active
+// needle segment, normalised so that sum_free q_i h^3 = P exactly.
+#include "rfa_internal.cuh"
+
+namespace rfa {
+
+namespace {
+
+template <int SP, int PP>
+__global__ void k_setup(const uint8_t *__restrict__ labels, const LabelCoef *__restrict__ tab,
+                        int nx, int ny, int nz, int pitch, double h, double dt, double T_a,
+                        int face, void *th0, void *th1, void *lo0, void *lo1, void *ab,
+                        void *s, uint8_t *label_pad, uint8_t *latch, double *omega,
+                        float *omega_c, int n_labels, unsigned *status)
+{
+    using T = typename std::conditional<SP == RFA_STATE_F64, double, float>::type;
+    size_t nvp = (size_t)pitch * ny * nz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nvp;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int x = (int)(i % pitch);
+        size_t r = i / pitch;
+        int y = (int)(r % ny);
+        int z = (int)(r / ny);
+        double a = 0.0, b = 0.0, th = 0.0;
+        uint8_t l = 0;
+        if (x < nx) {
+            l = labels[((size_t)z * ny + y) * nx + x];
+            if (l >= n_labels) {
+                atomicOr(status, kStatusBadLabel);
+                l = 0;
+            }
+            const LabelCoef t = tab[l];
+            bool face_vox = (x == 0 || y == 0 || z == 0 || x == nx - 1 || y == ny - 1 || z == nz - 1);
+            if (t.fixed) {
+                th = t.T_fixed - T_a;
+            } else if (face == RFA_FACE_DIRICHLET && face_vox) {
+                th = 0.0;
+            } else {
+                a = round_coef(coef_a(t, dt, h), PP);
+                b = round_coef(coef_b(t, dt), PP);
+            }
+        }
+        ((T *)th0)[i] = (T)th;
+        ((T *)th1)[i] = (T)th;
+        if (SP == RFA_STATE_F32C) {
+            // the pair (hi, lo) represents th exactly
+            float hi = (float)th;
+            ((float *)lo0)[i] = (float)(th - (double)hi);
+            ((float *)lo1)[i] = (float)(th - (double)hi);
+        }
+        if (PP == RFA_PARAM_BF16) {
+            ((uint32_t *)ab)[i] = (uint32_t)bf16_bits_rne(a) | ((uint32_t)bf16_bits_rne(b) << 16);
+        } else if (PP == RFA_PARAM_F32) {
+            ((float2 *)ab)[i] = make_float2((float)a, (float)b);
+        } else {
+            ((double2 *)ab)[i] = make_double2(a, b);
+        }
+        ((T *)s)[i] = (T)0;
+        label_pad[i] = l;
+        latch[i] = 0;
+        omega[i] = 0.0;
+        omega_c[i] = 0.0f;
+    }
+}
+
+__device__ double needle_distance(const NeedleGeom &g, double px, double py, double pz)
+{
+    double best = 1e300;
+    for (int k = 0; k < g.nseg; ++k) {
+        const Segment &sg = g.seg[k];
+        double ux = sg.p1[0] - sg.p0[0], uy = sg.p1[1] - sg.p0[1], uz = sg.p1[2] - sg.p0[2];
+        double wx = px - sg.p0[0], wy = py - sg.p0[1], wz = pz - sg.p0[2];
+        double uu = ux * ux + uy * uy + uz * uz;
+        double t = uu > 0.0 ? (wx * ux + wy * uy + wz * uz) / uu : 0.0;
+        t = fmin(fmax(t, 0.0), 1.0);
+        double ex = px - (sg.p0[0] + t * ux), ey = py - (sg.p0[1] + t * uy),
+               ez = pz - (sg.p0[2] + t * uz);
+        best = fmin(best, ex * ex + ey * ey + ez * ez);
+    }
+    return sqrt(best);
+}
+
+__device__ inline double needle_weight(const NeedleGeom &g, double d)
+{
+    double r = fmax(d, g.r0);
+    return 1.0 / (r * r * r * r);
+}
+
+// block-wide FP64 sum; every thread gets the result
+__device__ double block_sum(double v)
+{
+    __shared__ double sh[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    int nw = (blockDim.x + 31) >> 5;
+    v = lane < nw ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// pass 1: per-block sums of w over free voxels
+__global__ void k_source_sum(NeedleGeom geom, const uint8_t *__restrict__ label,
+                             const LabelCoef *__restrict__ tab, int nx, int ny, int nz,
+                             int pitch, double h, int face, double *partial)
+{
+    size_t nvp = (size_t)pitch * ny * nz;
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nvp;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int x = (int)(i % pitch);
+        if (x >= nx) continue;
+        size_t r = i / pitch;
+        int y = (int)(r % ny);
+        int z = (int)(r / ny);
+        bool face_vox = (x == 0 || y == 0 || z == 0 || x == nx - 1 || y == ny - 1 || z == nz - 1);
+        if (tab[label[i]].fixed || (face == RFA_FACE_DIRICHLET && face_vox)) continue;
+        acc += needle_weight(geom, needle_distance(geom, x * h, y * h, z * h));
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// pass 2 (fused with pass 3's input): W = sum of the partials in fixed order
+__global__ void k_sum_partials(const double *partial, int n, double *out)
+{
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partial[i];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) *out = acc;
+}
+
+// pass 3: s_i = (P w_i / (h^3 W) + Q_m) dt / (rho c)_i on free voxels
+template <int SP>
+__global__ void k_source_write(NeedleGeom geom, const uint8_t *__restrict__ label,
+                               const LabelCoef *__restrict__ tab, int nx, int ny, int nz,
+                               int pitch, double h, double dt, int face, const double *Wp,
+                               void *s)
+{
+    using T = typename std::conditional<SP == RFA_STATE_F64, double, float>::type;
+    size_t nvp = (size_t)pitch * ny * nz;
+    const double W = *Wp;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nvp;
+         i += (size_t)gridDim.x * blockDim.x) {
+        int x = (int)(i % pitch);
+        double v = 0.0;
+        if (x < nx) {
+            size_t r = i / pitch;
+            int y = (int)(r % ny);
+            int z = (int)(r / ny);
+            bool face_vox = (x == 0 || y == 0 || z == 0 || x == nx - 1 || y == ny - 1 || z == nz - 1);
+            const LabelCoef t = tab[label[i]];
+            if (!(t.fixed || (face == RFA_FACE_DIRICHLET && face_vox))) {
+                double rhoc = t.rho * t.c;
+                double q = (W > 0.0 && geom.nseg > 0)
+                               ? geom.P * needle_weight(geom, needle_distance(geom, x * h, y * h, z * h)) / (h * h * h * W)
+                               : 0.0;
+                v = q * dt / rhoc + t.Q_m * dt / rhoc;
+            }
+        }
+        ((T *)s)[i] = (T)v;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_setup(rfa_grid *g, const uint8_t *labels_dense_dev, int n_labels)
+{
+    dim3 blk(256), grd(148 * 8);
+#define SETUP_CASE(SPV, PPV)                                                                     \
+    if (g->sp == SPV && g->pp == PPV)                                                           \
+        k_setup<SPV, PPV><<<grd, blk, 0, g->stream>>>(                                          \
+            labels_dense_dev, g->d_table, g->nx, g->ny, g->nz, g->pitch, g->h, g->dt, g->T_a,   \
+            g->face, g->th[0], g->th[1], g->lo[0], g->lo[1], g->ab, g->s, g->label, g->latch,   \
+            g->omega, g->omega_c, n_labels, g->status);
+    SETUP_CASE(RFA_STATE_F32, RFA_PARAM_BF16)
+    SETUP_CASE(RFA_STATE_F32, RFA_PARAM_F32)
+    SETUP_CASE(RFA_STATE_F32, RFA_PARAM_F64)
+    SETUP_CASE(RFA_STATE_F32C, RFA_PARAM_BF16)
+    SETUP_CASE(RFA_STATE_F32C, RFA_PARAM_F32)
+    SETUP_CASE(RFA_STATE_F32C, RFA_PARAM_F64)
+    SETUP_CASE(RFA_STATE_F64, RFA_PARAM_BF16)
+    SETUP_CASE(RFA_STATE_F64, RFA_PARAM_F32)
+    SETUP_CASE(RFA_STATE_F64, RFA_PARAM_F64)
+#undef SETUP_CASE
+    return cudaGetLastError();
+}
+
+cudaError_t launch_source(rfa_grid *g)
+{
+    double *partial = (double *)g->red;
+    double *W = partial + kReduceBlocks;
+    k_source_sum<<<kReduceBlocks, 256, 0, g->stream>>>(g->geom, g->label, g->d_table, g->nx,
+                                                       g->ny, g->nz, g->pitch, g->h, g->face,
+                                                       partial);
+    k_sum_partials<<<1, 1024, 0, g->stream>>>(partial, kReduceBlocks, W);
+    if (g->sp == RFA_STATE_F64)
+        k_source_write<RFA_STATE_F64><<<148 * 8, 256, 0, g->stream>>>(
+            g->geom, g->label, g->d_table, g->nx, g->ny, g->nz, g->pitch, g->h, g->dt, g->face, W,
+            g->s);
+    else
+        k_source_write<RFA_STATE_F32><<<148 * 8, 256, 0, g->stream>>>(
+            g->geom, g->label, g->d_table, g->nx, g->ny, g->nz, g->pitch, g->h, g->dt, g->face, W,
+            g->s);
+    return cudaGetLastError();
+}
+
+}  // namespace rfa

@@ -1,0 +1,329 @@
+// kernels_step.cu -- one explicit step per launch (Eq. CUDAbioheat3d), fused
+// with the necrosis latch and the Arrhenius damage update.
+//
+// Per free voxel (theta = T - T_a; a, b, s as in rfa_internal.cuh):
+//     theta' = theta + a * sum_nb (theta_nb - theta) - b * theta + s
+// a neighbour outside the grid contributes nothing; fixed voxels have
+// a = b = s = 0.  The difference form keeps the FP32 stencil free of the
+// cancellation in sum_nb theta_nb - 6 theta.
+//
+// Thread mapping: one thread owns 4 consecutive x voxels (a float4 "quad") of
+// one row and streams along z over a chunk of planes, keeping the planes
+// z-1, z, z+1 of its quad in registers (2.5D streaming).  A warp covers 128
+// consecutive x voxels; the x neighbours across quads come from warp shuffles,
+// the y neighbours from the rows above/below (L1/L2 hits).
+//
+// Compensated state (F32C): the value is hi + lo.  Neighbour differences are
+// taken as (hi_nb - hi) + (lo_nb - lo), the increment is added to hi with an
+// error-free TwoSum, the rounding error goes to lo, and (hi, lo) is
+// renormalised with Fast2Sum.
+//
+// Damage: inc = dt A exp(-Ea / (R T_K)) is evaluated in FP32 as
+// exp2(c0 - c1 / T_K) with c0 = log2(A dt), c1 = Ea / (R ln 2) (ln-space keeps
+// A = 7.39e39 and exp(-100) inside FP32 range); Omega accumulates it in FP64
+// with Kahan compensation (compensation term kept in FP32).
+#include "rfa_internal.cuh"
+#include "rfa_update.cuh"
+
+#include <cmath>
+
+namespace rfa {
+
+namespace {
+
+template <typename T>
+struct Q4 {
+    T v[4];
+};
+
+__device__ __forceinline__ Q4<float> ldq(const float *p)
+{
+    float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+    return {{t.x, t.y, t.z, t.w}};
+}
+__device__ __forceinline__ Q4<double> ldq(const double *p)
+{
+    double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    return {{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void stq(float *p, const Q4<float> &q)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(q.v[0], q.v[1], q.v[2], q.v[3]);
+}
+__device__ __forceinline__ void stq(double *p, const Q4<double> &q)
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(q.v[0], q.v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(q.v[2], q.v[3]);
+}
+template <typename T>
+__device__ __forceinline__ Q4<T> zq()
+{
+    return {{T(0), T(0), T(0), T(0)}};
+}
+
+// coefficients of 4 consecutive voxels, converted to the arithmetic type
+template <int PP, typename R>
+__device__ __forceinline__ void load_ab(const void *ab, size_t i, R a[4], R b[4])
+{
+    if (PP == RFA_PARAM_BF16) {
+        uint4 u = __ldg(reinterpret_cast<const uint4 *>((const uint32_t *)ab + i));
+        uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            a[q] = (R)bf16_to_float(w[q] & 0xffffu);
+            b[q] = (R)bf16_to_float(w[q] >> 16);
+        }
+    } else if (PP == RFA_PARAM_F32) {
+        const float4 *p = reinterpret_cast<const float4 *>((const float2 *)ab + i);
+        float4 u = __ldg(p), v = __ldg(p + 1);
+        a[0] = (R)u.x; b[0] = (R)u.y; a[1] = (R)u.z; b[1] = (R)u.w;
+        a[2] = (R)v.x; b[2] = (R)v.y; a[3] = (R)v.z; b[3] = (R)v.w;
+    } else {
+        const double2 *p = (const double2 *)ab + i;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            double2 t = __ldg(p + q);
+            a[q] = (R)t.x;
+            b[q] = (R)t.y;
+        }
+    }
+}
+
+struct PlainArgs {
+    const void *th_in, *lo_in, *ab, *s;
+    void *th_out, *lo_out;
+    uint8_t *latch;
+    double *omega;
+    float *omega_c;
+    unsigned *status;
+    int nx, ny, nz, pitch, zchunk;
+    size_t plane;
+    double thr;  // latch threshold on theta
+    DamageConst dc;
+};
+
+template <int SP, int PP, bool DMG, bool LATCH>
+__global__ void __launch_bounds__(256) k_step_plain(const PlainArgs A)
+{
+    using T = typename std::conditional<SP == RFA_STATE_F64, double, float>::type;
+    constexpr bool COMP = (SP == RFA_STATE_F32C);
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (y >= A.ny) return;  // whole warp: blockDim.x == 32
+    const int x0 = 4 * (blockIdx.x * 32 + lane);
+    const bool inrow = x0 < A.pitch;
+    const int zb = blockIdx.z * A.zchunk;
+    const int ze = min(A.nz, zb + A.zchunk);
+    const T *hin = (const T *)A.th_in;
+    const float *lin = (const float *)A.lo_in;
+    T *hout = (T *)A.th_out;
+    float *lout = (float *)A.lo_out;
+    const size_t rowoff = (size_t)y * A.pitch + x0;
+    const bool hasYm = y > 0, hasYp = y < A.ny - 1;
+    const bool hasL = x0 > 0, hasR = x0 + 4 < A.nx;
+    const T thr = (T)A.thr;
+
+    Q4<T> hm = zq<T>(), hc = zq<T>(), hp = zq<T>();
+    Q4<float> lm = zq<float>(), lc = zq<float>(), lp = zq<float>();
+    if (inrow) {
+        if (zb > 0) hm = ldq(hin + (size_t)(zb - 1) * A.plane + rowoff);
+        hc = ldq(hin + (size_t)zb * A.plane + rowoff);
+        if (COMP) {
+            if (zb > 0) lm = ldq(lin + (size_t)(zb - 1) * A.plane + rowoff);
+            lc = ldq(lin + (size_t)zb * A.plane + rowoff);
+        }
+    }
+    bool bad = false;
+    for (int z = zb; z < ze; ++z) {
+        const size_t i = (size_t)z * A.plane + rowoff;
+        const bool hasZp = z + 1 < A.nz, hasZm = z > 0;
+        Q4<T> hym = zq<T>(), hyp = zq<T>();
+        Q4<float> lym = zq<float>(), lyp = zq<float>();
+        T aq[4], bq[4], sq[4];
+        T left = T(0), right = T(0);
+        float lleft = 0.f, lright = 0.f;
+        if (inrow) {
+            if (hasZp) {
+                hp = ldq(hin + i + A.plane);
+                if (COMP) lp = ldq(lin + i + A.plane);
+            }
+            if (hasYm) {
+                hym = ldq(hin + i - A.pitch);
+                if (COMP) lym = ldq(lin + i - A.pitch);
+            }
+            if (hasYp) {
+                hyp = ldq(hin + i + A.pitch);
+                if (COMP) lyp = ldq(lin + i + A.pitch);
+            }
+            load_ab<PP, T>(A.ab, i, aq, bq);
+            Q4<T> sv = ldq((const T *)A.s + i);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) sq[q] = sv.v[q];
+        }
+        // x neighbours across quads
+        left = __shfl_up_sync(FULL, hc.v[3], 1);
+        right = __shfl_down_sync(FULL, hc.v[0], 1);
+        if (COMP) {
+            lleft = __shfl_up_sync(FULL, lc.v[3], 1);
+            lright = __shfl_down_sync(FULL, lc.v[0], 1);
+        }
+        if (inrow && lane == 0 && hasL) {
+            left = hin[i - 1];
+            if (COMP) lleft = lin[i - 1];
+        }
+        if (inrow && lane == 31 && hasR) {
+            right = hin[i + 4];
+            if (COMP) lright = lin[i + 4];
+        }
+        if (inrow) {
+            Q4<T> ho;
+            Q4<float> lo;
+            uint32_t latch_bits = 0;
+            double Sd[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int x = x0 + q;
+                const T c = hc.v[q];
+                const T xm = q == 0 ? left : hc.v[q - 1];
+                const T xp = q == 3 ? right : hc.v[q + 1];
+                T nh;
+                float nl = 0.f;
+                if (COMP) {
+                    const float cl = lc.v[q];
+                    const float lxm = q == 0 ? lleft : lc.v[q - 1];
+                    const float lxp = q == 3 ? lright : lc.v[q + 1];
+                    // sum of neighbour differences (Eq. 2675-eq3 in x, y, z), fixed order
+                    float S = 0.f;
+                    S = acc(S, x > 0 ? cdiff((float)xm, lxm, (float)c, cl) : 0.f);
+                    S = acc(S, x + 1 < A.nx ? cdiff((float)xp, lxp, (float)c, cl) : 0.f);
+                    S = acc(S, hasYm ? cdiff((float)hym.v[q], lym.v[q], (float)c, cl) : 0.f);
+                    S = acc(S, hasYp ? cdiff((float)hyp.v[q], lyp.v[q], (float)c, cl) : 0.f);
+                    S = acc(S, hasZm ? cdiff((float)hm.v[q], lm.v[q], (float)c, cl) : 0.f);
+                    S = acc(S, hasZp ? cdiff((float)hp.v[q], lp.v[q], (float)c, cl) : 0.f);
+                    float h2;
+                    cupdate((float)c, cl, S, (float)aq[q], (float)bq[q], (float)sq[q], h2, nl);
+                    nh = (T)h2;
+                } else {
+                    T S = T(0);
+                    S = acc(S, x > 0 ? pdiff(xm, c) : T(0));
+                    S = acc(S, x + 1 < A.nx ? pdiff(xp, c) : T(0));
+                    S = acc(S, hasYm ? pdiff(hym.v[q], c) : T(0));
+                    S = acc(S, hasYp ? pdiff(hyp.v[q], c) : T(0));
+                    S = acc(S, hasZm ? pdiff(hm.v[q], c) : T(0));
+                    S = acc(S, hasZp ? pdiff(hp.v[q], c) : T(0));
+                    nh = pupdate(c, S, aq[q], bq[q], sq[q]);
+                }
+                if (x >= A.nx) {
+                    nh = T(0);
+                    nl = 0.f;
+                }
+                bad |= (x < A.nx) && !isfinite((double)nh);
+                ho.v[q] = nh;
+                lo.v[q] = nl;
+                if (LATCH && x < A.nx && nh + (T)nl >= thr) latch_bits |= 1u << (8 * q);
+                if (DMG) {
+                    if (SP == RFA_STATE_F64) {
+                        double tk = (double)nh + A.dc.TK0d;
+                        Sd[q] = exp2(A.dc.c0d - A.dc.c1d / tk);
+                    } else {
+                        Sd[q] = (double)arrhenius_inc(__fadd_rn((float)nh, nl), A.dc.c0, A.dc.c1,
+                                                      A.dc.TK0);
+                    }
+                }
+            }
+            stq(hout + i, ho);
+            if (COMP) stq(lout + i, lo);
+            if (LATCH && latch_bits) {
+                uint32_t *lp32 = reinterpret_cast<uint32_t *>(A.latch + i);
+                uint32_t old = *lp32;
+                if ((old | latch_bits) != old) *lp32 = old | latch_bits;
+            }
+            if (DMG) {
+                double2 *op = reinterpret_cast<double2 *>(A.omega + i);
+                float4 *cp = reinterpret_cast<float4 *>(A.omega_c + i);
+                double2 o01 = op[0], o23 = op[1];
+                float4 cc = *cp;
+                double om[4] = {o01.x, o01.y, o23.x, o23.y};
+                float ck[4] = {cc.x, cc.y, cc.z, cc.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (x0 + q < A.nx) kahan_add(om[q], ck[q], Sd[q]);
+                op[0] = make_double2(om[0], om[1]);
+                op[1] = make_double2(om[2], om[3]);
+                *cp = make_float4(ck[0], ck[1], ck[2], ck[3]);
+            }
+        }
+        hm = hc;
+        hc = hp;
+        if (COMP) {
+            lm = lc;
+            lc = lp;
+        }
+    }
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(A.status, kStatusNonfinite);
+}
+
+}  // namespace
+
+DamageConst damage_consts(const rfa_grid *g)
+{
+    DamageConst d;
+    double c0 = std::log2(g->A * g->dt);
+    double c1 = g->Ea / (g->R * std::log(2.0));
+    double TK0 = g->T_a + 273.15;
+    d.c0 = (float)c0;
+    d.c1 = (float)c1;
+    d.TK0 = (float)TK0;
+    d.c0d = c0;
+    d.c1d = c1;
+    d.TK0d = TK0;
+    return d;
+}
+
+cudaError_t launch_step_plain(rfa_grid *g, const void *th_in, const void *lo_in, void *th_out,
+                              void *lo_out, bool damage, bool latch)
+{
+    PlainArgs A;
+    A.th_in = th_in;
+    A.lo_in = lo_in;
+    A.th_out = th_out;
+    A.lo_out = lo_out;
+    A.ab = g->ab;
+    A.s = g->s;
+    A.latch = g->latch;
+    A.omega = g->omega;
+    A.omega_c = g->omega_c;
+    A.status = g->status;
+    A.nx = g->nx;
+    A.ny = g->ny;
+    A.nz = g->nz;
+    A.pitch = g->pitch;
+    A.plane = g->plane;
+    A.zchunk = g->nz < 64 ? g->nz : 32;
+    A.thr = g->T_thr - g->T_a;
+    A.dc = damage_consts(g);
+    dim3 blk(32, 8);
+    dim3 grd = plain_grid_dims(g, A.zchunk);
+#define PLAIN_CASE(SPV, PPV)                                                                  \
+    if (g->sp == SPV && g->pp == PPV) {                                                      \
+        if (damage && latch) k_step_plain<SPV, PPV, true, true><<<grd, blk, 0, g->stream>>>(A);  \
+        else if (latch) k_step_plain<SPV, PPV, false, true><<<grd, blk, 0, g->stream>>>(A);      \
+        else if (damage) k_step_plain<SPV, PPV, true, false><<<grd, blk, 0, g->stream>>>(A);     \
+        else k_step_plain<SPV, PPV, false, false><<<grd, blk, 0, g->stream>>>(A);                \
+    }
+    PLAIN_CASE(RFA_STATE_F32, RFA_PARAM_BF16)
+    PLAIN_CASE(RFA_STATE_F32, RFA_PARAM_F32)
+    PLAIN_CASE(RFA_STATE_F32, RFA_PARAM_F64)
+    PLAIN_CASE(RFA_STATE_F32C, RFA_PARAM_BF16)
+    PLAIN_CASE(RFA_STATE_F32C, RFA_PARAM_F32)
+    PLAIN_CASE(RFA_STATE_F32C, RFA_PARAM_F64)
+    PLAIN_CASE(RFA_STATE_F64, RFA_PARAM_BF16)
+    PLAIN_CASE(RFA_STATE_F64, RFA_PARAM_F32)
+    PLAIN_CASE(RFA_STATE_F64, RFA_PARAM_F64)
+#undef PLAIN_CASE
+    return cudaGetLastError();
+}
+
+}  // namespace rfa

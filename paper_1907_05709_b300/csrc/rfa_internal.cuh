@@ -1,0 +1,208 @@
+// rfa_internal.cuh -- internal declarations of the B300 bioheat library.
+//
+// Layout in HBM (every per-voxel field of a grid): [nz][ny][pitch] with x
+// fastest and pitch = nx rounded up to a multiple of 4, so every row starts on a
+// 16-byte boundary (float4 / TMA friendly).  Padding voxels (x >= nx) hold zero
+// and are never read as neighbours.
+//
+// State theta = T - T_a:
+//   F32  : float  th[2]                     (ping-pong)
+//   F32C : float  th[2] + float lo[2]       (compensated pair, value = hi + lo)
+//   F64  : double th[2]
+// Coefficients a = K dt / (rho c h^2) and b = w_b rho_b c_b dt / (rho c):
+//   BF16 : one uint32 per voxel, a in the low 16 bits, b in the high 16 bits
+//   F32  : float2 (a, b);  F64 : double2 (a, b)
+// Source s = (q + Q_m) dt / (rho c): float (F32/F32C) or double (F64).
+// Fixed voxels (vessels, Dirichlet faces) carry a = b = s = 0, so the update
+// leaves them unchanged without a branch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rfa.h"
+
+namespace rfa {
+
+constexpr unsigned kStatusNonfinite = 1u;
+constexpr unsigned kStatusTimeout = 2u;
+constexpr unsigned kStatusBadLabel = 4u;
+constexpr int kMaxSegments = 17;
+constexpr int kReduceBlocks = 592;  // 4 per SM on 148 SMs; fixed => deterministic reductions
+
+struct LabelCoef {
+    double k, rho, c, w_b, rho_b, c_b, Q_m, T_fixed;
+    int fixed;
+};
+
+struct Segment {
+    double p0[3], p1[3];
+};
+
+struct NeedleGeom {
+    Segment seg[kMaxSegments];
+    int nseg;
+    double r0, P;
+};
+
+// -------------------------------------------------------------- BF16 rounding
+// Round a double to the nearest bfloat16 (8 significant bits, ties to even)
+// and return its bit pattern.  Magnitudes below 2^-126 flush to signed zero.
+__host__ __device__ inline uint16_t bf16_bits_rne(double x)
+{
+    uint64_t u;
+#ifdef __CUDA_ARCH__
+    u = (uint64_t)__double_as_longlong(x);
+#else
+    std::memcpy(&u, &x, 8);
+#endif
+    uint64_t sign = u & 0x8000000000000000ull;
+    uint64_t mag = u & 0x7fffffffffffffffull;
+    if (mag < (uint64_t)(1023 - 126) << 52) return (uint16_t)(sign >> 48);
+    uint64_t lsb = (mag >> 45) & 1ull;
+    mag += (1ull << 44) - 1ull + lsb;       // half of the dropped range, ties to even
+    mag &= ~((1ull << 45) - 1ull);          // keep 7 fraction bits
+    // re-bias the exponent from binary64 (1023) to binary32 / bfloat16 (127)
+    uint64_t e = (mag >> 52) - 1023 + 127;
+    if (e >= 255) return (uint16_t)((sign >> 48) | 0x7f80u);   // overflow -> inf
+    uint32_t f = (uint32_t)(e << 7) | (uint32_t)((mag >> 45) & 0x7fu);
+    return (uint16_t)((sign >> 48) | f);
+}
+
+__host__ __device__ inline float bf16_to_float(uint32_t bits16)
+{
+    uint32_t u = bits16 << 16;
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+#endif
+}
+
+__host__ __device__ inline double round_coef(double x, int param_prec)
+{
+    if (param_prec == RFA_PARAM_BF16) return (double)bf16_to_float(bf16_bits_rne(x));
+    if (param_prec == RFA_PARAM_F32) return (double)(float)x;
+    return x;
+}
+
+// coefficient expressions (Eq. CUDAbioheat3d divided through by rho c_p)
+__host__ __device__ inline double coef_a(const LabelCoef &t, double dt, double h)
+{
+    return (t.k / (t.rho * t.c)) * dt / (h * h);
+}
+__host__ __device__ inline double coef_b(const LabelCoef &t, double dt)
+{
+    return (t.w_b * t.rho_b * t.c_b / (t.rho * t.c)) * dt;
+}
+
+// ------------------------------------------------------------ backward record
+struct Record {
+    bool valid = false;        // every step since set-up was recorded
+    int64_t seg = 0;           // checkpoint spacing
+    int64_t nsteps = 0;        // steps recorded
+    std::vector<void *> ck_hi; // checkpoint states (hi, lo) every seg steps
+    std::vector<void *> ck_lo;
+};
+
+// Schedules of the step
+struct Schedule {
+    int tb_depth = 1;      // steps per launch
+    int tile_variant = 0;  // blocked-kernel tile shape
+};
+
+}  // namespace rfa
+
+struct rfa_grid {
+    int nx = 0, ny = 0, nz = 0, pitch = 0;
+    size_t plane = 0, nvp = 0;  // pitch*ny, pitch*ny*nz
+    double h = 0, dt = 0, T_a = 37.0;
+    int sp = 0, pp = 0, face = 0;
+    cudaStream_t stream = nullptr;
+
+    void *th[2] = {nullptr, nullptr};
+    void *lo[2] = {nullptr, nullptr};
+    int cur = 0;
+    void *ab = nullptr;
+    void *s = nullptr;
+    uint8_t *label = nullptr;
+    uint8_t *latch = nullptr;
+    double *omega = nullptr;
+    float *omega_c = nullptr;
+    unsigned *status = nullptr;     // device status word
+    unsigned *status_host = nullptr;  // pinned mirror
+    void *red = nullptr;            // reduction partials (kReduceBlocks * 32 B)
+    void *stage = nullptr;          // staging buffer (nvox * 8 B)
+    rfa::LabelCoef *d_table = nullptr;
+    std::vector<rfa_tissue> table;
+    int n_labels = 0;
+
+    bool have_tissue = false, have_needle = false;
+    rfa_needle needle{};
+    rfa::NeedleGeom geom{};
+    int dmg = 0;
+    double A = 7.39e39, Ea = 2.577e5, R = 8.31, T_thr = 60.0;
+    int64_t steps = 0;
+    rfa::Schedule sched;
+    rfa::Record rec;
+
+    size_t state_elem() const { return sp == RFA_STATE_F64 ? 8 : 4; }
+    size_t ab_elem() const { return pp == RFA_PARAM_BF16 ? 4 : (pp == RFA_PARAM_F32 ? 8 : 16); }
+    size_t nvox() const { return (size_t)nx * ny * nz; }
+};
+
+namespace rfa {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+rfa_status cuda_fail(cudaError_t e, const char *what);
+#define RFA_CUDA(call)                                          \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return rfa::cuda_fail(e_, #call); \
+    } while (0)
+
+// ---------------------------------------------------------------- launchers
+// setup / source (kernels_setup.cu)
+cudaError_t launch_setup(rfa_grid *g, const uint8_t *labels_dense_dev, int n_labels);
+cudaError_t launch_source(rfa_grid *g);
+// plain one-step-per-launch kernel (kernels_step.cu)
+struct DamageConst {
+    float c0, c1, TK0;     // inc = exp2(c0 - c1 / (theta + TK0)), FP32 path
+    double c0d, c1d, TK0d; // same constants for the FP64 state
+};
+DamageConst damage_consts(const rfa_grid *g);
+cudaError_t launch_step_plain(rfa_grid *g, const void *th_in, const void *lo_in, void *th_out,
+                              void *lo_out, bool damage, bool latch);
+// temporal-blocked TMA kernel (kernels_tb.cu)
+bool tb_supported(const rfa_grid *g, int depth, int variant);
+cudaError_t launch_step_tb(rfa_grid *g, int depth, int variant, const void *th_in,
+                           const void *lo_in, void *th_out, void *lo_out, bool damage);
+// reductions and conversions (kernels_reduce.cu)
+cudaError_t launch_necrosis(rfa_grid *g, uint8_t *mask_dense_dev, double width_K,
+                            void *result_dev);
+cudaError_t launch_to_temperature(rfa_grid *g, void *dst_dense_dev, int as_f64);
+cudaError_t launch_get_field(rfa_grid *g, int field, double *dst_dense_dev);
+
+// adjoint (adjoint.cu)
+rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads);
+void record_free(rfa_grid *g);
+rfa_status record_begin(rfa_grid *g, int64_t nsteps);
+rfa_status record_checkpoint(rfa_grid *g, int64_t step_index);
+
+// forward stepping used by rfa_step and the adjoint recompute (runtime.cu)
+rfa_status advance(rfa_grid *g, int64_t nsteps, bool damage, bool latch);
+
+inline dim3 plain_grid_dims(const rfa_grid *g, int zchunk)
+{
+    int quads = (g->pitch + 3) / 4;
+    return dim3((unsigned)((quads + 31) / 32), (unsigned)((g->ny + 7) / 8),
+                (unsigned)((g->nz + zchunk - 1) / zchunk));
+}
+
+}  // namespace rfa
