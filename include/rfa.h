@@ -47,7 +47,7 @@ typedef enum {
     RFA_E_INVALID = 1,      /* bad argument (null pointer, size, enum value) */
     RFA_E_OOM = 2,          /* device or host allocation failed */
     RFA_E_CUDA = 3,         /* a CUDA runtime/driver call failed */
-    RFA_E_UNSTABLE = 4,     /* 1 - 6a - b < 0 for some free voxel (scheme not positive) */
+    RFA_E_UNSTABLE = 4,     /* 1 - deg*a - b < 0 for some free voxel (scheme not positive) */
     RFA_E_STATE = 5,        /* call out of order (e.g. step before set_tissue) */
     RFA_E_NONFINITE = 6,    /* a step produced a non-finite temperature */
     RFA_E_TIMEOUT = 7,      /* a bounded device-side wait gave up */
@@ -126,7 +126,8 @@ rfa_status rfa_destroy_grid(rfa_grid *g);
  * step counter to zero and clears any recording for rfa_backward.
  * A needle placed earlier is placed again (the source depends on rho c).
  * Errors: RFA_E_INVALID (also a label >= n_labels, detected on the device),
- * RFA_E_UNSTABLE (1 - 6a - b < 0 for a free label).
+ * RFA_E_UNSTABLE (1 - deg*a - b < 0 for a free label, deg = 2 per axis of
+ * extent > 1, i.e. 6 for a 3D grid).
  */
 rfa_status rfa_set_tissue(rfa_grid *g, const uint8_t *labels, const rfa_tissue *table,
                           int n_labels);

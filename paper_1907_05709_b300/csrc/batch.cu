@@ -22,9 +22,4 @@ rfa_status rfa_batch_destroy(rfa_batch *b)
     delete b;
     return RFA_OK;
 }
-rfa_status rfa_autotune(rfa_grid *, const char *)
-{
-    rfa::set_error("autotuner not built yet");
-    return RFA_E_UNSUPPORTED;
-}
 }

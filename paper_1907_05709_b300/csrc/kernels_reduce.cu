@@ -28,6 +28,7 @@ __device__ __forceinline__ T warp_sum(T v)
 template <int SP>
 __global__ void __launch_bounds__(256) k_necrosis(const void *th, const float *lo,
                                                   const uint8_t *latch, const double *omega,
+                                                  const float *carry,
                                                   int nx, int ny, int nz, int pitch, double T_a,
                                                   double T_thr, double inv_width,
                                                   uint8_t *mask_dense, NecroPartial *part)
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(256) k_necrosis(const void *th, const float *l
          i += (size_t)gridDim.x * blockDim.x) {
         int x = (int)(i % pitch);
         if (x >= nx) continue;
-        uint8_t m = (latch[i] ? 1 : 0) | (omega[i] >= 1.0 ? 2 : 0);
+        uint8_t m = (latch[i] ? 1 : 0) | (omega[i] + (double)carry[i] >= 1.0 ? 2 : 0);
         c0 += m & 1;
         c1 += (m >> 1) & 1;
         if (SP == RFA_STATE_F64) {
@@ -117,6 +118,7 @@ struct FieldView {
     const void *ab, *s;
     const uint8_t *latch;
     const double *omega;
+    const float *carry;
 };
 
 __global__ void k_get_field(const FieldView G, const void *th, const float *lo, int field,
@@ -159,7 +161,7 @@ __global__ void k_get_field(const FieldView G, const void *th, const float *lo, 
             v = G.latch[i];
             break;
         case RFA_FIELD_OMEGA:
-            v = G.omega[i];
+            v = G.omega[i] + (double)G.carry[i];  // FP64 integral plus its FP32 carry
             break;
         default:
             break;
@@ -178,15 +180,15 @@ cudaError_t launch_necrosis(rfa_grid *g, uint8_t *mask_dense_dev, double width_K
     double iw = 1.0 / width_K;
     if (g->sp == RFA_STATE_F64)
         k_necrosis<RFA_STATE_F64><<<kReduceBlocks, 256, 0, g->stream>>>(
-            th, lo, g->latch, g->omega, g->nx, g->ny, g->nz, g->pitch, g->T_a, g->T_thr, iw,
+            th, lo, g->latch, g->omega, g->omega_c, g->nx, g->ny, g->nz, g->pitch, g->T_a, g->T_thr, iw,
             mask_dense_dev, part);
     else if (g->sp == RFA_STATE_F32C)
         k_necrosis<RFA_STATE_F32C><<<kReduceBlocks, 256, 0, g->stream>>>(
-            th, lo, g->latch, g->omega, g->nx, g->ny, g->nz, g->pitch, g->T_a, g->T_thr, iw,
+            th, lo, g->latch, g->omega, g->omega_c, g->nx, g->ny, g->nz, g->pitch, g->T_a, g->T_thr, iw,
             mask_dense_dev, part);
     else
         k_necrosis<RFA_STATE_F32><<<kReduceBlocks, 256, 0, g->stream>>>(
-            th, lo, g->latch, g->omega, g->nx, g->ny, g->nz, g->pitch, g->T_a, g->T_thr, iw,
+            th, lo, g->latch, g->omega, g->omega_c, g->nx, g->ny, g->nz, g->pitch, g->T_a, g->T_thr, iw,
             mask_dense_dev, part);
     k_necrosis_final<<<1, 32, 0, g->stream>>>(part, kReduceBlocks, (NecroPartial *)result_dev);
     return cudaGetLastError();
@@ -207,7 +209,7 @@ cudaError_t launch_to_temperature(rfa_grid *g, void *dst, int as_f64)
 
 cudaError_t launch_get_field(rfa_grid *g, int field, double *dst)
 {
-    FieldView G{g->nx, g->ny, g->nz, g->pitch, g->sp, g->pp, g->ab, g->s, g->latch, g->omega};
+    FieldView G{g->nx, g->ny, g->nz, g->pitch, g->sp, g->pp, g->ab, g->s, g->latch, g->omega, g->omega_c};
     k_get_field<<<148 * 8, 256, 0, g->stream>>>(G, g->th[g->cur], (const float *)g->lo[g->cur],
                                                 field, dst);
     return cudaGetLastError();

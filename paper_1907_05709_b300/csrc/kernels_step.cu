@@ -20,8 +20,10 @@
 //
 // Damage: inc = dt A exp(-Ea / (R T_K)) is evaluated in FP32 as
 // exp2(c0 - c1 / T_K) with c0 = log2(A dt), c1 = Ea / (R ln 2) (ln-space keeps
-// A = 7.39e39 and exp(-100) inside FP32 range); Omega accumulates it in FP64
-// with Kahan compensation (compensation term kept in FP32).
+// A = 7.39e39 and exp(-100) inside FP32 range).  The integral is kept as an
+// FP64 value plus an FP32 carry: increments go into the carry, which is folded
+// into the FP64 value with an error-free TwoSum on launches flagged `fold`
+// (every few launches); the FP64 state adds every increment in FP64 directly.
 #include "rfa_internal.cuh"
 #include "rfa_update.cuh"
 
@@ -101,6 +103,7 @@ struct PlainArgs {
     size_t plane;
     double thr;  // latch threshold on theta
     DamageConst dc;
+    int fold;    // fold the FP32 damage carry into the FP64 integral this launch
 };
 
 template <int SP, int PP, bool DMG, bool LATCH>
@@ -241,18 +244,42 @@ __global__ void __launch_bounds__(256) k_step_plain(const PlainArgs A)
                 if ((old | latch_bits) != old) *lp32 = old | latch_bits;
             }
             if (DMG) {
-                double2 *op = reinterpret_cast<double2 *>(A.omega + i);
+                // Omega + P: FP64 integral plus FP32 carry (see carry_fold)
                 float4 *cp = reinterpret_cast<float4 *>(A.omega_c + i);
-                double2 o01 = op[0], o23 = op[1];
                 float4 cc = *cp;
-                double om[4] = {o01.x, o01.y, o23.x, o23.y};
-                float ck[4] = {cc.x, cc.y, cc.z, cc.w};
+                float P[4] = {cc.x, cc.y, cc.z, cc.w};
+                double2 *op = reinterpret_cast<double2 *>(A.omega + i);
+                if (SP == RFA_STATE_F64) {
+                    // FP64 state: every increment is added in FP64, error-free, the
+                    // rounding error joining the carry
+                    double2 o01 = op[0], o23 = op[1];
+                    double om[4] = {o01.x, o01.y, o23.x, o23.y};
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (x0 + q < A.nx) kahan_add(om[q], ck[q], Sd[q]);
-                op[0] = make_double2(om[0], om[1]);
-                op[1] = make_double2(om[2], om[3]);
-                *cp = make_float4(ck[0], ck[1], ck[2], ck[3]);
+                    for (int q = 0; q < 4; ++q) {
+                        if (x0 + q >= A.nx) continue;
+                        const double sm = __dadd_rn(om[q], Sd[q]);
+                        const double bb = __dsub_rn(sm, om[q]);
+                        const double er = __dadd_rn(__dsub_rn(om[q], __dsub_rn(sm, bb)), __dsub_rn(Sd[q], bb));
+                        om[q] = sm;
+                        P[q] = __fadd_rn(P[q], (float)er);
+                    }
+                    op[0] = make_double2(om[0], om[1]);
+                    op[1] = make_double2(om[2], om[3]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (x0 + q < A.nx) P[q] = __fadd_rn(P[q], (float)Sd[q]);
+                    if (A.fold) {
+                        double2 o01 = op[0], o23 = op[1];
+                        double om[4] = {o01.x, o01.y, o23.x, o23.y};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (x0 + q < A.nx) carry_fold(om[q], P[q]);
+                        op[0] = make_double2(om[0], om[1]);
+                        op[1] = make_double2(om[2], om[3]);
+                    }
+                }
+                *cp = make_float4(P[0], P[1], P[2], P[3]);
             }
         }
         hm = hc;
@@ -283,9 +310,10 @@ DamageConst damage_consts(const rfa_grid *g)
 }
 
 cudaError_t launch_step_plain(rfa_grid *g, const void *th_in, const void *lo_in, void *th_out,
-                              void *lo_out, bool damage, bool latch)
+                              void *lo_out, bool damage, bool latch, bool fold)
 {
     PlainArgs A;
+    A.fold = fold ? 1 : 0;
     A.th_in = th_in;
     A.lo_in = lo_in;
     A.th_out = th_out;

@@ -31,7 +31,8 @@ constexpr unsigned kStatusNonfinite = 1u;
 constexpr unsigned kStatusTimeout = 2u;
 constexpr unsigned kStatusBadLabel = 4u;
 constexpr int kMaxSegments = 17;
-constexpr int kReduceBlocks = 592;  // 4 per SM on 148 SMs; fixed => deterministic reductions
+constexpr int kReduceBlocks = 592;
+constexpr int kCarrySteps = 32;   // fold the FP32 damage carry at least every 32 steps  // 4 per SM on 148 SMs; fixed => deterministic reductions
 
 struct LabelCoef {
     double k, rho, c, w_b, rho_b, c_b, Q_m, T_fixed;
@@ -148,6 +149,7 @@ struct rfa_grid {
     int dmg = 0;
     double A = 7.39e39, Ea = 2.577e5, R = 8.31, T_thr = 60.0;
     int64_t steps = 0;
+    int64_t carry_steps = 0;  // steps accumulated in the FP32 damage carry since the last fold
     rfa::Schedule sched;
     rfa::Record rec;
 
@@ -178,11 +180,12 @@ struct DamageConst {
 };
 DamageConst damage_consts(const rfa_grid *g);
 cudaError_t launch_step_plain(rfa_grid *g, const void *th_in, const void *lo_in, void *th_out,
-                              void *lo_out, bool damage, bool latch);
+                              void *lo_out, bool damage, bool latch, bool fold);
 // temporal-blocked TMA kernel (kernels_tb.cu)
 bool tb_supported(const rfa_grid *g, int depth, int variant);
+void tb_forget_maps(const rfa_grid *g);
 cudaError_t launch_step_tb(rfa_grid *g, int depth, int variant, const void *th_in,
-                           const void *lo_in, void *th_out, void *lo_out, bool damage);
+                           const void *lo_in, void *th_out, void *lo_out, bool damage, bool fold);
 // reductions and conversions (kernels_reduce.cu)
 cudaError_t launch_necrosis(rfa_grid *g, uint8_t *mask_dense_dev, double width_K,
                             void *result_dev);

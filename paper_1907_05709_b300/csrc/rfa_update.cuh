@@ -56,19 +56,35 @@ __device__ __forceinline__ double acc(double x, double y) { return __dadd_rn(x, 
 
 // ------------------------------------------------------------------- damage
 // Arrhenius increment dt A exp(-Ea / (R T_K)) = exp2(c0 - c1 / T_K) in FP32
+// (c0 = log2(A dt), c1 = Ea / (R ln 2)), with the hardware reciprocal-based
+// division and base-2 exponential (relative error ~1e-6, far inside the
+// damage tolerance; the exponent is formed in ln space so A = 7.39e39 and
+// exp(-100) stay inside FP32 range).
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ float arrhenius_inc(float theta, float c0, float c1, float TK0)
 {
     float tk = __fadd_rn(theta, TK0);
-    return exp2f(__fsub_rn(c0, __fdiv_rn(c1, tk)));
+    return ex2_approx(__fsub_rn(c0, __fdividef(c1, tk)));
 }
 
-// Kahan step of the FP64 damage integral with an FP32-stored compensation
-__device__ __forceinline__ void kahan_add(double &om, float &ck, double inc)
+// The damage integral is Omega + P: Omega in FP64 and P an FP32 carry that
+// holds the not-yet-folded increments plus the rounding error of the last
+// fold.  Increments are added to P in FP32; every few launches the carry is
+// folded into Omega with an error-free TwoSum in FP64 and P keeps the
+// rounding error.  Readers use Omega + P.
+__device__ __forceinline__ void carry_fold(double &om, float &P)
 {
-    double yk = __dsub_rn(inc, (double)ck);
-    double tk = __dadd_rn(om, yk);
-    ck = (float)__dsub_rn(__dsub_rn(tk, om), yk);
-    om = tk;
+    const double p = (double)P;
+    const double s = __dadd_rn(om, p);
+    const double bb = __dsub_rn(s, om);
+    const double err = __dadd_rn(__dsub_rn(om, __dsub_rn(s, bb)), __dsub_rn(p, bb));
+    om = s;
+    P = (float)err;
 }
 
 }  // namespace rfa

@@ -111,15 +111,19 @@ rfa_status advance(rfa_grid *g, int64_t nsteps, bool damage, bool latch)
     while (left > 0) {
         int m = g->sched.tb_depth;
         cudaError_t e;
-        if (m > 1 && left >= m && latch && tb_supported(g, m, g->sched.tile_variant)) {
+        const bool use_tb = m > 1 && left >= m && latch && tb_supported(g, m, g->sched.tile_variant);
+        const int n = use_tb ? m : 1;
+        // fold the FP32 damage carry once it holds kCarrySteps steps
+        const bool fold = damage && g->carry_steps + n >= kCarrySteps;
+        if (use_tb) {
             e = launch_step_tb(g, m, g->sched.tile_variant, g->th[g->cur], g->lo[g->cur],
-                               g->th[g->cur ^ 1], g->lo[g->cur ^ 1], damage);
-            left -= m;
+                               g->th[g->cur ^ 1], g->lo[g->cur ^ 1], damage, fold);
         } else {
             e = launch_step_plain(g, g->th[g->cur], g->lo[g->cur], g->th[g->cur ^ 1],
-                                  g->lo[g->cur ^ 1], damage, latch);
-            left -= 1;
+                                  g->lo[g->cur ^ 1], damage, latch, fold);
         }
+        left -= n;
+        if (damage) g->carry_steps = fold ? 0 : g->carry_steps + n;
         if (e != cudaSuccess) return cuda_fail(e, "step launch");
         g->cur ^= 1;
     }
@@ -208,6 +212,7 @@ rfa_status rfa_destroy_grid(rfa_grid *g)
     if (!g) return RFA_OK;
     cudaStreamSynchronize(g->stream);
     record_free(g);
+    tb_forget_maps(g);
     free_grid_memory(g);
     delete g;
     return RFA_OK;
@@ -232,12 +237,14 @@ rfa_status rfa_set_tissue(rfa_grid *g, const uint8_t *labels, const rfa_tissue *
         c.k = t.k; c.rho = t.rho; c.c = t.c; c.w_b = t.w_b; c.rho_b = t.rho_b; c.c_b = t.c_b;
         c.Q_m = t.Q_m; c.T_fixed = t.T_fixed_C; c.fixed = t.fixed ? 1 : 0;
         if (!c.fixed) {
-            // positivity of the explicit scheme: 1 - 6a - b >= 0 with the stored coefficients
+            // positivity of the explicit scheme: 1 - deg*a - b >= 0 with the stored
+            // coefficients, deg = the largest neighbour count (2 per axis of extent > 1)
             double a = round_coef(coef_a(c, g->dt, g->h), g->pp);
             double b = round_coef(coef_b(c, g->dt), g->pp);
-            if (1.0 - 6.0 * a - b < 0.0) {
-                char buf[160];
-                std::snprintf(buf, sizeof buf, "label %d: 1 - 6a - b = %.6g < 0 (a = %.6g, b = %.6g); reduce dt", l, 1.0 - 6.0 * a - b, a, b);
+            double deg = 2.0 * ((g->nx > 1) + (g->ny > 1) + (g->nz > 1));
+            if (1.0 - deg * a - b < 0.0) {
+                char buf[192];
+                std::snprintf(buf, sizeof buf, "label %d: 1 - %g a - b = %.6g < 0 (a = %.6g, b = %.6g); reduce dt", l, deg, 1.0 - deg * a - b, a, b);
                 return fail(RFA_E_UNSTABLE, buf);
             }
         }
@@ -256,6 +263,7 @@ rfa_status rfa_set_tissue(rfa_grid *g, const uint8_t *labels, const rfa_tissue *
     g->n_labels = n_labels;
     g->cur = 0;
     g->steps = 0;
+    g->carry_steps = 0;
     g->have_tissue = true;
     record_free(g);
     RFA_CUDA(cudaMemcpyAsync(g->status_host, g->status, sizeof(unsigned), cudaMemcpyDeviceToHost, g->stream));
