@@ -106,7 +106,7 @@ struct PlainArgs {
     int fold;    // fold the FP32 damage carry into the FP64 integral this launch
 };
 
-template <int SP, int PP, bool DMG, bool LATCH>
+template <int SP, int PP, bool DMG, bool LATCH, bool FOLD>
 __global__ void __launch_bounds__(256) k_step_plain(const PlainArgs A)
 {
     using T = typename std::conditional<SP == RFA_STATE_F64, double, float>::type;
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(256) k_step_plain(const PlainArgs A)
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
                         if (x0 + q < A.nx) P[q] = __fadd_rn(P[q], (float)Sd[q]);
-                    if (A.fold) {
+                    if (FOLD) {
                         double2 o01 = op[0], o23 = op[1];
                         double om[4] = {o01.x, o01.y, o23.x, o23.y};
 #pragma unroll
@@ -334,12 +334,14 @@ cudaError_t launch_step_plain(rfa_grid *g, const void *th_in, const void *lo_in,
     A.dc = damage_consts(g);
     dim3 blk(32, 8);
     dim3 grd = plain_grid_dims(g, A.zchunk);
-#define PLAIN_CASE(SPV, PPV)                                                                  \
-    if (g->sp == SPV && g->pp == PPV) {                                                      \
-        if (damage && latch) k_step_plain<SPV, PPV, true, true><<<grd, blk, 0, g->stream>>>(A);  \
-        else if (latch) k_step_plain<SPV, PPV, false, true><<<grd, blk, 0, g->stream>>>(A);      \
-        else if (damage) k_step_plain<SPV, PPV, true, false><<<grd, blk, 0, g->stream>>>(A);     \
-        else k_step_plain<SPV, PPV, false, false><<<grd, blk, 0, g->stream>>>(A);                \
+#define PLAIN_CASE(SPV, PPV)                                                                       \
+    if (g->sp == SPV && g->pp == PPV) {                                                           \
+        if (damage && latch && fold) k_step_plain<SPV, PPV, true, true, true><<<grd, blk, 0, g->stream>>>(A);   \
+        else if (damage && latch) k_step_plain<SPV, PPV, true, true, false><<<grd, blk, 0, g->stream>>>(A);     \
+        else if (latch) k_step_plain<SPV, PPV, false, true, false><<<grd, blk, 0, g->stream>>>(A);              \
+        else if (damage && fold) k_step_plain<SPV, PPV, true, false, true><<<grd, blk, 0, g->stream>>>(A);      \
+        else if (damage) k_step_plain<SPV, PPV, true, false, false><<<grd, blk, 0, g->stream>>>(A);             \
+        else k_step_plain<SPV, PPV, false, false, false><<<grd, blk, 0, g->stream>>>(A);                        \
     }
     PLAIN_CASE(RFA_STATE_F32, RFA_PARAM_BF16)
     PLAIN_CASE(RFA_STATE_F32, RFA_PARAM_F32)

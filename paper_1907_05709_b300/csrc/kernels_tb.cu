@@ -10,7 +10,8 @@
 // Tiling.  A CTA owns an output tile of 64 (x) by TY = EY - 2M (y) voxels and a
 // chunk of z planes.  It loads the tile plus a 4-voxel x halo and an M-voxel y
 // halo (72 x EY columns) plane by plane with TMA (cp.async.bulk.tensor, one
-// mbarrier per ring slot, zero fill outside the grid) and streams along z:
+// mbarrier per ring slot, zero fill outside the grid) and streams along z; each
+// thread owns a quad of 4 consecutive x voxels of one tile row:
 // stage k (1 <= k <= M) computes step k on plane p0 - k when stage-0 plane p0
 // has arrived, reading the three planes q-1, q, q+1 of stage k-1 from a
 // 3-plane shared-memory ring.  The last stage writes the output tile to HBM.
@@ -43,22 +44,21 @@ namespace {
 constexpr int TB_EX = 72;       // loaded tile width: 64 output + 4 halo on each side
 constexpr int TB_TX = 64;       // output tile width
 constexpr int TB_HX = 4;        // x halo (keeps the TMA x coordinate 16-byte aligned)
-constexpr int TB_TR = 8;        // thread rows; a CTA has TB_EX * TB_TR = 576 threads
-constexpr int TB_THREADS = TB_EX * TB_TR;
+constexpr int TB_QX = TB_EX / 4;  // quads (4 consecutive x voxels) per tile row
 
 template <int M, int EY>
 struct Cfg {
-    static constexpr int RY = EY / TB_TR;        // tile rows per thread
+    static constexpr int THREADS = TB_QX * EY;   // one thread per quad of the tile plane
     static constexpr int TY = EY - 2 * M;        // output rows per tile
     static constexpr int S0 = M + 2;             // stage-0 ring slots (planes p0-M .. p0+1)
-    static constexpr int PLANE = TB_EX * EY;     // elements per tile plane
-    static constexpr int SLOT0 = 4 * PLANE;      // floats per stage-0 slot: hi, lo, ab, s
-    static constexpr int RINGK = 2 * PLANE;      // floats per stage-k slot: (hi, lo) pairs
+    static constexpr int PLANE = TB_EX * EY;     // floats per tile plane
+    static constexpr int SLOT0 = 4 * PLANE;      // stage-0 slot: hi, lo, ab, s planes
+    static constexpr int RINGK = 2 * PLANE;      // stage-k slot: hi, lo planes
     static constexpr int RING_OFF = S0 * SLOT0;  // float offset of the stage rings
     static constexpr int BAR_OFF = RING_OFF + (M - 1) * 3 * RINGK;
     static constexpr int SMEM = BAR_OFF * 4 + 8 * S0;
     static constexpr int MINB = SMEM <= 110 * 1024 ? 2 : 1;
-    static_assert(EY % TB_TR == 0 && TY > 0 && M <= TB_HX, "bad tile");
+    static_assert(TY > 0 && M <= TB_HX && SMEM <= 227 * 1024, "bad tile");
 };
 
 struct TBArgs {
@@ -67,7 +67,8 @@ struct TBArgs {
     double *omega;
     float *omega_c;
     unsigned *status;
-    int nx, ny, nz, pitch, zchunk;
+    int nx, ny, nz, pitch;
+    int xt, yt, zc;  // tiles in x and y, z chunks; work items = xt * yt * zc
     size_t plane;
     float thr;
     float c0, c1, TK0;
@@ -117,14 +118,19 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-template <int M, int EY, bool DMG>
-__global__ void __launch_bounds__(TB_THREADS, Cfg<M, EY>::MINB)
+__device__ __forceinline__ float4 ld4(const float *sm, int off)
+{
+    return *reinterpret_cast<const float4 *>(sm + off);
+}
+
+template <int M, int EY, bool DMG, bool FOLD>
+__global__ void __launch_bounds__(Cfg<M, EY>::THREADS, Cfg<M, EY>::MINB)
     k_step_tb(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
               const __grid_constant__ CUtensorMap tm_ab, const __grid_constant__ CUtensorMap tm_s,
               const TBArgs A)
 {
     using C = Cfg<M, EY>;
-    constexpr int RY = C::RY, S0 = C::S0, PLANE = C::PLANE;
+    constexpr int S0 = C::S0, PLANE = C::PLANE;
     extern __shared__ __align__(128) float sm[];
     const uint32_t sm_base = smem_u32(sm);
     if (sm_base & 127u) {  // TMA destinations need 128-byte alignment
@@ -132,31 +138,11 @@ __global__ void __launch_bounds__(TB_THREADS, Cfg<M, EY>::MINB)
         return;
     }
     const uint32_t bar_base = sm_base + 4u * C::BAR_OFF;
-
     const int tid = threadIdx.x;
-    const int xl = tid % TB_EX, tr = tid / TB_EX;
-    const int X0 = blockIdx.x * TB_TX;
-    const int Y0 = blockIdx.y * C::TY;
-    const int zb = blockIdx.z * A.zchunk;
-    const int ze = min(A.nz, zb + A.zchunk);
-    const int L = ze - zb + 2 * M;   // stage-0 planes zb-M .. ze+M-1
-    const int xg = X0 - TB_HX + xl;
-    const bool colok = xl >= 1 && xl < TB_EX - 1 && xg >= 0 && xg < A.nx;
-    const bool outcol = xl >= TB_HX && xl < TB_HX + TB_TX && xg < A.nx;
-    const bool xm_ok = xg > 0, xp_ok = xg + 1 < A.nx;
-
-    // per-row constants of this thread
-    int yg[RY], id[RY];
-    bool rowok[RY], ym_ok[RY], yp_ok[RY];
-#pragma unroll
-    for (int r = 0; r < RY; ++r) {
-        const int yl = tr * RY + r;
-        yg[r] = Y0 - M + yl;
-        id[r] = yl * TB_EX + xl;
-        rowok[r] = colok && yg[r] >= 0 && yg[r] < A.ny;
-        ym_ok[r] = yg[r] > 0;
-        yp_ok[r] = yg[r] + 1 < A.ny;
-    }
+    const int qx = tid % TB_QX, yl = tid / TB_QX;   // quad column and row in the tile
+    const int xl0 = 4 * qx;                          // first tile column of the quad
+    const int id = yl * TB_EX + xl0;                 // float offset of the quad in a plane
+    const int nitems = A.xt * A.yt * A.zc;
 
     if (tid == 0) {
         for (int j = 0; j < S0; ++j) mbar_init(bar_base + 8u * j, 1);
@@ -165,125 +151,209 @@ __global__ void __launch_bounds__(TB_THREADS, Cfg<M, EY>::MINB)
     }
     __syncthreads();
 
-    auto issue = [&](int itp) {  // stage-0 plane zb - M + itp into slot itp % S0
-        const int j = itp % S0;
+    // work item -> tile origin and z range (balanced z chunks)
+    auto item_geom = [&](int item, int &X0, int &Y0, int &zb, int &ze) {
+        const int tx = item % A.xt, r = item / A.xt;
+        const int ty = r % A.yt, zi = r / A.yt;
+        X0 = tx * TB_TX;
+        Y0 = ty * C::TY;
+        zb = (int)((long long)zi * A.nz / A.zc);
+        ze = (int)((long long)(zi + 1) * A.nz / A.zc);
+    };
+    // stage-0 plane z of the tile at (X0, Y0) into the ring slot of load number n
+    auto issue = [&](long long n, int X0, int Y0, int z) {
+        const int j = (int)(n % S0);
         const uint32_t dst = sm_base + 4u * (uint32_t)(j * C::SLOT0);
         const uint32_t bar = bar_base + 8u * j;
-        const int z = zb - M + itp;
         mbar_expect_tx(bar, (uint32_t)(C::SLOT0 * 4));
         tma_load_3d(dst, &tm_hi, X0 - TB_HX, Y0 - M, z, bar);
         tma_load_3d(dst + 4u * PLANE, &tm_lo, X0 - TB_HX, Y0 - M, z, bar);
         tma_load_3d(dst + 8u * PLANE, &tm_ab, X0 - TB_HX, Y0 - M, z, bar);
         tma_load_3d(dst + 12u * PLANE, &tm_s, X0 - TB_HX, Y0 - M, z, bar);
     };
-    if (tid == 0) issue(0);
 
-    float part[M + 1][RY], mx[M + 1][RY];
-#pragma unroll
-    for (int k = 0; k <= M; ++k)
-#pragma unroll
-        for (int r = 0; r < RY; ++r) {
-            part[k][r] = 0.f;
-            mx[k][r] = -3.0e38f;
-        }
+    long long nload = 0;  // stage-0 planes loaded by this CTA so far (ring slot / phase counter)
+    int item = blockIdx.x;
+    if (item < nitems && tid == 0) {
+        int X0, Y0, zb, ze;
+        item_geom(item, X0, Y0, zb, ze);
+        issue(0, X0, Y0, zb - M);
+    }
     bool bad = false;
-    // ring slot of plane p: ring0 (p - zb + M) % S0, stage rings (p - zb + M) % 3
-    int s0_cur = 0, s3_cur = 0;  // slots of stage-0 plane p0 (it % S0, it % 3)
+    for (; item < nitems; item += gridDim.x) {
+        int X0, Y0, zb, ze;
+        item_geom(item, X0, Y0, zb, ze);
+        const int L = ze - zb + 2 * M;   // stage-0 planes zb-M .. ze+M-1
+        const int xg0 = X0 - TB_HX + xl0;
+        const int yg = Y0 - M + yl;
+        const bool row_in = yg >= 0 && yg < A.ny;
+        const bool ym_ok = yg > 0, yp_ok = yg + 1 < A.ny;
+        bool xm_ok[4], xp_ok[4], xin[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int x = xg0 + j;
+            xin[j] = x >= 0 && x < A.nx;
+            // the tile's outer columns have no stored neighbour (their results are never used)
+            xm_ok[j] = x > 0 && (j > 0 || qx > 0);
+            xp_ok[j] = x + 1 < A.nx && (j < 3 || qx < TB_QX - 1);
+        }
+        const bool out_quad = qx >= 1 && qx < TB_QX - 1 && yl >= M && yl < EY - M && row_in && xg0 < A.nx;
 
-    for (int it = 0; it < L; ++it) {
-        const int p0 = zb - M + it;
-        if (tid == 0 && it + 1 < L) issue(it + 1);
+        float part[M + 1][4], mx[M + 1][4];
 #pragma unroll
-        for (int k = M; k >= 2; --k)
+        for (int k = 0; k <= M; ++k)
 #pragma unroll
-            for (int r = 0; r < RY; ++r) {
-                part[k][r] = part[k - 1][r];
-                mx[k][r] = mx[k - 1][r];
+            for (int j = 0; j < 4; ++j) {
+                part[k][j] = 0.f;
+                mx[k][j] = -3.0e38f;
             }
-#pragma unroll
-        for (int r = 0; r < RY; ++r) {
-            part[1][r] = 0.f;
-            mx[1][r] = -3.0e38f;
-        }
-        const bool ok = mbar_wait(bar_base + 8u * s0_cur, (uint32_t)((it / S0) & 1));
-        if (__syncthreads_or(!ok)) {
+        int s3_cur = 0;  // stage-ring slot of stage-0 plane p0 (it % 3)
+
+        for (int it = 0; it < L; ++it, ++nload) {
+            const int p0 = zb - M + it;
             if (tid == 0) {
-                atomicOr(A.status, kStatusTimeout);
-                if (it + 1 < L) mbar_wait(bar_base + 8u * ((it + 1) % S0), (uint32_t)(((it + 1) / S0) & 1));
+                if (it + 1 < L) {
+                    issue(nload + 1, X0, Y0, p0 + 1);
+                } else if (item + (int)gridDim.x < nitems) {  // first plane of the next item
+                    int X1, Y1, zb1, ze1;
+                    item_geom(item + gridDim.x, X1, Y1, zb1, ze1);
+                    issue(nload + 1, X1, Y1, zb1 - M);
+                }
             }
-            return;
-        }
+            // output-stage operands of plane p0 - M, loaded early to hide their latency
+            const int qo = p0 - M;
+            const bool out_now = out_quad && it >= 2 * M && qo >= 0 && qo < A.nz;
+            const size_t gio = out_now ? (size_t)qo * A.plane + (size_t)yg * A.pitch + xg0 : 0;
+            float4 carry4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            uint32_t latch4 = 0;
+            double2 om01 = make_double2(0.0, 0.0), om23 = om01;
+            if (out_now) {
+                latch4 = *reinterpret_cast<const uint32_t *>(A.latch + gio);
+                if (DMG) carry4 = *reinterpret_cast<const float4 *>(A.omega_c + gio);
+                if (DMG && FOLD) {
+                    om01 = reinterpret_cast<const double2 *>(A.omega + gio)[0];
+                    om23 = reinterpret_cast<const double2 *>(A.omega + gio)[1];
+                }
+            }
 #pragma unroll
-        for (int k = 1; k <= M; ++k) {
-            const int q = p0 - k;
-            if (it >= 2 * k && q >= 0 && q < A.nz) {
-                // slots of planes q-1, q, q+1 (stage k-1) and of the coefficients of q
-                const int sq0 = (s0_cur + S0 - k) % S0;              // ring0 slot of plane q
-                const int s3q = (s3_cur + 3 * M - k) % 3;            // stage-ring slot of plane q
-                const int cb = sq0 * C::SLOT0;                        // coefficients of plane q
-                const bool zm_ok = q > 0, zp_ok = q + 1 < A.nz;
+            for (int k = M; k >= 2; --k)
 #pragma unroll
-                for (int r = 0; r < RY; ++r) {
-                    const int yl = tr * RY + r;
-                    if (!(rowok[r] && yl >= k && yl < EY - k)) continue;
-                    const int i = id[r];
-                    float c, cl, S = 0.f;
+                for (int j = 0; j < 4; ++j) {
+                    part[k][j] = part[k - 1][j];
+                    mx[k][j] = mx[k - 1][j];
+                }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                part[1][j] = 0.f;
+                mx[1][j] = -3.0e38f;
+            }
+            const int s0_cur = (int)(nload % S0);
+            const bool ok = mbar_wait(bar_base + 8u * s0_cur, (uint32_t)((nload / S0) & 1));
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) {
+                    atomicOr(A.status, kStatusTimeout);
+                    mbar_wait(bar_base + 8u * ((nload + 1) % S0), (uint32_t)(((nload + 1) / S0) & 1));
+                }
+                return;
+            }
+#pragma unroll
+            for (int k = 1; k <= M; ++k) {
+                const int q = p0 - k;
+                if (it >= 2 * k && q >= 0 && q < A.nz && row_in && yl >= k && yl < EY - k) {
+                    const int sq0 = (s0_cur + S0 - k) % S0;   // ring0 slot of plane q
+                    const int s3q = (s3_cur + 3 * M - k) % 3; // stage-ring slot of plane q
+                    const int cb = sq0 * C::SLOT0;             // coefficients of plane q
+                    const bool zm_ok = q > 0, zp_ok = q + 1 < A.nz;
+                    // hi/lo planes q-1, q, q+1 of stage k-1
+                    int bc, bm, bp;
                     if (k == 1) {
-                        const int bc = cb, bm = ((sq0 + S0 - 1) % S0) * C::SLOT0, bp = ((sq0 + 1) % S0) * C::SLOT0;
-                        c = sm[bc + i];
-                        cl = sm[bc + PLANE + i];
-                        S = acc(S, xm_ok ? cdiff(sm[bc + i - 1], sm[bc + PLANE + i - 1], c, cl) : 0.f);
-                        S = acc(S, xp_ok ? cdiff(sm[bc + i + 1], sm[bc + PLANE + i + 1], c, cl) : 0.f);
-                        S = acc(S, ym_ok[r] ? cdiff(sm[bc + i - TB_EX], sm[bc + PLANE + i - TB_EX], c, cl) : 0.f);
-                        S = acc(S, yp_ok[r] ? cdiff(sm[bc + i + TB_EX], sm[bc + PLANE + i + TB_EX], c, cl) : 0.f);
-                        S = acc(S, zm_ok ? cdiff(sm[bm + i], sm[bm + PLANE + i], c, cl) : 0.f);
-                        S = acc(S, zp_ok ? cdiff(sm[bp + i], sm[bp + PLANE + i], c, cl) : 0.f);
+                        bc = cb;
+                        bm = ((sq0 + S0 - 1) % S0) * C::SLOT0;
+                        bp = ((sq0 + 1) % S0) * C::SLOT0;
                     } else {
-                        const float2 *R = reinterpret_cast<const float2 *>(sm + C::RING_OFF + ((k - 2) * 3 + s3q) * C::RINGK);
-                        const float2 *Rm = reinterpret_cast<const float2 *>(sm + C::RING_OFF + ((k - 2) * 3 + (s3q + 2) % 3) * C::RINGK);
-                        const float2 *Rp = reinterpret_cast<const float2 *>(sm + C::RING_OFF + ((k - 2) * 3 + (s3q + 1) % 3) * C::RINGK);
-                        const float2 cc = R[i];
-                        c = cc.x;
-                        cl = cc.y;
-                        float2 v;
-                        v = R[i - 1];      S = acc(S, xm_ok ? cdiff(v.x, v.y, c, cl) : 0.f);
-                        v = R[i + 1];      S = acc(S, xp_ok ? cdiff(v.x, v.y, c, cl) : 0.f);
-                        v = R[i - TB_EX];  S = acc(S, ym_ok[r] ? cdiff(v.x, v.y, c, cl) : 0.f);
-                        v = R[i + TB_EX];  S = acc(S, yp_ok[r] ? cdiff(v.x, v.y, c, cl) : 0.f);
-                        v = Rm[i];         S = acc(S, zm_ok ? cdiff(v.x, v.y, c, cl) : 0.f);
-                        v = Rp[i];         S = acc(S, zp_ok ? cdiff(v.x, v.y, c, cl) : 0.f);
+                        const int rk = C::RING_OFF + (k - 2) * 3 * C::RINGK;
+                        bc = rk + s3q * C::RINGK;
+                        bm = rk + ((s3q + 2) % 3) * C::RINGK;
+                        bp = rk + ((s3q + 1) % 3) * C::RINGK;
                     }
-                    const uint32_t w = __float_as_uint(sm[cb + 2 * PLANE + i]);
-                    float nh, nl;
-                    cupdate(c, cl, S, bf16_to_float(w & 0xffffu), bf16_to_float(w >> 16), sm[cb + 3 * PLANE + i], nh, nl);
-                    const float val = __fadd_rn(nh, nl);
-                    mx[k][r] = fmaxf(mx[k][r], val);
-                    if (DMG) part[k][r] = __fadd_rn(part[k][r], arrhenius_inc(val, A.c0, A.c1, A.TK0));
+                    const float4 ch = ld4(sm, bc + id), cl = ld4(sm, bc + PLANE + id);
+                    const float4 ymh = ld4(sm, bc + id - TB_EX), yml = ld4(sm, bc + PLANE + id - TB_EX);
+                    const float4 yph = ld4(sm, bc + id + TB_EX), ypl = ld4(sm, bc + PLANE + id + TB_EX);
+                    const float4 zmh = ld4(sm, bm + id), zml = ld4(sm, bm + PLANE + id);
+                    const float4 zph = ld4(sm, bp + id), zpl = ld4(sm, bp + PLANE + id);
+                    const int lo_off = qx > 0 ? -1 : 0, hi_off = qx < TB_QX - 1 ? 4 : 3;
+                    const float lh = sm[bc + id + lo_off], ll = sm[bc + PLANE + id + lo_off];
+                    const float rh = sm[bc + id + hi_off], rl = sm[bc + PLANE + id + hi_off];
+                    const uint4 w4 = *reinterpret_cast<const uint4 *>(sm + cb + 2 * PLANE + id);
+                    const float4 s4 = ld4(sm, cb + 3 * PLANE + id);
+                    const float c_[4] = {ch.x, ch.y, ch.z, ch.w}, cl_[4] = {cl.x, cl.y, cl.z, cl.w};
+                    const float ymh_[4] = {ymh.x, ymh.y, ymh.z, ymh.w}, yml_[4] = {yml.x, yml.y, yml.z, yml.w};
+                    const float yph_[4] = {yph.x, yph.y, yph.z, yph.w}, ypl_[4] = {ypl.x, ypl.y, ypl.z, ypl.w};
+                    const float zmh_[4] = {zmh.x, zmh.y, zmh.z, zmh.w}, zml_[4] = {zml.x, zml.y, zml.z, zml.w};
+                    const float zph_[4] = {zph.x, zph.y, zph.z, zph.w}, zpl_[4] = {zpl.x, zpl.y, zpl.z, zpl.w};
+                    const uint32_t w_[4] = {w4.x, w4.y, w4.z, w4.w};
+                    const float s_[4] = {s4.x, s4.y, s4.z, s4.w};
+                    float nh_[4], nl_[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float c = c_[j], l = cl_[j];
+                        const float xmh = j == 0 ? lh : c_[j - 1], xml = j == 0 ? ll : cl_[j - 1];
+                        const float xph = j == 3 ? rh : c_[j + 1], xpl = j == 3 ? rl : cl_[j + 1];
+                        float S = 0.f;
+                        S = acc(S, xm_ok[j] ? cdiff(xmh, xml, c, l) : 0.f);
+                        S = acc(S, xp_ok[j] ? cdiff(xph, xpl, c, l) : 0.f);
+                        S = acc(S, ym_ok ? cdiff(ymh_[j], yml_[j], c, l) : 0.f);
+                        S = acc(S, yp_ok ? cdiff(yph_[j], ypl_[j], c, l) : 0.f);
+                        S = acc(S, zm_ok ? cdiff(zmh_[j], zml_[j], c, l) : 0.f);
+                        S = acc(S, zp_ok ? cdiff(zph_[j], zpl_[j], c, l) : 0.f);
+                        cupdate(c, l, S, bf16_to_float(w_[j] & 0xffffu), bf16_to_float(w_[j] >> 16), s_[j],
+                                nh_[j], nl_[j]);
+                        const float val = __fadd_rn(nh_[j], nl_[j]);
+                        mx[k][j] = fmaxf(mx[k][j], val);
+                        if (DMG) part[k][j] = __fadd_rn(part[k][j], arrhenius_inc(val, A.c0, A.c1, A.TK0));
+                    }
                     if (k < M) {
-                        float2 *O = reinterpret_cast<float2 *>(sm + C::RING_OFF + ((k - 1) * 3 + s3q) * C::RINGK);
-                        O[i] = make_float2(nh, nl);
-                    } else if (outcol && yl >= M && yl < EY - M) {
-                        const size_t gi = (size_t)q * A.plane + (size_t)yg[r] * A.pitch + xg;
-                        A.hi_out[gi] = nh;
-                        A.lo_out[gi] = nl;
-                        bad |= !isfinite(nh);
-                        if (mx[k][r] >= A.thr && A.latch[gi] == 0) A.latch[gi] = 1;
+                        const int bo = C::RING_OFF + ((k - 1) * 3 + s3q) * C::RINGK;
+                        *reinterpret_cast<float4 *>(sm + bo + id) = make_float4(nh_[0], nh_[1], nh_[2], nh_[3]);
+                        *reinterpret_cast<float4 *>(sm + bo + PLANE + id) = make_float4(nl_[0], nl_[1], nl_[2], nl_[3]);
+                    } else if (out_now) {
+                        // output quad: 16-byte aligned (X0 % 64 == 0, pitch % 4 == 0); padding
+                        // voxels beyond nx are written as zero
+                        float o_h[4], o_l[4];
+                        uint32_t lbits = 0;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            o_h[j] = xin[j] ? nh_[j] : 0.f;
+                            o_l[j] = xin[j] ? nl_[j] : 0.f;
+                            bad |= xin[j] && !isfinite(nh_[j]);
+                            if (xin[j] && mx[k][j] >= A.thr) lbits |= 1u << (8 * j);
+                        }
+                        *reinterpret_cast<float4 *>(A.hi_out + gio) = make_float4(o_h[0], o_h[1], o_h[2], o_h[3]);
+                        *reinterpret_cast<float4 *>(A.lo_out + gio) = make_float4(o_l[0], o_l[1], o_l[2], o_l[3]);
+                        if ((latch4 | lbits) != latch4)
+                            *reinterpret_cast<uint32_t *>(A.latch + gio) = latch4 | lbits;
                         if (DMG) {
-                            float P = __fadd_rn(A.omega_c[gi], part[k][r]);
-                            if (A.fold) {
-                                double om = A.omega[gi];
-                                carry_fold(om, P);
-                                A.omega[gi] = om;
+                            float P[4] = {carry4.x, carry4.y, carry4.z, carry4.w};
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                if (xin[j]) P[j] = __fadd_rn(P[j], part[k][j]);
+                            if (FOLD) {
+                                double om[4] = {om01.x, om01.y, om23.x, om23.y};
+#pragma unroll
+                                for (int j = 0; j < 4; ++j)
+                                    if (xin[j]) carry_fold(om[j], P[j]);
+                                double2 *op = reinterpret_cast<double2 *>(A.omega + gio);
+                                op[0] = make_double2(om[0], om[1]);
+                                op[1] = make_double2(om[2], om[3]);
                             }
-                            A.omega_c[gi] = P;
+                            *reinterpret_cast<float4 *>(A.omega_c + gio) = make_float4(P[0], P[1], P[2], P[3]);
                         }
                     }
                 }
+                __syncthreads();
             }
-            __syncthreads();
+            s3_cur = s3_cur + 1 == 3 ? 0 : s3_cur + 1;
         }
-        s0_cur = s0_cur + 1 == S0 ? 0 : s0_cur + 1;
-        s3_cur = s3_cur + 1 == 3 ? 0 : s3_cur + 1;
     }
     if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(A.status, kStatusNonfinite);
 }
@@ -318,26 +388,38 @@ bool make_map(CUtensorMap *m, const void *base, CUtensorMapDataType dt, const rf
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int variant_ey(int variant) { return variant == 1 ? 24 : 16; }
+int variant_ey(int variant) { return variant == 1 ? 32 : 16; }
 
-template <int M, int EY, bool DMG>
+template <int M, int EY, bool DMG, bool FOLD>
 cudaError_t launch_inst(rfa_grid *g, const CUtensorMap *maps, const TBArgs &A0)
 {
     using C = Cfg<M, EY>;
-    cudaError_t e = cudaFuncSetAttribute(k_step_tb<M, EY, DMG>,
+    cudaError_t e = cudaFuncSetAttribute(k_step_tb<M, EY, DMG, FOLD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     TBArgs A = A0;
-    const int xt = (g->nx + TB_TX - 1) / TB_TX;
-    const int yt = (g->ny + C::TY - 1) / C::TY;
+    A.xt = (g->nx + TB_TX - 1) / TB_TX;
+    A.yt = (g->ny + C::TY - 1) / C::TY;
+    // persistent CTAs (all resident at once) walk the (tile, z-chunk) items; pick
+    // the number of z chunks that minimises the busiest CTA's plane count
     const int resident = 148 * C::MINB;
-    int zc = (2 * resident + xt * yt - 1) / (xt * yt);
-    int maxzc = g->nz / (4 * M) > 0 ? g->nz / (4 * M) : 1;
-    if (zc > maxzc) zc = maxzc;
-    if (zc < 1) zc = 1;
-    A.zchunk = (g->nz + zc - 1) / zc;
-    dim3 grd((unsigned)xt, (unsigned)yt, (unsigned)((g->nz + A.zchunk - 1) / A.zchunk));
-    k_step_tb<M, EY, DMG><<<grd, TB_THREADS, C::SMEM, g->stream>>>(maps[0], maps[1], maps[2], maps[3], A);
+    const long long tiles = (long long)A.xt * A.yt;
+    int best_zc = 1;
+    double best = 1e300;
+    for (int zc = 1; zc <= g->nz; ++zc) {
+        const long long items = tiles * zc;
+        const long long per_cta = (items + resident - 1) / resident;
+        const double cost = (double)per_cta * ((double)g->nz / zc + 2.0 * M);
+        if (cost < best * 0.999) {
+            best = cost;
+            best_zc = zc;
+        }
+        if ((double)g->nz / zc < 2.0 * M) break;
+    }
+    A.zc = best_zc;
+    const long long items = tiles * A.zc;
+    const unsigned grid = (unsigned)(items < resident ? items : resident);
+    k_step_tb<M, EY, DMG, FOLD><<<grid, C::THREADS, C::SMEM, g->stream>>>(maps[0], maps[1], maps[2], maps[3], A);
     return cudaGetLastError();
 }
 
@@ -359,7 +441,7 @@ bool tb_supported(const rfa_grid *g, int depth, int variant)
     if (g->sp != RFA_STATE_F32C || g->pp != RFA_PARAM_BF16) return false;
     if (variant < 0 || variant > 1) return false;
     if (variant == 0 && (depth < 2 || depth > 4)) return false;
-    if (variant == 1 && (depth < 2 || depth > 3)) return false;
+    if (variant == 1 && depth != 2) return false;
     return encode_fn() != nullptr;
 }
 
@@ -406,7 +488,6 @@ cudaError_t launch_step_tb(rfa_grid *g, int depth, int variant, const void *th_i
     A.nz = g->nz;
     A.pitch = g->pitch;
     A.plane = g->plane;
-    A.zchunk = g->nz;
     A.thr = (float)(g->T_thr - g->T_a);
     DamageConst dc = damage_consts(g);
     A.c0 = dc.c0;
@@ -415,13 +496,13 @@ cudaError_t launch_step_tb(rfa_grid *g, int depth, int variant, const void *th_i
     A.fold = fold ? 1 : 0;
 #define TB_CASE(MV, EYV)                                                                 \
     if (depth == MV && ey == EYV)                                                        \
-        return damage ? launch_inst<MV, EYV, true>(g, maps.data(), A)                   \
-                      : launch_inst<MV, EYV, false>(g, maps.data(), A);
+        return !damage ? launch_inst<MV, EYV, false, false>(g, maps.data(), A)          \
+               : fold  ? launch_inst<MV, EYV, true, true>(g, maps.data(), A)            \
+                       : launch_inst<MV, EYV, true, false>(g, maps.data(), A);
     TB_CASE(2, 16)
     TB_CASE(3, 16)
     TB_CASE(4, 16)
-    TB_CASE(2, 24)
-    TB_CASE(3, 24)
+    TB_CASE(2, 32)
 #undef TB_CASE
     return cudaErrorInvalidValue;
 }
