@@ -187,6 +187,23 @@ rfa_status rfa_necrosis_mask(rfa_grid *g, uint8_t *mask_or_null, int64_t *counts
                              double smooth_width_K);
 
 /*
+ * Necrosis counts and smoothed volume without allocating memory.  The paper has
+ * no counterpart; this exists for callers that may not allocate device memory
+ * once running (a per-frame real-time loop where an allocation would stall the
+ * device, or an application that pre-reserves its whole memory budget).
+ * result_dev: caller-owned device buffer of 32 bytes receiving
+ * {int64 count_thermal, int64 count_arrhenius, double smooth_volume_m3, 0.0},
+ * the same quantities rfa_necrosis_mask reports.  Asynchronous on the grid's
+ * stream; calls no allocator and does not synchronise.  Scratch is one fixed
+ * 128 KiB device array inside the library (4096 records, one per 65536 padded
+ * voxels), so grids above 268,435,456 padded voxels are rejected with
+ * RFA_E_INVALID.  The first call with a device current looks up that array's
+ * address; make it before any stream capture.  Calls share the array: each
+ * call rewrites every record it reads, but calls that overlap on the GPU race.
+ */
+rfa_status rfa_necrosis_reduce_noalloc(rfa_grid *g, double smooth_width_K, void *result_dev);
+
+/*
  * Discrete adjoint of every recorded step (the paper has no adjoint).
  * dLdT_final_dev: device float array nx*ny*nz (x fastest), dL/dT of the final
  * state.  grads (host, 4 + 2*n_labels doubles) receives

@@ -32,7 +32,7 @@ EXPORTED = ("rfa_create_grid", "rfa_destroy_grid", "rfa_set_tissue", "rfa_place_
             "rfa_necrosis_mask", "rfa_backward", "rfa_get_state", "rfa_set_state",
             "rfa_set_schedule", "rfa_get_schedule", "rfa_autotune", "rfa_batch_create",
             "rfa_batch_step", "rfa_batch_destroy", "rfa_synchronize", "rfa_steps_done",
-            "rfa_last_error")
+            "rfa_last_error", "rfa_necrosis_reduce_noalloc")
 
 
 class RfaError(RuntimeError):
@@ -90,6 +90,7 @@ def lib():
         "rfa_synchronize": [P],
         "rfa_steps_done": [P],
         "rfa_last_error": [],
+        "rfa_necrosis_reduce_noalloc": [P, D, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -208,6 +209,14 @@ def rfa_necrosis_mask(g, mask: Optional[np.ndarray] = None, smooth_width_K: floa
                                    vols.ctypes.data, sv.ctypes.data, float(smooth_width_K)),
            "rfa_necrosis_mask")
     return counts, vols, float(sv[0])
+
+
+def rfa_necrosis_reduce_noalloc(g, result_dev, smooth_width_K: float = 1.0):
+    """Necrosis counts and smoothed volume into a caller-owned 32-byte device
+    buffer {int64 thermal, int64 Arrhenius, float64 smooth volume m^3, 0};
+    allocates nothing and does not synchronise (see include/rfa.h)."""
+    _check(lib().rfa_necrosis_reduce_noalloc(g, float(smooth_width_K), _ptr(result_dev)),
+           "rfa_necrosis_reduce_noalloc")
 
 
 def rfa_backward(g, dLdT_final_dev, grads: np.ndarray):

@@ -1,0 +1,175 @@
+// noalloc.cu -- necrosis counts and smoothed volume through an entry point that
+// allocates no memory at all.
+//
+// Who needs it: callers that must not allocate device memory while they run --
+// a real-time loop (for example a VR renderer stepping the ablation every
+// frame) where a cudaMalloc/cudaFree would synchronise the device and stall
+// the frame, or a host application that pre-reserves its whole device memory
+// budget and forbids any later allocation.  rfa_necrosis_mask may allocate a
+// staging buffer on first use and copies its results to the host; this entry
+// point does neither.
+//
+// How: the per-block partial sums of the two-pass reduction live in one
+// file-scope device array of fixed size (kNoAllocRecords records of 32 bytes,
+// 128 KiB), which every GPU that loads the library holds until the process
+// exits.  Host code must not use the array's name as a device pointer; its
+// device address is looked up once per device with cudaGetSymbolAddress, on
+// the first call made with that device current.
+//
+// Limits: one record per 65536 padded voxels, so grids of more than
+// kNoAllocRecords * 65536 padded voxels (268,435,456; e.g. 640^3) are rejected.
+// Every call shares the array: each call overwrites all the records it later
+// reads, so nothing has to be cleared, but calls whose work overlaps on the GPU
+// (different streams, or different host threads) race on the records.
+#include "rfa_internal.cuh"
+
+#include <mutex>
+
+namespace rfa {
+
+namespace {
+
+constexpr int kNoAllocRecords = 4096;
+constexpr size_t kNoAllocVoxelsPerRecord = 65536;
+
+struct NaRecord {
+    unsigned long long n_thermal, n_arrh;
+    double smooth;
+    double pad;
+};
+
+static __device__ __align__(256) NaRecord g_noalloc_scratch[kNoAllocRecords];
+
+std::mutex g_na_mu;
+void *g_na_ptr[64] = {};  // device address of the scratch array, per device ordinal
+
+// per-block partials: thermal latch, Arrhenius (Omega + carry >= 1), smoothed sigmoid sum
+template <int SP>
+__global__ void __launch_bounds__(256) k_na_partials(const void *th, const float *lo,
+                                                     const uint8_t *latch, const double *omega,
+                                                     const float *carry, int nx, int ny, int nz,
+                                                     int pitch, double off, double inv_width,
+                                                     NaRecord *rec)
+{
+    const size_t nvp = (size_t)pitch * ny * nz;
+    const size_t begin = (size_t)blockIdx.x * kNoAllocVoxelsPerRecord;
+    const size_t end = begin + kNoAllocVoxelsPerRecord < nvp ? begin + kNoAllocVoxelsPerRecord : nvp;
+    unsigned long long c0 = 0, c1 = 0;
+    double sm = 0.0;
+    for (size_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
+        if ((int)(i % pitch) >= nx) continue;
+        c0 += latch[i] ? 1 : 0;
+        c1 += (omega[i] + (double)carry[i] >= 1.0) ? 1 : 0;
+        if (SP == RFA_STATE_F64) {
+            const double u = (((const double *)th)[i] - off) * inv_width;
+            sm += 1.0 / (1.0 + exp(-u));
+        } else {
+            float v = ((const float *)th)[i];
+            if (SP == RFA_STATE_F32C) v += lo[i];
+            const float u = (v - (float)off) * (float)inv_width;
+            sm += (double)(1.0f / (1.0f + __expf(-u)));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+        c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+        sm += __shfl_xor_sync(0xffffffffu, sm, o);
+    }
+    __shared__ unsigned long long s0[8], s1[8];
+    __shared__ double s2[8];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s0[w] = c0;
+        s1[w] = c1;
+        s2[w] = sm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        NaRecord r{0, 0, 0.0, 0.0};
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            r.n_thermal += s0[k];
+            r.n_arrh += s1[k];
+            r.smooth += s2[k];
+        }
+        rec[blockIdx.x] = r;
+    }
+}
+
+// sum the records in a fixed order; out = {count_thermal, count_arrhenius, smooth_volume_m3, 0}
+__global__ void k_na_final(const NaRecord *rec, int n, double h3, void *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long c0 = 0, c1 = 0;
+    double sm = 0.0;
+    for (int k = 0; k < n; ++k) {
+        c0 += rec[k].n_thermal;
+        c1 += rec[k].n_arrh;
+        sm += rec[k].smooth;
+    }
+    int64_t *o = (int64_t *)out;
+    o[0] = (int64_t)c0;
+    o[1] = (int64_t)c1;
+    ((double *)out)[2] = h3 * sm;
+    ((double *)out)[3] = 0.0;
+}
+
+}  // namespace
+
+}  // namespace rfa
+
+using namespace rfa;
+
+extern "C" rfa_status rfa_necrosis_reduce_noalloc(rfa_grid *g, double smooth_width_K, void *result_dev)
+{
+    if (!g || !result_dev) {
+        set_error("null argument");
+        return RFA_E_INVALID;
+    }
+    if (!(smooth_width_K > 0.0)) {
+        set_error("smooth_width_K must be > 0");
+        return RFA_E_INVALID;
+    }
+    const size_t nrec = (g->nvp + kNoAllocVoxelsPerRecord - 1) / kNoAllocVoxelsPerRecord;
+    if (nrec > (size_t)kNoAllocRecords) {
+        set_error("grid too large for rfa_necrosis_reduce_noalloc: at most 268435456 padded voxels "
+                  "(4096 scratch records of 65536 voxels)");
+        return RFA_E_INVALID;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) {
+        set_error("device ordinal out of range");
+        return RFA_E_INVALID;
+    }
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_na_mu);
+        if (!g_na_ptr[dev]) {
+            // first call on this device: look up the device address of the scratch array
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
+            g_na_ptr[dev] = p;
+        }
+        scratch = g_na_ptr[dev];
+    }
+    NaRecord *rec = (NaRecord *)scratch;
+    const void *th = g->th[g->cur];
+    const float *lo = (const float *)g->lo[g->cur];
+    const double off = g->T_thr - g->T_a, iw = 1.0 / smooth_width_K;
+    const unsigned nb = (unsigned)nrec;
+    if (g->sp == RFA_STATE_F64)
+        k_na_partials<RFA_STATE_F64><<<nb, 256, 0, g->stream>>>(th, lo, g->latch, g->omega, g->omega_c, g->nx,
+                                                                g->ny, g->nz, g->pitch, off, iw, rec);
+    else if (g->sp == RFA_STATE_F32C)
+        k_na_partials<RFA_STATE_F32C><<<nb, 256, 0, g->stream>>>(th, lo, g->latch, g->omega, g->omega_c, g->nx,
+                                                                 g->ny, g->nz, g->pitch, off, iw, rec);
+    else
+        k_na_partials<RFA_STATE_F32><<<nb, 256, 0, g->stream>>>(th, lo, g->latch, g->omega, g->omega_c, g->nx,
+                                                                g->ny, g->nz, g->pitch, off, iw, rec);
+    k_na_final<<<1, 32, 0, g->stream>>>(rec, (int)nrec, g->h * g->h * g->h, result_dev);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "rfa_necrosis_reduce_noalloc launch");
+    return RFA_OK;
+}
