@@ -1,14 +1,37 @@
-// adjoint.cu -- sqrt(N) checkpoint recording and the discrete adjoint.
+// adjoint.cu -- sqrt(N) checkpoint recording and the discrete adjoint of the
+// explicit step (the paper has no adjoint; this differentiates the scheme of
+// Eq. CUDAbioheat3d as implemented by the forward kernels).
+//
+// Forward step (free voxel i):  theta'_i = theta_i + a_i sum_nb (theta_j - theta_i) - b_i theta_i + s_i
+// Its transpose applied to lambda, with mu = a * lambda (a = b = 0 on fixed voxels):
+//     (A^T lambda)_i = lambda_i + sum_nb (mu_j - mu_i) - b_i lambda_i
+// Gradients over the recorded steps n = 0..N-1 (lambda^{n+1} = dL/dtheta^{n+1}):
+//     dL/dK_l   = sum_n sum_{i in l, free} lambda^{n+1}_i * dt/(rho c_l h^2) * (L theta^n)_i
+//     dL/dw_b,l = -sum_n sum_{i in l, free} lambda^{n+1}_i * rho_b c_b dt/(rho c_l) * theta^n_i
+//     Lambda_i  = sum_{n=1..N} lambda^n_i,  then with s_i = c_i w_i / W, c_i = P dt/(h^3 rho c_i):
+//     dL/dP     = sum_i Lambda_i c_i w_i / (P W)
+//     dL/dtip   = sum_i Lambda_i c_i dw_i / W - (dW / W^2) sum_i Lambda_i c_i w_i
+// with dw_i/dtip = 4 d_i^-6 (x_i - p*_i) outside the clamp radius (every
+// segment moves rigidly with the tip) and W = sum_free w, dW = sum_free dw.
+//
+// Trajectory: checkpoints (hi, lo) every ceil(sqrt(N)) steps are taken while
+// rfa_step records; the backward pass recomputes each segment with the
+// one-step kernel (bit-identical to the forward kernels), writing the hi part
+// of every state straight into a segment buffer, then runs the adjoint steps of
+// the segment in reverse.
 #include "rfa_internal.cuh"
 
 #include <cmath>
+#include <vector>
 
 namespace rfa {
 
+// ------------------------------------------------------------------ recording
 void record_free(rfa_grid *g)
 {
     for (void *p : g->rec.ck_hi) cudaFree(p);
-    for (void *p : g->rec.ck_lo) if (p) cudaFree(p);
+    for (void *p : g->rec.ck_lo)
+        if (p) cudaFree(p);
     g->rec.ck_hi.clear();
     g->rec.ck_lo.clear();
     g->rec.valid = false;
@@ -48,10 +71,433 @@ rfa_status record_checkpoint(rfa_grid *g, int64_t step_index)
     return RFA_OK;
 }
 
-rfa_status backward_impl(rfa_grid *, const float *, double *)
+namespace {
+
+constexpr int kMaxGradLabels = 8;
+
+struct AdjArgs {
+    const float *lam_in, *th;
+    float *lam_out, *Lam;
+    const void *ab;
+    const uint8_t *label;
+    const LabelCoef *tab;
+    int nx, ny, nz, pitch, zchunk, face;
+    size_t plane;
+    float fk[kMaxGradLabels], gw[kMaxGradLabels];
+    double *acc;  // [2 * kMaxGradLabels]: sum lambda f L(theta), -sum lambda g theta
+};
+
+template <int PP>
+__device__ __forceinline__ void adj_load_ab(const void *ab, size_t i, float a[4], float b[4])
 {
-    set_error("adjoint not built yet");
-    return RFA_E_UNSUPPORTED;
+    if (PP == RFA_PARAM_BF16) {
+        uint4 u = __ldg(reinterpret_cast<const uint4 *>((const uint32_t *)ab + i));
+        uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            a[q] = bf16_to_float(w[q] & 0xffffu);
+            b[q] = bf16_to_float(w[q] >> 16);
+        }
+    } else if (PP == RFA_PARAM_F32) {
+        const float4 *p = reinterpret_cast<const float4 *>((const float2 *)ab + i);
+        float4 u = __ldg(p), v = __ldg(p + 1);
+        a[0] = u.x; b[0] = u.y; a[1] = u.z; b[1] = u.w;
+        a[2] = v.x; b[2] = v.y; a[3] = v.z; b[3] = v.w;
+    } else {
+        const double2 *p = (const double2 *)ab + i;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            double2 t = __ldg(p + q);
+            a[q] = (float)t.x;
+            b[q] = (float)t.y;
+        }
+    }
+}
+
+__device__ __forceinline__ float4 ld4g(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+
+// one adjoint step: lam_out = A^T lam_in, Lam += lam_in, per-label contractions
+template <int PP>
+__global__ void __launch_bounds__(256) k_adjoint_step(const AdjArgs A)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    float accK[kMaxGradLabels], accW[kMaxGradLabels];
+#pragma unroll
+    for (int l = 0; l < kMaxGradLabels; ++l) accK[l] = accW[l] = 0.f;
+    const bool wvalid = y < A.ny;  // warp-uniform (blockDim.x == 32)
+    const int x0 = 4 * (blockIdx.x * 32 + lane);
+    const bool inrow = wvalid && x0 < A.pitch;
+    const int zb = blockIdx.z * A.zchunk;
+    const int ze = min(A.nz, zb + A.zchunk);
+    const size_t rowoff = (size_t)(wvalid ? y : 0) * A.pitch + x0;
+    const bool hasYm = y > 0, hasYp = y < A.ny - 1;
+    const bool dir = A.face == RFA_FACE_DIRICHLET;
+
+    if (wvalid) {
+        float4 lm = make_float4(0, 0, 0, 0), lc = lm, lp = lm;   // lambda at z-1, z, z+1
+        float4 tm = lm, tc = lm, tp = lm;                         // theta
+        float am[4] = {0, 0, 0, 0}, ac[4] = {0, 0, 0, 0}, ap[4] = {0, 0, 0, 0};
+        float bc[4] = {0, 0, 0, 0}, bp[4] = {0, 0, 0, 0}, bdum[4];
+        if (inrow) {
+            if (zb > 0) {
+                const size_t i = (size_t)(zb - 1) * A.plane + rowoff;
+                lm = ld4g(A.lam_in + i);
+                tm = ld4g(A.th + i);
+                adj_load_ab<PP>(A.ab, i, am, bdum);
+            }
+            const size_t i = (size_t)zb * A.plane + rowoff;
+            lc = ld4g(A.lam_in + i);
+            tc = ld4g(A.th + i);
+            adj_load_ab<PP>(A.ab, i, ac, bc);
+        }
+        for (int z = zb; z < ze; ++z) {
+            const size_t i = (size_t)z * A.plane + rowoff;
+            const bool hasZp = z + 1 < A.nz, hasZm = z > 0;
+            float4 lym = make_float4(0, 0, 0, 0), lyp = lym, tym = lym, typ = lym;
+            float aym[4] = {0, 0, 0, 0}, ayp[4] = {0, 0, 0, 0};
+            uint32_t lab4 = 0;
+            float4 Lc = make_float4(0, 0, 0, 0);
+            if (inrow) {
+                if (hasZp) {
+                    lp = ld4g(A.lam_in + i + A.plane);
+                    tp = ld4g(A.th + i + A.plane);
+                    adj_load_ab<PP>(A.ab, i + A.plane, ap, bp);
+                } else {
+                    lp = make_float4(0, 0, 0, 0);
+                    tp = lp;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) ap[q] = bp[q] = 0.f;
+                }
+                if (hasYm) {
+                    lym = ld4g(A.lam_in + i - A.pitch);
+                    tym = ld4g(A.th + i - A.pitch);
+                    adj_load_ab<PP>(A.ab, i - A.pitch, aym, bdum);
+                }
+                if (hasYp) {
+                    lyp = ld4g(A.lam_in + i + A.pitch);
+                    typ = ld4g(A.th + i + A.pitch);
+                    adj_load_ab<PP>(A.ab, i + A.pitch, ayp, bdum);
+                }
+                lab4 = __ldg(reinterpret_cast<const uint32_t *>(A.label + i));
+                Lc = ld4g(A.Lam + i);
+            }
+            const float lcv[4] = {lc.x, lc.y, lc.z, lc.w}, tcv[4] = {tc.x, tc.y, tc.z, tc.w};
+            const float lmv[4] = {lm.x, lm.y, lm.z, lm.w}, tmv[4] = {tm.x, tm.y, tm.z, tm.w};
+            const float lpv[4] = {lp.x, lp.y, lp.z, lp.w}, tpv[4] = {tp.x, tp.y, tp.z, tp.w};
+            const float lymv[4] = {lym.x, lym.y, lym.z, lym.w}, tymv[4] = {tym.x, tym.y, tym.z, tym.w};
+            const float lypv[4] = {lyp.x, lyp.y, lyp.z, lyp.w}, typv[4] = {typ.x, typ.y, typ.z, typ.w};
+            float mu[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) mu[q] = ac[q] * lcv[q];
+            // x neighbours across quads: mu and theta
+            float muL = __shfl_up_sync(FULL, mu[3], 1), muR = __shfl_down_sync(FULL, mu[0], 1);
+            float thL = __shfl_up_sync(FULL, tcv[3], 1), thR = __shfl_down_sync(FULL, tcv[0], 1);
+            if (inrow && lane == 0 && x0 > 0) {
+                float a1[1], b1[1];
+                (void)b1;
+                // scalar neighbour at x0 - 1 (coefficient and lambda)
+                if (PP == RFA_PARAM_BF16) {
+                    uint32_t w = __ldg((const uint32_t *)A.ab + i - 1);
+                    a1[0] = bf16_to_float(w & 0xffffu);
+                } else if (PP == RFA_PARAM_F32) {
+                    a1[0] = __ldg((const float2 *)A.ab + i - 1).x;
+                } else {
+                    a1[0] = (float)__ldg((const double2 *)A.ab + i - 1).x;
+                }
+                muL = a1[0] * __ldg(A.lam_in + i - 1);
+                thL = __ldg(A.th + i - 1);
+            }
+            if (inrow && lane == 31 && x0 + 4 < A.nx) {
+                float a1;
+                if (PP == RFA_PARAM_BF16) {
+                    uint32_t w = __ldg((const uint32_t *)A.ab + i + 4);
+                    a1 = bf16_to_float(w & 0xffffu);
+                } else if (PP == RFA_PARAM_F32) {
+                    a1 = __ldg((const float2 *)A.ab + i + 4).x;
+                } else {
+                    a1 = (float)__ldg((const double2 *)A.ab + i + 4).x;
+                }
+                muR = a1 * __ldg(A.lam_in + i + 4);
+                thR = __ldg(A.th + i + 4);
+            }
+            if (inrow) {
+                float lo_[4], Lo_[4];
+                const float Lcv[4] = {Lc.x, Lc.y, Lc.z, Lc.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int x = x0 + q;
+                    const float l = lcv[q], t = tcv[q], m = mu[q];
+                    const float muxm = q == 0 ? muL : mu[q - 1], muxp = q == 3 ? muR : mu[q + 1];
+                    const float txm = q == 0 ? thL : tcv[q - 1], txp = q == 3 ? thR : tcv[q + 1];
+                    float smu = 0.f, lt = 0.f;
+                    if (x > 0) { smu += muxm - m; lt += txm - t; }
+                    if (x + 1 < A.nx) { smu += muxp - m; lt += txp - t; }
+                    if (hasYm) { smu += aym[q] * lymv[q] - m; lt += tymv[q] - t; }
+                    if (hasYp) { smu += ayp[q] * lypv[q] - m; lt += typv[q] - t; }
+                    if (hasZm) { smu += am[q] * lmv[q] - m; lt += tmv[q] - t; }
+                    if (hasZp) { smu += ap[q] * lpv[q] - m; lt += tpv[q] - t; }
+                    const bool valid = x < A.nx;
+                    lo_[q] = valid ? l + smu - bc[q] * l : 0.f;
+                    Lo_[q] = valid ? Lcv[q] + l : 0.f;
+                    const int lab = (lab4 >> (8 * q)) & 0xff;
+                    const bool face_vox = dir && (x == 0 || x == A.nx - 1 || y == 0 || y == A.ny - 1 ||
+                                                  z == 0 || z == A.nz - 1);
+                    // fixed labels carry fk = gw = 0; Dirichlet faces are excluded here
+                    const bool free_vox = valid && !face_vox;
+                    const float vk = free_vox ? l * lt : 0.f, vw = free_vox ? l * t : 0.f;
+#pragma unroll
+                    for (int L = 0; L < kMaxGradLabels; ++L) {
+                        accK[L] += lab == L ? vk : 0.f;
+                        accW[L] += lab == L ? vw : 0.f;
+                    }
+                }
+                *reinterpret_cast<float4 *>(A.lam_out + i) = make_float4(lo_[0], lo_[1], lo_[2], lo_[3]);
+                *reinterpret_cast<float4 *>(A.Lam + i) = make_float4(Lo_[0], Lo_[1], Lo_[2], Lo_[3]);
+            }
+            lm = lc; lc = lp; tm = tc; tc = tp;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                am[q] = ac[q];
+                ac[q] = ap[q];
+                bc[q] = bp[q];
+            }
+        }
+    }
+    // block reduction of the per-label sums, then one FP64 atomic per label and block
+    __shared__ float sK[8][kMaxGradLabels], sW[8][kMaxGradLabels];
+    const int w = threadIdx.y;
+#pragma unroll
+    for (int L = 0; L < kMaxGradLabels; ++L) {
+        float k = accK[L] * A.fk[L], v = accW[L] * A.gw[L];
+        for (int o = 16; o > 0; o >>= 1) {
+            k += __shfl_xor_sync(FULL, k, o);
+            v += __shfl_xor_sync(FULL, v, o);
+        }
+        if (lane == 0) {
+            sK[w][L] = k;
+            sW[w][L] = v;
+        }
+    }
+    __syncthreads();
+    if (w == 0 && lane < kMaxGradLabels) {
+        double k = 0.0, v = 0.0;
+        for (int j = 0; j < (int)blockDim.y; ++j) {
+            k += sK[j][lane];
+            v += sW[j][lane];
+        }
+        if (k != 0.0) atomicAdd(&A.acc[lane], k);
+        if (v != 0.0) atomicAdd(&A.acc[kMaxGradLabels + lane], -v);
+    }
+}
+
+// padded lambda^N from the caller's dense dL/dT; zero Lambda
+__global__ void k_adj_init(const float *dLdT, float *lam, float *Lam, int nx, int ny, int nz, int pitch)
+{
+    size_t nvp = (size_t)pitch * ny * nz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nvp; i += (size_t)gridDim.x * blockDim.x) {
+        int x = (int)(i % pitch);
+        size_t r = i / pitch;
+        lam[i] = x < nx ? dLdT[r * nx + x] : 0.f;
+        Lam[i] = 0.f;
+    }
+}
+
+__device__ double adj_needle_distance(const NeedleGeom &g, double px, double py, double pz, double q[3])
+{
+    double best = 1e300;
+    for (int k = 0; k < g.nseg; ++k) {
+        const Segment &sg = g.seg[k];
+        double ux = sg.p1[0] - sg.p0[0], uy = sg.p1[1] - sg.p0[1], uz = sg.p1[2] - sg.p0[2];
+        double wx = px - sg.p0[0], wy = py - sg.p0[1], wz = pz - sg.p0[2];
+        double uu = ux * ux + uy * uy + uz * uz;
+        double t = uu > 0.0 ? (wx * ux + wy * uy + wz * uz) / uu : 0.0;
+        t = fmin(fmax(t, 0.0), 1.0);
+        double cx = sg.p0[0] + t * ux, cy = sg.p0[1] + t * uy, cz = sg.p0[2] + t * uz;
+        double d2 = (px - cx) * (px - cx) + (py - cy) * (py - cy) + (pz - cz) * (pz - cz);
+        if (d2 < best) {
+            best = d2;
+            q[0] = cx;
+            q[1] = cy;
+            q[2] = cz;
+        }
+    }
+    return sqrt(best);
+}
+
+// partial sums over free voxels: [W, dW(3), sum Lam c w, sum Lam c dw(3)]
+__global__ void k_src_grad_partials(NeedleGeom geom, const float *Lam, const uint8_t *label,
+                                    const LabelCoef *tab, int nx, int ny, int nz, int pitch, double h,
+                                    double dt, int face, double *part)
+{
+    size_t nvp = (size_t)pitch * ny * nz;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nvp; i += (size_t)gridDim.x * blockDim.x) {
+        int x = (int)(i % pitch);
+        if (x >= nx) continue;
+        size_t r = i / pitch;
+        int y = (int)(r % ny), z = (int)(r / ny);
+        bool face_vox = (x == 0 || y == 0 || z == 0 || x == nx - 1 || y == ny - 1 || z == nz - 1);
+        const LabelCoef t = tab[label[i]];
+        if (t.fixed || (face == RFA_FACE_DIRICHLET && face_vox)) continue;
+        double p[3] = {x * h, y * h, z * h}, q[3] = {0, 0, 0};
+        double d = adj_needle_distance(geom, p[0], p[1], p[2], q);
+        double rr = fmax(d, geom.r0);
+        double w = 1.0 / (rr * rr * rr * rr);
+        double dw[3] = {0, 0, 0};
+        if (d > geom.r0) {
+            double d6 = d * d * d * d * d * d;
+            for (int c = 0; c < 3; ++c) dw[c] = 4.0 * (p[c] - q[c]) / d6;
+        }
+        double cL = (double)Lam[i] * geom.P * dt / (h * h * h * t.rho * t.c);
+        acc[0] += w;
+        for (int c = 0; c < 3; ++c) acc[1 + c] += dw[c];
+        acc[4] += cL * w;
+        for (int c = 0; c < 3; ++c) acc[5 + c] += cL * dw[c];
+    }
+    __shared__ double sh[8][8];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = 0; k < 8; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[wid][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        double v = 0.0;
+        for (int j = 0; j < (int)(blockDim.x >> 5); ++j) v += sh[j][threadIdx.x];
+        part[(size_t)blockIdx.x * 8 + threadIdx.x] = v;
+    }
+}
+
+__global__ void k_src_grad_final(const double *part, int nblocks, double *out)
+{
+    if (threadIdx.x < 8) {
+        double v = 0.0;
+        for (int b = 0; b < nblocks; ++b) v += part[(size_t)b * 8 + threadIdx.x];
+        out[threadIdx.x] = v;
+    }
+}
+
+cudaError_t launch_adjoint_step(rfa_grid *g, const AdjArgs &A0, const float *lam_in, float *lam_out,
+                                const float *th)
+{
+    AdjArgs A = A0;
+    A.lam_in = lam_in;
+    A.lam_out = lam_out;
+    A.th = th;
+    dim3 blk(32, 8);
+    dim3 grd = plain_grid_dims(g, A.zchunk);
+    if (g->pp == RFA_PARAM_BF16) k_adjoint_step<RFA_PARAM_BF16><<<grd, blk, 0, g->stream>>>(A);
+    else if (g->pp == RFA_PARAM_F32) k_adjoint_step<RFA_PARAM_F32><<<grd, blk, 0, g->stream>>>(A);
+    else k_adjoint_step<RFA_PARAM_F64><<<grd, blk, 0, g->stream>>>(A);
+    return cudaGetLastError();
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf()
+    {
+        if (p) cudaFree(p);
+    }
+};
+
+}  // namespace
+
+rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads)
+{
+    if (g->sp == RFA_STATE_F64) {
+        set_error("rfa_backward supports FP32 and compensated FP32 states");
+        return RFA_E_UNSUPPORTED;
+    }
+    if (!g->have_tissue || !g->rec.valid || g->rec.nsteps != g->steps || g->rec.ck_hi.empty()) {
+        set_error("rfa_backward needs every step since rfa_set_tissue recorded (rfa_step(..., 1))");
+        return RFA_E_STATE;
+    }
+    if (g->n_labels > kMaxGradLabels) {
+        set_error("rfa_backward supports at most 8 labels");
+        return RFA_E_UNSUPPORTED;
+    }
+    const int64_t N = g->rec.nsteps, seg = g->rec.seg;
+    const size_t nvp = g->nvp;
+    DevBuf segbuf, lob, lam, Lam, acc, part;
+    const size_t seg_bytes = (size_t)seg * nvp * 4;
+    if (cudaMalloc(&segbuf.p, seg_bytes) != cudaSuccess || cudaMalloc(&lob.p, 2 * nvp * 4) != cudaSuccess ||
+        cudaMalloc(&lam.p, 2 * nvp * 4) != cudaSuccess || cudaMalloc(&Lam.p, nvp * 4) != cudaSuccess ||
+        cudaMalloc(&acc.p, 64 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&part.p, (size_t)kReduceBlocks * 8 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("backward workspace allocation failed");
+        return RFA_E_OOM;
+    }
+    float *sb = (float *)segbuf.p, *lo2 = (float *)lob.p, *lam2 = (float *)lam.p;
+    double *accd = (double *)acc.p;
+    RFA_CUDA(cudaMemsetAsync(accd, 0, 64 * sizeof(double), g->stream));
+    k_adj_init<<<148 * 8, 256, 0, g->stream>>>(dLdT, lam2, (float *)Lam.p, g->nx, g->ny, g->nz, g->pitch);
+    RFA_CUDA(cudaGetLastError());
+
+    AdjArgs A{};
+    A.Lam = (float *)Lam.p;
+    A.ab = g->ab;
+    A.label = g->label;
+    A.tab = g->d_table;
+    A.nx = g->nx;
+    A.ny = g->ny;
+    A.nz = g->nz;
+    A.pitch = g->pitch;
+    A.plane = g->plane;
+    A.zchunk = g->nz < 64 ? g->nz : 32;
+    A.face = g->face;
+    A.acc = accd;
+    for (int l = 0; l < kMaxGradLabels; ++l) {
+        A.fk[l] = A.gw[l] = 0.f;
+        if (l < g->n_labels && !g->table[l].fixed) {
+            const rfa_tissue &t = g->table[l];
+            A.fk[l] = (float)((1.0 / (t.rho * t.c)) * g->dt / (g->h * g->h));
+            A.gw[l] = (float)((t.rho_b * t.c_b / (t.rho * t.c)) * g->dt);
+        }
+    }
+    int lcur = 0;  // lambda ping-pong index holding lambda^{n+1}
+    const int64_t nck = (int64_t)g->rec.ck_hi.size();
+    for (int64_t c = nck - 1; c >= 0; --c) {
+        const int64_t s0 = c * seg, s1 = (s0 + seg < N) ? s0 + seg : N;
+        // recompute theta^{s0} .. theta^{s1-1}; hi parts land in the segment buffer
+        RFA_CUDA(cudaMemcpyAsync(sb, g->rec.ck_hi[c], nvp * 4, cudaMemcpyDeviceToDevice, g->stream));
+        if (g->sp == RFA_STATE_F32C)
+            RFA_CUDA(cudaMemcpyAsync(lo2, g->rec.ck_lo[c], nvp * 4, cudaMemcpyDeviceToDevice, g->stream));
+        for (int64_t st = s0; st + 1 < s1; ++st) {
+            const int j = (int)(st - s0);
+            const float *lin = g->sp == RFA_STATE_F32C ? lo2 + (size_t)(j & 1) * nvp : nullptr;
+            float *lout = g->sp == RFA_STATE_F32C ? lo2 + (size_t)((j + 1) & 1) * nvp : nullptr;
+            RFA_CUDA(launch_step_plain(g, sb + (size_t)j * nvp, lin, sb + (size_t)(j + 1) * nvp, lout, false,
+                                       false, false));
+        }
+        for (int64_t st = s1 - 1; st >= s0; --st) {
+            const float *th = sb + (size_t)(st - s0) * nvp;
+            RFA_CUDA(launch_adjoint_step(g, A, lam2 + (size_t)lcur * nvp, lam2 + (size_t)(lcur ^ 1) * nvp, th));
+            lcur ^= 1;
+        }
+    }
+    // source contractions
+    k_src_grad_partials<<<kReduceBlocks, 256, 0, g->stream>>>(g->geom, (const float *)Lam.p, g->label,
+                                                               g->d_table, g->nx, g->ny, g->nz, g->pitch,
+                                                               g->h, g->dt, g->face, (double *)part.p);
+    k_src_grad_final<<<1, 32, 0, g->stream>>>((const double *)part.p, kReduceBlocks, accd + 32);
+    RFA_CUDA(cudaGetLastError());
+    double host[64];
+    RFA_CUDA(cudaMemcpyAsync(host, accd, sizeof host, cudaMemcpyDeviceToHost, g->stream));
+    RFA_CUDA(cudaStreamSynchronize(g->stream));
+    const double W = host[32], A1 = host[36];
+    const double *dW = host + 33, *A2 = host + 37;
+    const double P = g->geom.P;
+    grads[0] = (W > 0.0 && P > 0.0) ? A1 / (P * W) : 0.0;
+    for (int c = 0; c < 3; ++c) grads[1 + c] = W > 0.0 ? A2[c] / W - dW[c] * A1 / (W * W) : 0.0;
+    for (int l = 0; l < g->n_labels; ++l) {
+        grads[4 + l] = host[l];
+        grads[4 + g->n_labels + l] = host[kMaxGradLabels + l];
+    }
+    return RFA_OK;
 }
 
 }  // namespace rfa
