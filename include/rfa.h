@@ -234,14 +234,25 @@ rfa_status rfa_autotune(rfa_grid *g, const char *cache_path);
 
 /*
  * Batched stepping of several grids in one persistent launch per call
- * (independent needle configurations on grids of uneven size).  Members must
- * be F32C grids with tissue and needle set, all on the same stream; they stay
- * owned by the caller and must outlive the batch.  rfa_batch_step advances
- * every member by nsteps, capturing the launch in a CUDA graph.
+ * (independent needle configurations on grids of uneven size; the paper runs
+ * one configuration at a time).  Members must be F32C grids with BF16
+ * coefficients and tissue set, all on the same stream and with the same damage
+ * setting; they stay owned by the caller and must outlive the batch.
+ * rfa_batch_step advances every member by nsteps: whole blocks of tb_depth steps
+ * in one cooperative persistent launch (replayed from a CUDA graph captured per
+ * block count), the remainder as one-step launches.  States are bit-identical
+ * to stepping each member alone.  Device-side faults of the batched launch are
+ * reported by rfa_synchronize on the first member.
  */
 rfa_status rfa_batch_create(rfa_grid *const *members, int n, rfa_batch **out);
 rfa_status rfa_batch_step(rfa_batch *b, int64_t nsteps);
 rfa_status rfa_batch_destroy(rfa_batch *b);
+/* Pick the batch's steps-per-block depth and tile variant by timing every
+ * candidate on snapshots of all members' states (restored afterwards);
+ * cache_path (may be NULL) is a text file of cached choices. */
+rfa_status rfa_batch_autotune(rfa_batch *b, const char *cache_path);
+/* Current batch schedule; uses_graph = 1 if launches replay a CUDA graph. */
+rfa_status rfa_batch_get_schedule(rfa_batch *b, int *tb_depth, int *tile_variant, int *uses_graph);
 
 /* Wait for the grid's stream and report deferred device errors. */
 rfa_status rfa_synchronize(rfa_grid *g);

@@ -32,7 +32,8 @@ EXPORTED = ("rfa_create_grid", "rfa_destroy_grid", "rfa_set_tissue", "rfa_place_
             "rfa_necrosis_mask", "rfa_backward", "rfa_get_state", "rfa_set_state",
             "rfa_set_schedule", "rfa_get_schedule", "rfa_autotune", "rfa_batch_create",
             "rfa_batch_step", "rfa_batch_destroy", "rfa_synchronize", "rfa_steps_done",
-            "rfa_last_error", "rfa_necrosis_reduce_noalloc")
+            "rfa_last_error", "rfa_necrosis_reduce_noalloc", "rfa_batch_autotune",
+            "rfa_batch_get_schedule")
 
 
 class RfaError(RuntimeError):
@@ -91,6 +92,8 @@ def lib():
         "rfa_steps_done": [P],
         "rfa_last_error": [],
         "rfa_necrosis_reduce_noalloc": [P, D, P],
+        "rfa_batch_autotune": [P, ctypes.c_char_p],
+        "rfa_batch_get_schedule": [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -265,6 +268,18 @@ def rfa_batch_step(b, nsteps: int):
 
 def rfa_batch_destroy(b):
     _check(lib().rfa_batch_destroy(b), "rfa_batch_destroy")
+
+
+def rfa_batch_autotune(b, cache_path: Optional[str] = None):
+    _check(lib().rfa_batch_autotune(b, None if cache_path is None else cache_path.encode()),
+           "rfa_batch_autotune")
+
+
+def rfa_batch_get_schedule(b):
+    d, v, gr = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().rfa_batch_get_schedule(b, ctypes.byref(d), ctypes.byref(v), ctypes.byref(gr)),
+           "rfa_batch_get_schedule")
+    return d.value, v.value, bool(gr.value)
 
 
 def rfa_synchronize(g):

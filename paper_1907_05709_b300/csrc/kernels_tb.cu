@@ -61,20 +61,6 @@ struct Cfg {
     static_assert(TY > 0 && M <= TB_HX && SMEM <= 227 * 1024, "bad tile");
 };
 
-struct TBArgs {
-    float *hi_out, *lo_out;
-    uint8_t *latch;
-    double *omega;
-    float *omega_c;
-    unsigned *status;
-    int nx, ny, nz, pitch;
-    int xt, yt, zc;  // tiles in x and y, z chunks; work items = xt * yt * zc
-    size_t plane;
-    float thr;
-    float c0, c1, TK0;
-    int fold;
-};
-
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -123,66 +109,68 @@ __device__ __forceinline__ float4 ld4(const float *sm, int off)
     return *reinterpret_cast<const float4 *>(sm + off);
 }
 
-template <int M, int EY, bool DMG, bool FOLD>
-__global__ void __launch_bounds__(Cfg<M, EY>::THREADS, Cfg<M, EY>::MINB)
-    k_step_tb(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
-              const __grid_constant__ CUtensorMap tm_ab, const __grid_constant__ CUtensorMap tm_s,
-              const TBArgs A)
+// per-CTA pipeline state, kept across work items and time blocks
+struct TBPipe {
+    float *sm;
+    uint32_t sm_base, bar_base;
+    long long nload;  // stage-0 planes loaded so far (ring slot and mbarrier phase)
+};
+
+template <int M, int EY>
+__device__ __forceinline__ void tb_item_geom(const TBTile &T, int item, int &X0, int &Y0, int &zb, int &ze)
+{
+    const int tx = item % T.xt, r = item / T.xt;
+    const int ty = r % T.yt, zi = r / T.yt;
+    X0 = tx * TB_TX;
+    Y0 = ty * Cfg<M, EY>::TY;
+    zb = (int)((long long)zi * T.nz / T.zc);
+    ze = (int)((long long)(zi + 1) * T.nz / T.zc);
+}
+
+// stage-0 plane z of the tile at (X0, Y0) into the ring slot of load number n
+template <int M, int EY>
+__device__ __forceinline__ void tb_issue(const TBPipe &P, long long n, const TBTile &T, int X0, int Y0, int z)
+{
+    using C = Cfg<M, EY>;
+    const int j = (int)(n % C::S0);
+    const uint32_t dst = P.sm_base + 4u * (uint32_t)(j * C::SLOT0);
+    const uint32_t bar = P.bar_base + 8u * j;
+    mbar_expect_tx(bar, (uint32_t)(C::SLOT0 * 4));
+    tma_load_3d(dst, &T.maps[0], X0 - TB_HX, Y0 - M, z, bar);
+    tma_load_3d(dst + 4u * C::PLANE, &T.maps[1], X0 - TB_HX, Y0 - M, z, bar);
+    tma_load_3d(dst + 8u * C::PLANE, &T.maps[2], X0 - TB_HX, Y0 - M, z, bar);
+    tma_load_3d(dst + 12u * C::PLANE, &T.maps[3], X0 - TB_HX, Y0 - M, z, bar);
+}
+
+// Advance work items first, first + stride, ... < nitems by M steps.
+// get(item, local) returns the item's TBTile and sets its index in that tile.
+// Returns false if a wait timed out (kStatusTimeout recorded, CTA must leave).
+template <int M, int EY, bool DMG, bool FOLD, class Get>
+__device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &get, unsigned *status,
+                       bool &bad)
 {
     using C = Cfg<M, EY>;
     constexpr int S0 = C::S0, PLANE = C::PLANE;
-    extern __shared__ __align__(128) float sm[];
-    const uint32_t sm_base = smem_u32(sm);
-    if (sm_base & 127u) {  // TMA destinations need 128-byte alignment
-        if (threadIdx.x == 0) atomicOr(A.status, kStatusTimeout);
-        return;
-    }
-    const uint32_t bar_base = sm_base + 4u * C::BAR_OFF;
+    float *sm = P.sm;
+    const uint32_t bar_base = P.bar_base;
     const int tid = threadIdx.x;
     const int qx = tid % TB_QX, yl = tid / TB_QX;   // quad column and row in the tile
     const int xl0 = 4 * qx;                          // first tile column of the quad
     const int id = yl * TB_EX + xl0;                 // float offset of the quad in a plane
-    const int nitems = A.xt * A.yt * A.zc;
 
-    if (tid == 0) {
-        for (int j = 0; j < S0; ++j) mbar_init(bar_base + 8u * j, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-
-    // work item -> tile origin and z range (balanced z chunks)
-    auto item_geom = [&](int item, int &X0, int &Y0, int &zb, int &ze) {
-        const int tx = item % A.xt, r = item / A.xt;
-        const int ty = r % A.yt, zi = r / A.yt;
-        X0 = tx * TB_TX;
-        Y0 = ty * C::TY;
-        zb = (int)((long long)zi * A.nz / A.zc);
-        ze = (int)((long long)(zi + 1) * A.nz / A.zc);
-    };
-    // stage-0 plane z of the tile at (X0, Y0) into the ring slot of load number n
-    auto issue = [&](long long n, int X0, int Y0, int z) {
-        const int j = (int)(n % S0);
-        const uint32_t dst = sm_base + 4u * (uint32_t)(j * C::SLOT0);
-        const uint32_t bar = bar_base + 8u * j;
-        mbar_expect_tx(bar, (uint32_t)(C::SLOT0 * 4));
-        tma_load_3d(dst, &tm_hi, X0 - TB_HX, Y0 - M, z, bar);
-        tma_load_3d(dst + 4u * PLANE, &tm_lo, X0 - TB_HX, Y0 - M, z, bar);
-        tma_load_3d(dst + 8u * PLANE, &tm_ab, X0 - TB_HX, Y0 - M, z, bar);
-        tma_load_3d(dst + 12u * PLANE, &tm_s, X0 - TB_HX, Y0 - M, z, bar);
-    };
-
-    long long nload = 0;  // stage-0 planes loaded by this CTA so far (ring slot / phase counter)
-    int item = blockIdx.x;
+    int item = first;
     if (item < nitems && tid == 0) {
+        int local;
+        const TBTile &T = get(item, local);
         int X0, Y0, zb, ze;
-        item_geom(item, X0, Y0, zb, ze);
-        issue(0, X0, Y0, zb - M);
+        tb_item_geom<M, EY>(T, local, X0, Y0, zb, ze);
+        tb_issue<M, EY>(P, P.nload, T, X0, Y0, zb - M);
     }
-    bool bad = false;
-    for (; item < nitems; item += gridDim.x) {
+    for (; item < nitems; item += stride) {
+        int local;
+        const TBTile &A = get(item, local);
         int X0, Y0, zb, ze;
-        item_geom(item, X0, Y0, zb, ze);
+        tb_item_geom<M, EY>(A, local, X0, Y0, zb, ze);
         const int L = ze - zb + 2 * M;   // stage-0 planes zb-M .. ze+M-1
         const int xg0 = X0 - TB_HX + xl0;
         const int yg = Y0 - M + yl;
@@ -209,15 +197,17 @@ __global__ void __launch_bounds__(Cfg<M, EY>::THREADS, Cfg<M, EY>::MINB)
             }
         int s3_cur = 0;  // stage-ring slot of stage-0 plane p0 (it % 3)
 
-        for (int it = 0; it < L; ++it, ++nload) {
+        for (int it = 0; it < L; ++it, ++P.nload) {
             const int p0 = zb - M + it;
             if (tid == 0) {
                 if (it + 1 < L) {
-                    issue(nload + 1, X0, Y0, p0 + 1);
-                } else if (item + (int)gridDim.x < nitems) {  // first plane of the next item
+                    tb_issue<M, EY>(P, P.nload + 1, A, X0, Y0, p0 + 1);
+                } else if (item + stride < nitems) {  // first plane of the next item
+                    int local1;
+                    const TBTile &T1 = get(item + stride, local1);
                     int X1, Y1, zb1, ze1;
-                    item_geom(item + gridDim.x, X1, Y1, zb1, ze1);
-                    issue(nload + 1, X1, Y1, zb1 - M);
+                    tb_item_geom<M, EY>(T1, local1, X1, Y1, zb1, ze1);
+                    tb_issue<M, EY>(P, P.nload + 1, T1, X1, Y1, zb1 - M);
                 }
             }
             // output-stage operands of plane p0 - M, loaded early to hide their latency
@@ -247,14 +237,14 @@ __global__ void __launch_bounds__(Cfg<M, EY>::THREADS, Cfg<M, EY>::MINB)
                 part[1][j] = 0.f;
                 mx[1][j] = -3.0e38f;
             }
-            const int s0_cur = (int)(nload % S0);
-            const bool ok = mbar_wait(bar_base + 8u * s0_cur, (uint32_t)((nload / S0) & 1));
+            const int s0_cur = (int)(P.nload % S0);
+            const bool ok = mbar_wait(bar_base + 8u * s0_cur, (uint32_t)((P.nload / S0) & 1));
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) {
-                    atomicOr(A.status, kStatusTimeout);
-                    mbar_wait(bar_base + 8u * ((nload + 1) % S0), (uint32_t)(((nload + 1) / S0) & 1));
+                    atomicOr(status, kStatusTimeout);
+                    mbar_wait(bar_base + 8u * ((P.nload + 1) % S0), (uint32_t)(((P.nload + 1) / S0) & 1));
                 }
-                return;
+                return false;
             }
 #pragma unroll
             for (int k = 1; k <= M; ++k) {
@@ -355,7 +345,126 @@ __global__ void __launch_bounds__(Cfg<M, EY>::THREADS, Cfg<M, EY>::MINB)
             s3_cur = s3_cur + 1 == 3 ? 0 : s3_cur + 1;
         }
     }
-    if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(A.status, kStatusNonfinite);
+    return true;
+}
+
+template <int M, int EY>
+__device__ __forceinline__ bool tb_setup(TBPipe &P, unsigned *status)
+{
+    using C = Cfg<M, EY>;
+    extern __shared__ __align__(128) float sm[];
+    P.sm = sm;
+    P.sm_base = smem_u32(sm);
+    P.bar_base = P.sm_base + 4u * C::BAR_OFF;
+    P.nload = 0;
+    if (P.sm_base & 127u) {  // TMA destinations need 128-byte alignment
+        if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+        return false;
+    }
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < C::S0; ++j) mbar_init(P.bar_base + 8u * j, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    return true;
+}
+
+struct TBMaps {
+    CUtensorMap m[4];
+};
+
+// one grid, M steps
+template <int M, int EY, bool DMG, bool FOLD>
+__global__ void __launch_bounds__(Cfg<M, EY>::THREADS, Cfg<M, EY>::MINB)
+    k_step_tb(const __grid_constant__ TBMaps maps, const TBTile T0, unsigned *status)
+{
+    TBPipe P;
+    if (!tb_setup<M, EY>(P, status)) return;
+    TBTile T = T0;
+    T.maps = maps.m;
+    auto get = [&](int item, int &local) -> const TBTile & {
+        local = item;
+        return T;
+    };
+    bool bad = false;
+    tb_run<M, EY, DMG, FOLD>(P, blockIdx.x, gridDim.x, T.xt * T.yt * T.zc, get, status, bad);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusNonfinite);
+}
+
+// ------------------------------------------------------------------ batch
+// A batch member: tile descriptors for both ping-pong parities (tile[p] reads
+// state p and writes state p ^ 1), its first work item and its parity at t = 0.
+struct TBMember {
+    TBTile tile[2];
+    int item_begin, cur0;
+};
+
+// Software grid barrier for a cooperative (co-resident) grid; bounded spin.
+// bar[0] counts arrivals, bar[1] is the generation.
+__device__ bool grid_sync(unsigned *bar, unsigned nblocks)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = bar + 1;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+        int ok = 1;
+        if (arrived == nblocks) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vgen == g) {
+                if (clock64() - t0 > (1ll << 32)) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// every member, ntime blocks of M steps, one persistent launch
+template <int M, int EY, bool DMG>
+__global__ void __launch_bounds__(Cfg<M, EY>::THREADS, Cfg<M, EY>::MINB)
+    k_batch_tb(const TBMember *mem, int nmem, int nitems, int ntime, int fold_every, unsigned *gbar,
+               unsigned *status)
+{
+    TBPipe P;
+    if (!tb_setup<M, EY>(P, status)) return;
+    bool bad = false;
+    for (int t = 0; t < ntime; ++t) {
+        auto get = [&](int item, int &local) -> const TBTile & {
+            int lo = 0, hi = nmem - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (mem[mid].item_begin <= item) lo = mid;
+                else hi = mid - 1;
+            }
+            local = item - mem[lo].item_begin;
+            return mem[lo].tile[(mem[lo].cur0 + t) & 1];
+        };
+        const bool fold = DMG && ((t + 1) % fold_every == 0 || t == ntime - 1);
+        const bool ok = fold ? tb_run<M, EY, DMG, true>(P, blockIdx.x, gridDim.x, nitems, get, status, bad)
+                             : tb_run<M, EY, DMG, false>(P, blockIdx.x, gridDim.x, nitems, get, status, bad);
+        if (!ok) break;
+        if (!grid_sync(gbar, gridDim.x)) {
+            if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+            break;
+        }
+        // the next block's TMA (async proxy) reads what other CTAs just stored
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusNonfinite);
 }
 
 // ------------------------------------------------------------------ host side
@@ -390,37 +499,92 @@ bool make_map(CUtensorMap *m, const void *base, CUtensorMapDataType dt, const rf
 
 int variant_ey(int variant) { return variant == 1 ? 32 : 16; }
 
-template <int M, int EY, bool DMG, bool FOLD>
-cudaError_t launch_inst(rfa_grid *g, const CUtensorMap *maps, const TBArgs &A0)
+// tiles and balanced z chunks of one grid: the busiest of `resident` persistent
+// CTAs should stream as few planes as possible (each item costs chunk + 2M planes)
+template <int M, int EY>
+void tile_plan(const rfa_grid *g, int resident, int max_chunk, TBTile &T)
 {
     using C = Cfg<M, EY>;
-    cudaError_t e = cudaFuncSetAttribute(k_step_tb<M, EY, DMG, FOLD>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-    if (e != cudaSuccess) return e;
-    TBArgs A = A0;
-    A.xt = (g->nx + TB_TX - 1) / TB_TX;
-    A.yt = (g->ny + C::TY - 1) / C::TY;
-    // persistent CTAs (all resident at once) walk the (tile, z-chunk) items; pick
-    // the number of z chunks that minimises the busiest CTA's plane count
-    const int resident = 148 * C::MINB;
-    const long long tiles = (long long)A.xt * A.yt;
+    T.xt = (g->nx + TB_TX - 1) / TB_TX;
+    T.yt = (g->ny + C::TY - 1) / C::TY;
+    const long long tiles = (long long)T.xt * T.yt;
     int best_zc = 1;
     double best = 1e300;
     for (int zc = 1; zc <= g->nz; ++zc) {
         const long long items = tiles * zc;
         const long long per_cta = (items + resident - 1) / resident;
         const double cost = (double)per_cta * ((double)g->nz / zc + 2.0 * M);
-        if (cost < best * 0.999) {
+        if ((double)g->nz / zc <= max_chunk && cost < best * 0.999) {
             best = cost;
             best_zc = zc;
         }
         if ((double)g->nz / zc < 2.0 * M) break;
     }
-    A.zc = best_zc;
-    const long long items = tiles * A.zc;
+    T.zc = best_zc;
+}
+
+void fill_tile(const rfa_grid *g, int parity, TBTile &T)
+{
+    T.maps = nullptr;
+    T.hi_out = (float *)g->th[parity ^ 1];
+    T.lo_out = (float *)g->lo[parity ^ 1];
+    T.latch = g->latch;
+    T.omega = g->omega;
+    T.omega_c = g->omega_c;
+    T.nx = g->nx;
+    T.ny = g->ny;
+    T.nz = g->nz;
+    T.pitch = g->pitch;
+    T.plane = g->plane;
+    T.thr = (float)(g->T_thr - g->T_a);
+    DamageConst dc = damage_consts(g);
+    T.c0 = dc.c0;
+    T.c1 = dc.c1;
+    T.TK0 = dc.TK0;
+}
+
+template <int M, int EY, bool DMG, bool FOLD>
+cudaError_t launch_inst(rfa_grid *g, const TBMaps &maps, TBTile T)
+{
+    using C = Cfg<M, EY>;
+    cudaError_t e = cudaFuncSetAttribute(k_step_tb<M, EY, DMG, FOLD>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    const int resident = 148 * C::MINB;
+    tile_plan<M, EY>(g, resident, 1 << 30, T);
+    const long long items = (long long)T.xt * T.yt * T.zc;
     const unsigned grid = (unsigned)(items < resident ? items : resident);
-    k_step_tb<M, EY, DMG, FOLD><<<grid, C::THREADS, C::SMEM, g->stream>>>(maps[0], maps[1], maps[2], maps[3], A);
+    k_step_tb<M, EY, DMG, FOLD><<<grid, C::THREADS, C::SMEM, g->stream>>>(maps, T, g->status);
     return cudaGetLastError();
+}
+
+template <int M, int EY, bool DMG>
+cudaError_t launch_batch_inst(const TBMember *mem, int nmem, int nitems, int ntime, int fold_every,
+                              unsigned *gbar, unsigned *status, cudaStream_t stream)
+{
+    using C = Cfg<M, EY>;
+    cudaError_t e = cudaFuncSetAttribute(k_batch_tb<M, EY, DMG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         C::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_tb<M, EY, DMG>, C::THREADS, C::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = nsm * per_sm < nitems ? nsm * per_sm : nitems;
+    // cooperative launch: every CTA is resident at once, which the grid barrier needs
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)C::THREADS);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batch_tb<M, EY, DMG>, mem, nmem, nitems, ntime, fold_every, gbar, status);
 }
 
 // tensor maps per (grid, input buffers, tile height); erased when the grid is destroyed
@@ -455,55 +619,104 @@ void tb_forget_maps(const rfa_grid *g)
     }
 }
 
+bool tb_make_maps(const rfa_grid *g, int variant, const void *th_in, const void *lo_in, CUtensorMap out[4])
+{
+    const int ey = variant_ey(variant);
+    auto &c = map_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto key = std::make_tuple((const rfa_grid *)g, th_in, lo_in, ey);
+    auto it = c.m.find(key);
+    if (it == c.m.end()) {
+        std::array<CUtensorMap, 4> maps;
+        if (!make_map(&maps[0], th_in, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, g, ey) ||
+            !make_map(&maps[1], lo_in, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, g, ey) ||
+            !make_map(&maps[2], g->ab, CU_TENSOR_MAP_DATA_TYPE_UINT32, g, ey) ||
+            !make_map(&maps[3], g->s, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, g, ey))
+            return false;
+        it = c.m.emplace(key, maps).first;
+    }
+    for (int k = 0; k < 4; ++k) out[k] = it->second[k];
+    return true;
+}
+
 cudaError_t launch_step_tb(rfa_grid *g, int depth, int variant, const void *th_in, const void *lo_in,
                            void *th_out, void *lo_out, bool damage, bool fold)
 {
     const int ey = variant_ey(variant);
-    std::array<CUtensorMap, 4> maps;
-    {
-        auto &c = map_cache();
-        std::lock_guard<std::mutex> lk(c.mu);
-        auto key = std::make_tuple((const rfa_grid *)g, th_in, lo_in, ey);
-        auto it = c.m.find(key);
-        if (it == c.m.end()) {
-            if (!make_map(&maps[0], th_in, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, g, ey) ||
-                !make_map(&maps[1], lo_in, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, g, ey) ||
-                !make_map(&maps[2], g->ab, CU_TENSOR_MAP_DATA_TYPE_UINT32, g, ey) ||
-                !make_map(&maps[3], g->s, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, g, ey))
-                return cudaErrorInvalidValue;
-            c.m[key] = maps;
-        } else {
-            maps = it->second;
-        }
-    }
-    TBArgs A;
-    A.hi_out = (float *)th_out;
-    A.lo_out = (float *)lo_out;
-    A.latch = g->latch;
-    A.omega = g->omega;
-    A.omega_c = g->omega_c;
-    A.status = g->status;
-    A.nx = g->nx;
-    A.ny = g->ny;
-    A.nz = g->nz;
-    A.pitch = g->pitch;
-    A.plane = g->plane;
-    A.thr = (float)(g->T_thr - g->T_a);
-    DamageConst dc = damage_consts(g);
-    A.c0 = dc.c0;
-    A.c1 = dc.c1;
-    A.TK0 = dc.TK0;
-    A.fold = fold ? 1 : 0;
+    TBMaps maps;
+    if (!tb_make_maps(g, variant, th_in, lo_in, maps.m)) return cudaErrorInvalidValue;
+    TBTile T;
+    fill_tile(g, g->th[0] == th_in ? 0 : 1, T);
+    T.hi_out = (float *)th_out;
+    T.lo_out = (float *)lo_out;
 #define TB_CASE(MV, EYV)                                                                 \
     if (depth == MV && ey == EYV)                                                        \
-        return !damage ? launch_inst<MV, EYV, false, false>(g, maps.data(), A)          \
-               : fold  ? launch_inst<MV, EYV, true, true>(g, maps.data(), A)            \
-                       : launch_inst<MV, EYV, true, false>(g, maps.data(), A);
+        return !damage ? launch_inst<MV, EYV, false, false>(g, maps, T)                 \
+               : fold  ? launch_inst<MV, EYV, true, true>(g, maps, T)                   \
+                       : launch_inst<MV, EYV, true, false>(g, maps, T);
     TB_CASE(2, 16)
     TB_CASE(3, 16)
     TB_CASE(4, 16)
     TB_CASE(2, 32)
 #undef TB_CASE
+    return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------ batch host side
+// Descriptor of one member for both parities; `maps_dev` receives 8 tensor maps
+// (parity 0 then 1) that the caller copies to device memory at `maps_dev_addr`.
+bool tb_batch_member(const rfa_grid *g, int depth, int variant, int max_chunk, TBMemberHost &out)
+{
+    TBTile T;
+    fill_tile(g, 0, T);
+    const int ey = variant_ey(variant);
+#define PLAN_CASE(MV, EYV) \
+    if (depth == MV && ey == EYV) tile_plan<MV, EYV>(g, 1 << 30, max_chunk, T);
+    PLAN_CASE(2, 16)
+    PLAN_CASE(3, 16)
+    PLAN_CASE(4, 16)
+    PLAN_CASE(2, 32)
+#undef PLAN_CASE
+    for (int p = 0; p < 2; ++p) {
+        if (!tb_make_maps(g, variant, g->th[p], g->lo[p], out.maps + 4 * p)) return false;
+        fill_tile(g, p, out.tile[p]);
+        out.tile[p].xt = T.xt;
+        out.tile[p].yt = T.yt;
+        out.tile[p].zc = T.zc;
+    }
+    out.items = T.xt * T.yt * T.zc;
+    return true;
+}
+
+size_t tb_member_bytes() { return sizeof(TBMember); }
+
+void tb_pack_member(const TBMemberHost &h, const CUtensorMap *maps_dev, int item_begin, int cur0, void *dst)
+{
+    TBMember m;
+    for (int p = 0; p < 2; ++p) {
+        m.tile[p] = h.tile[p];
+        m.tile[p].maps = maps_dev + 4 * p;
+    }
+    m.item_begin = item_begin;
+    m.cur0 = cur0;
+    std::memcpy(dst, &m, sizeof m);
+}
+
+cudaError_t launch_batch_tb(int depth, int variant, bool damage, const void *members_dev, int nmem,
+                            int nitems, int ntime, unsigned *gbar, unsigned *status, cudaStream_t stream)
+{
+    const int ey = variant_ey(variant);
+    const int fold_every = kCarrySteps / depth > 0 ? kCarrySteps / depth : 1;
+    const TBMember *mem = (const TBMember *)members_dev;
+#define BATCH_CASE(MV, EYV)                                                                                    \
+    if (depth == MV && ey == EYV)                                                                              \
+        return damage ? launch_batch_inst<MV, EYV, true>(mem, nmem, nitems, ntime, fold_every, gbar, status, stream) \
+                      : launch_batch_inst<MV, EYV, false>(mem, nmem, nitems, ntime, fold_every, gbar, status, stream);
+    BATCH_CASE(2, 16)
+    BATCH_CASE(3, 16)
+    BATCH_CASE(4, 16)
+    BATCH_CASE(2, 32)
+#undef BATCH_CASE
     return cudaErrorInvalidValue;
 }
 

@@ -17,6 +17,7 @@
 // leaves them unchanged without a branch.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstring>
@@ -186,6 +187,31 @@ bool tb_supported(const rfa_grid *g, int depth, int variant);
 void tb_forget_maps(const rfa_grid *g);
 cudaError_t launch_step_tb(rfa_grid *g, int depth, int variant, const void *th_in,
                            const void *lo_in, void *th_out, void *lo_out, bool damage, bool fold);
+// blocked stepping geometry (kernels_tb.cu): outputs and tiling of one grid;
+// `maps` points at the tensor maps (hi, lo, ab, s) of the input state
+struct TBTile {
+    const CUtensorMap *maps;
+    float *hi_out, *lo_out;
+    uint8_t *latch;
+    double *omega;
+    float *omega_c;
+    int nx, ny, nz, pitch;
+    size_t plane;
+    int xt, yt, zc;  // tiles in x and y, z chunks; work items = xt * yt * zc
+    float thr;
+    float c0, c1, TK0;
+};
+// a batch member on the host: tiles and tensor maps for both ping-pong parities
+struct TBMemberHost {
+    TBTile tile[2];
+    CUtensorMap maps[8];
+    int items = 0;
+};
+bool tb_batch_member(const rfa_grid *g, int depth, int variant, int max_chunk, TBMemberHost &out);
+size_t tb_member_bytes();
+void tb_pack_member(const TBMemberHost &h, const CUtensorMap *maps_dev, int item_begin, int cur0, void *dst);
+cudaError_t launch_batch_tb(int depth, int variant, bool damage, const void *members_dev, int nmem,
+                            int nitems, int ntime, unsigned *gbar, unsigned *status, cudaStream_t stream);
 // reductions and conversions (kernels_reduce.cu)
 cudaError_t launch_necrosis(rfa_grid *g, uint8_t *mask_dense_dev, double width_K,
                             void *result_dev);

@@ -173,26 +173,36 @@ def _point_line_distance(p, a, d):
     return float(np.linalg.norm(w - np.dot(w, d) * d))
 
 
-def paint_labels(nx, ny, nz, h, tumors, vessels, z_chunk: int = 32) -> np.ndarray:
+def paint_labels(nx, ny, nz, h, tumors, vessels, z_chunk: int = 64) -> np.ndarray:
     """Rasterise spheres (tumours) and infinite cylinders (vessels) at voxel
-    centres, vessel > tumour > liver.  Works in z-chunks to bound memory."""
+    centres, vessel > tumour > liver.  Spheres are painted inside their bounding
+    boxes; cylinders per z-chunk; coordinates in float32."""
     labels = np.zeros((nz, ny, nx), dtype=np.uint8)
-    xs = np.arange(nx, dtype=np.float64) * h
-    ys = np.arange(ny, dtype=np.float64) * h
-    for z0 in range(0, nz, z_chunk):
-        z1 = min(nz, z0 + z_chunk)
-        zs = np.arange(z0, z1, dtype=np.float64) * h
-        Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
-        lab = labels[z0:z1]
-        for (cx, cy, cz, r) in tumors:
-            inside = (X - cx) ** 2 + (Y - cy) ** 2 + (Z - cz) ** 2 <= r * r
-            lab[inside] = TUMOR
-        for (a, d, r) in vessels:
-            wx, wy, wz = X - a[0], Y - a[1], Z - a[2]
-            t = wx * d[0] + wy * d[1] + wz * d[2]
-            px, py, pz = wx - t * d[0], wy - t * d[1], wz - t * d[2]
-            inside = px * px + py * py + pz * pz <= r * r
-            lab[inside] = VESSEL
+    f = np.float32
+    for (cx, cy, cz, r) in tumors:
+        lo = [max(0, int(np.floor((c - r) / h))) for c in (cz, cy, cx)]
+        hi = [min(n, int(np.ceil((c + r) / h)) + 1) for c, n in ((cz, nz), (cy, ny), (cx, nx))]
+        if any(a >= b for a, b in zip(lo, hi)):
+            continue
+        zs = (np.arange(lo[0], hi[0], dtype=f) * f(h) - f(cz))[:, None, None]
+        ys = (np.arange(lo[1], hi[1], dtype=f) * f(h) - f(cy))[None, :, None]
+        xs = (np.arange(lo[2], hi[2], dtype=f) * f(h) - f(cx))[None, None, :]
+        inside = zs * zs + ys * ys + xs * xs <= f(r * r)
+        labels[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]][inside] = TUMOR
+    xs = np.arange(nx, dtype=f) * f(h)
+    ys = np.arange(ny, dtype=f) * f(h)
+    for (a, d, r) in vessels:
+        a = np.asarray(a, dtype=np.float64)
+        d = np.asarray(d, dtype=np.float64)
+        wx = (xs - f(a[0]))[None, None, :]
+        wy = (ys - f(a[1]))[None, :, None]
+        for z0 in range(0, nz, z_chunk):
+            z1 = min(nz, z0 + z_chunk)
+            wz = (np.arange(z0, z1, dtype=f) * f(h) - f(a[2]))[:, None, None]
+            t = wx * f(d[0]) + wy * f(d[1]) + wz * f(d[2])
+            # squared distance to the axis = |w|^2 - t^2
+            dist2 = wx * wx + wy * wy + wz * wz - t * t
+            labels[z0:z1][dist2 <= f(r * r)] = VESSEL
     return labels
 
 
