@@ -62,7 +62,7 @@ def workload_config(c, name):
             "n_tines": c.needle.n_tines if c.needle.kind == 1 else 0,
             "power_W": c.needle.power, "arrhenius": bool(c.damage.enable),
             "state": "fp32 hi+lo compensated", "coefficients": "bf16",
-            "l2": "inputs larger than L2 (working set ~42 B/voxel)"}
+            "l2": "inputs larger than L2 (working set ~46 B/voxel, 0.8 GB)"}
 
 
 # ------------------------------------------------------------------ clocks
@@ -125,12 +125,14 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ roofline
-def algorithmic_bytes_per_voxel(arrhenius: bool) -> int:
+def algorithmic_bytes_per_voxel(arrhenius: bool, depth: int) -> float:
     """Compulsory HBM bytes per voxel for one launch of the step kernel
     (compensated FP32 state, BF16 coefficients): theta hi+lo read and written
-    (16), packed a/b (4), source (4), latch read+write (2), and with the damage
-    integral Omega (FP64) and its FP32 Kahan term read and written (24)."""
-    return 16 + 4 + 4 + 2 + (24 if arrhenius else 0)
+    (16), packed a/b (4), source (4), latch read+write (2); with the damage
+    integral its FP32 carry read and written (8) and the FP64 value read and
+    written (16) on the launches that fold the carry (every 32 steps)."""
+    fold = 16.0 * depth / 32.0
+    return 16 + 4 + 4 + 2 + ((8 + fold) if arrhenius else 0)
 
 
 def kernel_source_sha():
@@ -232,6 +234,82 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ secondary
+def _ms_between(torch, stream, fn):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def measure_adjoint(rfa, stream):
+    """128^3, h = 0.75 mm, straight 20 W needle, 2000 steps: recorded forward
+    (sqrt(N) checkpoints) vs rfa_backward (recompute + adjoint + contractions),
+    seed = the C3 loss gradient of an arbitrary target."""
+    import torch
+    case = ph.adjoint_case_128()
+    g = rfa.Grid.from_case(case, damage=False, cuda_stream=stream.cuda_stream)
+    rfa.rfa_autotune(g.handle, None)      # the forward runs with the tuned schedule
+    seed = torch.full(case.labels.shape, 1e-6, dtype=torch.float32, device="cuda")
+    fwd = lambda: g.step(case.nsteps, record=True)
+    out = {}
+
+    def reset():
+        g.set_tissue(case.labels, case.table)
+
+    reset()
+    fwd()
+    g.backward(seed)          # warm-up
+    reset()
+    t_f = _ms_between(torch, stream, fwd)
+    t_b = _ms_between(torch, stream, lambda: out.setdefault("g", g.backward(seed)))
+    reset()
+    sched = rfa.rfa_get_schedule(g.handle)
+    t_plain = _ms_between(torch, stream, lambda: g.step(case.nsteps))
+    g.close()
+    return {"workload": "adjoint128", "grid": [case.nx, case.ny, case.nz], "time_steps": case.nsteps,
+            "forward_recorded_ms": t_f, "backward_ms": t_b, "forward_unrecorded_ms": t_plain,
+            "backward_over_forward": t_b / t_f, "schedule": sched}
+
+
+def measure_batched(rfa, stream, args):
+    """64 needle configurations on {96,128,160,192}^3 grids, 4000 steps (or
+    --batch-steps): one batched persistent launch per call vs the per-needle loop
+    of one-step launches, and vs the per-needle loop with the tuned schedule."""
+    import torch
+    cases = ph.batch_members(0, 64, args.batch_steps)
+    grids = [rfa.Grid.from_case(c, damage=False, cuda_stream=stream.cuda_stream) for c in cases]
+    vox = sum(c.nvox for c in cases)
+    n = args.batch_steps
+    b = rfa.rfa_batch_create([g.handle for g in grids])
+    rfa.rfa_batch_autotune(b, None)
+    rfa.rfa_batch_step(b, 24)             # warm-up (graph capture)
+    t_batch = _ms_between(torch, stream, lambda: rfa.rfa_batch_step(b, n))
+    d, v, graph = rfa.rfa_batch_get_schedule(b)
+    rfa.rfa_batch_destroy(b)
+
+    def loop(depth, variant):
+        for g in grids:
+            g.set_schedule(depth, variant)
+        for g in grids:
+            g.step(n)
+
+    t_plain = _ms_between(torch, stream, lambda: loop(1, 0))
+    t_tuned = _ms_between(torch, stream, lambda: loop(d, v))
+    for g in grids:
+        g.close()
+    return {"workload": "batch64", "members": len(cases), "voxels": vox, "time_steps": n,
+            "batched_ms": t_batch, "batched_gvox_steps_s": vox * n / t_batch / 1e6,
+            "plain_loop_ms": t_plain, "plain_loop_gvox_steps_s": vox * n / t_plain / 1e6,
+            "tuned_loop_ms": t_tuned, "batched_over_plain_loop": t_plain / t_batch,
+            "batched_over_tuned_loop": t_tuned / t_batch,
+            "schedule": {"tb_depth": d, "tile_variant": v, "cuda_graph": graph}}
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
@@ -279,8 +357,7 @@ def run_ours(args):
 
     def one_step(host: bool):
         lab = labels_pin if host else labels_dev
-        g.set_tissue(lab, case.table)
-        g.place_needle(case.needle)
+        g.set_tissue(lab, case.table)       # S1, and S2 (the placed needle is placed again)
         g.set_damage(int(d.enable), d.A, d.Ea, d.R, d.T_thr_C)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -346,7 +423,7 @@ def run_ours(args):
     # roofline of the dominant kernel (the step kernel)
     launches_per_step = (case.nsteps // depth + case.nsteps % depth) if depth > 1 else case.nsteps
     avg_launch_ms = kern_ms / (args.steps * launches_per_step)
-    nbytes = algorithmic_bytes_per_voxel(bool(d.enable)) * case.nvox
+    nbytes = algorithmic_bytes_per_voxel(bool(d.enable), depth) * case.nvox
     peak, peak_kind = measured_peak_hbm()
     achieved = nbytes / (avg_launch_ms * 1e-3) / 1e9
     kname = "k_step_tb" if depth > 1 else "k_step_plain"
@@ -355,7 +432,13 @@ def run_ours(args):
             "kernel": kname, "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
             "algorithmic_bytes_per_launch": nbytes, "avg_launch_us": avg_launch_ms * 1e3,
             "steps_per_launch": depth}
-    kernels_per_step = 1 + 3 + launches_per_step + 2
+    kernels_per_step = 2 + 3 + launches_per_step + 2   # setup (2), source (3), steps, necrosis (2)
+    secondary = None
+    if rank == 0 and not args.no_secondary:
+        secondary = {"adjoint": measure_adjoint(rfa, stream),
+                     "batched": measure_batched(rfa, stream, args)}
+    if dist is not None:
+        dist.barrier()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -366,7 +449,8 @@ def run_ours(args):
                                schedule={"tb_depth": depth, "tile_variant": variant}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": kernels_per_step * args.steps,
-                "necrosis_voxels": [int(counts[0]), int(counts[1])]}
+                "necrosis_voxels": [int(counts[0]), int(counts[1])],
+                "secondary": secondary}
         print(json.dumps(line), flush=True)
     g.close()
     if dist is not None:
@@ -386,6 +470,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-secondary", action="store_true", help="skip the adjoint and batched measurements")
+    ap.add_argument("--batch-steps", type=int, default=4000)
     args = ap.parse_args()
     if args.schedule == "plain":
         args.schedule = "tb1"

@@ -251,7 +251,8 @@ rfa_status rfa_batch_destroy(rfa_batch *b);
  * candidate on snapshots of all members' states (restored afterwards);
  * cache_path (may be NULL) is a text file of cached choices. */
 rfa_status rfa_batch_autotune(rfa_batch *b, const char *cache_path);
-/* Current batch schedule; uses_graph = 1 if launches replay a CUDA graph. */
+/* Current batch schedule; uses_graph = 1 if launches replay a CUDA graph
+ * (when 0, rfa_last_error() gives the reason capture was not used). */
 rfa_status rfa_batch_get_schedule(rfa_batch *b, int *tb_depth, int *tile_variant, int *uses_graph);
 
 /* Wait for the grid's stream and report deferred device errors. */

@@ -117,15 +117,15 @@ __device__ __forceinline__ void adj_load_ab(const void *ab, size_t i, float a[4]
 __device__ __forceinline__ float4 ld4g(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
 
 // one adjoint step: lam_out = A^T lam_in, Lam += lam_in, per-label contractions
-template <int PP>
-__global__ void __launch_bounds__(256) k_adjoint_step(const AdjArgs A)
+template <int PP, int NL>
+__global__ void __launch_bounds__(256, 2) k_adjoint_step(const AdjArgs A)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    float accK[kMaxGradLabels], accW[kMaxGradLabels];
+    float accK[NL], accW[NL];
 #pragma unroll
-    for (int l = 0; l < kMaxGradLabels; ++l) accK[l] = accW[l] = 0.f;
+    for (int l = 0; l < NL; ++l) accK[l] = accW[l] = 0.f;
     const bool wvalid = y < A.ny;  // warp-uniform (blockDim.x == 32)
     const int x0 = 4 * (blockIdx.x * 32 + lane);
     const bool inrow = wvalid && x0 < A.pitch;
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(256) k_adjoint_step(const AdjArgs A)
                     const bool free_vox = valid && !face_vox;
                     const float vk = free_vox ? l * lt : 0.f, vw = free_vox ? l * t : 0.f;
 #pragma unroll
-                    for (int L = 0; L < kMaxGradLabels; ++L) {
+                    for (int L = 0; L < NL; ++L) {
                         accK[L] += lab == L ? vk : 0.f;
                         accW[L] += lab == L ? vw : 0.f;
                     }
@@ -266,10 +266,10 @@ __global__ void __launch_bounds__(256) k_adjoint_step(const AdjArgs A)
         }
     }
     // block reduction of the per-label sums, then one FP64 atomic per label and block
-    __shared__ float sK[8][kMaxGradLabels], sW[8][kMaxGradLabels];
+    __shared__ float sK[8][NL], sW[8][NL];
     const int w = threadIdx.y;
 #pragma unroll
-    for (int L = 0; L < kMaxGradLabels; ++L) {
+    for (int L = 0; L < NL; ++L) {
         float k = accK[L] * A.fk[L], v = accW[L] * A.gw[L];
         for (int o = 16; o > 0; o >>= 1) {
             k += __shfl_xor_sync(FULL, k, o);
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(256) k_adjoint_step(const AdjArgs A)
         }
     }
     __syncthreads();
-    if (w == 0 && lane < kMaxGradLabels) {
+    if (w == 0 && lane < NL) {
         double k = 0.0, v = 0.0;
         for (int j = 0; j < (int)blockDim.y; ++j) {
             k += sK[j][lane];
@@ -389,9 +389,17 @@ cudaError_t launch_adjoint_step(rfa_grid *g, const AdjArgs &A0, const float *lam
     A.th = th;
     dim3 blk(32, 8);
     dim3 grd = plain_grid_dims(g, A.zchunk);
-    if (g->pp == RFA_PARAM_BF16) k_adjoint_step<RFA_PARAM_BF16><<<grd, blk, 0, g->stream>>>(A);
-    else if (g->pp == RFA_PARAM_F32) k_adjoint_step<RFA_PARAM_F32><<<grd, blk, 0, g->stream>>>(A);
-    else k_adjoint_step<RFA_PARAM_F64><<<grd, blk, 0, g->stream>>>(A);
+    const bool few = g->n_labels <= 4;
+    if (g->pp == RFA_PARAM_BF16) {
+        if (few) k_adjoint_step<RFA_PARAM_BF16, 4><<<grd, blk, 0, g->stream>>>(A);
+        else k_adjoint_step<RFA_PARAM_BF16, 8><<<grd, blk, 0, g->stream>>>(A);
+    } else if (g->pp == RFA_PARAM_F32) {
+        if (few) k_adjoint_step<RFA_PARAM_F32, 4><<<grd, blk, 0, g->stream>>>(A);
+        else k_adjoint_step<RFA_PARAM_F32, 8><<<grd, blk, 0, g->stream>>>(A);
+    } else {
+        if (few) k_adjoint_step<RFA_PARAM_F64, 4><<<grd, blk, 0, g->stream>>>(A);
+        else k_adjoint_step<RFA_PARAM_F64, 8><<<grd, blk, 0, g->stream>>>(A);
+    }
     return cudaGetLastError();
 }
 
@@ -447,7 +455,7 @@ rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads)
     A.nz = g->nz;
     A.pitch = g->pitch;
     A.plane = g->plane;
-    A.zchunk = g->nz < 64 ? g->nz : 32;
+    A.zchunk = choose_zchunk(g, 2);
     A.face = g->face;
     A.acc = accd;
     for (int l = 0; l < kMaxGradLabels; ++l) {

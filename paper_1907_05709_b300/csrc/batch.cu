@@ -6,7 +6,8 @@
 // cooperative grid of exactly the resident CTAs walks all items of all members
 // for one block of M steps, meets at a bounded software grid barrier, and
 // continues with the next block, so nsteps cost one launch.  The launch is
-// captured once per block count into a CUDA graph and replayed.  Steps that do
+// built once per block count into a CUDA graph (barrier reset + cooperative
+// kernel node) and replayed.  Steps that do
 // not fill a block run as one-step launches per member afterwards.
 #include "rfa_internal.cuh"
 
@@ -31,6 +32,8 @@ struct rfa_batch {
     void *h_members = nullptr;  // pinned staging of the member descriptors
     std::map<int64_t, cudaGraphExec_t> graphs;
     bool use_graphs = true;
+    int grid = 0;             // co-resident CTAs of the batch kernel
+    std::string graph_error;  // why graph capture was given up, if it was
 };
 
 namespace rfa {
@@ -63,7 +66,7 @@ rfa_status build_plan(rfa_batch *b)
     b->hosts.assign(n, TBMemberHost{});
     b->item_begin.assign(n + 1, 0);
     for (int m = 0; m < n; ++m) {
-        if (!tb_batch_member(b->members[m], b->depth, b->variant, 32, b->hosts[m]))
+        if (!tb_batch_member(b->members[m], b->depth, b->variant, 64, b->hosts[m]))
             return bfail(RFA_E_CUDA, "tensor map creation failed for a batch member");
         b->item_begin[m + 1] = b->item_begin[m] + b->hosts[m].items;
     }
@@ -81,6 +84,7 @@ rfa_status build_plan(rfa_batch *b)
     RFA_CUDA(cudaMemcpyAsync(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
                              b->stream));
     RFA_CUDA(cudaStreamSynchronize(b->stream));
+    RFA_CUDA(prepare_batch_tb(b->depth, b->variant, b->damage, b->nitems, &b->grid));
     return RFA_OK;
 }
 
@@ -101,7 +105,7 @@ cudaError_t enqueue_blocks(rfa_batch *b, int64_t ntime)
     cudaError_t e = cudaMemsetAsync(b->d_gbar, 0, 2 * sizeof(unsigned), b->stream);
     if (e != cudaSuccess) return e;
     return launch_batch_tb(b->depth, b->variant, b->damage, b->d_members, (int)b->members.size(), b->nitems,
-                           (int)ntime, b->d_gbar, b->members[0]->status, b->stream);
+                           (int)ntime, b->d_gbar, b->members[0]->status, b->stream, b->grid);
 }
 
 rfa_status run_blocks(rfa_batch *b, int64_t ntime)
@@ -110,18 +114,12 @@ rfa_status run_blocks(rfa_batch *b, int64_t ntime)
     if (b->use_graphs) {
         auto it = b->graphs.find(ntime);
         if (it == b->graphs.end()) {
-            cudaGraph_t graph = nullptr;
             cudaGraphExec_t exec = nullptr;
-            cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
-            if (e == cudaSuccess) {
-                cudaError_t e1 = enqueue_blocks(b, ntime);
-                cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
-                e = e1 != cudaSuccess ? e1 : e2;
-            }
-            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-            if (graph) cudaGraphDestroy(graph);
+            cudaError_t e = graph_batch_tb(b->depth, b->variant, b->damage, b->d_members, (int)b->members.size(),
+                                           b->nitems, (int)ntime, b->d_gbar, b->members[0]->status, b->grid, &exec);
             if (e != cudaSuccess) {
                 // graphs unavailable for this launch kind: keep launching directly
+                b->graph_error = cudaGetErrorString(e);
                 cudaGetLastError();
                 b->use_graphs = false;
             } else {
@@ -344,6 +342,7 @@ rfa_status rfa_batch_get_schedule(rfa_batch *b, int *tb_depth, int *tile_variant
     if (tb_depth) *tb_depth = b->depth;
     if (tile_variant) *tile_variant = b->variant;
     if (uses_graph) *uses_graph = b->use_graphs ? 1 : 0;
+    if (!b->use_graphs) set_error("graph capture not used: " + b->graph_error);
     return RFA_OK;
 }
 

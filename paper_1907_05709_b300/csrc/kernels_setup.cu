@@ -17,6 +17,17 @@ namespace rfa {
 
 namespace {
 
+// rounded update coefficients of every free label (one thread per label)
+__global__ void k_label_coef(LabelCoef *tab, int n_labels, double dt, double h, int pp)
+{
+    const int l = threadIdx.x;
+    if (l >= n_labels) return;
+    LabelCoef t = tab[l];
+    t.a = t.fixed ? 0.0 : round_coef(coef_a(t, dt, h), pp);
+    t.b = t.fixed ? 0.0 : round_coef(coef_b(t, dt), pp);
+    tab[l] = t;
+}
+
 template <int SP, int PP>
 __global__ void k_setup(const uint8_t *__restrict__ labels, const LabelCoef *__restrict__ tab,
                         int nx, int ny, int nz, int pitch, double h, double dt, double T_a,
@@ -47,8 +58,8 @@ __global__ void k_setup(const uint8_t *__restrict__ labels, const LabelCoef *__r
             } else if (face == RFA_FACE_DIRICHLET && face_vox) {
                 th = 0.0;
             } else {
-                a = round_coef(coef_a(t, dt, h), PP);
-                b = round_coef(coef_b(t, dt), PP);
+                a = t.a;
+                b = t.b;
             }
         }
         ((T *)th0)[i] = (T)th;
@@ -74,27 +85,27 @@ __global__ void k_setup(const uint8_t *__restrict__ labels, const LabelCoef *__r
     }
 }
 
-__device__ double needle_distance(const NeedleGeom &g, double px, double py, double pz)
+// squared distance from a voxel centre to the nearest active segment
+__device__ double needle_dist2(const NeedleGeom &g, double px, double py, double pz)
 {
     double best = 1e300;
     for (int k = 0; k < g.nseg; ++k) {
         const Segment &sg = g.seg[k];
         double ux = sg.p1[0] - sg.p0[0], uy = sg.p1[1] - sg.p0[1], uz = sg.p1[2] - sg.p0[2];
         double wx = px - sg.p0[0], wy = py - sg.p0[1], wz = pz - sg.p0[2];
-        double uu = ux * ux + uy * uy + uz * uz;
-        double t = uu > 0.0 ? (wx * ux + wy * uy + wz * uz) / uu : 0.0;
+        double t = (wx * ux + wy * uy + wz * uz) * sg.inv_uu;
         t = fmin(fmax(t, 0.0), 1.0);
-        double ex = px - (sg.p0[0] + t * ux), ey = py - (sg.p0[1] + t * uy),
-               ez = pz - (sg.p0[2] + t * uz);
+        double ex = wx - t * ux, ey = wy - t * uy, ez = wz - t * uz;
         best = fmin(best, ex * ex + ey * ey + ez * ez);
     }
-    return sqrt(best);
+    return best;
 }
 
-__device__ inline double needle_weight(const NeedleGeom &g, double d)
+// w = max(d, r0)^-4 = 1 / max(d^2, r0^2)^2
+__device__ inline double needle_weight2(const NeedleGeom &g, double d2)
 {
-    double r = fmax(d, g.r0);
-    return 1.0 / (r * r * r * r);
+    double r2 = fmax(d2, g.r0 * g.r0);
+    return 1.0 / (r2 * r2);
 }
 
 // block-wide FP64 sum; every thread gets the result
@@ -115,7 +126,7 @@ __device__ double block_sum(double v)
 // pass 1: per-block sums of w over free voxels
 __global__ void k_source_sum(NeedleGeom geom, const uint8_t *__restrict__ label,
                              const LabelCoef *__restrict__ tab, int nx, int ny, int nz,
-                             int pitch, double h, int face, double *partial)
+                             int pitch, double h, int face, double *partial, double *wbuf)
 {
     size_t nvp = (size_t)pitch * ny * nz;
     double acc = 0.0;
@@ -128,7 +139,9 @@ __global__ void k_source_sum(NeedleGeom geom, const uint8_t *__restrict__ label,
         int z = (int)(r / ny);
         bool face_vox = (x == 0 || y == 0 || z == 0 || x == nx - 1 || y == ny - 1 || z == nz - 1);
         if (tab[label[i]].fixed || (face == RFA_FACE_DIRICHLET && face_vox)) continue;
-        acc += needle_weight(geom, needle_distance(geom, x * h, y * h, z * h));
+        const double w = needle_weight2(geom, needle_dist2(geom, x * h, y * h, z * h));
+        wbuf[i] = w;
+        acc += w;
     }
     acc = block_sum(acc);
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
@@ -148,7 +161,7 @@ template <int SP>
 __global__ void k_source_write(NeedleGeom geom, const uint8_t *__restrict__ label,
                                const LabelCoef *__restrict__ tab, int nx, int ny, int nz,
                                int pitch, double h, double dt, int face, const double *Wp,
-                               void *s)
+                               const double *wbuf, void *s)
 {
     using T = typename std::conditional<SP == RFA_STATE_F64, double, float>::type;
     size_t nvp = (size_t)pitch * ny * nz;
@@ -165,9 +178,7 @@ __global__ void k_source_write(NeedleGeom geom, const uint8_t *__restrict__ labe
             const LabelCoef t = tab[label[i]];
             if (!(t.fixed || (face == RFA_FACE_DIRICHLET && face_vox))) {
                 double rhoc = t.rho * t.c;
-                double q = (W > 0.0 && geom.nseg > 0)
-                               ? geom.P * needle_weight(geom, needle_distance(geom, x * h, y * h, z * h)) / (h * h * h * W)
-                               : 0.0;
+                double q = (W > 0.0 && geom.nseg > 0) ? geom.P * wbuf[i] / (h * h * h * W) : 0.0;
                 v = q * dt / rhoc + t.Q_m * dt / rhoc;
             }
         }
@@ -180,6 +191,7 @@ __global__ void k_source_write(NeedleGeom geom, const uint8_t *__restrict__ labe
 cudaError_t launch_setup(rfa_grid *g, const uint8_t *labels_dense_dev, int n_labels)
 {
     dim3 blk(256), grd(148 * 8);
+    k_label_coef<<<1, 256, 0, g->stream>>>(g->d_table, n_labels, g->dt, g->h, g->pp);
 #define SETUP_CASE(SPV, PPV)                                                                     \
     if (g->sp == SPV && g->pp == PPV)                                                           \
         k_setup<SPV, PPV><<<grd, blk, 0, g->stream>>>(                                          \
@@ -205,16 +217,16 @@ cudaError_t launch_source(rfa_grid *g)
     double *W = partial + kReduceBlocks;
     k_source_sum<<<kReduceBlocks, 256, 0, g->stream>>>(g->geom, g->label, g->d_table, g->nx,
                                                        g->ny, g->nz, g->pitch, g->h, g->face,
-                                                       partial);
+                                                       partial, (double *)g->stage);
     k_sum_partials<<<1, 1024, 0, g->stream>>>(partial, kReduceBlocks, W);
     if (g->sp == RFA_STATE_F64)
         k_source_write<RFA_STATE_F64><<<148 * 8, 256, 0, g->stream>>>(
             g->geom, g->label, g->d_table, g->nx, g->ny, g->nz, g->pitch, g->h, g->dt, g->face, W,
-            g->s);
+            (const double *)g->stage, g->s);
     else
         k_source_write<RFA_STATE_F32><<<148 * 8, 256, 0, g->stream>>>(
             g->geom, g->label, g->d_table, g->nx, g->ny, g->nz, g->pitch, g->h, g->dt, g->face, W,
-            g->s);
+            (const double *)g->stage, g->s);
     return cudaGetLastError();
 }
 

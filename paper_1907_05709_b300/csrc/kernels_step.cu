@@ -329,7 +329,7 @@ cudaError_t launch_step_plain(rfa_grid *g, const void *th_in, const void *lo_in,
     A.nz = g->nz;
     A.pitch = g->pitch;
     A.plane = g->plane;
-    A.zchunk = g->nz < 64 ? g->nz : 32;
+    A.zchunk = choose_zchunk(g, 3);
     A.thr = g->T_thr - g->T_a;
     A.dc = damage_consts(g);
     dim3 blk(32, 8);

@@ -168,7 +168,7 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
     }
     for (; item < nitems; item += stride) {
         int local;
-        const TBTile &A = get(item, local);
+        const TBTile A = get(item, local);  // by value: the descriptor may live in global memory
         int X0, Y0, zb, ze;
         tb_item_geom<M, EY>(A, local, X0, Y0, zb, ze);
         const int L = ze - zb + 2 * M;   // stage-0 planes zb-M .. ze+M-1
@@ -558,21 +558,30 @@ cudaError_t launch_inst(rfa_grid *g, const TBMaps &maps, TBTile T)
     return cudaGetLastError();
 }
 
+// shared-memory opt-in and the co-resident grid size of the batch kernel
+// (host-side queries, kept outside stream capture)
 template <int M, int EY, bool DMG>
-cudaError_t launch_batch_inst(const TBMember *mem, int nmem, int nitems, int ntime, int fold_every,
-                              unsigned *gbar, unsigned *status, cudaStream_t stream)
+cudaError_t prepare_batch_inst(int nitems, int *grid)
 {
     using C = Cfg<M, EY>;
     cudaError_t e = cudaFuncSetAttribute(k_batch_tb<M, EY, DMG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          C::SMEM);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_tb<M, EY, DMG>, C::THREADS, C::SMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int grid = nsm * per_sm < nitems ? nsm * per_sm : nitems;
+    *grid = nsm * per_sm < nitems ? nsm * per_sm : nitems;
+    return cudaSuccess;
+}
+
+template <int M, int EY, bool DMG>
+cudaError_t launch_batch_inst(const TBMember *mem, int nmem, int nitems, int ntime, int fold_every,
+                              unsigned *gbar, unsigned *status, cudaStream_t stream, int grid)
+{
+    using C = Cfg<M, EY>;
     // cooperative launch: every CTA is resident at once, which the grid barrier needs
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
@@ -670,13 +679,11 @@ bool tb_batch_member(const rfa_grid *g, int depth, int variant, int max_chunk, T
     TBTile T;
     fill_tile(g, 0, T);
     const int ey = variant_ey(variant);
-#define PLAN_CASE(MV, EYV) \
-    if (depth == MV && ey == EYV) tile_plan<MV, EYV>(g, 1 << 30, max_chunk, T);
-    PLAN_CASE(2, 16)
-    PLAN_CASE(3, 16)
-    PLAN_CASE(4, 16)
-    PLAN_CASE(2, 32)
-#undef PLAN_CASE
+    // batch items: every member's tiles with z chunks of at most max_chunk planes
+    // (the persistent grid balances the many items of all members)
+    T.xt = (g->nx + TB_TX - 1) / TB_TX;
+    T.yt = (g->ny + (ey - 2 * depth) - 1) / (ey - 2 * depth);
+    T.zc = (g->nz + max_chunk - 1) / max_chunk;
     for (int p = 0; p < 2; ++p) {
         if (!tb_make_maps(g, variant, g->th[p], g->lo[p], out.maps + 4 * p)) return false;
         fill_tile(g, p, out.tile[p]);
@@ -702,16 +709,89 @@ void tb_pack_member(const TBMemberHost &h, const CUtensorMap *maps_dev, int item
     std::memcpy(dst, &m, sizeof m);
 }
 
-cudaError_t launch_batch_tb(int depth, int variant, bool damage, const void *members_dev, int nmem,
-                            int nitems, int ntime, unsigned *gbar, unsigned *status, cudaStream_t stream)
+cudaError_t prepare_batch_tb(int depth, int variant, bool damage, int nitems, int *grid)
+{
+    const int ey = variant_ey(variant);
+#define PREP_CASE(MV, EYV)                                                              \
+    if (depth == MV && ey == EYV)                                                       \
+        return damage ? prepare_batch_inst<MV, EYV, true>(nitems, grid)                 \
+                      : prepare_batch_inst<MV, EYV, false>(nitems, grid);
+    PREP_CASE(2, 16)
+    PREP_CASE(3, 16)
+    PREP_CASE(4, 16)
+    PREP_CASE(2, 32)
+#undef PREP_CASE
+    return cudaErrorInvalidValue;
+}
+
+// A two-node graph (barrier reset, then the batch kernel as a cooperative
+// kernel node): stream capture does not accept cooperative launches.
+template <int M, int EY, bool DMG>
+cudaError_t graph_batch_inst(const TBMember *mem, int nmem, int nitems, int ntime, int fold_every,
+                             unsigned *gbar, unsigned *status, int grid, cudaGraphExec_t *exec)
+{
+    using C = Cfg<M, EY>;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphNode_t nmemset = nullptr, nkernel = nullptr;
+    cudaMemsetParams mp = {};
+    mp.dst = gbar;
+    mp.value = 0;
+    mp.elementSize = sizeof(unsigned);
+    mp.width = 2;
+    mp.height = 1;
+    mp.pitch = 0;
+    e = cudaGraphAddMemsetNode(&nmemset, graph, nullptr, 0, &mp);
+    void *args[] = {(void *)&mem, (void *)&nmem, (void *)&nitems, (void *)&ntime, (void *)&fold_every,
+                    (void *)&gbar, (void *)&status};
+    if (e == cudaSuccess) {
+        cudaKernelNodeParams kp = {};
+        kp.func = (void *)k_batch_tb<M, EY, DMG>;
+        kp.gridDim = dim3((unsigned)grid);
+        kp.blockDim = dim3((unsigned)C::THREADS);
+        kp.sharedMemBytes = C::SMEM;
+        kp.kernelParams = args;
+        e = cudaGraphAddKernelNode(&nkernel, graph, &nmemset, 1, &kp);
+    }
+    if (e == cudaSuccess) {
+        cudaLaunchAttributeValue v = {};
+        v.cooperative = 1;
+        e = cudaGraphKernelNodeSetAttribute(nkernel, cudaLaunchAttributeCooperative, &v);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    return e;
+}
+
+cudaError_t graph_batch_tb(int depth, int variant, bool damage, const void *members_dev, int nmem, int nitems,
+                           int ntime, unsigned *gbar, unsigned *status, int grid, cudaGraphExec_t *exec)
 {
     const int ey = variant_ey(variant);
     const int fold_every = kCarrySteps / depth > 0 ? kCarrySteps / depth : 1;
     const TBMember *mem = (const TBMember *)members_dev;
-#define BATCH_CASE(MV, EYV)                                                                                    \
-    if (depth == MV && ey == EYV)                                                                              \
-        return damage ? launch_batch_inst<MV, EYV, true>(mem, nmem, nitems, ntime, fold_every, gbar, status, stream) \
-                      : launch_batch_inst<MV, EYV, false>(mem, nmem, nitems, ntime, fold_every, gbar, status, stream);
+#define GRAPH_CASE(MV, EYV)                                                                                        \
+    if (depth == MV && ey == EYV)                                                                                  \
+        return damage ? graph_batch_inst<MV, EYV, true>(mem, nmem, nitems, ntime, fold_every, gbar, status, grid, exec) \
+                      : graph_batch_inst<MV, EYV, false>(mem, nmem, nitems, ntime, fold_every, gbar, status, grid, exec);
+    GRAPH_CASE(2, 16)
+    GRAPH_CASE(3, 16)
+    GRAPH_CASE(4, 16)
+    GRAPH_CASE(2, 32)
+#undef GRAPH_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_batch_tb(int depth, int variant, bool damage, const void *members_dev, int nmem,
+                            int nitems, int ntime, unsigned *gbar, unsigned *status, cudaStream_t stream, int grid)
+{
+    const int ey = variant_ey(variant);
+    const int fold_every = kCarrySteps / depth > 0 ? kCarrySteps / depth : 1;
+    const TBMember *mem = (const TBMember *)members_dev;
+#define BATCH_CASE(MV, EYV)                                                                                           \
+    if (depth == MV && ey == EYV)                                                                                     \
+        return damage ? launch_batch_inst<MV, EYV, true>(mem, nmem, nitems, ntime, fold_every, gbar, status, stream, grid) \
+                      : launch_batch_inst<MV, EYV, false>(mem, nmem, nitems, ntime, fold_every, gbar, status, stream, grid);
     BATCH_CASE(2, 16)
     BATCH_CASE(3, 16)
     BATCH_CASE(4, 16)

@@ -5,9 +5,9 @@
 // a real-time loop (for example a VR renderer stepping the ablation every
 // frame) where a cudaMalloc/cudaFree would synchronise the device and stall
 // the frame, or a host application that pre-reserves its whole device memory
-// budget and forbids any later allocation.  rfa_necrosis_mask may allocate a
-// staging buffer on first use and copies its results to the host; this entry
-// point does neither.
+// budget and forbids any later allocation.  This entry point calls no allocator
+// and, unlike rfa_necrosis_mask, neither copies to the host nor synchronises;
+// its only scratch is the fixed array below.
 //
 // How: the per-block partial sums of the two-pass reduction live in one
 // file-scope device array of fixed size (kNoAllocRecords records of 32 bytes,

@@ -38,10 +38,12 @@ constexpr int kCarrySteps = 32;   // fold the FP32 damage carry at least every 3
 struct LabelCoef {
     double k, rho, c, w_b, rho_b, c_b, Q_m, T_fixed;
     int fixed;
+    double a, b;  // stored (rounded) update coefficients, filled on the device by k_label_coef
 };
 
 struct Segment {
     double p0[3], p1[3];
+    double inv_uu;  // 1 / |p1 - p0|^2 (0 for a point)
 };
 
 struct NeedleGeom {
@@ -210,8 +212,11 @@ struct TBMemberHost {
 bool tb_batch_member(const rfa_grid *g, int depth, int variant, int max_chunk, TBMemberHost &out);
 size_t tb_member_bytes();
 void tb_pack_member(const TBMemberHost &h, const CUtensorMap *maps_dev, int item_begin, int cur0, void *dst);
+cudaError_t prepare_batch_tb(int depth, int variant, bool damage, int nitems, int *grid);
+cudaError_t graph_batch_tb(int depth, int variant, bool damage, const void *members_dev, int nmem, int nitems,
+                           int ntime, unsigned *gbar, unsigned *status, int grid, cudaGraphExec_t *exec);
 cudaError_t launch_batch_tb(int depth, int variant, bool damage, const void *members_dev, int nmem,
-                            int nitems, int ntime, unsigned *gbar, unsigned *status, cudaStream_t stream);
+                            int nitems, int ntime, unsigned *gbar, unsigned *status, cudaStream_t stream, int grid);
 // reductions and conversions (kernels_reduce.cu)
 cudaError_t launch_necrosis(rfa_grid *g, uint8_t *mask_dense_dev, double width_K,
                             void *result_dev);
@@ -226,6 +231,22 @@ rfa_status record_checkpoint(rfa_grid *g, int64_t step_index);
 
 // forward stepping used by rfa_step and the adjoint recompute (runtime.cu)
 rfa_status advance(rfa_grid *g, int64_t nsteps, bool damage, bool latch);
+
+// z planes per block of the z-streaming kernels (blocks of 32 x 8 quads): short
+// enough that at least two waves of resident blocks fill the 148 SMs, long
+// enough (>= 4) that the two extra planes a chunk reads stay a small overhead
+inline int choose_zchunk(const rfa_grid *g, int blocks_per_sm)
+{
+    const int quads = (g->pitch + 3) / 4;
+    const long long bxy = (long long)((quads + 31) / 32) * ((g->ny + 7) / 8);
+    const long long target = 2LL * 148 * blocks_per_sm;
+    const long long nchunks = (target + bxy - 1) / bxy;
+    long long zc = (g->nz + nchunks - 1) / nchunks;
+    if (zc < 4) zc = 4;
+    if (zc > 32) zc = 32;
+    if (zc > g->nz) zc = g->nz;
+    return (int)zc;
+}
 
 inline dim3 plain_grid_dims(const rfa_grid *g, int zchunk)
 {

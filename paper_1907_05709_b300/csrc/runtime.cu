@@ -91,6 +91,11 @@ static rfa_status build_geometry(const rfa_needle &nd, NeedleGeom &g)
     } else {
         return fail(RFA_E_INVALID, "unknown needle kind");
     }
+    for (int k = 0; k < g.nseg; ++k) {
+        double uu = 0.0;
+        for (int d = 0; d < 3; ++d) uu += (g.seg[k].p1[d] - g.seg[k].p0[d]) * (g.seg[k].p1[d] - g.seg[k].p0[d]);
+        g.seg[k].inv_uu = uu > 0.0 ? 1.0 / uu : 0.0;
+    }
     return RFA_OK;
 }
 
@@ -180,6 +185,7 @@ rfa_status rfa_create_grid(int nx, int ny, int nz, double h_m, double dt_s, int 
     alloc((void **)&g->status, 256);
     alloc(&g->red, kReduceBlocks * 32 + 256);
     alloc((void **)&g->d_table, 256 * sizeof(LabelCoef));
+    alloc(&g->stage, nvp * 8);  // labels in, source weights, host copies
     if (e == cudaSuccess) e = cudaMallocHost((void **)&g->status_host, 256);
     if (e != cudaSuccess) {
         rfa_status st = (e == cudaErrorMemoryAllocation) ? fail(RFA_E_OOM, "device allocation failed")
@@ -247,12 +253,6 @@ rfa_status rfa_set_tissue(rfa_grid *g, const uint8_t *labels, const rfa_tissue *
                 std::snprintf(buf, sizeof buf, "label %d: 1 - %g a - b = %.6g < 0 (a = %.6g, b = %.6g); reduce dt", l, deg, 1.0 - deg * a - b, a, b);
                 return fail(RFA_E_UNSTABLE, buf);
             }
-        }
-    }
-    if (!g->stage) {
-        if (cudaMalloc(&g->stage, n * 8) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(RFA_E_OOM, "staging allocation failed");
         }
     }
     RFA_CUDA(cudaMemcpyAsync(g->d_table, tab.data(), 256 * sizeof(LabelCoef), cudaMemcpyHostToDevice, g->stream));
