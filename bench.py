@@ -130,30 +130,36 @@ def algorithmic_bytes_per_voxel(arrhenius: bool, depth: int) -> float:
     (compensated FP32 state, BF16 coefficients): theta hi+lo read and written
     (16), packed a/b (4), source (4), latch read+write (2); with the damage
     integral its FP32 carry read and written (8) and the FP64 value read and
-    written (16) on the launches that fold the carry (every 32 steps)."""
-    fold = 16.0 * depth / 32.0
+    written (16) on the launches that fold the carry (every 128 steps)."""
+    fold = 16.0 * depth / 128.0
     return 16 + 4 + 4 + 2 + ((8 + fold) if arrhenius else 0)
 
 
-def kernel_source_sha():
+KERNEL_SOURCES = {
+    "k_step_tb": ["kernels_tb.cu", "rfa_update.cuh", "rfa_internal.cuh"],
+    "k_step_plain": ["kernels_step.cu", "rfa_update.cuh", "rfa_internal.cuh"],
+}
+
+
+def kernel_source_sha(kernel: str):
+    """Hash of the source files that define ``kernel``."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1907_05709_b300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def load_traffic(kernel: str, nvox: int):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+    """DRAM bytes per launch from the committed ncu summary (profiles/traffic.json),
+    if it was taken on the current sources of that kernel (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(p))
     except Exception:
         return None
     e = d.get(kernel)
-    if not e or e.get("source_sha") != kernel_source_sha():
+    if not e or e.get("source_sha") != kernel_source_sha(kernel):
         return None
     return e["bytes_per_voxel_per_launch"] * nvox
 
@@ -458,6 +464,33 @@ def run_ours(args):
     return 0
 
 
+def profile_case(name):
+    """Short fixed cases for ncu captures of the secondary kernels (no JSON line)."""
+    import torch
+    import paper_1907_05709_b300 as rfa
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    if name == "batch16":
+        cases = ph.batch_members(0, 16, 100, sizes=(96, 128, 160))
+        grids = [rfa.Grid.from_case(c, damage=False, cuda_stream=stream.cuda_stream) for c in cases]
+        b = rfa.rfa_batch_create([g.handle for g in grids])
+        for _ in range(3):
+            rfa.rfa_batch_step(b, 8)
+        rfa.rfa_batch_destroy(b)
+    elif name == "adjoint128":
+        case = ph.adjoint_case_128(nsteps=200)
+        g = rfa.Grid.from_case(case, damage=False, cuda_stream=stream.cuda_stream)
+        g.set_schedule(2, 0)
+        g.step(case.nsteps, record=True)
+        seed = torch.full(case.labels.shape, 1e-6, dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            g.backward(seed)
+    else:
+        raise SystemExit(f"unknown profile case {name}")
+    torch.cuda.synchronize()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -472,7 +505,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-secondary", action="store_true", help="skip the adjoint and batched measurements")
     ap.add_argument("--batch-steps", type=int, default=4000)
+    ap.add_argument("--profile-case", default=None, help="batch16 | adjoint128: short case for ncu")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case(args.profile_case)
     if args.schedule == "plain":
         args.schedule = "tb1"
     if args.impl == "reference":

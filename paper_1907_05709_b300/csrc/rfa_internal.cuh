@@ -32,8 +32,8 @@ constexpr unsigned kStatusNonfinite = 1u;
 constexpr unsigned kStatusTimeout = 2u;
 constexpr unsigned kStatusBadLabel = 4u;
 constexpr int kMaxSegments = 17;
-constexpr int kReduceBlocks = 592;
-constexpr int kCarrySteps = 32;   // fold the FP32 damage carry at least every 32 steps  // 4 per SM on 148 SMs; fixed => deterministic reductions
+constexpr int kReduceBlocks = 592;  // 4 per SM on 148 SMs; fixed => deterministic reductions
+constexpr int kCarrySteps = 128;   // fold the FP32 damage carry into the FP64 integral every 128 steps
 
 struct LabelCoef {
     double k, rho, c, w_b, rho_b, c_b, Q_m, T_fixed;
