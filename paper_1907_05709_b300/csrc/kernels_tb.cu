@@ -36,6 +36,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 
 namespace rfa {
 
@@ -104,6 +105,10 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// x - n or x + n for x one period out of [0, n)
+__device__ __forceinline__ int wrap_lo(int x, int n) { return x < 0 ? x + n : x; }
+__device__ __forceinline__ int wrap_hi(int x, int n) { return x >= n ? x - n : x; }
+
 __device__ __forceinline__ float4 ld4(const float *sm, int off)
 {
     return *reinterpret_cast<const float4 *>(sm + off);
@@ -129,21 +134,24 @@ __device__ __forceinline__ void tb_item_geom(const TBTile &T, int item, int &X0,
 
 // stage-0 plane z of the tile at (X0, Y0) into the ring slot of load number n
 template <int M, int EY>
-__device__ __forceinline__ void tb_issue(const TBPipe &P, long long n, const TBTile &T, int X0, int Y0, int z)
+__device__ __forceinline__ void tb_issue(const TBPipe &P, long long n, const CUtensorMap *maps, int X0, int Y0,
+                                         int z)
 {
     using C = Cfg<M, EY>;
     const int j = (int)(n % C::S0);
     const uint32_t dst = P.sm_base + 4u * (uint32_t)(j * C::SLOT0);
     const uint32_t bar = P.bar_base + 8u * j;
     mbar_expect_tx(bar, (uint32_t)(C::SLOT0 * 4));
-    tma_load_3d(dst, &T.maps[0], X0 - TB_HX, Y0 - M, z, bar);
-    tma_load_3d(dst + 4u * C::PLANE, &T.maps[1], X0 - TB_HX, Y0 - M, z, bar);
-    tma_load_3d(dst + 8u * C::PLANE, &T.maps[2], X0 - TB_HX, Y0 - M, z, bar);
-    tma_load_3d(dst + 12u * C::PLANE, &T.maps[3], X0 - TB_HX, Y0 - M, z, bar);
+    tma_load_3d(dst, &maps[0], X0 - TB_HX, Y0 - M, z, bar);
+    tma_load_3d(dst + 4u * C::PLANE, &maps[1], X0 - TB_HX, Y0 - M, z, bar);
+    tma_load_3d(dst + 8u * C::PLANE, &maps[2], X0 - TB_HX, Y0 - M, z, bar);
+    tma_load_3d(dst + 12u * C::PLANE, &maps[3], X0 - TB_HX, Y0 - M, z, bar);
 }
 
 // Advance work items first, first + stride, ... < nitems by M steps.
-// get(item, local) returns the item's TBTile and sets its index in that tile.
+// get(item, local, maps) returns the item's TBTile (a reference to kernel
+// parameters for one grid; a register copy for the batch), its index in that
+// tile and the tensor maps of the tile's input state.
 // Returns false if a wait timed out (kStatusTimeout recorded, CTA must leave).
 template <int M, int EY, bool DMG, bool FOLD, class Get>
 __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &get, unsigned *status,
@@ -161,14 +169,16 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
     int item = first;
     if (item < nitems && tid == 0) {
         int local;
-        const TBTile &T = get(item, local);
+        const CUtensorMap *mp;
+        const TBTile &T = get(item, local, mp);
         int X0, Y0, zb, ze;
         tb_item_geom<M, EY>(T, local, X0, Y0, zb, ze);
-        tb_issue<M, EY>(P, P.nload, T, X0, Y0, zb - M);
+        tb_issue<M, EY>(P, P.nload, mp, X0, Y0, zb - M);
     }
     for (; item < nitems; item += stride) {
         int local;
-        const TBTile A = get(item, local);  // by value: the descriptor may live in global memory
+        const CUtensorMap *maps;
+        decltype(auto) A = get(item, local, maps);
         int X0, Y0, zb, ze;
         tb_item_geom<M, EY>(A, local, X0, Y0, zb, ze);
         const int L = ze - zb + 2 * M;   // stage-0 planes zb-M .. ze+M-1
@@ -185,29 +195,37 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
             xm_ok[j] = x > 0 && (j > 0 || qx > 0);
             xp_ok[j] = x + 1 < A.nx && (j < 3 || qx < TB_QX - 1);
         }
+        const bool x_inner = xm_ok[0] && xm_ok[1] && xm_ok[2] && xm_ok[3] && xp_ok[0] && xp_ok[1] &&
+                             xp_ok[2] && xp_ok[3];
         const bool out_quad = qx >= 1 && qx < TB_QX - 1 && yl >= M && yl < EY - M && row_in && xg0 < A.nx;
 
-        float part[M + 1][4], mx[M + 1][4];
+        // per-voxel partials of the planes in flight: row k-1 belongs to stage k
+        float part[M][4], mx[M][4];
 #pragma unroll
-        for (int k = 0; k <= M; ++k)
+        for (int k = 0; k < M; ++k)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 part[k][j] = 0.f;
                 mx[k][j] = -3.0e38f;
             }
-        int s3_cur = 0;  // stage-ring slot of stage-0 plane p0 (it % 3)
+        // ring slots of stage-0 plane p0, advanced incrementally (no division):
+        // ring0 slot = nload % S0 with mbarrier phase (nload / S0) & 1; stage rings it % 3
+        int s0_cur = (int)(P.nload % S0);
+        uint32_t phase = (uint32_t)((P.nload / S0) & 1);
+        int s3_cur = 0;
 
         for (int it = 0; it < L; ++it, ++P.nload) {
             const int p0 = zb - M + it;
             if (tid == 0) {
                 if (it + 1 < L) {
-                    tb_issue<M, EY>(P, P.nload + 1, A, X0, Y0, p0 + 1);
+                    tb_issue<M, EY>(P, P.nload + 1, maps, X0, Y0, p0 + 1);
                 } else if (item + stride < nitems) {  // first plane of the next item
                     int local1;
-                    const TBTile &T1 = get(item + stride, local1);
+                    const CUtensorMap *maps1;
+                    decltype(auto) T1 = get(item + stride, local1, maps1);
                     int X1, Y1, zb1, ze1;
                     tb_item_geom<M, EY>(T1, local1, X1, Y1, zb1, ze1);
-                    tb_issue<M, EY>(P, P.nload + 1, T1, X1, Y1, zb1 - M);
+                    tb_issue<M, EY>(P, P.nload + 1, maps1, X1, Y1, zb1 - M);
                 }
             }
             // output-stage operands of plane p0 - M, loaded early to hide their latency
@@ -226,7 +244,7 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
                 }
             }
 #pragma unroll
-            for (int k = M; k >= 2; --k)
+            for (int k = M - 1; k >= 1; --k)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     part[k][j] = part[k - 1][j];
@@ -234,15 +252,15 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
                 }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                part[1][j] = 0.f;
-                mx[1][j] = -3.0e38f;
+                part[0][j] = 0.f;
+                mx[0][j] = -3.0e38f;
             }
-            const int s0_cur = (int)(P.nload % S0);
-            const bool ok = mbar_wait(bar_base + 8u * s0_cur, (uint32_t)((P.nload / S0) & 1));
+            const bool ok = mbar_wait(bar_base + 8u * s0_cur, phase);
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) {
                     atomicOr(status, kStatusTimeout);
-                    mbar_wait(bar_base + 8u * ((P.nload + 1) % S0), (uint32_t)(((P.nload + 1) / S0) & 1));
+                    const int sn = s0_cur + 1 == S0 ? 0 : s0_cur + 1;
+                    mbar_wait(bar_base + 8u * sn, sn == 0 ? phase ^ 1u : phase);
                 }
                 return false;
             }
@@ -250,21 +268,21 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
             for (int k = 1; k <= M; ++k) {
                 const int q = p0 - k;
                 if (it >= 2 * k && q >= 0 && q < A.nz && row_in && yl >= k && yl < EY - k) {
-                    const int sq0 = (s0_cur + S0 - k) % S0;   // ring0 slot of plane q
-                    const int s3q = (s3_cur + 3 * M - k) % 3; // stage-ring slot of plane q
-                    const int cb = sq0 * C::SLOT0;             // coefficients of plane q
+                    // ring slots of planes q-1, q, q+1 (compile-time k, conditional wrap)
+                    const int sq0 = wrap_lo(s0_cur - k, S0);          // ring0 slot of plane q
+                    const int s3q = wrap_lo(s3_cur - (k % 3), 3);      // stage-ring slot of plane q
+                    const int cb = sq0 * C::SLOT0;                      // coefficients of plane q
                     const bool zm_ok = q > 0, zp_ok = q + 1 < A.nz;
-                    // hi/lo planes q-1, q, q+1 of stage k-1
                     int bc, bm, bp;
                     if (k == 1) {
                         bc = cb;
-                        bm = ((sq0 + S0 - 1) % S0) * C::SLOT0;
-                        bp = ((sq0 + 1) % S0) * C::SLOT0;
+                        bm = wrap_lo(sq0 - 1, S0) * C::SLOT0;
+                        bp = wrap_hi(sq0 + 1, S0) * C::SLOT0;
                     } else {
                         const int rk = C::RING_OFF + (k - 2) * 3 * C::RINGK;
                         bc = rk + s3q * C::RINGK;
-                        bm = rk + ((s3q + 2) % 3) * C::RINGK;
-                        bp = rk + ((s3q + 1) % 3) * C::RINGK;
+                        bm = rk + wrap_lo(s3q - 1, 3) * C::RINGK;
+                        bp = rk + wrap_hi(s3q + 1, 3) * C::RINGK;
                     }
                     const float4 ch = ld4(sm, bc + id), cl = ld4(sm, bc + PLANE + id);
                     const float4 ymh = ld4(sm, bc + id - TB_EX), yml = ld4(sm, bc + PLANE + id - TB_EX);
@@ -276,32 +294,60 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
                     const float rh = sm[bc + id + hi_off], rl = sm[bc + PLANE + id + hi_off];
                     const uint4 w4 = *reinterpret_cast<const uint4 *>(sm + cb + 2 * PLANE + id);
                     const float4 s4 = ld4(sm, cb + 3 * PLANE + id);
-                    const float c_[4] = {ch.x, ch.y, ch.z, ch.w}, cl_[4] = {cl.x, cl.y, cl.z, cl.w};
-                    const float ymh_[4] = {ymh.x, ymh.y, ymh.z, ymh.w}, yml_[4] = {yml.x, yml.y, yml.z, yml.w};
-                    const float yph_[4] = {yph.x, yph.y, yph.z, yph.w}, ypl_[4] = {ypl.x, ypl.y, ypl.z, ypl.w};
-                    const float zmh_[4] = {zmh.x, zmh.y, zmh.z, zmh.w}, zml_[4] = {zml.x, zml.y, zml.z, zml.w};
-                    const float zph_[4] = {zph.x, zph.y, zph.z, zph.w}, zpl_[4] = {zpl.x, zpl.y, zpl.z, zpl.w};
-                    const uint32_t w_[4] = {w4.x, w4.y, w4.z, w4.w};
-                    const float s_[4] = {s4.x, s4.y, s4.z, s4.w};
-                    float nh_[4], nl_[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float c = c_[j], l = cl_[j];
-                        const float xmh = j == 0 ? lh : c_[j - 1], xml = j == 0 ? ll : cl_[j - 1];
-                        const float xph = j == 3 ? rh : c_[j + 1], xpl = j == 3 ? rl : cl_[j + 1];
-                        float S = 0.f;
-                        S = acc(S, xm_ok[j] ? cdiff(xmh, xml, c, l) : 0.f);
-                        S = acc(S, xp_ok[j] ? cdiff(xph, xpl, c, l) : 0.f);
-                        S = acc(S, ym_ok ? cdiff(ymh_[j], yml_[j], c, l) : 0.f);
-                        S = acc(S, yp_ok ? cdiff(yph_[j], ypl_[j], c, l) : 0.f);
-                        S = acc(S, zm_ok ? cdiff(zmh_[j], zml_[j], c, l) : 0.f);
-                        S = acc(S, zp_ok ? cdiff(zph_[j], zpl_[j], c, l) : 0.f);
-                        cupdate(c, l, S, bf16_to_float(w_[j] & 0xffffu), bf16_to_float(w_[j] >> 16), s_[j],
-                                nh_[j], nl_[j]);
-                        const float val = __fadd_rn(nh_[j], nl_[j]);
-                        mx[k][j] = fmaxf(mx[k][j], val);
-                        if (DMG) part[k][j] = __fadd_rn(part[k][j], arrhenius_inc(val, A.c0, A.c1, A.TK0));
+                    // voxel pairs (0,1) and (2,3) of the quad
+                    const float2 C01 = make_float2(ch.x, ch.y), C23 = make_float2(ch.z, ch.w);
+                    const float2 L01 = make_float2(cl.x, cl.y), L23 = make_float2(cl.z, cl.w);
+                    // neighbour differences, fixed order x-, x+, y-, y+, z-, z+; a neighbour
+                    // outside the grid adds +0
+                    const float2 z2 = make_float2(0.f, 0.f);
+                    float2 S01 = z2, S23 = z2, d01, d23;
+                    d01 = cdiff2(make_float2(lh, ch.x), make_float2(ll, cl.x), C01, L01);
+                    d23 = cdiff2(make_float2(ch.y, ch.z), make_float2(cl.y, cl.z), C23, L23);
+                    S01 = add2(S01, make_float2(xm_ok[0] ? d01.x : 0.f, xm_ok[1] ? d01.y : 0.f));
+                    S23 = add2(S23, make_float2(xm_ok[2] ? d23.x : 0.f, xm_ok[3] ? d23.y : 0.f));
+                    d01 = cdiff2(make_float2(ch.y, ch.z), make_float2(cl.y, cl.z), C01, L01);
+                    d23 = cdiff2(make_float2(ch.w, rh), make_float2(cl.w, rl), C23, L23);
+                    S01 = add2(S01, make_float2(xp_ok[0] ? d01.x : 0.f, xp_ok[1] ? d01.y : 0.f));
+                    S23 = add2(S23, make_float2(xp_ok[2] ? d23.x : 0.f, xp_ok[3] ? d23.y : 0.f));
+                    d01 = cdiff2(make_float2(ymh.x, ymh.y), make_float2(yml.x, yml.y), C01, L01);
+                    d23 = cdiff2(make_float2(ymh.z, ymh.w), make_float2(yml.z, yml.w), C23, L23);
+                    S01 = add2(S01, ym_ok ? d01 : z2);
+                    S23 = add2(S23, ym_ok ? d23 : z2);
+                    d01 = cdiff2(make_float2(yph.x, yph.y), make_float2(ypl.x, ypl.y), C01, L01);
+                    d23 = cdiff2(make_float2(yph.z, yph.w), make_float2(ypl.z, ypl.w), C23, L23);
+                    S01 = add2(S01, yp_ok ? d01 : z2);
+                    S23 = add2(S23, yp_ok ? d23 : z2);
+                    d01 = cdiff2(make_float2(zmh.x, zmh.y), make_float2(zml.x, zml.y), C01, L01);
+                    d23 = cdiff2(make_float2(zmh.z, zmh.w), make_float2(zml.z, zml.w), C23, L23);
+                    S01 = add2(S01, zm_ok ? d01 : z2);
+                    S23 = add2(S23, zm_ok ? d23 : z2);
+                    d01 = cdiff2(make_float2(zph.x, zph.y), make_float2(zpl.x, zpl.y), C01, L01);
+                    d23 = cdiff2(make_float2(zph.z, zph.w), make_float2(zpl.z, zpl.w), C23, L23);
+                    S01 = add2(S01, zp_ok ? d01 : z2);
+                    S23 = add2(S23, zp_ok ? d23 : z2);
+                    const float2 a01 = make_float2(bf16_to_float(w4.x & 0xffffu), bf16_to_float(w4.y & 0xffffu));
+                    const float2 a23 = make_float2(bf16_to_float(w4.z & 0xffffu), bf16_to_float(w4.w & 0xffffu));
+                    const float2 b01 = make_float2(bf16_to_float(w4.x >> 16), bf16_to_float(w4.y >> 16));
+                    const float2 b23 = make_float2(bf16_to_float(w4.z >> 16), bf16_to_float(w4.w >> 16));
+                    float2 H01, H23, N01, N23;
+                    cupdate2(C01, L01, S01, a01, b01, make_float2(s4.x, s4.y), H01, N01);
+                    cupdate2(C23, L23, S23, a23, b23, make_float2(s4.z, s4.w), H23, N23);
+                    const float2 V01 = add2(H01, N01), V23 = add2(H23, N23);
+                    mx[k - 1][0] = fmaxf(mx[k - 1][0], V01.x);
+                    mx[k - 1][1] = fmaxf(mx[k - 1][1], V01.y);
+                    mx[k - 1][2] = fmaxf(mx[k - 1][2], V23.x);
+                    mx[k - 1][3] = fmaxf(mx[k - 1][3], V23.y);
+                    if (DMG) {
+                        const float2 i01 = arrhenius_inc2(V01, A.c0, A.c1, A.TK0);
+                        const float2 i23 = arrhenius_inc2(V23, A.c0, A.c1, A.TK0);
+                        const float2 p01 = add2(make_float2(part[k - 1][0], part[k - 1][1]), i01);
+                        const float2 p23 = add2(make_float2(part[k - 1][2], part[k - 1][3]), i23);
+                        part[k - 1][0] = p01.x;
+                        part[k - 1][1] = p01.y;
+                        part[k - 1][2] = p23.x;
+                        part[k - 1][3] = p23.y;
                     }
+                    const float nh_[4] = {H01.x, H01.y, H23.x, H23.y}, nl_[4] = {N01.x, N01.y, N23.x, N23.y};
                     if (k < M) {
                         const int bo = C::RING_OFF + ((k - 1) * 3 + s3q) * C::RINGK;
                         *reinterpret_cast<float4 *>(sm + bo + id) = make_float4(nh_[0], nh_[1], nh_[2], nh_[3]);
@@ -316,7 +362,7 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
                             o_h[j] = xin[j] ? nh_[j] : 0.f;
                             o_l[j] = xin[j] ? nl_[j] : 0.f;
                             bad |= xin[j] && !isfinite(nh_[j]);
-                            if (xin[j] && mx[k][j] >= A.thr) lbits |= 1u << (8 * j);
+                            if (xin[j] && mx[k - 1][j] >= A.thr) lbits |= 1u << (8 * j);
                         }
                         *reinterpret_cast<float4 *>(A.hi_out + gio) = make_float4(o_h[0], o_h[1], o_h[2], o_h[3]);
                         *reinterpret_cast<float4 *>(A.lo_out + gio) = make_float4(o_l[0], o_l[1], o_l[2], o_l[3]);
@@ -326,7 +372,7 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
                             float P[4] = {carry4.x, carry4.y, carry4.z, carry4.w};
 #pragma unroll
                             for (int j = 0; j < 4; ++j)
-                                if (xin[j]) P[j] = __fadd_rn(P[j], part[k][j]);
+                                if (xin[j]) P[j] = __fadd_rn(P[j], part[k - 1][j]);
                             if (FOLD) {
                                 double om[4] = {om01.x, om01.y, om23.x, om23.y};
 #pragma unroll
@@ -343,6 +389,10 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
                 __syncthreads();
             }
             s3_cur = s3_cur + 1 == 3 ? 0 : s3_cur + 1;
+            if (++s0_cur == S0) {
+                s0_cur = 0;
+                phase ^= 1u;
+            }
         }
     }
     return true;
@@ -381,14 +431,14 @@ __global__ void __launch_bounds__(Cfg<M, EY>::THREADS, Cfg<M, EY>::MINB)
 {
     TBPipe P;
     if (!tb_setup<M, EY>(P, status)) return;
-    TBTile T = T0;
-    T.maps = maps.m;
-    auto get = [&](int item, int &local) -> const TBTile & {
+    // the descriptor stays in kernel-parameter space (constant-bank operands)
+    auto get = [&](int item, int &local, const CUtensorMap *&mp) -> const TBTile & {
         local = item;
-        return T;
+        mp = maps.m;
+        return T0;
     };
     bool bad = false;
-    tb_run<M, EY, DMG, FOLD>(P, blockIdx.x, gridDim.x, T.xt * T.yt * T.zc, get, status, bad);
+    tb_run<M, EY, DMG, FOLD>(P, blockIdx.x, gridDim.x, T0.xt * T0.yt * T0.zc, get, status, bad);
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusNonfinite);
 }
 
@@ -443,7 +493,7 @@ __global__ void __launch_bounds__(Cfg<M, EY>::THREADS, Cfg<M, EY>::MINB)
     if (!tb_setup<M, EY>(P, status)) return;
     bool bad = false;
     for (int t = 0; t < ntime; ++t) {
-        auto get = [&](int item, int &local) -> const TBTile & {
+        auto get = [&](int item, int &local, const CUtensorMap *&mp) -> TBTile {
             int lo = 0, hi = nmem - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
@@ -451,7 +501,9 @@ __global__ void __launch_bounds__(Cfg<M, EY>::THREADS, Cfg<M, EY>::MINB)
                 else hi = mid - 1;
             }
             local = item - mem[lo].item_begin;
-            return mem[lo].tile[(mem[lo].cur0 + t) & 1];
+            const TBTile T = mem[lo].tile[(mem[lo].cur0 + t) & 1];  // register copy of the global descriptor
+            mp = T.maps;
+            return T;
         };
         const bool fold = DMG && ((t + 1) % fold_every == 0 || t == ntime - 1);
         const bool ok = fold ? tb_run<M, EY, DMG, true>(P, blockIdx.x, gridDim.x, nitems, get, status, bad)

@@ -23,9 +23,10 @@ def test_blocked_equals_one_step(sched, dims):
     assert np.array_equal(a["theta"], b["theta"])
     assert np.array_equal(a["T"], b["T"])
     assert np.array_equal(a["latch"], b["latch"])
-    # the blocked kernel sums the increments of a block in FP32 before the FP64 Kahan step
+    # the blocked kernel sums a block's increments in FP32 before adding them to the
+    # FP32 carry of the FP64 integral; both carries hold <= 128 steps (~128 * 2^-24)
     rel = np.abs(a["omega"] - b["omega"]) / np.maximum(a["omega"], 1e-300)
-    assert rel.max() <= 1e-6
+    assert rel.max() <= 2e-5
 
 
 @pytest.mark.parametrize("sched", [(2, 0), (3, 0), (4, 0), (2, 1)])
