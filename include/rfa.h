@@ -255,6 +255,13 @@ rfa_status rfa_batch_autotune(rfa_batch *b, const char *cache_path);
  * (when 0, rfa_last_error() gives the reason capture was not used). */
 rfa_status rfa_batch_get_schedule(rfa_batch *b, int *tb_depth, int *tile_variant, int *uses_graph);
 
+/* Diagnostic (the paper has no counterpart): launch a kernel that waits on a
+ * device flag nothing sets, with the same bounded-spin pattern as the
+ * library's real waits, and report how it ended.  Returns RFA_E_TIMEOUT when the
+ * wait gave up after spin_limit_cycles (1..2^32) SM clocks; the context stays
+ * usable.  Uses the current device and the legacy default stream; synchronous. */
+rfa_status rfa_selftest_wait_timeout(long long spin_limit_cycles);
+
 /* Wait for the grid's stream and report deferred device errors. */
 rfa_status rfa_synchronize(rfa_grid *g);
 

@@ -33,7 +33,7 @@ EXPORTED = ("rfa_create_grid", "rfa_destroy_grid", "rfa_set_tissue", "rfa_place_
             "rfa_set_schedule", "rfa_get_schedule", "rfa_autotune", "rfa_batch_create",
             "rfa_batch_step", "rfa_batch_destroy", "rfa_synchronize", "rfa_steps_done",
             "rfa_last_error", "rfa_necrosis_reduce_noalloc", "rfa_batch_autotune",
-            "rfa_batch_get_schedule")
+            "rfa_batch_get_schedule", "rfa_selftest_wait_timeout")
 
 
 class RfaError(RuntimeError):
@@ -94,6 +94,7 @@ def lib():
         "rfa_necrosis_reduce_noalloc": [P, D, P],
         "rfa_batch_autotune": [P, ctypes.c_char_p],
         "rfa_batch_get_schedule": [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)],
+        "rfa_selftest_wait_timeout": [ctypes.c_longlong],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -280,6 +281,10 @@ def rfa_batch_get_schedule(b):
     _check(lib().rfa_batch_get_schedule(b, ctypes.byref(d), ctypes.byref(v), ctypes.byref(gr)),
            "rfa_batch_get_schedule")
     return d.value, v.value, bool(gr.value)
+
+
+def rfa_selftest_wait_timeout(spin_limit_cycles: int):
+    _check(lib().rfa_selftest_wait_timeout(int(spin_limit_cycles)), "rfa_selftest_wait_timeout")
 
 
 def rfa_synchronize(g):

@@ -346,3 +346,30 @@ def random_small_case(seed: int, nx: int, ny: int, nz: int, h: float = 1e-3, dt:
     return Case(name=f"small{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, h=h, dt=dt, nsteps=nsteps,
                 labels=labels, table=default_table(), needle=needle,
                 damage=damage if damage is not None else Damage(), face_bc=face_bc)
+
+
+def paper_tip_case(T_tip_C: float = 90.0, n: int = 64, nsteps: int = 1200) -> Case:
+    """The paper's evaluation set-up (Sec. "Evaluation Methods"): 0.5 mm voxels,
+    a needle tip modelled as a voxel hemisphere five voxels across in x and y
+    and three voxels deep in z, held at T_tip (90 or 60 C), time step 0.1 s,
+    liver with the paper's printed constants (Q_m = 10714 W/m^3); no RF source.
+    Label 1 is the tip.  Probe voxels: see paper_tip_probes()."""
+    h = 0.5e-3
+    labels = np.zeros((n, n, n), dtype=np.uint8)
+    c = n // 2
+    for dz in range(3):
+        for dy in range(-2, 3):
+            for dx in range(-2, 3):
+                if (dx / 2.5) ** 2 + (dy / 2.5) ** 2 + (dz / 3.0) ** 2 <= 1.0:
+                    labels[c + dz, c + dy, c + dx] = 1
+    tip = Tissue(fixed=1, T_fixed_C=T_tip_C)
+    return Case(name=f"papertip{int(T_tip_C)}", nx=n, ny=n, nz=n, h=h, dt=0.1, nsteps=nsteps,
+                labels=labels, table=[paper_liver(), tip], needle=Needle(kind=STRAIGHT, power=0.0),
+                damage=Damage(enable=0, T_thr_C=42.5))
+
+
+def paper_tip_probes(n: int = 64):
+    """Voxel indices (z, y, x) 2.5 mm and 5 mm beyond the tip's outer x face."""
+    c = n // 2
+    return {"2.5mm": (c, c, c + 2 + 5), "5mm": (c, c, c + 2 + 10)}
+

@@ -103,3 +103,14 @@ def test_erfc_line_on_gpu():
     orc = run_oracle(case, rfa.PARAM_F64, 800)
     gpu = run_gpu(case, rfa.STATE_F64, rfa.PARAM_F64, 800)
     compare(case, gpu, orc, rfa.STATE_F64)
+
+
+@pytest.mark.parametrize("T_tip", [90.0, 60.0])
+def test_paper_fixed_tip_setup(T_tip):
+    """The paper's hemispherical 90 C / 60 C tip at 0.5 mm, dt = 0.1 s, 120 s."""
+    case = ph.paper_tip_case(T_tip, nsteps=1200)
+    orc = run_oracle(case, rfa.PARAM_BF16, 1200, damage=False)
+    gpu = run_gpu(case, rfa.STATE_F32C, rfa.PARAM_BF16, 1200, damage=False)
+    compare(case, gpu, orc, rfa.STATE_F32C, damage=False)
+    gpu64 = run_gpu(case, rfa.STATE_F64, rfa.PARAM_BF16, 1200, damage=False)
+    compare(case, gpu64, orc, rfa.STATE_F64, damage=False)

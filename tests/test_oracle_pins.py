@@ -312,3 +312,25 @@ def test_dense_brute_force_latch_and_damage():
     om = np.array([math.fsum(v) for v in incs])
     assert np.array_equal(st.latch.ravel() != 0, latch)
     assert np.allclose(st.omega.ravel(), om, rtol=1e-12, atol=0)
+
+
+# ------------------------------------------------------------------ paper set-up
+def test_paper_fixed_tip_experiment_properties():
+    """Sec. 'Evaluation Methods' / 'Simulation of Heat Propagation': a 5x5x3-voxel
+    hemispherical tip at 0.5 mm held at 90 C, dt = 0.1 s.  The simulated heating is
+    monotone at both probes, nearer is hotter, and the 5 mm probe stays below the
+    42.5 C tissue-death threshold after one minute (as the paper reports)."""
+    case = ph.paper_tip_case(90.0, nsteps=1200)
+    m = oracle.setup(case, "f64")
+    st = oracle.initial_state(m)
+    pr = ph.paper_tip_probes()
+    prev = None
+    for k in range(12):
+        oracle.run(m, st, 100)
+        t25, t50 = (st.theta[pr["2.5mm"]] + 37.0, st.theta[pr["5mm"]] + 37.0)
+        assert t25 > t50 > 37.0
+        if prev is not None:
+            assert t25 > prev[0] and t50 > prev[1]
+        prev = (t25, t50)
+        if k == 5:      # t = 60 s
+            assert t50 < 42.5
