@@ -355,8 +355,9 @@ def run_ours(args):
                              if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
         except rfa.RfaError:
             pass
-    elif args.schedule.startswith("tb"):
-        g.set_schedule(int(args.schedule[2:]), 0)
+    elif args.schedule.startswith("tb"):        # tbN or tbNvV: depth N, tile variant V
+        dv = args.schedule[2:].split("v")
+        g.set_schedule(int(dv[0]), int(dv[1]) if len(dv) > 1 else 0)
     depth, variant = rfa.rfa_get_schedule(g.handle)
 
     step_ms = []
@@ -499,7 +500,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="umbrella256")
     ap.add_argument("--sim-steps", type=int, default=None, help="override time steps per bench step")
-    ap.add_argument("--schedule", default="auto", help="auto | plain | tbN")
+    ap.add_argument("--schedule", default="auto", help="auto | plain | tbN | tbNvV")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

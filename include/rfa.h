@@ -224,7 +224,11 @@ rfa_status rfa_set_state(rfa_grid *g, const void *blob, size_t n);
 
 /*
  * Temporal blocking: advance tb_depth steps per launch (1 = one step per
- * launch); tile_variant selects the xy tile of the blocked kernel (0 = default).
+ * launch); tile_variant selects the xy tile of the blocked kernel (0: 64 x 12
+ * output voxels per plane at depth 2, 64 x 10 at depth 3; 1: 64 x 28 at depth
+ * 2; 2: 64 x 10 at depth 2 with planes requested two ahead).  The blocked kernel needs compensated FP32 state, BF16 coefficients and
+ * Dirichlet faces; otherwise rfa_set_schedule returns RFA_E_UNSUPPORTED and
+ * the autotuner keeps one step per launch.
  * rfa_autotune times the candidates on a scratch copy of the grid's state and
  * keeps the fastest; cache_path (may be NULL) is a JSON file read and updated.
  */
@@ -236,7 +240,7 @@ rfa_status rfa_autotune(rfa_grid *g, const char *cache_path);
  * Batched stepping of several grids in one persistent launch per call
  * (independent needle configurations on grids of uneven size; the paper runs
  * one configuration at a time).  Members must be F32C grids with BF16
- * coefficients and tissue set, all on the same stream and with the same damage
+ * coefficients, Dirichlet faces and tissue set, all on the same stream and with the same damage
  * setting; they stay owned by the caller and must outlive the batch.
  * rfa_batch_step advances every member by nsteps: whole blocks of tb_depth steps
  * in one cooperative persistent launch (replayed from a CUDA graph captured per

@@ -133,7 +133,7 @@ extern "C" rfa_status rfa_autotune(rfa_grid *g, const char *cache_path)
         }
     }
     std::vector<std::pair<int, int>> cands = {{1, 0}};
-    for (int v = 0; v <= 1; ++v)
+    for (int v = 0; v <= 2; ++v)
         for (int d = 2; d <= 8; ++d)
             if (tb_supported(g, d, v)) cands.push_back({d, v});
     if (cands.size() == 1) {
@@ -155,7 +155,7 @@ extern "C" rfa_status rfa_autotune(rfa_grid *g, const char *cache_path)
     cudaEventCreate(&e1);
     const Schedule saved = g->sched;
     const bool dmg = g->dmg != 0;
-    // 24 steps is a whole number of blocks for every depth up to 4
+    // 24 steps is a whole number of blocks for every depth (2 or 3)
     const int64_t nwarm = 12, ntime = 24;
     float best = 1e30f;
     Schedule pick = saved;

@@ -187,6 +187,8 @@ rfa_status rfa_batch_create(rfa_grid *const *members, int n, rfa_batch **out)
         if (!g->have_tissue) return bfail(RFA_E_STATE, "every member needs rfa_set_tissue first");
         if (g->sp != RFA_STATE_F32C || g->pp != RFA_PARAM_BF16)
             return bfail(RFA_E_UNSUPPORTED, "batched stepping needs compensated FP32 state and BF16 coefficients");
+        if (g->face != RFA_FACE_DIRICHLET)
+            return bfail(RFA_E_UNSUPPORTED, "batched stepping needs Dirichlet faces");
         if (g->stream != members[0]->stream) return bfail(RFA_E_INVALID, "members must share one stream");
         if (g->dmg != members[0]->dmg) return bfail(RFA_E_INVALID, "members must share the damage setting");
         for (int k = 0; k < m; ++k)
@@ -246,13 +248,14 @@ rfa_status rfa_batch_autotune(rfa_batch *b, const char *cache_path)
         const std::string s = ss.str();
         const size_t pos = s.find(std::string("\"") + key + "\"");
         int d = 0, v = 0;
-        if (pos != std::string::npos && std::sscanf(s.c_str() + s.find('[', pos) + 1, "%d , %d", &d, &v) == 2) {
+        if (pos != std::string::npos && std::sscanf(s.c_str() + s.find('[', pos) + 1, "%d , %d", &d, &v) == 2 &&
+            ((v == 0 && (d == 2 || d == 3)) || ((v == 1 || v == 2) && d == 2))) {
             b->depth = d;
             b->variant = v;
             return build_plan(b);
         }
     }
-    const int cands[4][2] = {{2, 0}, {3, 0}, {4, 0}, {2, 1}};
+    const int cands[4][2] = {{2, 0}, {3, 0}, {2, 1}, {2, 2}};
     // snapshot every member's evolving state; restored after each trial
     std::vector<MemberSnap> snaps(b->members.size());
     rfa_status st = RFA_OK;
@@ -298,7 +301,7 @@ rfa_status rfa_batch_autotune(rfa_batch *b, const char *cache_path)
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const bool graphs = b->use_graphs;
-    for (int c = 0; c < 4 && st == RFA_OK; ++c) {
+    for (int c = 0; c < (int)(sizeof cands / sizeof cands[0]) && st == RFA_OK; ++c) {
         b->depth = cands[c][0];
         b->variant = cands[c][1];
         b->use_graphs = false;

@@ -10,19 +10,21 @@
 // Tiling.  A CTA owns an output tile of 64 (x) by TY = EY - 2M (y) voxels and a
 // chunk of z planes.  It loads the tile plus a 4-voxel x halo and an M-voxel y
 // halo (72 x EY columns) plane by plane with TMA (cp.async.bulk.tensor, one
-// mbarrier per ring slot, zero fill outside the grid) and streams along z; each
-// thread owns a quad of 4 consecutive x voxels of one tile row:
-// stage k (1 <= k <= M) computes step k on plane p0 - k when stage-0 plane p0
-// has arrived, reading the three planes q-1, q, q+1 of stage k-1 from a
-// 3-plane shared-memory ring.  The last stage writes the output tile to HBM.
-// The valid region shrinks by one voxel per stage in x and y (trapezoid).
+// mbarrier per ring slot, zero fill outside the grid) and streams along z.
+// A thread works on quads of 4 consecutive x voxels of one tile row (paired
+// FP32 instructions on voxels (0,1) and (2,3)): stage k (1 <= k <= M) computes
+// step k on plane p0 - k when stage-0 plane p0 has arrived, reading the three
+// planes q-1, q, q+1 of stage k-1 from a 3-plane shared-memory ring.  The
+// valid region shrinks by one voxel per stage in x and y (trapezoid); stage
+// k < M covers tile rows k .. EY-1-k, the last stage only the output tile, and
+// writes it to HBM.  Two CTA barriers per plane for M = 2.
 //
 // Numerics.  Every stage uses the same update (rfa_update.cuh) and the same
 // neighbour order as the one-step kernel, so a launch of depth M produces
 // bit-identical states to M one-step launches.  The latch takes the maximum
-// of the M new values; the M Arrhenius increments are summed in FP32
-// registers and added to the FP32 carry of the FP64 integral; on launches
-// flagged `fold` the carry is folded into the FP64 value (error-free TwoSum).
+// of the M new values; the M Arrhenius increments are summed in FP32 and
+// added to the FP32 carry of the FP64 integral; on launches flagged `fold`
+// the carry is folded into the FP64 value (error-free TwoSum).
 //
 // Waits on mbarriers are bounded (clock64); on timeout the kernel records
 // kStatusTimeout in the grid's status word and every thread leaves.
@@ -47,19 +49,41 @@ constexpr int TB_TX = 64;       // output tile width
 constexpr int TB_HX = 4;        // x halo (keeps the TMA x coordinate 16-byte aligned)
 constexpr int TB_QX = TB_EX / 4;  // quads (4 consecutive x voxels) per tile row
 
-template <int M, int EY>
+// Tile variants: height EY of the loaded tile and prefetch distance PD (stage-0
+// planes requested ahead of the one being consumed).
+//   0: EY = 16, PD = 1 (2 CTAs per SM at depth 2)
+//   1: EY = 32, PD = 1 (1 CTA per SM)
+//   2: EY = 14, PD = 2 (2 CTAs per SM at depth 2)
+__host__ __device__ constexpr int tile_ey(int v) { return v == 1 ? 32 : v == 2 ? 14 : 16; }
+__host__ __device__ constexpr int tile_pd(int v) { return v == 2 ? 2 : 1; }
+
+template <int M, int V>
 struct Cfg {
-    static constexpr int THREADS = TB_QX * EY;   // one thread per quad of the tile plane
-    static constexpr int TY = EY - 2 * M;        // output rows per tile
-    static constexpr int S0 = M + 2;             // stage-0 ring slots (planes p0-M .. p0+1)
-    static constexpr int PLANE = TB_EX * EY;     // floats per tile plane
-    static constexpr int SLOT0 = 4 * PLANE;      // stage-0 slot: hi, lo, ab, s planes
-    static constexpr int RINGK = 2 * PLANE;      // stage-k slot: hi, lo planes
-    static constexpr int RING_OFF = S0 * SLOT0;  // float offset of the stage rings
-    static constexpr int BAR_OFF = RING_OFF + (M - 1) * 3 * RINGK;
+    static constexpr int EY = tile_ey(V);
+    static constexpr int PD = tile_pd(V);
+    static constexpr int TY = EY - 2 * M;                 // output rows per tile
+    static constexpr int NQ1 = (EY - 2) * TB_QX;          // quads of stage 1 (tile rows 1 .. EY-2)
+    static constexpr int NQO = TY * (TB_QX - 2);          // quads of the last stage (the output tile)
+    static constexpr int THREADS = (NQ1 + 31) / 32 * 32;  // one thread per stage-1 quad
+    static constexpr int S0 = M + 1 + PD;                 // stage-0 ring slots (planes p0-M .. p0+PD)
+    static constexpr int BOX = TB_EX * EY;                // floats of one TMA box (a tile plane)
+    // stride of the planes in shared memory: TMA destinations need 128-byte alignment
+    static constexpr int PLANE = (BOX + 31) / 32 * 32;
+    static constexpr int SLOT0 = 4 * PLANE;               // stage-0 slot: hi, lo, ab, s planes
+    // ring of stage k (1 <= k < M): 3 slots of hi, lo; from stage 2 on also the
+    // running Arrhenius sum and the running maximum of the voxel's values
+    __host__ __device__ static constexpr int ring_planes(int k) { return k >= 2 ? 4 : 2; }
+    __host__ __device__ static constexpr int ring_off(int k)
+    {
+        int o = S0 * SLOT0;
+        for (int j = 1; j < k; ++j) o += 3 * ring_planes(j) * PLANE;
+        return o;
+    }
+    static constexpr int BAR_OFF = ring_off(M);
     static constexpr int SMEM = BAR_OFF * 4 + 8 * S0;
     static constexpr int MINB = SMEM <= 110 * 1024 ? 2 : 1;
-    static_assert(TY > 0 && M <= TB_HX && SMEM <= 227 * 1024, "bad tile");
+    static_assert(TY > 0 && M >= 2 && M <= TB_HX && SMEM <= 227 * 1024, "bad tile");
+    static_assert((PLANE * 4) % 128 == 0 && (SLOT0 * 4) % 128 == 0, "TMA destinations must be 128-byte aligned");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -121,27 +145,25 @@ struct TBPipe {
     long long nload;  // stage-0 planes loaded so far (ring slot and mbarrier phase)
 };
 
-template <int M, int EY>
+template <int M, int V>
 __device__ __forceinline__ void tb_item_geom(const TBTile &T, int item, int &X0, int &Y0, int &zb, int &ze)
 {
     const int tx = item % T.xt, r = item / T.xt;
     const int ty = r % T.yt, zi = r / T.yt;
     X0 = tx * TB_TX;
-    Y0 = ty * Cfg<M, EY>::TY;
+    Y0 = ty * Cfg<M, V>::TY;
     zb = (int)((long long)zi * T.nz / T.zc);
     ze = (int)((long long)(zi + 1) * T.nz / T.zc);
 }
 
-// stage-0 plane z of the tile at (X0, Y0) into the ring slot of load number n
-template <int M, int EY>
-__device__ __forceinline__ void tb_issue(const TBPipe &P, long long n, const CUtensorMap *maps, int X0, int Y0,
-                                         int z)
+// stage-0 plane z of the tile at (X0, Y0) into ring slot j
+template <int M, int V>
+__device__ __forceinline__ void tb_issue(const TBPipe &P, int j, const CUtensorMap *maps, int X0, int Y0, int z)
 {
-    using C = Cfg<M, EY>;
-    const int j = (int)(n % C::S0);
+    using C = Cfg<M, V>;
     const uint32_t dst = P.sm_base + 4u * (uint32_t)(j * C::SLOT0);
     const uint32_t bar = P.bar_base + 8u * j;
-    mbar_expect_tx(bar, (uint32_t)(C::SLOT0 * 4));
+    mbar_expect_tx(bar, (uint32_t)(4 * C::BOX * 4));   // four boxes of 4-byte elements
     tma_load_3d(dst, &maps[0], X0 - TB_HX, Y0 - M, z, bar);
     tma_load_3d(dst + 4u * C::PLANE, &maps[1], X0 - TB_HX, Y0 - M, z, bar);
     tma_load_3d(dst + 8u * C::PLANE, &maps[2], X0 - TB_HX, Y0 - M, z, bar);
@@ -153,79 +175,100 @@ __device__ __forceinline__ void tb_issue(const TBPipe &P, long long n, const CUt
 // parameters for one grid; a register copy for the batch), its index in that
 // tile and the tensor maps of the tile's input state.
 // Returns false if a wait timed out (kStatusTimeout recorded, CTA must leave).
-template <int M, int EY, bool DMG, bool FOLD, class Get>
+//
+// Thread -> quad maps (fixed for the kernel): stage k < M covers tile rows
+// k .. EY-1-k with all TB_QX quads (thread t takes quad t + k TB_QX); the last
+// stage covers only the output tile (thread t takes row M + t / 16, quad
+// 1 + t % 16), so no warp of the last stage works on halo columns.
+//
+// Faces: the kernel is used with Dirichlet faces only, where every face voxel
+// is fixed (a = b = s = 0) and its neighbour sum is multiplied by a = 0; voxels
+// outside the grid are loaded as zeros (TMA zero fill, a = b = s = 0) and
+// compute to exact zeros.  So no neighbour needs an in-grid test: every sum
+// that reaches a free voxel has only in-grid terms.
+//
+// Latch and damage: stage k >= 2 receives the values of stage k-1 as its
+// centre operand, so it evaluates the Arrhenius increment and the latch
+// maximum of those; the last stage adds those of its own result.  For M = 2
+// nothing is carried between planes; for M = 3 the running sum and maximum
+// travel with the values through the stage-2 ring.  The sums keep the order
+// ((inc_1 + inc_2) + ...) of the per-step evaluation.
+template <int M, int V, bool DMG, bool FOLD, class Get>
 __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &get, unsigned *status,
                        bool &bad)
 {
-    using C = Cfg<M, EY>;
+    using C = Cfg<M, V>;
     constexpr int S0 = C::S0, PLANE = C::PLANE;
     float *sm = P.sm;
     const uint32_t bar_base = P.bar_base;
     const int tid = threadIdx.x;
-    const int qx = tid % TB_QX, yl = tid / TB_QX;   // quad column and row in the tile
-    const int xl0 = 4 * qx;                          // first tile column of the quad
-    const int id = yl * TB_EX + xl0;                 // float offset of the quad in a plane
 
+    // per-stage quad of this thread: plane offset, x-neighbour offsets, active
+    int mid[M + 1], mxl[M + 1], mxh[M + 1];
+    bool mact[M + 1];
+#pragma unroll
+    for (int k = 1; k < M; ++k) {
+        const int u = tid + k * TB_QX;
+        const int yl = u / TB_QX, qx = u - yl * TB_QX;
+        mact[k] = tid < (C::EY - 2 * k) * TB_QX;
+        mid[k] = yl * TB_EX + 4 * qx;
+        mxl[k] = qx > 0 ? -1 : 0;             // the tile's outer columns read themselves
+        mxh[k] = qx < TB_QX - 1 ? 4 : 3;      // (their results are never used)
+    }
+    mact[M] = tid < C::NQO;
+    mid[M] = (M + tid / 16) * TB_EX + 4 * (1 + tid % 16);
+    mxl[M] = -1;
+    mxh[M] = 4;
+    mid[0] = mxl[0] = mxh[0] = 0;
+    mact[0] = false;
+
+    constexpr int PD = C::PD;
     int item = first;
-    if (item < nitems && tid == 0) {
+    if (item < nitems && tid == 0) {  // the first PD planes of the first item
         int local;
         const CUtensorMap *mp;
         const TBTile &T = get(item, local, mp);
         int X0, Y0, zb, ze;
-        tb_item_geom<M, EY>(T, local, X0, Y0, zb, ze);
-        tb_issue<M, EY>(P, P.nload, mp, X0, Y0, zb - M);
+        tb_item_geom<M, V>(T, local, X0, Y0, zb, ze);
+#pragma unroll
+        for (int j = 0; j < PD; ++j) tb_issue<M, V>(P, (int)((P.nload + j) % S0), mp, X0, Y0, zb - M + j);
     }
     for (; item < nitems; item += stride) {
         int local;
         const CUtensorMap *maps;
         decltype(auto) A = get(item, local, maps);
         int X0, Y0, zb, ze;
-        tb_item_geom<M, EY>(A, local, X0, Y0, zb, ze);
+        tb_item_geom<M, V>(A, local, X0, Y0, zb, ze);
         const int L = ze - zb + 2 * M;   // stage-0 planes zb-M .. ze+M-1
-        const int xg0 = X0 - TB_HX + xl0;
-        const int yg = Y0 - M + yl;
-        const bool row_in = yg >= 0 && yg < A.ny;
-        const bool ym_ok = yg > 0, yp_ok = yg + 1 < A.ny;
-        bool xm_ok[4], xp_ok[4], xin[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int x = xg0 + j;
-            xin[j] = x >= 0 && x < A.nx;
-            // the tile's outer columns have no stored neighbour (their results are never used)
-            xm_ok[j] = x > 0 && (j > 0 || qx > 0);
-            xp_ok[j] = x + 1 < A.nx && (j < 3 || qx < TB_QX - 1);
-        }
-        const bool x_inner = xm_ok[0] && xm_ok[1] && xm_ok[2] && xm_ok[3] && xp_ok[0] && xp_ok[1] &&
-                             xp_ok[2] && xp_ok[3];
-        const bool out_quad = qx >= 1 && qx < TB_QX - 1 && yl >= M && yl < EY - M && row_in && xg0 < A.nx;
+        // output quad of this thread
+        const int xg0 = X0 + 4 * (tid % 16);
+        const int yg = Y0 + tid / 16;
+        const bool out_quad = mact[M] && yg < A.ny && xg0 < A.nx;
+        const int nin = A.nx - xg0;      // voxels of the quad inside the grid (>= 4: all)
 
-        // per-voxel partials of the planes in flight: row k-1 belongs to stage k
-        float part[M][4], mx[M][4];
-#pragma unroll
-        for (int k = 0; k < M; ++k)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                part[k][j] = 0.f;
-                mx[k][j] = -3.0e38f;
-            }
-        // ring slots of stage-0 plane p0, advanced incrementally (no division):
-        // ring0 slot = nload % S0 with mbarrier phase (nload / S0) & 1; stage rings it % 3
+        // ring-0 slot offsets of planes p0 - d (d = 0 .. S0-1) and stage-ring
+        // slots e[r] of planes p0 - d with d % 3 == r; both rotate once per plane
         int s0_cur = (int)(P.nload % S0);
         uint32_t phase = (uint32_t)((P.nload / S0) & 1);
-        int s3_cur = 0;
+        int r0[S0];
+#pragma unroll
+        for (int d = 0; d < S0; ++d) r0[d] = ((s0_cur - d + S0) % S0) * C::SLOT0;
+        int e[3] = {0, 2, 1};
 
         for (int it = 0; it < L; ++it, ++P.nload) {
             const int p0 = zb - M + it;
-            if (tid == 0) {
-                if (it + 1 < L) {
-                    tb_issue<M, EY>(P, P.nload + 1, maps, X0, Y0, p0 + 1);
-                } else if (item + stride < nitems) {  // first plane of the next item
+            const int s0_next = s0_cur + 1 == S0 ? 0 : s0_cur + 1;
+            if (tid == 0) {  // request plane p0 + PD (of this item, else of the next one)
+                const int s0_pd = s0_cur + PD >= S0 ? s0_cur + PD - S0 : s0_cur + PD;
+                if (it + PD < L) {
+                    tb_issue<M, V>(P, s0_pd, maps, X0, Y0, p0 + PD);
+                } else if (item + stride < nitems) {
                     int local1;
                     const CUtensorMap *maps1;
                     decltype(auto) T1 = get(item + stride, local1, maps1);
                     int X1, Y1, zb1, ze1;
-                    tb_item_geom<M, EY>(T1, local1, X1, Y1, zb1, ze1);
-                    tb_issue<M, EY>(P, P.nload + 1, maps1, X1, Y1, zb1 - M);
+                    tb_item_geom<M, V>(T1, local1, X1, Y1, zb1, ze1);
+                    tb_issue<M, V>(P, s0_pd, maps1, X1, Y1, zb1 - M + (it + PD - L));
                 }
             }
             // output-stage operands of plane p0 - M, loaded early to hide their latency
@@ -243,165 +286,157 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
                     om23 = reinterpret_cast<const double2 *>(A.omega + gio)[1];
                 }
             }
-#pragma unroll
-            for (int k = M - 1; k >= 1; --k)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    part[k][j] = part[k - 1][j];
-                    mx[k][j] = mx[k - 1][j];
-                }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                part[0][j] = 0.f;
-                mx[0][j] = -3.0e38f;
-            }
             const bool ok = mbar_wait(bar_base + 8u * s0_cur, phase);
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0) {
-                    atomicOr(status, kStatusTimeout);
-                    const int sn = s0_cur + 1 == S0 ? 0 : s0_cur + 1;
-                    mbar_wait(bar_base + 8u * sn, sn == 0 ? phase ^ 1u : phase);
-                }
-                return false;
-            }
 #pragma unroll
             for (int k = 1; k <= M; ++k) {
-                const int q = p0 - k;
-                if (it >= 2 * k && q >= 0 && q < A.nz && row_in && yl >= k && yl < EY - k) {
-                    // ring slots of planes q-1, q, q+1 (compile-time k, conditional wrap)
-                    const int sq0 = wrap_lo(s0_cur - k, S0);          // ring0 slot of plane q
-                    const int s3q = wrap_lo(s3_cur - (k % 3), 3);      // stage-ring slot of plane q
-                    const int cb = sq0 * C::SLOT0;                      // coefficients of plane q
-                    const bool zm_ok = q > 0, zp_ok = q + 1 < A.nz;
-                    int bc, bm, bp;
+                if (it >= 2 * k && mact[k]) {
+                    const int id = mid[k];
+                    const int cb = r0[k];                     // coefficients of plane q = p0 - k
+                    int bc, bm, bp;                           // planes q, q - 1, q + 1 of stage k - 1
                     if (k == 1) {
-                        bc = cb;
-                        bm = wrap_lo(sq0 - 1, S0) * C::SLOT0;
-                        bp = wrap_hi(sq0 + 1, S0) * C::SLOT0;
+                        bc = r0[1];
+                        bm = r0[2];
+                        bp = r0[0];
                     } else {
-                        const int rk = C::RING_OFF + (k - 2) * 3 * C::RINGK;
-                        bc = rk + s3q * C::RINGK;
-                        bm = rk + wrap_lo(s3q - 1, 3) * C::RINGK;
-                        bp = rk + wrap_hi(s3q + 1, 3) * C::RINGK;
+                        const int rk = C::ring_off(k - 1), sl = C::ring_planes(k - 1) * PLANE;
+                        bc = rk + e[k % 3] * sl;
+                        bm = rk + e[(k + 1) % 3] * sl;
+                        bp = rk + e[(k - 1) % 3] * sl;
                     }
                     const float4 ch = ld4(sm, bc + id), cl = ld4(sm, bc + PLANE + id);
                     const float4 ymh = ld4(sm, bc + id - TB_EX), yml = ld4(sm, bc + PLANE + id - TB_EX);
                     const float4 yph = ld4(sm, bc + id + TB_EX), ypl = ld4(sm, bc + PLANE + id + TB_EX);
                     const float4 zmh = ld4(sm, bm + id), zml = ld4(sm, bm + PLANE + id);
                     const float4 zph = ld4(sm, bp + id), zpl = ld4(sm, bp + PLANE + id);
-                    const int lo_off = qx > 0 ? -1 : 0, hi_off = qx < TB_QX - 1 ? 4 : 3;
-                    const float lh = sm[bc + id + lo_off], ll = sm[bc + PLANE + id + lo_off];
-                    const float rh = sm[bc + id + hi_off], rl = sm[bc + PLANE + id + hi_off];
+                    const float lh = sm[bc + id + mxl[k]], ll = sm[bc + PLANE + id + mxl[k]];
+                    const float rh = sm[bc + id + mxh[k]], rl = sm[bc + PLANE + id + mxh[k]];
                     const uint4 w4 = *reinterpret_cast<const uint4 *>(sm + cb + 2 * PLANE + id);
                     const float4 s4 = ld4(sm, cb + 3 * PLANE + id);
                     // voxel pairs (0,1) and (2,3) of the quad
                     const float2 C01 = make_float2(ch.x, ch.y), C23 = make_float2(ch.z, ch.w);
                     const float2 L01 = make_float2(cl.x, cl.y), L23 = make_float2(cl.z, cl.w);
-                    // neighbour differences, fixed order x-, x+, y-, y+, z-, z+; a neighbour
-                    // outside the grid adds +0
-                    const float2 z2 = make_float2(0.f, 0.f);
-                    float2 S01 = z2, S23 = z2, d01, d23;
-                    d01 = cdiff2(make_float2(lh, ch.x), make_float2(ll, cl.x), C01, L01);
-                    d23 = cdiff2(make_float2(ch.y, ch.z), make_float2(cl.y, cl.z), C23, L23);
-                    S01 = add2(S01, make_float2(xm_ok[0] ? d01.x : 0.f, xm_ok[1] ? d01.y : 0.f));
-                    S23 = add2(S23, make_float2(xm_ok[2] ? d23.x : 0.f, xm_ok[3] ? d23.y : 0.f));
-                    d01 = cdiff2(make_float2(ch.y, ch.z), make_float2(cl.y, cl.z), C01, L01);
-                    d23 = cdiff2(make_float2(ch.w, rh), make_float2(cl.w, rl), C23, L23);
-                    S01 = add2(S01, make_float2(xp_ok[0] ? d01.x : 0.f, xp_ok[1] ? d01.y : 0.f));
-                    S23 = add2(S23, make_float2(xp_ok[2] ? d23.x : 0.f, xp_ok[3] ? d23.y : 0.f));
-                    d01 = cdiff2(make_float2(ymh.x, ymh.y), make_float2(yml.x, yml.y), C01, L01);
-                    d23 = cdiff2(make_float2(ymh.z, ymh.w), make_float2(yml.z, yml.w), C23, L23);
-                    S01 = add2(S01, ym_ok ? d01 : z2);
-                    S23 = add2(S23, ym_ok ? d23 : z2);
-                    d01 = cdiff2(make_float2(yph.x, yph.y), make_float2(ypl.x, ypl.y), C01, L01);
-                    d23 = cdiff2(make_float2(yph.z, yph.w), make_float2(ypl.z, ypl.w), C23, L23);
-                    S01 = add2(S01, yp_ok ? d01 : z2);
-                    S23 = add2(S23, yp_ok ? d23 : z2);
-                    d01 = cdiff2(make_float2(zmh.x, zmh.y), make_float2(zml.x, zml.y), C01, L01);
-                    d23 = cdiff2(make_float2(zmh.z, zmh.w), make_float2(zml.z, zml.w), C23, L23);
-                    S01 = add2(S01, zm_ok ? d01 : z2);
-                    S23 = add2(S23, zm_ok ? d23 : z2);
-                    d01 = cdiff2(make_float2(zph.x, zph.y), make_float2(zpl.x, zpl.y), C01, L01);
-                    d23 = cdiff2(make_float2(zph.z, zph.w), make_float2(zpl.z, zpl.w), C23, L23);
-                    S01 = add2(S01, zp_ok ? d01 : z2);
-                    S23 = add2(S23, zp_ok ? d23 : z2);
+                    // neighbour differences in the fixed order x-, x+, y-, y+, z-, z+
+                    float2 S01 = cdiff2(make_float2(lh, ch.x), make_float2(ll, cl.x), C01, L01);
+                    float2 S23 = cdiff2(make_float2(ch.y, ch.z), make_float2(cl.y, cl.z), C23, L23);
+                    S01 = add2(S01, cdiff2(make_float2(ch.y, ch.z), make_float2(cl.y, cl.z), C01, L01));
+                    S23 = add2(S23, cdiff2(make_float2(ch.w, rh), make_float2(cl.w, rl), C23, L23));
+                    S01 = add2(S01, cdiff2(make_float2(ymh.x, ymh.y), make_float2(yml.x, yml.y), C01, L01));
+                    S23 = add2(S23, cdiff2(make_float2(ymh.z, ymh.w), make_float2(yml.z, yml.w), C23, L23));
+                    S01 = add2(S01, cdiff2(make_float2(yph.x, yph.y), make_float2(ypl.x, ypl.y), C01, L01));
+                    S23 = add2(S23, cdiff2(make_float2(yph.z, yph.w), make_float2(ypl.z, ypl.w), C23, L23));
+                    S01 = add2(S01, cdiff2(make_float2(zmh.x, zmh.y), make_float2(zml.x, zml.y), C01, L01));
+                    S23 = add2(S23, cdiff2(make_float2(zmh.z, zmh.w), make_float2(zml.z, zml.w), C23, L23));
+                    S01 = add2(S01, cdiff2(make_float2(zph.x, zph.y), make_float2(zpl.x, zpl.y), C01, L01));
+                    S23 = add2(S23, cdiff2(make_float2(zph.z, zph.w), make_float2(zpl.z, zpl.w), C23, L23));
                     const float2 a01 = make_float2(bf16_to_float(w4.x & 0xffffu), bf16_to_float(w4.y & 0xffffu));
                     const float2 a23 = make_float2(bf16_to_float(w4.z & 0xffffu), bf16_to_float(w4.w & 0xffffu));
                     const float2 b01 = make_float2(bf16_to_float(w4.x >> 16), bf16_to_float(w4.y >> 16));
                     const float2 b23 = make_float2(bf16_to_float(w4.z >> 16), bf16_to_float(w4.w >> 16));
-                    float2 H01, H23, N01, N23;
-                    cupdate2(C01, L01, S01, a01, b01, make_float2(s4.x, s4.y), H01, N01);
-                    cupdate2(C23, L23, S23, a23, b23, make_float2(s4.z, s4.w), H23, N23);
-                    const float2 V01 = add2(H01, N01), V23 = add2(H23, N23);
-                    mx[k - 1][0] = fmaxf(mx[k - 1][0], V01.x);
-                    mx[k - 1][1] = fmaxf(mx[k - 1][1], V01.y);
-                    mx[k - 1][2] = fmaxf(mx[k - 1][2], V23.x);
-                    mx[k - 1][3] = fmaxf(mx[k - 1][3], V23.y);
-                    if (DMG) {
-                        const float2 i01 = arrhenius_inc2(V01, A.c0, A.c1, A.TK0);
-                        const float2 i23 = arrhenius_inc2(V23, A.c0, A.c1, A.TK0);
-                        const float2 p01 = add2(make_float2(part[k - 1][0], part[k - 1][1]), i01);
-                        const float2 p23 = add2(make_float2(part[k - 1][2], part[k - 1][3]), i23);
-                        part[k - 1][0] = p01.x;
-                        part[k - 1][1] = p01.y;
-                        part[k - 1][2] = p23.x;
-                        part[k - 1][3] = p23.y;
+                    float2 H01, H23, N01, N23, T01, T23;
+                    cupdate2(C01, L01, S01, a01, b01, make_float2(s4.x, s4.y), H01, N01, T01);
+                    cupdate2(C23, L23, S23, a23, b23, make_float2(s4.z, s4.w), H23, N23, T23);
+                    // running Arrhenius sum and maximum of the values of stages 1 .. k-1
+                    float2 P01 = make_float2(0.f, 0.f), P23 = P01, X01 = T01, X23 = T23;
+                    if (k >= 2) {
+                        if (DMG) {
+                            P01 = arrhenius_inc2(T01, A.c0, A.c1, A.TK0);
+                            P23 = arrhenius_inc2(T23, A.c0, A.c1, A.TK0);
+                        }
+                        if (k >= 3) {  // earlier stages' sum and maximum, stored with the values
+                            const float4 pp = ld4(sm, bc + 2 * PLANE + id), pm = ld4(sm, bc + 3 * PLANE + id);
+                            if (DMG) {
+                                P01 = add2(make_float2(pp.x, pp.y), P01);
+                                P23 = add2(make_float2(pp.z, pp.w), P23);
+                            }
+                            X01 = make_float2(fmaxf(pm.x, T01.x), fmaxf(pm.y, T01.y));
+                            X23 = make_float2(fmaxf(pm.z, T23.x), fmaxf(pm.w, T23.y));
+                        }
                     }
-                    const float nh_[4] = {H01.x, H01.y, H23.x, H23.y}, nl_[4] = {N01.x, N01.y, N23.x, N23.y};
                     if (k < M) {
-                        const int bo = C::RING_OFF + ((k - 1) * 3 + s3q) * C::RINGK;
-                        *reinterpret_cast<float4 *>(sm + bo + id) = make_float4(nh_[0], nh_[1], nh_[2], nh_[3]);
-                        *reinterpret_cast<float4 *>(sm + bo + PLANE + id) = make_float4(nl_[0], nl_[1], nl_[2], nl_[3]);
+                        const int ro = C::ring_off(k), sl = C::ring_planes(k) * PLANE;
+                        const int bo = ro + e[k % 3] * sl;
+                        *reinterpret_cast<float4 *>(sm + bo + id) = make_float4(H01.x, H01.y, H23.x, H23.y);
+                        *reinterpret_cast<float4 *>(sm + bo + PLANE + id) = make_float4(N01.x, N01.y, N23.x, N23.y);
+                        if (k >= 2) {
+                            *reinterpret_cast<float4 *>(sm + bo + 2 * PLANE + id) =
+                                make_float4(P01.x, P01.y, P23.x, P23.y);
+                            *reinterpret_cast<float4 *>(sm + bo + 3 * PLANE + id) =
+                                make_float4(X01.x, X01.y, X23.x, X23.y);
+                        }
                     } else if (out_now) {
-                        // output quad: 16-byte aligned (X0 % 64 == 0, pitch % 4 == 0); padding
-                        // voxels beyond nx are written as zero
-                        float o_h[4], o_l[4];
+                        // last stage: this step's own value, then the output quad (16-byte
+                        // aligned: X0 % 64 == 0, pitch % 4 == 0; padding voxels compute to 0)
+                        const float2 V01 = add2(H01, N01), V23 = add2(H23, N23);
+                        *reinterpret_cast<float4 *>(A.hi_out + gio) = make_float4(H01.x, H01.y, H23.x, H23.y);
+                        *reinterpret_cast<float4 *>(A.lo_out + gio) = make_float4(N01.x, N01.y, N23.x, N23.y);
+                        bad |= !(isfinite(H01.x) && isfinite(H01.y) && isfinite(H23.x) && isfinite(H23.y));
+                        const float mx[4] = {fmaxf(X01.x, V01.x), fmaxf(X01.y, V01.y), fmaxf(X23.x, V23.x),
+                                             fmaxf(X23.y, V23.y)};
                         uint32_t lbits = 0;
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            o_h[j] = xin[j] ? nh_[j] : 0.f;
-                            o_l[j] = xin[j] ? nl_[j] : 0.f;
-                            bad |= xin[j] && !isfinite(nh_[j]);
-                            if (xin[j] && mx[k - 1][j] >= A.thr) lbits |= 1u << (8 * j);
-                        }
-                        *reinterpret_cast<float4 *>(A.hi_out + gio) = make_float4(o_h[0], o_h[1], o_h[2], o_h[3]);
-                        *reinterpret_cast<float4 *>(A.lo_out + gio) = make_float4(o_l[0], o_l[1], o_l[2], o_l[3]);
+                        for (int j = 0; j < 4; ++j)
+                            if (j < nin && mx[j] >= A.thr) lbits |= 1u << (8 * j);
                         if ((latch4 | lbits) != latch4)
                             *reinterpret_cast<uint32_t *>(A.latch + gio) = latch4 | lbits;
                         if (DMG) {
-                            float P[4] = {carry4.x, carry4.y, carry4.z, carry4.w};
+                            P01 = add2(P01, arrhenius_inc2(V01, A.c0, A.c1, A.TK0));
+                            P23 = add2(P23, arrhenius_inc2(V23, A.c0, A.c1, A.TK0));
+                            const float part[4] = {P01.x, P01.y, P23.x, P23.y};
+                            float Pc[4] = {carry4.x, carry4.y, carry4.z, carry4.w};
 #pragma unroll
                             for (int j = 0; j < 4; ++j)
-                                if (xin[j]) P[j] = __fadd_rn(P[j], part[k - 1][j]);
+                                if (j < nin) Pc[j] = __fadd_rn(Pc[j], part[j]);
                             if (FOLD) {
                                 double om[4] = {om01.x, om01.y, om23.x, om23.y};
 #pragma unroll
                                 for (int j = 0; j < 4; ++j)
-                                    if (xin[j]) carry_fold(om[j], P[j]);
+                                    if (j < nin) carry_fold(om[j], Pc[j]);
                                 double2 *op = reinterpret_cast<double2 *>(A.omega + gio);
                                 op[0] = make_double2(om[0], om[1]);
                                 op[1] = make_double2(om[2], om[3]);
                             }
-                            *reinterpret_cast<float4 *>(A.omega_c + gio) = make_float4(P[0], P[1], P[2], P[3]);
+                            *reinterpret_cast<float4 *>(A.omega_c + gio) = make_float4(Pc[0], Pc[1], Pc[2], Pc[3]);
                         }
                     }
                 }
-                __syncthreads();
+                if (k == 1) {
+                    // the stage-1 barrier also agrees on the stage-0 wait: a CTA whose
+                    // wait timed out leaves (stage 1 only wrote shared memory)
+                    if (__syncthreads_or(!ok)) {
+                        if (tid == 0) {  // let the requests in flight land first (bounded)
+                            atomicOr(status, kStatusTimeout);
+#pragma unroll
+                            for (int j = 1; j <= PD; ++j) {
+                                const int sj = s0_cur + j >= S0 ? s0_cur + j - S0 : s0_cur + j;
+                                mbar_wait(bar_base + 8u * sj, s0_cur + j >= S0 ? phase ^ 1u : phase);
+                            }
+                        }
+                        return false;
+                    }
+                } else {
+                    __syncthreads();
+                }
             }
-            s3_cur = s3_cur + 1 == 3 ? 0 : s3_cur + 1;
-            if (++s0_cur == S0) {
-                s0_cur = 0;
-                phase ^= 1u;
-            }
+            // rotate the ring slots by one plane
+            const int t0 = r0[S0 - 1];
+#pragma unroll
+            for (int d = S0 - 1; d > 0; --d) r0[d] = r0[d - 1];
+            r0[0] = t0;
+            const int t1 = e[2];
+            e[2] = e[1];
+            e[1] = e[0];
+            e[0] = t1;
+            if (s0_next == 0) phase ^= 1u;
+            s0_cur = s0_next;
         }
     }
     return true;
 }
 
-template <int M, int EY>
+template <int M, int V>
 __device__ __forceinline__ bool tb_setup(TBPipe &P, unsigned *status)
 {
-    using C = Cfg<M, EY>;
+    using C = Cfg<M, V>;
     extern __shared__ __align__(128) float sm[];
     P.sm = sm;
     P.sm_base = smem_u32(sm);
@@ -425,12 +460,12 @@ struct TBMaps {
 };
 
 // one grid, M steps
-template <int M, int EY, bool DMG, bool FOLD>
-__global__ void __launch_bounds__(Cfg<M, EY>::THREADS, Cfg<M, EY>::MINB)
+template <int M, int V, bool DMG, bool FOLD>
+__global__ void __launch_bounds__(Cfg<M, V>::THREADS, Cfg<M, V>::MINB)
     k_step_tb(const __grid_constant__ TBMaps maps, const TBTile T0, unsigned *status)
 {
     TBPipe P;
-    if (!tb_setup<M, EY>(P, status)) return;
+    if (!tb_setup<M, V>(P, status)) return;
     // the descriptor stays in kernel-parameter space (constant-bank operands)
     auto get = [&](int item, int &local, const CUtensorMap *&mp) -> const TBTile & {
         local = item;
@@ -438,7 +473,7 @@ __global__ void __launch_bounds__(Cfg<M, EY>::THREADS, Cfg<M, EY>::MINB)
         return T0;
     };
     bool bad = false;
-    tb_run<M, EY, DMG, FOLD>(P, blockIdx.x, gridDim.x, T0.xt * T0.yt * T0.zc, get, status, bad);
+    tb_run<M, V, DMG, FOLD>(P, blockIdx.x, gridDim.x, T0.xt * T0.yt * T0.zc, get, status, bad);
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusNonfinite);
 }
 
@@ -484,13 +519,13 @@ __device__ bool grid_sync(unsigned *bar, unsigned nblocks)
 }
 
 // every member, ntime blocks of M steps, one persistent launch
-template <int M, int EY, bool DMG>
-__global__ void __launch_bounds__(Cfg<M, EY>::THREADS, Cfg<M, EY>::MINB)
+template <int M, int V, bool DMG>
+__global__ void __launch_bounds__(Cfg<M, V>::THREADS, Cfg<M, V>::MINB)
     k_batch_tb(const TBMember *mem, int nmem, int nitems, int ntime, int fold_every, unsigned *gbar,
                unsigned *status)
 {
     TBPipe P;
-    if (!tb_setup<M, EY>(P, status)) return;
+    if (!tb_setup<M, V>(P, status)) return;
     bool bad = false;
     for (int t = 0; t < ntime; ++t) {
         auto get = [&](int item, int &local, const CUtensorMap *&mp) -> TBTile {
@@ -506,8 +541,8 @@ __global__ void __launch_bounds__(Cfg<M, EY>::THREADS, Cfg<M, EY>::MINB)
             return T;
         };
         const bool fold = DMG && ((t + 1) % fold_every == 0 || t == ntime - 1);
-        const bool ok = fold ? tb_run<M, EY, DMG, true>(P, blockIdx.x, gridDim.x, nitems, get, status, bad)
-                             : tb_run<M, EY, DMG, false>(P, blockIdx.x, gridDim.x, nitems, get, status, bad);
+        const bool ok = fold ? tb_run<M, V, DMG, true>(P, blockIdx.x, gridDim.x, nitems, get, status, bad)
+                             : tb_run<M, V, DMG, false>(P, blockIdx.x, gridDim.x, nitems, get, status, bad);
         if (!ok) break;
         if (!grid_sync(gbar, gridDim.x)) {
             if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
@@ -549,14 +584,14 @@ bool make_map(CUtensorMap *m, const void *base, CUtensorMapDataType dt, const rf
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int variant_ey(int variant) { return variant == 1 ? 32 : 16; }
+int variant_ey(int variant) { return tile_ey(variant); }
 
 // tiles and balanced z chunks of one grid: the busiest of `resident` persistent
 // CTAs should stream as few planes as possible (each item costs chunk + 2M planes)
-template <int M, int EY>
+template <int M, int V>
 void tile_plan(const rfa_grid *g, int resident, int max_chunk, TBTile &T)
 {
-    using C = Cfg<M, EY>;
+    using C = Cfg<M, V>;
     T.xt = (g->nx + TB_TX - 1) / TB_TX;
     T.yt = (g->ny + C::TY - 1) / C::TY;
     const long long tiles = (long long)T.xt * T.yt;
@@ -595,45 +630,45 @@ void fill_tile(const rfa_grid *g, int parity, TBTile &T)
     T.TK0 = dc.TK0;
 }
 
-template <int M, int EY, bool DMG, bool FOLD>
+template <int M, int V, bool DMG, bool FOLD>
 cudaError_t launch_inst(rfa_grid *g, const TBMaps &maps, TBTile T)
 {
-    using C = Cfg<M, EY>;
-    cudaError_t e = cudaFuncSetAttribute(k_step_tb<M, EY, DMG, FOLD>,
+    using C = Cfg<M, V>;
+    cudaError_t e = cudaFuncSetAttribute(k_step_tb<M, V, DMG, FOLD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     const int resident = 148 * C::MINB;
-    tile_plan<M, EY>(g, resident, 1 << 30, T);
+    tile_plan<M, V>(g, resident, 1 << 30, T);
     const long long items = (long long)T.xt * T.yt * T.zc;
     const unsigned grid = (unsigned)(items < resident ? items : resident);
-    k_step_tb<M, EY, DMG, FOLD><<<grid, C::THREADS, C::SMEM, g->stream>>>(maps, T, g->status);
+    k_step_tb<M, V, DMG, FOLD><<<grid, C::THREADS, C::SMEM, g->stream>>>(maps, T, g->status);
     return cudaGetLastError();
 }
 
 // shared-memory opt-in and the co-resident grid size of the batch kernel
 // (host-side queries, kept outside stream capture)
-template <int M, int EY, bool DMG>
+template <int M, int V, bool DMG>
 cudaError_t prepare_batch_inst(int nitems, int *grid)
 {
-    using C = Cfg<M, EY>;
-    cudaError_t e = cudaFuncSetAttribute(k_batch_tb<M, EY, DMG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    using C = Cfg<M, V>;
+    cudaError_t e = cudaFuncSetAttribute(k_batch_tb<M, V, DMG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          C::SMEM);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_tb<M, EY, DMG>, C::THREADS, C::SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_tb<M, V, DMG>, C::THREADS, C::SMEM);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     *grid = nsm * per_sm < nitems ? nsm * per_sm : nitems;
     return cudaSuccess;
 }
 
-template <int M, int EY, bool DMG>
+template <int M, int V, bool DMG>
 cudaError_t launch_batch_inst(const TBMember *mem, int nmem, int nitems, int ntime, int fold_every,
                               unsigned *gbar, unsigned *status, cudaStream_t stream, int grid)
 {
-    using C = Cfg<M, EY>;
+    using C = Cfg<M, V>;
     // cooperative launch: every CTA is resident at once, which the grid barrier needs
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
@@ -645,7 +680,7 @@ cudaError_t launch_batch_inst(const TBMember *mem, int nmem, int nitems, int nti
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_batch_tb<M, EY, DMG>, mem, nmem, nitems, ntime, fold_every, gbar, status);
+    return cudaLaunchKernelEx(&cfg, k_batch_tb<M, V, DMG>, mem, nmem, nitems, ntime, fold_every, gbar, status);
 }
 
 // tensor maps per (grid, input buffers, tile height); erased when the grid is destroyed
@@ -664,9 +699,10 @@ MapCache &map_cache()
 bool tb_supported(const rfa_grid *g, int depth, int variant)
 {
     if (g->sp != RFA_STATE_F32C || g->pp != RFA_PARAM_BF16) return false;
-    if (variant < 0 || variant > 1) return false;
-    if (variant == 0 && (depth < 2 || depth > 4)) return false;
-    if (variant == 1 && depth != 2) return false;
+    if (variant < 0 || variant > 2) return false;
+    if (g->face != RFA_FACE_DIRICHLET) return false;  // insulated faces: one-step kernel
+    if (variant == 0 && (depth < 2 || depth > 3)) return false;
+    if (variant >= 1 && depth != 2) return false;
     return encode_fn() != nullptr;
 }
 
@@ -703,22 +739,21 @@ bool tb_make_maps(const rfa_grid *g, int variant, const void *th_in, const void 
 cudaError_t launch_step_tb(rfa_grid *g, int depth, int variant, const void *th_in, const void *lo_in,
                            void *th_out, void *lo_out, bool damage, bool fold)
 {
-    const int ey = variant_ey(variant);
     TBMaps maps;
     if (!tb_make_maps(g, variant, th_in, lo_in, maps.m)) return cudaErrorInvalidValue;
     TBTile T;
     fill_tile(g, g->th[0] == th_in ? 0 : 1, T);
     T.hi_out = (float *)th_out;
     T.lo_out = (float *)lo_out;
-#define TB_CASE(MV, EYV)                                                                 \
-    if (depth == MV && ey == EYV)                                                        \
-        return !damage ? launch_inst<MV, EYV, false, false>(g, maps, T)                 \
-               : fold  ? launch_inst<MV, EYV, true, true>(g, maps, T)                   \
-                       : launch_inst<MV, EYV, true, false>(g, maps, T);
-    TB_CASE(2, 16)
-    TB_CASE(3, 16)
-    TB_CASE(4, 16)
-    TB_CASE(2, 32)
+#define TB_CASE(MV, VV)                                                                 \
+    if (depth == MV && variant == VV)                                                        \
+        return !damage ? launch_inst<MV, VV, false, false>(g, maps, T)                 \
+               : fold  ? launch_inst<MV, VV, true, true>(g, maps, T)                   \
+                       : launch_inst<MV, VV, true, false>(g, maps, T);
+    TB_CASE(2, 0)
+    TB_CASE(3, 0)
+    TB_CASE(2, 1)
+    TB_CASE(2, 2)
 #undef TB_CASE
     return cudaErrorInvalidValue;
 }
@@ -763,26 +798,25 @@ void tb_pack_member(const TBMemberHost &h, const CUtensorMap *maps_dev, int item
 
 cudaError_t prepare_batch_tb(int depth, int variant, bool damage, int nitems, int *grid)
 {
-    const int ey = variant_ey(variant);
-#define PREP_CASE(MV, EYV)                                                              \
-    if (depth == MV && ey == EYV)                                                       \
-        return damage ? prepare_batch_inst<MV, EYV, true>(nitems, grid)                 \
-                      : prepare_batch_inst<MV, EYV, false>(nitems, grid);
-    PREP_CASE(2, 16)
-    PREP_CASE(3, 16)
-    PREP_CASE(4, 16)
-    PREP_CASE(2, 32)
+#define PREP_CASE(MV, VV)                                                              \
+    if (depth == MV && variant == VV)                                                       \
+        return damage ? prepare_batch_inst<MV, VV, true>(nitems, grid)                 \
+                      : prepare_batch_inst<MV, VV, false>(nitems, grid);
+    PREP_CASE(2, 0)
+    PREP_CASE(3, 0)
+    PREP_CASE(2, 1)
+    PREP_CASE(2, 2)
 #undef PREP_CASE
     return cudaErrorInvalidValue;
 }
 
 // A two-node graph (barrier reset, then the batch kernel as a cooperative
 // kernel node): stream capture does not accept cooperative launches.
-template <int M, int EY, bool DMG>
+template <int M, int V, bool DMG>
 cudaError_t graph_batch_inst(const TBMember *mem, int nmem, int nitems, int ntime, int fold_every,
                              unsigned *gbar, unsigned *status, int grid, cudaGraphExec_t *exec)
 {
-    using C = Cfg<M, EY>;
+    using C = Cfg<M, V>;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaGraphCreate(&graph, 0);
     if (e != cudaSuccess) return e;
@@ -799,7 +833,7 @@ cudaError_t graph_batch_inst(const TBMember *mem, int nmem, int nitems, int ntim
                     (void *)&gbar, (void *)&status};
     if (e == cudaSuccess) {
         cudaKernelNodeParams kp = {};
-        kp.func = (void *)k_batch_tb<M, EY, DMG>;
+        kp.func = (void *)k_batch_tb<M, V, DMG>;
         kp.gridDim = dim3((unsigned)grid);
         kp.blockDim = dim3((unsigned)C::THREADS);
         kp.sharedMemBytes = C::SMEM;
@@ -819,17 +853,16 @@ cudaError_t graph_batch_inst(const TBMember *mem, int nmem, int nitems, int ntim
 cudaError_t graph_batch_tb(int depth, int variant, bool damage, const void *members_dev, int nmem, int nitems,
                            int ntime, unsigned *gbar, unsigned *status, int grid, cudaGraphExec_t *exec)
 {
-    const int ey = variant_ey(variant);
     const int fold_every = kCarrySteps / depth > 0 ? kCarrySteps / depth : 1;
     const TBMember *mem = (const TBMember *)members_dev;
-#define GRAPH_CASE(MV, EYV)                                                                                        \
-    if (depth == MV && ey == EYV)                                                                                  \
-        return damage ? graph_batch_inst<MV, EYV, true>(mem, nmem, nitems, ntime, fold_every, gbar, status, grid, exec) \
-                      : graph_batch_inst<MV, EYV, false>(mem, nmem, nitems, ntime, fold_every, gbar, status, grid, exec);
-    GRAPH_CASE(2, 16)
-    GRAPH_CASE(3, 16)
-    GRAPH_CASE(4, 16)
-    GRAPH_CASE(2, 32)
+#define GRAPH_CASE(MV, VV)                                                                                        \
+    if (depth == MV && variant == VV)                                                                                  \
+        return damage ? graph_batch_inst<MV, VV, true>(mem, nmem, nitems, ntime, fold_every, gbar, status, grid, exec) \
+                      : graph_batch_inst<MV, VV, false>(mem, nmem, nitems, ntime, fold_every, gbar, status, grid, exec);
+    GRAPH_CASE(2, 0)
+    GRAPH_CASE(3, 0)
+    GRAPH_CASE(2, 1)
+    GRAPH_CASE(2, 2)
 #undef GRAPH_CASE
     return cudaErrorInvalidValue;
 }
@@ -837,17 +870,16 @@ cudaError_t graph_batch_tb(int depth, int variant, bool damage, const void *memb
 cudaError_t launch_batch_tb(int depth, int variant, bool damage, const void *members_dev, int nmem,
                             int nitems, int ntime, unsigned *gbar, unsigned *status, cudaStream_t stream, int grid)
 {
-    const int ey = variant_ey(variant);
     const int fold_every = kCarrySteps / depth > 0 ? kCarrySteps / depth : 1;
     const TBMember *mem = (const TBMember *)members_dev;
-#define BATCH_CASE(MV, EYV)                                                                                           \
-    if (depth == MV && ey == EYV)                                                                                     \
-        return damage ? launch_batch_inst<MV, EYV, true>(mem, nmem, nitems, ntime, fold_every, gbar, status, stream, grid) \
-                      : launch_batch_inst<MV, EYV, false>(mem, nmem, nitems, ntime, fold_every, gbar, status, stream, grid);
-    BATCH_CASE(2, 16)
-    BATCH_CASE(3, 16)
-    BATCH_CASE(4, 16)
-    BATCH_CASE(2, 32)
+#define BATCH_CASE(MV, VV)                                                                                           \
+    if (depth == MV && variant == VV)                                                                                     \
+        return damage ? launch_batch_inst<MV, VV, true>(mem, nmem, nitems, ntime, fold_every, gbar, status, stream, grid) \
+                      : launch_batch_inst<MV, VV, false>(mem, nmem, nitems, ntime, fold_every, gbar, status, stream, grid);
+    BATCH_CASE(2, 0)
+    BATCH_CASE(3, 0)
+    BATCH_CASE(2, 1)
+    BATCH_CASE(2, 2)
 #undef BATCH_CASE
     return cudaErrorInvalidValue;
 }

@@ -51,10 +51,11 @@ __device__ __forceinline__ float2 cdiff2(float2 nh, float2 nl, float2 c, float2 
     return add2(sub2(nh, c), sub2(nl, cl));
 }
 
+// (th returns the old value c + cl rounded to FP32, the operand of -b theta)
 __device__ __forceinline__ void cupdate2(float2 c, float2 cl, float2 S, float2 a, float2 b, float2 s,
-                                         float2 &nh, float2 &nl)
+                                         float2 &nh, float2 &nl, float2 &th)
 {
-    float2 th = add2(c, cl);
+    th = add2(c, cl);
     float2 delta = __ffma2_rn(a, S, __ffma2_rn(neg2(b), th, s));
     float2 s1 = add2(c, delta);
     float2 bb = sub2(s1, c);

@@ -9,7 +9,7 @@ from tests.parity_util import compare, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
-SCHEDULES = [(2, 0), (3, 0), (4, 0), (2, 1)]
+SCHEDULES = [(2, 0), (3, 0), (2, 1), (2, 2)]
 
 
 @pytest.mark.parametrize("sched", SCHEDULES)
@@ -29,7 +29,7 @@ def test_blocked_equals_one_step(sched, dims):
     assert rel.max() <= 2e-5
 
 
-@pytest.mark.parametrize("sched", [(2, 0), (3, 0), (4, 0), (2, 1)])
+@pytest.mark.parametrize("sched", [(2, 0), (3, 0), (2, 1), (2, 2)])
 def test_blocked_parity_with_oracle(sched):
     case = ph.random_small_case(21, 71, 45, 38, kind=ph.UMBRELLA, power=6.0)
     n = 301
@@ -41,7 +41,7 @@ def test_blocked_parity_with_oracle(sched):
 def test_blocked_homogeneous_64_2000_steps():
     case = ph.homogeneous_case(damage=ph.Damage(enable=1))
     orc = run_oracle(case, rfa.PARAM_BF16, 2000)
-    gpu = run_gpu(case, rfa.STATE_F32C, rfa.PARAM_BF16, 2000, schedule=(4, 0))
+    gpu = run_gpu(case, rfa.STATE_F32C, rfa.PARAM_BF16, 2000, schedule=(3, 0))
     res = compare(case, gpu, orc, rfa.STATE_F32C)
     assert res["err_T"] < 1e-4
 
@@ -55,6 +55,18 @@ def test_schedule_rejected_where_unsupported():
     with pytest.raises(rfa.RfaError) as e:
         g.set_schedule(9, 0)
     assert e.value.status == 1
+    g.close()
+    # insulated faces: the blocked kernel needs Dirichlet faces (one step per launch)
+    ins = ph.random_small_case(3, 20, 20, 20, face_bc=ph.INSULATED)
+    g = rfa.Grid.from_case(ins)
+    with pytest.raises(rfa.RfaError) as e:
+        g.set_schedule(2, 0)
+    assert e.value.status == 8
+    rfa.rfa_autotune(g.handle, None)
+    assert rfa.rfa_get_schedule(g.handle) == (1, 0)
+    with pytest.raises(rfa.RfaError) as e:
+        rfa.rfa_batch_create([g.handle])
+    assert e.value.status == 8
     g.close()
 
 
