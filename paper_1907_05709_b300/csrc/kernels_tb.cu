@@ -101,7 +101,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-// bounded wait for the phase with the given parity; false on timeout
+// bounded wait for the phase with the given parity; false on timeout.  Each
+// try_wait may suspend the thread for up to kSuspendNs (it resumes as soon as
+// the phase completes), so waiting warps do not spin on the issue slots.
+constexpr uint32_t kSuspendNs = 100000;
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 {
     const long long t0 = clock64();
@@ -109,10 +112,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
-            : "r"(bar), "r"(parity)
+            : "r"(bar), "r"(parity), "r"(kSuspendNs)
             : "memory");
         if (done) return true;
         if (clock64() - t0 > (1ll << 32)) return false;  // ~2 s at 2 GHz
@@ -254,6 +257,7 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
 #pragma unroll
         for (int d = 0; d < S0; ++d) r0[d] = ((s0_cur - d + S0) % S0) * C::SLOT0;
         int e[3] = {0, 2, 1};
+        float4 k1ch = make_float4(0.f, 0.f, 0.f, 0.f), k1cl = k1ch, k1mh = k1ch, k1ml = k1ch;
 
         for (int it = 0; it < L; ++it, ++P.nload) {
             const int p0 = zb - M + it;
@@ -303,11 +307,17 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
                         bm = rk + e[(k + 1) % 3] * sl;
                         bp = rk + e[(k - 1) % 3] * sl;
                     }
-                    const float4 ch = ld4(sm, bc + id), cl = ld4(sm, bc + PLANE + id);
+                    float4 ch, cl, zmh, zml;
+                    if (k == 1 && it > 2) {  // this column's planes p0-2, p0-1, kept from the last iteration
+                        ch = k1ch; cl = k1cl; zmh = k1mh; zml = k1ml;
+                    } else {
+                        ch = ld4(sm, bc + id); cl = ld4(sm, bc + PLANE + id);
+                        zmh = ld4(sm, bm + id); zml = ld4(sm, bm + PLANE + id);
+                    }
                     const float4 ymh = ld4(sm, bc + id - TB_EX), yml = ld4(sm, bc + PLANE + id - TB_EX);
                     const float4 yph = ld4(sm, bc + id + TB_EX), ypl = ld4(sm, bc + PLANE + id + TB_EX);
-                    const float4 zmh = ld4(sm, bm + id), zml = ld4(sm, bm + PLANE + id);
                     const float4 zph = ld4(sm, bp + id), zpl = ld4(sm, bp + PLANE + id);
+                    if (k == 1) { k1mh = ch; k1ml = cl; k1ch = zph; k1cl = zpl; }
                     const float lh = sm[bc + id + mxl[k]], ll = sm[bc + PLANE + id + mxl[k]];
                     const float rh = sm[bc + id + mxh[k]], rl = sm[bc + PLANE + id + mxh[k]];
                     const uint4 w4 = *reinterpret_cast<const uint4 *>(sm + cb + 2 * PLANE + id);
@@ -315,11 +325,17 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
                     // voxel pairs (0,1) and (2,3) of the quad
                     const float2 C01 = make_float2(ch.x, ch.y), C23 = make_float2(ch.z, ch.w);
                     const float2 L01 = make_float2(cl.x, cl.y), L23 = make_float2(cl.z, cl.w);
-                    // neighbour differences in the fixed order x-, x+, y-, y+, z-, z+
-                    float2 S01 = cdiff2(make_float2(lh, ch.x), make_float2(ll, cl.x), C01, L01);
-                    float2 S23 = cdiff2(make_float2(ch.y, ch.z), make_float2(cl.y, cl.z), C23, L23);
-                    S01 = add2(S01, cdiff2(make_float2(ch.y, ch.z), make_float2(cl.y, cl.z), C01, L01));
-                    S23 = add2(S23, cdiff2(make_float2(ch.w, rh), make_float2(cl.w, rl), C23, L23));
+                    // neighbour differences in the fixed order x-, x+, y-, y+, z-, z+; the x
+                    // differences voxel by voxel, written into the halves of the pairs
+                    const float xh[6] = {lh, ch.x, ch.y, ch.z, ch.w, rh}, xl[6] = {ll, cl.x, cl.y, cl.z, cl.w, rl};
+                    float dm[4], dp[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        dm[j] = cdiff(xh[j], xl[j], xh[j + 1], xl[j + 1]);
+                        dp[j] = cdiff(xh[j + 2], xl[j + 2], xh[j + 1], xl[j + 1]);
+                    }
+                    float2 S01 = add2(make_float2(dm[0], dm[1]), make_float2(dp[0], dp[1]));
+                    float2 S23 = add2(make_float2(dm[2], dm[3]), make_float2(dp[2], dp[3]));
                     S01 = add2(S01, cdiff2(make_float2(ymh.x, ymh.y), make_float2(yml.x, yml.y), C01, L01));
                     S23 = add2(S23, cdiff2(make_float2(ymh.z, ymh.w), make_float2(yml.z, yml.w), C23, L23));
                     S01 = add2(S01, cdiff2(make_float2(yph.x, yph.y), make_float2(ypl.x, ypl.y), C01, L01));
@@ -528,7 +544,7 @@ __global__ void __launch_bounds__(Cfg<M, V>::THREADS, Cfg<M, V>::MINB)
     if (!tb_setup<M, V>(P, status)) return;
     bool bad = false;
     for (int t = 0; t < ntime; ++t) {
-        auto get = [&](int item, int &local, const CUtensorMap *&mp) -> TBTile {
+        auto get = [&](int item, int &local, const CUtensorMap *&mp) -> const TBTile & {
             int lo = 0, hi = nmem - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
@@ -536,7 +552,7 @@ __global__ void __launch_bounds__(Cfg<M, V>::THREADS, Cfg<M, V>::MINB)
                 else hi = mid - 1;
             }
             local = item - mem[lo].item_begin;
-            const TBTile T = mem[lo].tile[(mem[lo].cur0 + t) & 1];  // register copy of the global descriptor
+            const TBTile &T = mem[lo].tile[(mem[lo].cur0 + t) & 1];  // fields read from global (L1) on use
             mp = T.maps;
             return T;
         };
