@@ -15,10 +15,11 @@
 // segment moves rigidly with the tip) and W = sum_free w, dW = sum_free dw.
 //
 // Trajectory: checkpoints (hi, lo) every ceil(sqrt(N)) steps are taken while
-// rfa_step records; the backward pass recomputes each segment with the
-// one-step kernel (bit-identical to the forward kernels), writing the hi part
-// of every state straight into a segment buffer, then runs the adjoint steps of
-// the segment in reverse.
+// rfa_step records; the backward pass replays each segment -- two steps per
+// launch with the blocked kernel in replay mode, which also stores the
+// intermediate state, else one step per launch (both bit-identical to the
+// forward kernels) -- writing the hi part of every state straight into a
+// segment buffer, then runs the adjoint steps of the segment in reverse.
 #include "rfa_internal.cuh"
 
 #include <cmath>
@@ -126,6 +127,8 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_step(const AdjArgs A)
     float accK[NL], accW[NL];
 #pragma unroll
     for (int l = 0; l < NL; ++l) accK[l] = accW[l] = 0.f;
+    float runK = 0.f, runW = 0.f;  // open run of quads of label run_lab (255: none)
+    unsigned run_lab = 255u;
     const bool wvalid = y < A.ny;  // warp-uniform (blockDim.x == 32)
     const int x0 = 4 * (blockIdx.x * 32 + lane);
     const bool inrow = wvalid && x0 < A.pitch;
@@ -133,7 +136,6 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_step(const AdjArgs A)
     const int ze = min(A.nz, zb + A.zchunk);
     const size_t rowoff = (size_t)(wvalid ? y : 0) * A.pitch + x0;
     const bool hasYm = y > 0, hasYp = y < A.ny - 1;
-    const bool dir = A.face == RFA_FACE_DIRICHLET;
 
     if (wvalid) {
         float4 lm = make_float4(0, 0, 0, 0), lc = lm, lp = lm;   // lambda at z-1, z, z+1
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_step(const AdjArgs A)
                 thR = __ldg(A.th + i + 4);
             }
             if (inrow) {
-                float lo_[4], Lo_[4];
+                float lo_[4], Lo_[4], vk4[4], vw4[4];
                 const float Lcv[4] = {Lc.x, Lc.y, Lc.z, Lc.w};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -241,16 +243,39 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_step(const AdjArgs A)
                     const bool valid = x < A.nx;
                     lo_[q] = valid ? l + smu - bc[q] * l : 0.f;
                     Lo_[q] = valid ? Lcv[q] + l : 0.f;
-                    const int lab = (lab4 >> (8 * q)) & 0xff;
-                    const bool face_vox = dir && (x == 0 || x == A.nx - 1 || y == 0 || y == A.ny - 1 ||
-                                                  z == 0 || z == A.nz - 1);
-                    // fixed labels carry fk = gw = 0; Dirichlet faces are excluded here
-                    const bool free_vox = valid && !face_vox;
-                    const float vk = free_vox ? l * lt : 0.f, vw = free_vox ? l * t : 0.f;
+                    // free voxels are exactly those with a > 0 (fixed labels and Dirichlet
+                    // faces carry a = 0; every tissue has K > 0)
+                    const bool free_vox = valid && ac[q] > 0.f;
+                    vk4[q] = free_vox ? l * lt : 0.f;
+                    vw4[q] = free_vox ? l * t : 0.f;
+                }
+                // per-label sums: a run of quads of one label adds into (runK, runW);
+                // other quads flush the run and go voxel by voxel
+                if (lab4 == run_lab * 0x01010101u) {
+                    runK += (vk4[0] + vk4[1]) + (vk4[2] + vk4[3]);
+                    runW += (vw4[0] + vw4[1]) + (vw4[2] + vw4[3]);
+                } else {
 #pragma unroll
                     for (int L = 0; L < NL; ++L) {
-                        accK[L] += lab == L ? vk : 0.f;
-                        accW[L] += lab == L ? vw : 0.f;
+                        accK[L] += run_lab == (unsigned)L ? runK : 0.f;
+                        accW[L] += run_lab == (unsigned)L ? runW : 0.f;
+                    }
+                    runK = runW = 0.f;
+                    run_lab = 255u;
+                    if (lab4 == (lab4 & 0xffu) * 0x01010101u) {
+                        run_lab = lab4 & 0xffu;
+                        runK = (vk4[0] + vk4[1]) + (vk4[2] + vk4[3]);
+                        runW = (vw4[0] + vw4[1]) + (vw4[2] + vw4[3]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const unsigned lab = (lab4 >> (8 * q)) & 0xffu;
+#pragma unroll
+                            for (int L = 0; L < NL; ++L) {
+                                accK[L] += lab == (unsigned)L ? vk4[q] : 0.f;
+                                accW[L] += lab == (unsigned)L ? vw4[q] : 0.f;
+                            }
+                        }
                     }
                 }
                 *reinterpret_cast<float4 *>(A.lam_out + i) = make_float4(lo_[0], lo_[1], lo_[2], lo_[3]);
@@ -264,6 +289,11 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_step(const AdjArgs A)
                 bc[q] = bp[q];
             }
         }
+    }
+#pragma unroll
+    for (int L = 0; L < NL; ++L) {  // close the last run
+        accK[L] += run_lab == (unsigned)L ? runK : 0.f;
+        accW[L] += run_lab == (unsigned)L ? runW : 0.f;
     }
     // block reduction of the per-label sums, then one FP64 atomic per label and block
     __shared__ float sK[8][NL], sW[8][NL];
@@ -466,6 +496,10 @@ rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads)
             A.gw[l] = (float)((t.rho_b * t.c_b / (t.rho * t.c)) * g->dt);
         }
     }
+    // replay schedule: the depth-2 blocked kernel (the grid's tile if it runs depth 2)
+    int replay_variant = -1;
+    if (g->sched.tb_depth == 2 && tb_supported(g, 2, g->sched.tile_variant)) replay_variant = g->sched.tile_variant;
+    else if (tb_supported(g, 2, 0)) replay_variant = 0;
     int lcur = 0;  // lambda ping-pong index holding lambda^{n+1}
     const int64_t nck = (int64_t)g->rec.ck_hi.size();
     for (int64_t c = nck - 1; c >= 0; --c) {
@@ -474,12 +508,24 @@ rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads)
         RFA_CUDA(cudaMemcpyAsync(sb, g->rec.ck_hi[c], nvp * 4, cudaMemcpyDeviceToDevice, g->stream));
         if (g->sp == RFA_STATE_F32C)
             RFA_CUDA(cudaMemcpyAsync(lo2, g->rec.ck_lo[c], nvp * 4, cudaMemcpyDeviceToDevice, g->stream));
-        for (int64_t st = s0; st + 1 < s1; ++st) {
-            const int j = (int)(st - s0);
-            const float *lin = g->sp == RFA_STATE_F32C ? lo2 + (size_t)(j & 1) * nvp : nullptr;
-            float *lout = g->sp == RFA_STATE_F32C ? lo2 + (size_t)((j + 1) & 1) * nvp : nullptr;
-            RFA_CUDA(launch_step_plain(g, sb + (size_t)j * nvp, lin, sb + (size_t)(j + 1) * nvp, lout, false,
-                                       false, false));
+        // two steps per launch with the blocked kernel where it applies (it also
+        // stores the intermediate state), the remainder one step at a time
+        const int64_t nstate = s1 - s0;
+        int64_t j = 0;
+        int lc = 0;  // lo buffer of state j
+        while (j + 1 < nstate) {
+            const float *lin = g->sp == RFA_STATE_F32C ? lo2 + (size_t)lc * nvp : nullptr;
+            float *lout = g->sp == RFA_STATE_F32C ? lo2 + (size_t)(lc ^ 1) * nvp : nullptr;
+            if (replay_variant >= 0 && j + 2 < nstate) {
+                RFA_CUDA(launch_step_tb_rec(g, 2, replay_variant, sb + (size_t)j * nvp, lin,
+                                            sb + (size_t)(j + 2) * nvp, lout, sb + (size_t)(j + 1) * nvp));
+                j += 2;
+            } else {
+                RFA_CUDA(launch_step_plain(g, sb + (size_t)j * nvp, lin, sb + (size_t)(j + 1) * nvp, lout, false,
+                                           false, false));
+                j += 1;
+            }
+            lc ^= 1;
         }
         for (int64_t st = s1 - 1; st >= s0; --st) {
             const float *th = sb + (size_t)(st - s0) * nvp;
@@ -496,6 +542,7 @@ rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads)
     double host[64];
     RFA_CUDA(cudaMemcpyAsync(host, accd, sizeof host, cudaMemcpyDeviceToHost, g->stream));
     RFA_CUDA(cudaStreamSynchronize(g->stream));
+    tb_forget_maps(g);  // tensor maps of the segment buffers, freed on return
     const double W = host[32], A1 = host[36];
     const double *dW = host + 33, *A2 = host + 37;
     const double P = g->geom.P;

@@ -196,10 +196,11 @@ __device__ __forceinline__ void tb_issue(const TBPipe &P, int j, const CUtensorM
 // nothing is carried between planes; for M = 3 the running sum and maximum
 // travel with the values through the stage-2 ring.  The sums keep the order
 // ((inc_1 + inc_2) + ...) of the per-step evaluation.
-template <int M, int V, bool DMG, bool FOLD, class Get>
+template <int M, int V, bool DMG, bool FOLD, bool REC, class Get>
 __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &get, unsigned *status,
                        bool &bad)
 {
+    static_assert(!(REC && DMG), "the replay has no damage integral");
     using C = Cfg<M, V>;
     constexpr int S0 = C::S0, PLANE = C::PLANE;
     float *sm = P.sm;
@@ -217,6 +218,18 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
         mid[k] = yl * TB_EX + 4 * qx;
         mxl[k] = qx > 0 ? -1 : 0;             // the tile's outer columns read themselves
         mxh[k] = qx < TB_QX - 1 ? 4 : 3;      // (their results are never used)
+    }
+    // replay: stage k < M also stores its quads that lie in the output tile
+    bool mrec[M + 1];
+    int mxo[M + 1], myo[M + 1];  // tile column of the quad's first voxel minus the x halo, row minus M
+#pragma unroll
+    for (int k = 0; k <= M; ++k) {
+        const int u = tid + k * TB_QX;
+        const int yl = u / TB_QX, qx = u - yl * TB_QX;
+        mrec[k] = REC && k >= 1 && k < M && tid < (C::EY - 2 * k) * TB_QX && yl >= M && yl < C::EY - M &&
+                  qx >= 1 && qx < TB_QX - 1;
+        mxo[k] = 4 * qx - TB_HX;
+        myo[k] = yl - M;
     }
     mact[M] = tid < C::NQO;
     mid[M] = (M + tid / 16) * TB_EX + 4 * (1 + tid % 16);
@@ -282,7 +295,7 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
             float4 carry4 = make_float4(0.f, 0.f, 0.f, 0.f);
             uint32_t latch4 = 0;
             double2 om01 = make_double2(0.0, 0.0), om23 = om01;
-            if (out_now) {
+            if (out_now && !REC) {
                 latch4 = *reinterpret_cast<const uint32_t *>(A.latch + gio);
                 if (DMG) carry4 = *reinterpret_cast<const float4 *>(A.omega_c + gio);
                 if (DMG && FOLD) {
@@ -379,6 +392,14 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
                             *reinterpret_cast<float4 *>(sm + bo + 3 * PLANE + id) =
                                 make_float4(X01.x, X01.y, X23.x, X23.y);
                         }
+                        if (REC && mrec[k]) {
+                            const int q = p0 - k, xr = X0 + mxo[k], yr = Y0 + myo[k];
+                            if (q >= zb && q < ze && yr < A.ny && xr < A.nx) {  // this item's planes only
+                                float *dst = A.rec_hi + (size_t)(k - 1) * A.rec_stride + (size_t)q * A.plane +
+                                             (size_t)yr * A.pitch + xr;
+                                *reinterpret_cast<float4 *>(dst) = make_float4(H01.x, H01.y, H23.x, H23.y);
+                            }
+                        }
                     } else if (out_now) {
                         // last stage: this step's own value, then the output quad (16-byte
                         // aligned: X0 % 64 == 0, pitch % 4 == 0; padding voxels compute to 0)
@@ -386,32 +407,34 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
                         *reinterpret_cast<float4 *>(A.hi_out + gio) = make_float4(H01.x, H01.y, H23.x, H23.y);
                         *reinterpret_cast<float4 *>(A.lo_out + gio) = make_float4(N01.x, N01.y, N23.x, N23.y);
                         bad |= !(isfinite(H01.x) && isfinite(H01.y) && isfinite(H23.x) && isfinite(H23.y));
-                        const float mx[4] = {fmaxf(X01.x, V01.x), fmaxf(X01.y, V01.y), fmaxf(X23.x, V23.x),
-                                             fmaxf(X23.y, V23.y)};
-                        uint32_t lbits = 0;
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if (j < nin && mx[j] >= A.thr) lbits |= 1u << (8 * j);
-                        if ((latch4 | lbits) != latch4)
-                            *reinterpret_cast<uint32_t *>(A.latch + gio) = latch4 | lbits;
-                        if (DMG) {
-                            P01 = add2(P01, arrhenius_inc2(V01, A.c0, A.c1, A.TK0));
-                            P23 = add2(P23, arrhenius_inc2(V23, A.c0, A.c1, A.TK0));
-                            const float part[4] = {P01.x, P01.y, P23.x, P23.y};
-                            float Pc[4] = {carry4.x, carry4.y, carry4.z, carry4.w};
+                        if (!REC) {  // latch and damage (the replay leaves them alone)
+                            const float mx[4] = {fmaxf(X01.x, V01.x), fmaxf(X01.y, V01.y), fmaxf(X23.x, V23.x),
+                                                 fmaxf(X23.y, V23.y)};
+                            uint32_t lbits = 0;
 #pragma unroll
                             for (int j = 0; j < 4; ++j)
-                                if (j < nin) Pc[j] = __fadd_rn(Pc[j], part[j]);
-                            if (FOLD) {
-                                double om[4] = {om01.x, om01.y, om23.x, om23.y};
+                                if (j < nin && mx[j] >= A.thr) lbits |= 1u << (8 * j);
+                            if ((latch4 | lbits) != latch4)
+                                *reinterpret_cast<uint32_t *>(A.latch + gio) = latch4 | lbits;
+                            if (DMG) {
+                                P01 = add2(P01, arrhenius_inc2(V01, A.c0, A.c1, A.TK0));
+                                P23 = add2(P23, arrhenius_inc2(V23, A.c0, A.c1, A.TK0));
+                                const float part[4] = {P01.x, P01.y, P23.x, P23.y};
+                                float Pc[4] = {carry4.x, carry4.y, carry4.z, carry4.w};
 #pragma unroll
                                 for (int j = 0; j < 4; ++j)
-                                    if (j < nin) carry_fold(om[j], Pc[j]);
-                                double2 *op = reinterpret_cast<double2 *>(A.omega + gio);
-                                op[0] = make_double2(om[0], om[1]);
-                                op[1] = make_double2(om[2], om[3]);
+                                    if (j < nin) Pc[j] = __fadd_rn(Pc[j], part[j]);
+                                if (FOLD) {
+                                    double om[4] = {om01.x, om01.y, om23.x, om23.y};
+#pragma unroll
+                                    for (int j = 0; j < 4; ++j)
+                                        if (j < nin) carry_fold(om[j], Pc[j]);
+                                    double2 *op = reinterpret_cast<double2 *>(A.omega + gio);
+                                    op[0] = make_double2(om[0], om[1]);
+                                    op[1] = make_double2(om[2], om[3]);
+                                }
+                                *reinterpret_cast<float4 *>(A.omega_c + gio) = make_float4(Pc[0], Pc[1], Pc[2], Pc[3]);
                             }
-                            *reinterpret_cast<float4 *>(A.omega_c + gio) = make_float4(Pc[0], Pc[1], Pc[2], Pc[3]);
                         }
                     }
                 }
@@ -476,7 +499,7 @@ struct TBMaps {
 };
 
 // one grid, M steps
-template <int M, int V, bool DMG, bool FOLD>
+template <int M, int V, bool DMG, bool FOLD, bool REC>
 __global__ void __launch_bounds__(Cfg<M, V>::THREADS, Cfg<M, V>::MINB)
     k_step_tb(const __grid_constant__ TBMaps maps, const TBTile T0, unsigned *status)
 {
@@ -489,7 +512,7 @@ __global__ void __launch_bounds__(Cfg<M, V>::THREADS, Cfg<M, V>::MINB)
         return T0;
     };
     bool bad = false;
-    tb_run<M, V, DMG, FOLD>(P, blockIdx.x, gridDim.x, T0.xt * T0.yt * T0.zc, get, status, bad);
+    tb_run<M, V, DMG, FOLD, REC>(P, blockIdx.x, gridDim.x, T0.xt * T0.yt * T0.zc, get, status, bad);
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusNonfinite);
 }
 
@@ -544,7 +567,7 @@ __global__ void __launch_bounds__(Cfg<M, V>::THREADS, Cfg<M, V>::MINB)
     if (!tb_setup<M, V>(P, status)) return;
     bool bad = false;
     for (int t = 0; t < ntime; ++t) {
-        auto get = [&](int item, int &local, const CUtensorMap *&mp) -> const TBTile & {
+        auto get = [&](int item, int &local, const CUtensorMap *&mp) -> TBTile {
             int lo = 0, hi = nmem - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
@@ -552,13 +575,13 @@ __global__ void __launch_bounds__(Cfg<M, V>::THREADS, Cfg<M, V>::MINB)
                 else hi = mid - 1;
             }
             local = item - mem[lo].item_begin;
-            const TBTile &T = mem[lo].tile[(mem[lo].cur0 + t) & 1];  // fields read from global (L1) on use
+            const TBTile T = mem[lo].tile[(mem[lo].cur0 + t) & 1];  // register copy of the global descriptor
             mp = T.maps;
             return T;
         };
         const bool fold = DMG && ((t + 1) % fold_every == 0 || t == ntime - 1);
-        const bool ok = fold ? tb_run<M, V, DMG, true>(P, blockIdx.x, gridDim.x, nitems, get, status, bad)
-                             : tb_run<M, V, DMG, false>(P, blockIdx.x, gridDim.x, nitems, get, status, bad);
+        const bool ok = fold ? tb_run<M, V, DMG, true, false>(P, blockIdx.x, gridDim.x, nitems, get, status, bad)
+                             : tb_run<M, V, DMG, false, false>(P, blockIdx.x, gridDim.x, nitems, get, status, bad);
         if (!ok) break;
         if (!grid_sync(gbar, gridDim.x)) {
             if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
@@ -644,20 +667,22 @@ void fill_tile(const rfa_grid *g, int parity, TBTile &T)
     T.c0 = dc.c0;
     T.c1 = dc.c1;
     T.TK0 = dc.TK0;
+    T.rec_hi = nullptr;
+    T.rec_stride = g->nvp;
 }
 
-template <int M, int V, bool DMG, bool FOLD>
+template <int M, int V, bool DMG, bool FOLD, bool REC = false>
 cudaError_t launch_inst(rfa_grid *g, const TBMaps &maps, TBTile T)
 {
     using C = Cfg<M, V>;
-    cudaError_t e = cudaFuncSetAttribute(k_step_tb<M, V, DMG, FOLD>,
+    cudaError_t e = cudaFuncSetAttribute(k_step_tb<M, V, DMG, FOLD, REC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     const int resident = 148 * C::MINB;
     tile_plan<M, V>(g, resident, 1 << 30, T);
     const long long items = (long long)T.xt * T.yt * T.zc;
     const unsigned grid = (unsigned)(items < resident ? items : resident);
-    k_step_tb<M, V, DMG, FOLD><<<grid, C::THREADS, C::SMEM, g->stream>>>(maps, T, g->status);
+    k_step_tb<M, V, DMG, FOLD, REC><<<grid, C::THREADS, C::SMEM, g->stream>>>(maps, T, g->status);
     return cudaGetLastError();
 }
 
@@ -771,6 +796,23 @@ cudaError_t launch_step_tb(rfa_grid *g, int depth, int variant, const void *th_i
     TB_CASE(2, 1)
     TB_CASE(2, 2)
 #undef TB_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step_tb_rec(rfa_grid *g, int depth, int variant, const void *th_in, const void *lo_in,
+                               void *th_out, void *lo_out, float *rec_hi)
+{
+    TBMaps maps;
+    if (!tb_make_maps(g, variant, th_in, lo_in, maps.m)) return cudaErrorInvalidValue;
+    TBTile T;
+    fill_tile(g, 0, T);
+    T.hi_out = (float *)th_out;
+    T.lo_out = (float *)lo_out;
+    T.rec_hi = rec_hi;
+    if (depth == 2 && variant == 0) return launch_inst<2, 0, false, false, true>(g, maps, T);
+    if (depth == 3 && variant == 0) return launch_inst<3, 0, false, false, true>(g, maps, T);
+    if (depth == 2 && variant == 1) return launch_inst<2, 1, false, false, true>(g, maps, T);
+    if (depth == 2 && variant == 2) return launch_inst<2, 2, false, false, true>(g, maps, T);
     return cudaErrorInvalidValue;
 }
 

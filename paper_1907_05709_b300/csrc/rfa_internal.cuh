@@ -189,6 +189,10 @@ bool tb_supported(const rfa_grid *g, int depth, int variant);
 void tb_forget_maps(const rfa_grid *g);
 cudaError_t launch_step_tb(rfa_grid *g, int depth, int variant, const void *th_in,
                            const void *lo_in, void *th_out, void *lo_out, bool damage, bool fold);
+// replay for the adjoint: depth steps without latch or damage; the hi parts of
+// the depth - 1 intermediate states go to rec_hi + (k - 1) * nvp (k = 1 .. depth-1)
+cudaError_t launch_step_tb_rec(rfa_grid *g, int depth, int variant, const void *th_in, const void *lo_in,
+                               void *th_out, void *lo_out, float *rec_hi);
 // blocked stepping geometry (kernels_tb.cu): outputs and tiling of one grid;
 // `maps` points at the tensor maps (hi, lo, ab, s) of the input state
 struct TBTile {
@@ -202,6 +206,8 @@ struct TBTile {
     int xt, yt, zc;  // tiles in x and y, z chunks; work items = xt * yt * zc
     float thr;
     float c0, c1, TK0;
+    float *rec_hi;  // replay: hi of the intermediate states (stage k at rec_hi + (k - 1) * rec_stride)
+    size_t rec_stride;
 };
 // a batch member on the host: tiles and tensor maps for both ping-pong parities
 struct TBMemberHost {
