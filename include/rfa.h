@@ -259,6 +259,23 @@ rfa_status rfa_batch_autotune(rfa_batch *b, const char *cache_path);
  * (when 0, rfa_last_error() gives the reason capture was not used). */
 rfa_status rfa_batch_get_schedule(rfa_batch *b, int *tb_depth, int *tile_variant, int *uses_graph);
 
+/*
+ * Breathing motion (Sec. "Consideration of Breathing Motion", Eq. breathing):
+ * the simulation runs in the reference space; the temperature in the moving
+ * space at one instant is T(x) = T_ref(x + u_inv(x)), with u_inv the inverse
+ * motion vector field of that instant.  T_ref is sampled by trilinear
+ * interpolation of the current state; sample positions outside the grid take
+ * the nearest face value (a non-finite displacement samples the low face).
+ *   u_inv_dev : device float, 3 dense planes [3][nz][ny][nx] (x, y, z
+ *               components, metres), caller-owned, read only.
+ *   dst_dev   : device, nx*ny*nz values in degrees C, x fastest; float, or
+ *               double when as_f64 != 0.  Caller-owned.
+ * FP64 states interpolate in FP64; FP32 states in FP32 (hi and lo parts
+ * separately).  Asynchronous on the grid's stream; the state is not changed.
+ * Errors: RFA_E_INVALID (null pointer), RFA_E_STATE (no tissue yet).
+ */
+rfa_status rfa_warp_temperature(rfa_grid *g, const float *u_inv_dev, void *dst_dev, int as_f64);
+
 /* Diagnostic (the paper has no counterpart): launch a kernel that waits on a
  * device flag nothing sets, with the same bounded-spin pattern as the
  * library's real waits, and report how it ended.  Returns RFA_E_TIMEOUT when the

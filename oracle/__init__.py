@@ -185,3 +185,36 @@ def necrosis(m: Model, st: State, T_a: Optional[float] = None, width_K: float = 
     T = st.theta + Ta
     vs = h3 * float(np.sum(1.0 / (1.0 + np.exp(-(T - thr_C) / width_K))))
     return mask, (n_th, n_ar), (h3 * n_th, h3 * n_ar), vs
+
+
+def warp_temperature(theta: np.ndarray, u_inv: np.ndarray, h: float, T_a: float) -> np.ndarray:
+    """Breathing motion (Sec. "Consideration of Breathing Motion", Eq. breathing):
+    T(x) = T_ref(x + u_inv(x)), T_ref = T_a + theta sampled by trilinear
+    interpolation, in FP64.  theta: [nz][ny][nx]; u_inv: [3][nz][ny][nx] (x, y, z
+    components, metres).  Per axis, with voxel index c and displacement
+    d = u / h in voxels: i = c + floor(d); i < 0 samples voxel 0, i >= n-1 samples
+    voxel n-1, otherwise the segment [i, i+1] at weight f = d - floor(d)."""
+    nz, ny, nx = theta.shape
+    d = u_inv.astype(np.float64) / h
+    cz, cy, cx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+
+    def axis(c, dd, n):
+        dd = np.clip(np.nan_to_num(dd, nan=-(n + 1.0)), -(n + 1.0), n + 1.0)
+        fl = np.floor(dd)
+        i = c + fl.astype(np.int64)
+        low, high = i < 0, i >= n - 1
+        i0 = np.where(low, 0, np.where(high, n - 1, i))
+        i1 = np.where(low | high, i0, i + 1)
+        f = np.where(low | high, 0.0, dd - fl)
+        return i0, i1, f
+
+    x0, x1, fx = axis(cx, d[0], nx)
+    y0, y1, fy = axis(cy, d[1], ny)
+    z0, z1, fz = axis(cz, d[2], nz)
+    out = np.zeros(theta.shape)
+    # sum over the 8 corners of the cell, each with its product of 1-D weights
+    for zi, wz in ((z0, 1.0 - fz), (z1, fz)):
+        for yi, wy in ((y0, 1.0 - fy), (y1, fy)):
+            for xi, wx in ((x0, 1.0 - fx), (x1, fx)):
+                out += wz * wy * wx * theta[zi, yi, xi]
+    return out + T_a

@@ -33,7 +33,7 @@ EXPORTED = ("rfa_create_grid", "rfa_destroy_grid", "rfa_set_tissue", "rfa_place_
             "rfa_set_schedule", "rfa_get_schedule", "rfa_autotune", "rfa_batch_create",
             "rfa_batch_step", "rfa_batch_destroy", "rfa_synchronize", "rfa_steps_done",
             "rfa_last_error", "rfa_necrosis_reduce_noalloc", "rfa_batch_autotune",
-            "rfa_batch_get_schedule", "rfa_selftest_wait_timeout")
+            "rfa_batch_get_schedule", "rfa_selftest_wait_timeout", "rfa_warp_temperature")
 
 
 class RfaError(RuntimeError):
@@ -95,6 +95,7 @@ def lib():
         "rfa_batch_autotune": [P, ctypes.c_char_p],
         "rfa_batch_get_schedule": [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)],
         "rfa_selftest_wait_timeout": [ctypes.c_longlong],
+        "rfa_warp_temperature": [P, P, P, I],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -198,6 +199,12 @@ def rfa_step(g, nsteps: int, record_for_backward: int = 0):
 def rfa_get_temperature(g, dst, dst_is_device: bool, as_f64: bool = False):
     _check(lib().rfa_get_temperature(g, _ptr(dst), int(bool(dst_is_device)), int(bool(as_f64))),
            "rfa_get_temperature")
+
+
+def rfa_warp_temperature(g, u_inv_dev, dst_dev, as_f64: bool = False):
+    """u_inv_dev: CUDA float32 tensor [3, nz, ny, nx] (metres); dst_dev: CUDA tensor [nz, ny, nx]."""
+    _check(lib().rfa_warp_temperature(g, _ptr(u_inv_dev), _ptr(dst_dev), int(bool(as_f64))),
+           "rfa_warp_temperature")
 
 
 def rfa_get_field(g, field: int, dst: np.ndarray):

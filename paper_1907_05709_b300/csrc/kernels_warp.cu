@@ -1,0 +1,133 @@
+// kernels_warp.cu -- the breathing-motion resampling of the temperature field
+// (Sec. "Consideration of Breathing Motion", Eq. breathing): the simulation
+// runs in the reference space X, and the temperature shown in the moving space
+// x at time t is T(x) = T_ref(x + u_inv(x, t)), with u_inv the inverse motion
+// vector field.  T_ref is sampled by trilinear interpolation of the voxel
+// values; sample positions are clamped to the grid (the nearest face value
+// outside it).
+//
+// Precision: the fractional sample offset is formed from the displacement in
+// voxels alone (x + d with x integer: floor(x + d) = x + floor(d)), so FP32
+// keeps it to ~1e-7 voxel.  Compensated states interpolate hi and lo
+// separately in FP32 and add them at the end; FP64 states interpolate in FP64.
+#include "rfa_internal.cuh"
+
+namespace rfa {
+namespace {
+
+template <class R>
+struct Axis {
+    int i0, i1;
+    R f;
+};
+
+// sample coordinate c + d (c integer voxel index, d displacement in voxels),
+// clamped to [0, n-1]: i = c + floor(d); below 0 -> voxel 0, at or past n-1 ->
+// voxel n-1, else between i and i+1 with weight f = d - floor(d)
+template <class R>
+__device__ __forceinline__ Axis<R> axis_sample(int c, R d, int n)
+{
+    Axis<R> a;
+    d = fmin(fmax(d, -(R)(n + 1)), (R)(n + 1));  // also maps NaN to the low face
+    const R fl = floor(d);
+    const long long i = (long long)c + (long long)fl;
+    if (i < 0) {
+        a.i0 = a.i1 = 0;
+        a.f = R(0);
+    } else if (i >= n - 1) {
+        a.i0 = a.i1 = n - 1;
+        a.f = R(0);
+    } else {
+        a.i0 = (int)i;
+        a.i1 = (int)i + 1;
+        a.f = d - fl;
+    }
+    return a;
+}
+
+template <class R>
+__device__ __forceinline__ R lerp_(R a, R b, R f)
+{
+    return a + f * (b - a);
+}
+
+template <class R, class Load>
+__device__ __forceinline__ R trilinear(const Axis<R> &ax, const Axis<R> &ay, const Axis<R> &az, const Load &v)
+{
+    const R c00 = lerp_(v(ax.i0, ay.i0, az.i0), v(ax.i1, ay.i0, az.i0), ax.f);
+    const R c10 = lerp_(v(ax.i0, ay.i1, az.i0), v(ax.i1, ay.i1, az.i0), ax.f);
+    const R c01 = lerp_(v(ax.i0, ay.i0, az.i1), v(ax.i1, ay.i0, az.i1), ax.f);
+    const R c11 = lerp_(v(ax.i0, ay.i1, az.i1), v(ax.i1, ay.i1, az.i1), ax.f);
+    return lerp_(lerp_(c00, c10, ay.f), lerp_(c01, c11, ay.f), az.f);
+}
+
+template <int SP>
+__global__ void k_warp(const void *th, const float *lo, const float *u, int nx, int ny, int nz, int pitch,
+                       size_t plane, double h, double T_a, void *dst, int as_f64)
+{
+    const size_t n = (size_t)nx * ny * nz;
+    for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < n; j += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(j % nx);
+        const size_t r = j / nx;
+        const int y = (int)(r % ny), z = (int)(r / ny);
+        double T;
+        if (SP == RFA_STATE_F64) {
+            const Axis<double> ax = axis_sample<double>(x, (double)u[j] / h, nx);
+            const Axis<double> ay = axis_sample<double>(y, (double)u[j + n] / h, ny);
+            const Axis<double> az = axis_sample<double>(z, (double)u[j + 2 * n] / h, nz);
+            const double *t = (const double *)th;
+            T = trilinear<double>(ax, ay, az, [&](int i, int k, int l) {
+                    return t[(size_t)l * plane + (size_t)k * pitch + i];
+                }) + T_a;
+        } else {
+            const float hf = (float)h;
+            const Axis<float> ax = axis_sample<float>(x, __fdiv_rn(u[j], hf), nx);
+            const Axis<float> ay = axis_sample<float>(y, __fdiv_rn(u[j + n], hf), ny);
+            const Axis<float> az = axis_sample<float>(z, __fdiv_rn(u[j + 2 * n], hf), nz);
+            const float *t = (const float *)th;
+            const float vh = trilinear<float>(ax, ay, az, [&](int i, int k, int l) {
+                return t[(size_t)l * plane + (size_t)k * pitch + i];
+            });
+            float vl = 0.f;
+            if (SP == RFA_STATE_F32C)
+                vl = trilinear<float>(ax, ay, az, [&](int i, int k, int l) {
+                    return lo[(size_t)l * plane + (size_t)k * pitch + i];
+                });
+            T = ((double)vh + (double)vl) + T_a;
+        }
+        if (as_f64) ((double *)dst)[j] = T;
+        else ((float *)dst)[j] = (float)T;
+    }
+}
+
+}  // namespace
+}  // namespace rfa
+
+using namespace rfa;
+
+extern "C" rfa_status rfa_warp_temperature(rfa_grid *g, const float *u_inv_dev, void *dst_dev, int as_f64)
+{
+    if (!g || !u_inv_dev || !dst_dev) {
+        set_error("null argument");
+        return RFA_E_INVALID;
+    }
+    if (!g->have_tissue) {
+        set_error("rfa_set_tissue must come first");
+        return RFA_E_STATE;
+    }
+    const void *th = g->th[g->cur];
+    const float *lo = (const float *)g->lo[g->cur];
+    const unsigned blocks = 148 * 8;
+    if (g->sp == RFA_STATE_F64)
+        k_warp<RFA_STATE_F64><<<blocks, 256, 0, g->stream>>>(th, lo, u_inv_dev, g->nx, g->ny, g->nz, g->pitch,
+                                                            g->plane, g->h, g->T_a, dst_dev, as_f64);
+    else if (g->sp == RFA_STATE_F32C)
+        k_warp<RFA_STATE_F32C><<<blocks, 256, 0, g->stream>>>(th, lo, u_inv_dev, g->nx, g->ny, g->nz, g->pitch,
+                                                             g->plane, g->h, g->T_a, dst_dev, as_f64);
+    else
+        k_warp<RFA_STATE_F32><<<blocks, 256, 0, g->stream>>>(th, lo, u_inv_dev, g->nx, g->ny, g->nz, g->pitch,
+                                                            g->plane, g->h, g->T_a, dst_dev, as_f64);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "rfa_warp_temperature launch");
+    return RFA_OK;
+}

@@ -373,3 +373,28 @@ def paper_tip_probes(n: int = 64):
     c = n // 2
     return {"2.5mm": (c, c, c + 2 + 5), "5mm": (c, c, c + 2 + 10)}
 
+
+
+def breathing_field(case: Case, t_s: float, seed: int = 0, period_s: float = 4.0) -> np.ndarray:
+    """Synthetic inverse motion vector field u_inv(x, t) of one breathing instant
+    (metres, float32 [3][nz][ny][nx]; the paper's fields come from 4D CT, which
+    is not available).  Craniocaudal motion along z, strongest above a seeded
+    diaphragm level z_d, with a small lateral component:
+        s(t)  = sin^2(pi t / period)               (0 at exhale, 1 at inhale)
+        w(z)  = (1 + tanh((z - z_d) / L)) / 2,      L = 20 mm
+        u_z   = -A s(t) w(z),   u_x = 0.15 A s(t) w(z) sin(pi y / Y),   u_y = 0
+    with A ~ U(5, 10) mm.  |du/dx| <= A / (2 L) <= 0.25, so x -> x + u_inv is a
+    diffeomorphism."""
+    rng = np.random.default_rng(seed)
+    A = rng.uniform(5e-3, 10e-3)
+    zd = case.h * case.nz * rng.uniform(0.4, 0.6)
+    L = 20e-3
+    s = math.sin(math.pi * t_s / period_s) ** 2
+    z = (np.arange(case.nz) * case.h)[:, None, None]
+    y = (np.arange(case.ny) * case.h)[None, :, None]
+    Y = max(case.h * (case.ny - 1), case.h)
+    w = 0.5 * (1.0 + np.tanh((z - zd) / L))
+    u = np.zeros((3, case.nz, case.ny, case.nx), np.float32)
+    u[2] = np.broadcast_to(-A * s * w, (case.nz, case.ny, case.nx))
+    u[0] = np.broadcast_to(0.15 * A * s * w * np.sin(math.pi * y / Y), (case.nz, case.ny, case.nx))
+    return u
