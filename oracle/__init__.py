@@ -38,9 +38,9 @@ def lib():
                                _P_D, _P_D, _P_D, _P_D, _P_U8, _P_D]
         L.or_source.argtypes = [i, i, i, d, d, _P_D, _P_D, _P_U8, _P_D, _P_D, _P_D]
         L.or_run.argtypes = [i, i, i, i64, _P_D, _P_D, _P_D, _P_D, _P_U8, _P_D, _P_U8, d, d,
-                             i, d, d, d, d, _P_D, _P_D, i]
+                             i, d, d, d, d, _P_D, _P_D, i, _P_D]
         L.or_adjoint.argtypes = [i, i, i, i64, d, d, _P_D, _P_D, _P_D, _P_D, _P_U8, _P_U8, i,
-                                 _P_D, _P_D, _P_D, _P_D, _P_D, _P_D, _P_D, i]
+                                 _P_D, _P_D, _P_D, _P_D, _P_D, _P_D, _P_D, i, _P_D, _P_D, _P_D]
         L.or_source_grad.argtypes = [i, i, i, d, d, _P_D, _P_D, _P_U8, _P_D, _P_D]
         for f in ("or_setup", "or_source", "or_run", "or_adjoint", "or_source_grad"):
             getattr(L, f).restype = ctypes.c_int
@@ -103,10 +103,54 @@ class Model:
     tab: np.ndarray
     needle: np.ndarray
     T_a: float
+    # conservative conduction (None: the centre form): face weights [6][nz][ny][nx]
+    # for x-, x+, y-, y+, z-, z+ and their derivatives by the voxel's K (dwa) and
+    # by the neighbour's K (dwb)
+    wf: Optional[np.ndarray] = None
+    dwa: Optional[np.ndarray] = None
+    dwb: Optional[np.ndarray] = None
 
 
-def setup(case, param_mode: str = "f64") -> Model:
-    """Coefficients, fixed set, initial state and RF source of ``case``."""
+def face_weights(case, param_mode: str):
+    """Conservative conduction, div(K grad T) of Eq. 2675-eq1_Kath with the face
+    conductance of two voxels the harmonic mean of their K:
+        w(l, m) = dt / (rho_l c_l h^2) * 2 K_l K_m / (K_l + K_m)
+    for a voxel of label l and its neighbour of label m, rounded to FP32 for the
+    'bf16' and 'f32' parameter modes (the values the GPU's label-pair table
+    holds), and the exact derivatives dw/dK_l, dw/dK_m.  Returns (wf, dwa, dwb),
+    each [6][nz][ny][nx] for the directions x-, x+, y-, y+, z-, z+ (0 outside)."""
+    L = len(case.table)
+    W = np.zeros((L, L))
+    DA = np.zeros((L, L))
+    DB = np.zeros((L, L))
+    for l, tl in enumerate(case.table):
+        g = case.dt / (tl.rho * tl.c * case.h * case.h)
+        for m, tm in enumerate(case.table):
+            Ks = tl.k + tm.k
+            if Ks > 0.0:
+                W[l, m] = g * (2.0 * tl.k * tm.k / Ks)
+                DA[l, m] = g * 2.0 * tm.k * tm.k / (Ks * Ks)
+                DB[l, m] = g * 2.0 * tl.k * tl.k / (Ks * Ks)
+    if param_mode in ("bf16", "f32"):
+        W = W.astype(np.float32).astype(np.float64)
+    lab = case.labels.astype(np.int64).reshape(case.nz, case.ny, case.nx)
+    out = [np.zeros((6, case.nz, case.ny, case.nx)) for _ in range(3)]
+    # (array axis, shift): x- reads x-1, i.e. the neighbour label at index - 1
+    for d, (ax, sh) in enumerate(((2, -1), (2, 1), (1, -1), (1, 1), (0, -1), (0, 1))):
+        n = lab.shape[ax]
+        idx = np.arange(n) + sh
+        ok = (idx >= 0) & (idx < n)
+        nb = np.take(lab, np.clip(idx, 0, n - 1), axis=ax)
+        okb = np.broadcast_to(ok.reshape([-1 if k == ax else 1 for k in range(3)]), lab.shape)
+        for arr, T in zip(out, (W, DA, DB)):
+            arr[d] = np.where(okb, T[lab, nb], 0.0)
+    return tuple(np.ascontiguousarray(a) for a in out)
+
+
+def setup(case, param_mode: str = "f64", conduction: str = "centre") -> Model:
+    """Coefficients, fixed set, initial state and RF source of ``case``;
+    ``conduction`` = 'centre' (K at the voxel, the paper's form) or 'harmonic'
+    (conservative form, see ``face_weights``)."""
     nx, ny, nz = case.nx, case.ny, case.nz
     shape = (nz, ny, nx)
     labels = np.ascontiguousarray(case.labels.astype(np.uint8).reshape(shape))
@@ -121,8 +165,13 @@ def setup(case, param_mode: str = "f64") -> Model:
     W = ctypes.c_double(0.0)
     _check(lib().or_source(nx, ny, nz, case.h, case.dt, _pd(nd), _pd(rhoc), _pu8(fx), _pd(s),
                            _pd(dist), ctypes.byref(W)), "source")
-    return Model(nx, ny, nz, case.h, case.dt, a, b, qm, rhoc, fx, th0, s, dist, W.value,
-                 labels, tab, nd, case.T_a_C)
+    m = Model(nx, ny, nz, case.h, case.dt, a, b, qm, rhoc, fx, th0, s, dist, W.value,
+              labels, tab, nd, case.T_a_C)
+    if conduction == "harmonic":
+        m.wf, m.dwa, m.dwb = face_weights(case, param_mode)
+    elif conduction != "centre":
+        raise ValueError(conduction)
+    return m
 
 
 @dataclasses.dataclass
@@ -151,7 +200,8 @@ def run(m: Model, st: State, nsteps: int, damage=None, T_thr_C: float = 60.0,
     thr = dmg.T_thr_C if dmg is not None else T_thr_C
     _check(lib().or_run(m.nx, m.ny, m.nz, int(nsteps), _pd(m.a), _pd(m.b), _pd(m.s), _pd(m.qm),
                         _pu8(m.isfixed), _pd(st.theta), _pu8(st.latch), m.T_a, thr, en, m.dt,
-                        A, Ea, R, _pd(st.omega), _pd(st.omega_c), int(nthreads)), "run")
+                        A, Ea, R, _pd(st.omega), _pd(st.omega_c), int(nthreads),
+                        None if m.wf is None else _pd(m.wf)), "run")
     st.steps += int(nsteps)
     return st
 
@@ -166,7 +216,9 @@ def adjoint(m: Model, nsteps: int, lam_N: np.ndarray, nthreads: int = 0):
     _check(lib().or_adjoint(m.nx, m.ny, m.nz, int(nsteps), m.h, m.dt, _pd(m.a), _pd(m.b),
                             _pd(m.s), _pd(m.qm), _pu8(m.isfixed), _pu8(m.labels), nl, _pd(m.tab),
                             _pd(m.rhoc), _pd(m.theta0), _pd(lam), _pd(Lam), _pd(gk), _pd(gw),
-                            int(nthreads)), "adjoint")
+                            int(nthreads), None if m.wf is None else _pd(m.wf),
+                            None if m.wf is None else _pd(m.dwa),
+                            None if m.wf is None else _pd(m.dwb)), "adjoint")
     g = np.zeros(4)
     _check(lib().or_source_grad(m.nx, m.ny, m.nz, m.h, m.dt, _pd(m.needle), _pd(m.rhoc),
                                 _pu8(m.isfixed), _pd(Lam), _pd(g)), "source_grad")

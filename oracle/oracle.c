@@ -232,11 +232,45 @@ int or_source(int nx, int ny, int nz, double h, double dt, const double *nd,
  * omega_i += dt * A * exp(-Ea / (R * T_K)) (Eq. eq-tissState's integrand,
  * right-rectangle rule on the new temperature), compensated by Kahan's method.
  */
+/*
+ * Conductive term of free voxel i.  Centre form (wf == NULL): the paper's
+ * K * (sum of second differences) with K taken at the voxel, a_i * sum_nb
+ * (theta_nb - theta_i).  Conservative form (wf != NULL): div(K grad T) with the
+ * face conductance between two voxels the harmonic mean of their K,
+ * sum_nb wf[d][i] (theta_nb - theta_i), wf[d][i] = dt/(rho c_i h^2) *
+ * 2 K_i K_nb / (K_i + K_nb) for direction d = x-, x+, y-, y+, z-, z+ (0 outside
+ * the grid).
+ */
+static double conduction(int nx, int ny, int nz, const double *a, const double *wf, const double *cur,
+                         int x, int y, int z)
+{
+    const size_t n = (size_t)nx * ny * nz, i = IDX(x, y, z);
+    const double t = cur[i];
+    if (!wf) {
+        double sum = 0.0;
+        if (x > 0)      sum += cur[IDX(x - 1, y, z)] - t;
+        if (x < nx - 1) sum += cur[IDX(x + 1, y, z)] - t;
+        if (y > 0)      sum += cur[IDX(x, y - 1, z)] - t;
+        if (y < ny - 1) sum += cur[IDX(x, y + 1, z)] - t;
+        if (z > 0)      sum += cur[IDX(x, y, z - 1)] - t;
+        if (z < nz - 1) sum += cur[IDX(x, y, z + 1)] - t;
+        return a[i] * sum;
+    }
+    double f = 0.0;
+    if (x > 0)      f += wf[0 * n + i] * (cur[IDX(x - 1, y, z)] - t);
+    if (x < nx - 1) f += wf[1 * n + i] * (cur[IDX(x + 1, y, z)] - t);
+    if (y > 0)      f += wf[2 * n + i] * (cur[IDX(x, y - 1, z)] - t);
+    if (y < ny - 1) f += wf[3 * n + i] * (cur[IDX(x, y + 1, z)] - t);
+    if (z > 0)      f += wf[4 * n + i] * (cur[IDX(x, y, z - 1)] - t);
+    if (z < nz - 1) f += wf[5 * n + i] * (cur[IDX(x, y, z + 1)] - t);
+    return f;
+}
+
 int or_run(int nx, int ny, int nz, int64_t nsteps,
            const double *a, const double *b, const double *s, const double *qm,
            const uint8_t *isfixed, double *theta, uint8_t *latch, double T_a, double T_thr,
            int damage, double dt, double A, double Ea, double R, double *omega, double *omega_c,
-           int nthreads)
+           int nthreads, const double *wf)
 {
     size_t n = (size_t)nx * ny * nz;
     double *cur = theta;
@@ -258,14 +292,7 @@ int or_run(int nx, int ny, int nz, int64_t nsteps,
                         tn = t;   /* Alg. 1 else-branch: copy the input value */
                     } else {
                         /* central second differences in x, y, z (Eq. 2675-eq3) */
-                        double sum = 0.0;
-                        if (x > 0)      sum += cur[IDX(x - 1, y, z)] - t;
-                        if (x < nx - 1) sum += cur[IDX(x + 1, y, z)] - t;
-                        if (y > 0)      sum += cur[IDX(x, y - 1, z)] - t;
-                        if (y < ny - 1) sum += cur[IDX(x, y + 1, z)] - t;
-                        if (z > 0)      sum += cur[IDX(x, y, z - 1)] - t;
-                        if (z < nz - 1) sum += cur[IDX(x, y, z + 1)] - t;
-                        tn = t + a[i] * sum - b[i] * t + s[i] + qm[i];
+                        tn = t + conduction(nx, ny, nz, a, wf, cur, x, y, z) - b[i] * t + s[i] + qm[i];
                     }
                     nxt[i] = tn;
                     if (tn + T_a >= T_thr) latch[i] = 1;
@@ -292,21 +319,37 @@ int or_run(int nx, int ny, int nz, int64_t nsteps,
 /* ---------------------------------------------------------------- adjoint */
 
 /* d theta'_j / d theta_i of one step (the step matrix entry A[j][i]). */
-static double step_entry(int nx, int ny, int nz, const double *a, const double *b,
+static double step_entry(int nx, int ny, int nz, const double *a, const double *b, const double *wf,
                          const uint8_t *isfixed, int xj, int yj, int zj, int xi, int yi, int zi)
 {
-    size_t j = IDX(xj, yj, zj);
+    const size_t n = (size_t)nx * ny * nz, j = IDX(xj, yj, zj);
     if (isfixed[j]) return (xj == xi && yj == yi && zj == zi) ? 1.0 : 0.0;
-    if (xj == xi && yj == yi && zj == zi) {
-        int deg = (xj > 0) + (xj < nx - 1) + (yj > 0) + (yj < ny - 1) + (zj > 0) + (zj < nz - 1);
-        return 1.0 - a[j] * deg - b[j];
+    if (!wf) {
+        if (xj == xi && yj == yi && zj == zi) {
+            int deg = (xj > 0) + (xj < nx - 1) + (yj > 0) + (yj < ny - 1) + (zj > 0) + (zj < nz - 1);
+            return 1.0 - a[j] * deg - b[j];
+        }
+        return a[j];  /* i is a grid neighbour of j */
     }
-    return a[j];  /* i is a grid neighbour of j */
+    if (xj == xi && yj == yi && zj == zi) {
+        double w = 0.0;
+        if (xj > 0)      w += wf[0 * n + j];
+        if (xj < nx - 1) w += wf[1 * n + j];
+        if (yj > 0)      w += wf[2 * n + j];
+        if (yj < ny - 1) w += wf[3 * n + j];
+        if (zj > 0)      w += wf[4 * n + j];
+        if (zj < nz - 1) w += wf[5 * n + j];
+        return 1.0 - w - b[j];
+    }
+    /* i is the neighbour of j in direction d */
+    const int d = xi < xj ? 0 : xi > xj ? 1 : yi < yj ? 2 : yi > yj ? 3 : zi < zj ? 4 : 5;
+    return wf[(size_t)d * n + j];
 }
 
 /* one forward step without latch/damage (used to recompute the trajectory) */
-static void plain_step(int nx, int ny, int nz, const double *a, const double *b, const double *s,
-                       const double *qm, const uint8_t *isfixed, const double *cur, double *nxt)
+static void plain_step(int nx, int ny, int nz, const double *a, const double *b, const double *wf,
+                       const double *s, const double *qm, const uint8_t *isfixed, const double *cur,
+                       double *nxt)
 {
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < nz; ++z)
@@ -315,14 +358,7 @@ static void plain_step(int nx, int ny, int nz, const double *a, const double *b,
                 size_t i = IDX(x, y, z);
                 double t = cur[i];
                 if (isfixed[i]) { nxt[i] = t; continue; }
-                double sum = 0.0;
-                if (x > 0)      sum += cur[IDX(x - 1, y, z)] - t;
-                if (x < nx - 1) sum += cur[IDX(x + 1, y, z)] - t;
-                if (y > 0)      sum += cur[IDX(x, y - 1, z)] - t;
-                if (y < ny - 1) sum += cur[IDX(x, y + 1, z)] - t;
-                if (z > 0)      sum += cur[IDX(x, y, z - 1)] - t;
-                if (z < nz - 1) sum += cur[IDX(x, y, z + 1)] - t;
-                nxt[i] = t + a[i] * sum - b[i] * t + s[i] + qm[i];
+                nxt[i] = t + conduction(nx, ny, nz, a, wf, cur, x, y, z) - b[i] * t + s[i] + qm[i];
             }
 }
 
@@ -337,7 +373,8 @@ int or_adjoint(int nx, int ny, int nz, int64_t nsteps, double h, double dt,
                const double *a, const double *b, const double *s, const double *qm,
                const uint8_t *isfixed, const uint8_t *labels, int n_labels, const double *tab,
                const double *rhoc, const double *theta0, double *lam,
-               double *Lambda, double *g_k, double *g_wb, int nthreads)
+               double *Lambda, double *g_k, double *g_wb, int nthreads,
+               const double *wf, const double *dwa, const double *dwb)
 {
     size_t n = (size_t)nx * ny * nz;
 #ifdef _OPENMP
@@ -358,7 +395,7 @@ int or_adjoint(int nx, int ny, int nz, int64_t nsteps, double h, double dt,
     memcpy(traj, theta0, n * sizeof(double));
     for (int64_t st = 0; st < nsteps; ++st) {
         if (st % seg == 0) memcpy(ck + (size_t)(st / seg) * n, traj, n * sizeof(double));
-        plain_step(nx, ny, nz, a, b, s, qm, isfixed, traj, traj + n);
+        plain_step(nx, ny, nz, a, b, wf, s, qm, isfixed, traj, traj + n);
         memcpy(traj, traj + n, n * sizeof(double));
     }
     memset(Lambda, 0, n * sizeof(double));
@@ -369,7 +406,7 @@ int or_adjoint(int nx, int ny, int nz, int64_t nsteps, double h, double dt,
         /* recompute theta^{s0} .. theta^{s1-1} */
         memcpy(traj, ck + (size_t)c * n, n * sizeof(double));
         for (int64_t st = s0; st + 1 < s1; ++st)
-            plain_step(nx, ny, nz, a, b, s, qm, isfixed, traj + (size_t)(st - s0) * n,
+            plain_step(nx, ny, nz, a, b, wf, s, qm, isfixed, traj + (size_t)(st - s0) * n,
                        traj + (size_t)(st - s0 + 1) * n);
         for (int64_t st = s1 - 1; st >= s0; --st) {
             const double *th = traj + (size_t)(st - s0) * n;   /* theta^st; lam = lambda^{st+1} */
@@ -384,26 +421,43 @@ int or_adjoint(int nx, int ny, int nz, int64_t nsteps, double h, double dt,
                         if (!isfixed[i]) {
                             int l = labels[i];
                             const double *t = tab + (size_t)l * T_NCOL;
-                            double t0 = th[i], lap = 0.0;
-                            if (x > 0)      lap += th[IDX(x - 1, y, z)] - t0;
-                            if (x < nx - 1) lap += th[IDX(x + 1, y, z)] - t0;
-                            if (y > 0)      lap += th[IDX(x, y - 1, z)] - t0;
-                            if (y < ny - 1) lap += th[IDX(x, y + 1, z)] - t0;
-                            if (z > 0)      lap += th[IDX(x, y, z - 1)] - t0;
-                            if (z < nz - 1) lap += th[IDX(x, y, z + 1)] - t0;
-                            double da_dk = (1.0 / rhoc[i]) * dt / (h * h);
+                            double t0 = th[i];
+                            if (!wf) {
+                                double lap = 0.0;
+                                if (x > 0)      lap += th[IDX(x - 1, y, z)] - t0;
+                                if (x < nx - 1) lap += th[IDX(x + 1, y, z)] - t0;
+                                if (y > 0)      lap += th[IDX(x, y - 1, z)] - t0;
+                                if (y < ny - 1) lap += th[IDX(x, y + 1, z)] - t0;
+                                if (z > 0)      lap += th[IDX(x, y, z - 1)] - t0;
+                                if (z < nz - 1) lap += th[IDX(x, y, z + 1)] - t0;
+                                double da_dk = (1.0 / rhoc[i]) * dt / (h * h);
+                                pk[(size_t)z * n_labels + l] += lam[i] * da_dk * lap;
+                            } else {
+                                /* d wf[d][i] / dK of the voxel's label (dwa) and of the
+                                   neighbour's label (dwb) */
+                                const int nbx[6] = {x - 1, x + 1, x, x, x, x}, nby[6] = {y, y, y - 1, y + 1, y, y};
+                                const int nbz[6] = {z, z, z, z, z - 1, z + 1};
+                                for (int d = 0; d < 6; ++d) {
+                                    if (nbx[d] < 0 || nbx[d] >= nx || nby[d] < 0 || nby[d] >= ny || nbz[d] < 0 ||
+                                        nbz[d] >= nz)
+                                        continue;
+                                    const size_t j = IDX(nbx[d], nby[d], nbz[d]);
+                                    const double v = lam[i] * (th[j] - t0);
+                                    pk[(size_t)z * n_labels + l] += dwa[(size_t)d * n + i] * v;
+                                    pk[(size_t)z * n_labels + labels[j]] += dwb[(size_t)d * n + i] * v;
+                                }
+                            }
                             double db_dw = (t[T_RHOB] * t[T_CB] / rhoc[i]) * dt;
-                            pk[(size_t)z * n_labels + l] += lam[i] * da_dk * lap;
                             pw[(size_t)z * n_labels + l] -= lam[i] * db_dw * t0;
                         }
                         /* (A^T lam)_i = sum_j A[j][i] lam_j over j = i and its neighbours */
-                        double acc = step_entry(nx, ny, nz, a, b, isfixed, x, y, z, x, y, z) * lam[i];
-                        if (x > 0)      acc += step_entry(nx, ny, nz, a, b, isfixed, x - 1, y, z, x, y, z) * lam[IDX(x - 1, y, z)];
-                        if (x < nx - 1) acc += step_entry(nx, ny, nz, a, b, isfixed, x + 1, y, z, x, y, z) * lam[IDX(x + 1, y, z)];
-                        if (y > 0)      acc += step_entry(nx, ny, nz, a, b, isfixed, x, y - 1, z, x, y, z) * lam[IDX(x, y - 1, z)];
-                        if (y < ny - 1) acc += step_entry(nx, ny, nz, a, b, isfixed, x, y + 1, z, x, y, z) * lam[IDX(x, y + 1, z)];
-                        if (z > 0)      acc += step_entry(nx, ny, nz, a, b, isfixed, x, y, z - 1, x, y, z) * lam[IDX(x, y, z - 1)];
-                        if (z < nz - 1) acc += step_entry(nx, ny, nz, a, b, isfixed, x, y, z + 1, x, y, z) * lam[IDX(x, y, z + 1)];
+                        double acc = step_entry(nx, ny, nz, a, b, wf, isfixed, x, y, z, x, y, z) * lam[i];
+                        if (x > 0)      acc += step_entry(nx, ny, nz, a, b, wf, isfixed, x - 1, y, z, x, y, z) * lam[IDX(x - 1, y, z)];
+                        if (x < nx - 1) acc += step_entry(nx, ny, nz, a, b, wf, isfixed, x + 1, y, z, x, y, z) * lam[IDX(x + 1, y, z)];
+                        if (y > 0)      acc += step_entry(nx, ny, nz, a, b, wf, isfixed, x, y - 1, z, x, y, z) * lam[IDX(x, y - 1, z)];
+                        if (y < ny - 1) acc += step_entry(nx, ny, nz, a, b, wf, isfixed, x, y + 1, z, x, y, z) * lam[IDX(x, y + 1, z)];
+                        if (z > 0)      acc += step_entry(nx, ny, nz, a, b, wf, isfixed, x, y, z - 1, x, y, z) * lam[IDX(x, y, z - 1)];
+                        if (z < nz - 1) acc += step_entry(nx, ny, nz, a, b, wf, isfixed, x, y, z + 1, x, y, z) * lam[IDX(x, y, z + 1)];
                         lnew[i] = acc;
                     }
             for (int z = 0; z < nz; ++z)

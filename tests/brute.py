@@ -50,3 +50,31 @@ def evolve(A, c, theta0, N):
     MN = power_augmented(A, c, N)
     n = A.shape[0]
     return MN[:n, :n] @ theta0 + MN[:n, n]
+
+
+def step_matrix_faces(wf, b, c_src, isfixed):
+    """A and c of one step of the conservative form: free voxel j gets weight
+    wf[d][j] on its neighbour in direction d (x-, x+, y-, y+, z-, z+) and
+    1 - sum_d wf[d][j] - b[j] on itself."""
+    nz, ny, nx = b.shape
+    n = nx * ny * nz
+    A = np.zeros((n, n))
+    c = np.zeros(n)
+    lin = lambda x, y, z: (z * ny + y) * nx + x
+    offs = ((-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1))
+    for z in range(nz):
+        for y in range(ny):
+            for x in range(nx):
+                j = lin(x, y, z)
+                if isfixed[z, y, x]:
+                    A[j, j] = 1.0
+                    continue
+                diag = 1.0 - b[z, y, x]
+                for d, (dx, dy, dz) in enumerate(offs):
+                    X, Y, Z = x + dx, y + dy, z + dz
+                    if 0 <= X < nx and 0 <= Y < ny and 0 <= Z < nz:
+                        A[j, lin(X, Y, Z)] += wf[d, z, y, x]
+                        diag -= wf[d, z, y, x]
+                A[j, j] = diag
+                c[j] = c_src[z, y, x]
+    return A, c
