@@ -260,6 +260,24 @@ rfa_status rfa_batch_autotune(rfa_batch *b, const char *cache_path);
 rfa_status rfa_batch_get_schedule(rfa_batch *b, int *tb_depth, int *tile_variant, int *uses_graph);
 
 /*
+ * Conduction form.  RFA_COND_CENTRE (default): K taken at the voxel,
+ * K_i * sum of second differences -- the paper's Eq. 2675-eq2 with scalar K,
+ * applied voxel-wise.  RFA_COND_HARMONIC: the conservative div(K grad T) of Eq.
+ * 2675-eq1_Kath with the face conductance of two voxels the harmonic mean of
+ * their K: theta'_i = theta_i + sum_nb w(l_i, l_nb) (theta_nb - theta_i) - ...,
+ * w(l, m) = dt / (rho_l c_l h^2) * 2 K_l K_m / (K_l + K_m) (FP32 label-pair
+ * table; FP64 with FP64 coefficients).  The two agree where K is uniform.  The
+ * harmonic form runs one step per launch (no blocked or batched stepping), at
+ * most 16 labels; rfa_backward differentiates it (dL/dK through both labels of
+ * every face).  May be set before or after rfa_set_tissue; changing it after
+ * recorded steps invalidates the recording.
+ * Errors: RFA_E_INVALID (unknown mode), RFA_E_UNSUPPORTED (more than 16
+ * labels), RFA_E_UNSTABLE (1 - deg * max_m w(l, m) - b_l < 0 for a free label).
+ */
+enum { RFA_COND_CENTRE = 0, RFA_COND_HARMONIC = 1 };
+rfa_status rfa_set_conduction(rfa_grid *g, int mode);
+
+/*
  * Breathing motion (Sec. "Consideration of Breathing Motion", Eq. breathing):
  * the simulation runs in the reference space; the temperature in the moving
  * space at one instant is T(x) = T_ref(x + u_inv(x)), with u_inv the inverse

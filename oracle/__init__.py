@@ -147,10 +147,12 @@ def face_weights(case, param_mode: str):
     return tuple(np.ascontiguousarray(a) for a in out)
 
 
-def setup(case, param_mode: str = "f64", conduction: str = "centre") -> Model:
+def setup(case, param_mode: str = "f64", conduction: Optional[str] = None) -> Model:
     """Coefficients, fixed set, initial state and RF source of ``case``;
     ``conduction`` = 'centre' (K at the voxel, the paper's form) or 'harmonic'
-    (conservative form, see ``face_weights``)."""
+    (conservative form, see ``face_weights``); default: ``case.conduction``."""
+    if conduction is None:
+        conduction = getattr(case, "conduction", "centre")
     nx, ny, nz = case.nx, case.ny, case.nz
     shape = (nz, ny, nx)
     labels = np.ascontiguousarray(case.labels.astype(np.uint8).reshape(shape))

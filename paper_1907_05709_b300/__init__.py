@@ -33,7 +33,8 @@ EXPORTED = ("rfa_create_grid", "rfa_destroy_grid", "rfa_set_tissue", "rfa_place_
             "rfa_set_schedule", "rfa_get_schedule", "rfa_autotune", "rfa_batch_create",
             "rfa_batch_step", "rfa_batch_destroy", "rfa_synchronize", "rfa_steps_done",
             "rfa_last_error", "rfa_necrosis_reduce_noalloc", "rfa_batch_autotune",
-            "rfa_batch_get_schedule", "rfa_selftest_wait_timeout", "rfa_warp_temperature")
+            "rfa_batch_get_schedule", "rfa_selftest_wait_timeout", "rfa_warp_temperature",
+            "rfa_set_conduction")
 
 
 class RfaError(RuntimeError):
@@ -96,6 +97,7 @@ def lib():
         "rfa_batch_get_schedule": [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)],
         "rfa_selftest_wait_timeout": [ctypes.c_longlong],
         "rfa_warp_temperature": [P, P, P, I],
+        "rfa_set_conduction": [P, I],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -199,6 +201,13 @@ def rfa_step(g, nsteps: int, record_for_backward: int = 0):
 def rfa_get_temperature(g, dst, dst_is_device: bool, as_f64: bool = False):
     _check(lib().rfa_get_temperature(g, _ptr(dst), int(bool(dst_is_device)), int(bool(as_f64))),
            "rfa_get_temperature")
+
+
+COND_CENTRE, COND_HARMONIC = 0, 1
+
+
+def rfa_set_conduction(g, mode: int):
+    _check(lib().rfa_set_conduction(g, int(mode)), "rfa_set_conduction")
 
 
 def rfa_warp_temperature(g, u_inv_dev, dst_dev, as_f64: bool = False):
@@ -324,6 +333,8 @@ class Grid:
                   damage=True):
         g = cls(case.nx, case.ny, case.nz, case.h, case.dt, state_prec, param_prec, case.face_bc,
                 case.T_a_C, cuda_stream)
+        if getattr(case, "conduction", "centre") == "harmonic":
+            rfa_set_conduction(g.handle, COND_HARMONIC)
         g.set_tissue(case.labels, case.table)
         g.place_needle(case.needle)
         d = case.damage

@@ -520,6 +520,10 @@ rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads)
                 RFA_CUDA(launch_step_tb_rec(g, 2, replay_variant, sb + (size_t)j * nvp, lin,
                                             sb + (size_t)(j + 2) * nvp, lout, sb + (size_t)(j + 1) * nvp));
                 j += 2;
+            } else if (g->cond == RFA_COND_HARMONIC) {
+                RFA_CUDA(launch_step_cond(g, sb + (size_t)j * nvp, lin, sb + (size_t)(j + 1) * nvp, lout, false,
+                                          false, false));
+                j += 1;
             } else {
                 RFA_CUDA(launch_step_plain(g, sb + (size_t)j * nvp, lin, sb + (size_t)(j + 1) * nvp, lout, false,
                                            false, false));
@@ -529,7 +533,11 @@ rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads)
         }
         for (int64_t st = s1 - 1; st >= s0; --st) {
             const float *th = sb + (size_t)(st - s0) * nvp;
-            RFA_CUDA(launch_adjoint_step(g, A, lam2 + (size_t)lcur * nvp, lam2 + (size_t)(lcur ^ 1) * nvp, th));
+            if (g->cond == RFA_COND_HARMONIC)
+                RFA_CUDA(launch_adjoint_cond(g, lam2 + (size_t)lcur * nvp, lam2 + (size_t)(lcur ^ 1) * nvp,
+                                             (float *)Lam.p, th, accd));
+            else
+                RFA_CUDA(launch_adjoint_step(g, A, lam2 + (size_t)lcur * nvp, lam2 + (size_t)(lcur ^ 1) * nvp, th));
             lcur ^= 1;
         }
     }

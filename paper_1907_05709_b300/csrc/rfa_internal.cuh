@@ -155,6 +155,9 @@ struct rfa_grid {
     int64_t carry_steps = 0;  // steps accumulated in the FP32 damage carry since the last fold
     rfa::Schedule sched;
     rfa::Record rec;
+    int cond = 0;              // RFA_COND_CENTRE or RFA_COND_HARMONIC
+    void *d_wpair = nullptr;   // conservative form: label-pair weights (float, double for FP64 coefficients)
+    float *d_wadj = nullptr;   // FP32 weights and their K derivatives for the adjoint (3 tables)
 
     size_t state_elem() const { return sp == RFA_STATE_F64 ? 8 : 4; }
     size_t ab_elem() const { return pp == RFA_PARAM_BF16 ? 4 : (pp == RFA_PARAM_F32 ? 8 : 16); }
@@ -184,6 +187,13 @@ struct DamageConst {
 DamageConst damage_consts(const rfa_grid *g);
 cudaError_t launch_step_plain(rfa_grid *g, const void *th_in, const void *lo_in, void *th_out,
                               void *lo_out, bool damage, bool latch, bool fold);
+// conservative conduction (kernels_cond.cu): label-pair tables of at most kCondLabels labels
+constexpr int kCondLabels = 16;
+rfa_status cond_build_tables(rfa_grid *g, const rfa_tissue *table, int n_labels);
+cudaError_t launch_step_cond(rfa_grid *g, const void *th_in, const void *lo_in, void *th_out, void *lo_out,
+                             bool damage, bool latch, bool fold);
+cudaError_t launch_adjoint_cond(rfa_grid *g, const float *lam_in, float *lam_out, float *Lam, const float *th,
+                                double *acc);
 // temporal-blocked TMA kernel (kernels_tb.cu)
 bool tb_supported(const rfa_grid *g, int depth, int variant);
 void tb_forget_maps(const rfa_grid *g);

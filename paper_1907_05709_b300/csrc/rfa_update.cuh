@@ -23,11 +23,9 @@ __device__ __forceinline__ float cdiff(float nh, float nl, float c, float cl)
 // New pair from the old pair and the difference sum S.  The increment is added
 // to hi error-free (TwoSum), its rounding error joins lo, and the pair is
 // renormalised (Fast2Sum) so |lo| stays within half an ulp of hi.
-__device__ __forceinline__ void cupdate(float c, float cl, float S, float a, float b, float s,
-                                        float &nh, float &nl)
+// (hi, lo) + delta: TwoSum of hi and delta, the error joins lo, Fast2Sum renormalises
+__device__ __forceinline__ void cadd(float c, float cl, float delta, float &nh, float &nl)
 {
-    float th = __fadd_rn(c, cl);
-    float delta = __fmaf_rn(a, S, __fmaf_rn(-b, th, s));
     float s1 = __fadd_rn(c, delta);
     float bb = __fsub_rn(s1, c);
     float e1 = __fadd_rn(__fsub_rn(c, __fsub_rn(s1, bb)), __fsub_rn(delta, bb));
@@ -35,6 +33,14 @@ __device__ __forceinline__ void cupdate(float c, float cl, float S, float a, flo
     float s2 = __fadd_rn(s1, l1);
     nl = __fsub_rn(l1, __fsub_rn(s2, s1));
     nh = s2;
+}
+
+__device__ __forceinline__ void cupdate(float c, float cl, float S, float a, float b, float s,
+                                        float &nh, float &nl)
+{
+    float th = __fadd_rn(c, cl);
+    float delta = __fmaf_rn(a, S, __fmaf_rn(-b, th, s));
+    cadd(c, cl, delta, nh, nl);
 }
 
 // ------------------------------------------------- compensated FP32, voxel pairs

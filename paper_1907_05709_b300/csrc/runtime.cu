@@ -28,7 +28,8 @@ static rfa_status fail(rfa_status st, const std::string &msg)
 static void free_grid_memory(rfa_grid *g)
 {
     void *ptrs[] = {g->th[0], g->th[1], g->lo[0], g->lo[1], g->ab, g->s, g->label, g->latch,
-                    g->omega, g->omega_c, g->status, g->red, g->stage, g->d_table};
+                    g->omega, g->omega_c, g->status, g->red, g->stage, g->d_table, g->d_wpair,
+                    g->d_wadj};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (g->status_host) cudaFreeHost(g->status_host);
@@ -123,6 +124,9 @@ rfa_status advance(rfa_grid *g, int64_t nsteps, bool damage, bool latch)
         if (use_tb) {
             e = launch_step_tb(g, m, g->sched.tile_variant, g->th[g->cur], g->lo[g->cur],
                                g->th[g->cur ^ 1], g->lo[g->cur ^ 1], damage, fold);
+        } else if (g->cond == RFA_COND_HARMONIC) {
+            e = launch_step_cond(g, g->th[g->cur], g->lo[g->cur], g->th[g->cur ^ 1], g->lo[g->cur ^ 1], damage,
+                                 latch, fold);
         } else {
             e = launch_step_plain(g, g->th[g->cur], g->lo[g->cur], g->th[g->cur ^ 1],
                                   g->lo[g->cur ^ 1], damage, latch, fold);
@@ -185,6 +189,8 @@ rfa_status rfa_create_grid(int nx, int ny, int nz, double h_m, double dt_s, int 
     alloc((void **)&g->status, 256);
     alloc(&g->red, kReduceBlocks * 32 + 256);
     alloc((void **)&g->d_table, 256 * sizeof(LabelCoef));
+    alloc(&g->d_wpair, kCondLabels * kCondLabels * 8);
+    alloc((void **)&g->d_wadj, 3 * kCondLabels * kCondLabels * 4);
     alloc(&g->stage, nvp * 8);  // labels in, source weights, host copies
     if (e == cudaSuccess) e = cudaMallocHost((void **)&g->status_host, 256);
     if (e != cudaSuccess) {
@@ -254,6 +260,10 @@ rfa_status rfa_set_tissue(rfa_grid *g, const uint8_t *labels, const rfa_tissue *
                 return fail(RFA_E_UNSTABLE, buf);
             }
         }
+    }
+    if (g->cond == RFA_COND_HARMONIC) {
+        const rfa_status st = cond_build_tables(g, table, n_labels);
+        if (st != RFA_OK) return st;
     }
     RFA_CUDA(cudaMemcpyAsync(g->d_table, tab.data(), 256 * sizeof(LabelCoef), cudaMemcpyHostToDevice, g->stream));
     RFA_CUDA(cudaMemcpyAsync(g->stage, labels, n, dev_labels ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));

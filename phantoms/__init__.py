@@ -131,6 +131,7 @@ class Case:
     damage: Damage
     T_a_C: float = 37.0
     face_bc: int = DIRICHLET
+    conduction: str = "centre"      # "centre" (K at the voxel) or "harmonic" (conservative)
 
     @property
     def nvox(self) -> int:
