@@ -169,6 +169,8 @@ def setup(case, param_mode: str = "f64", conduction: Optional[str] = None) -> Mo
                            _pd(dist), ctypes.byref(W)), "source")
     m = Model(nx, ny, nz, case.h, case.dt, a, b, qm, rhoc, fx, th0, s, dist, W.value,
               labels, tab, nd, case.T_a_C)
+    if getattr(case, "source", "needle") == "potential":
+        _, _, m.s = potential_source(case, m)
     if conduction == "harmonic":
         m.wf, m.dwa, m.dwb = face_weights(case, param_mode)
     elif conduction != "centre":
@@ -272,3 +274,102 @@ def warp_temperature(theta: np.ndarray, u_inv: np.ndarray, h: float, T_a: float)
             for xi, wx in ((x0, 1.0 - fx), (x1, fx)):
                 out += wz * wy * wx * theta[zi, yi, xi]
     return out + T_a
+
+
+# ------------------------------------------------------------ potential source
+def harmonic_faces(vals: np.ndarray):
+    """Face values 2 u v / (u + v) of a per-voxel field to each neighbour, [6][nz][ny][nx]
+    for x-, x+, y-, y+, z-, z+ (0 outside the grid)."""
+    out = np.zeros((6,) + vals.shape)
+    for d, (ax, sh) in enumerate(((2, -1), (2, 1), (1, -1), (1, 1), (0, -1), (0, 1))):
+        n = vals.shape[ax]
+        idx = np.arange(n) + sh
+        ok = (idx >= 0) & (idx < n)
+        nb = np.take(vals, np.clip(idx, 0, n - 1), axis=ax)
+        s = vals + nb
+        hm = np.divide(2.0 * vals * nb, s, out=np.zeros_like(s), where=s > 0)
+        okb = np.broadcast_to(ok.reshape([-1 if k == ax else 1 for k in range(3)]), vals.shape)
+        out[d] = np.where(okb, hm, 0.0)
+    return out
+
+
+def _shift(v, d):
+    """Neighbour values of v in direction d (x-, x+, y-, y+, z-, z+), 0 outside."""
+    ax, sh = ((2, -1), (2, 1), (1, -1), (1, 1), (0, -1), (0, 1))[d]
+    n = v.shape[ax]
+    idx = np.arange(n) + sh
+    ok = (idx >= 0) & (idx < n)
+    nb = np.take(v, np.clip(idx, 0, n - 1), axis=ax)
+    okb = np.broadcast_to(ok.reshape([-1 if k == ax else 1 for k in range(3)]), v.shape)
+    return np.where(okb, nb, 0.0), okb
+
+
+def potential_solve(sig_face: np.ndarray, electrode: np.ndarray, ground: np.ndarray) -> np.ndarray:
+    """Electric potential of Eq. 2675-eq1_Linte's source term: div(sigma grad V) = 0
+    on the free voxels (neither electrode nor ground), V = 1 on the electrode and
+    V = 0 on the ground, discretised with the face conductances sig_face
+    ([6][nz][ny][nx]): sum_nb sigma_f (V_nb - V_i) = 0.  Direct sparse solve."""
+    import scipy.sparse as sp
+    from scipy.sparse.linalg import spsolve
+    shape = electrode.shape
+    free = ~(electrode | ground)
+    Vfix = electrode.astype(np.float64)
+    nfree = int(free.sum())
+    V = Vfix.copy()
+    if nfree == 0:
+        return V
+    idx = -np.ones(shape, np.int64)
+    idx[free] = np.arange(nfree)
+    rows, cols, vals = [], [], []
+    diag = np.zeros(nfree)
+    rhs = np.zeros(nfree)
+    for d in range(6):
+        nb_idx, ok = _shift(idx.astype(np.float64), d)
+        nb_fix, _ = _shift(Vfix, d)
+        m = free & ok
+        sf = sig_face[d][m]
+        i = idx[m]
+        j = nb_idx[m].astype(np.int64)
+        np.add.at(diag, i, sf)
+        jf = j >= 0
+        rows.append(i[jf]); cols.append(j[jf]); vals.append(-sf[jf])
+        np.add.at(rhs, i[~jf], sf[~jf] * nb_fix[m][~jf])
+    rows.append(np.arange(nfree)); cols.append(np.arange(nfree)); vals.append(diag)
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(nfree, nfree))
+    V[free] = spsolve(A, rhs)
+    return V
+
+
+def joule(V: np.ndarray, sig_face: np.ndarray, h: float) -> np.ndarray:
+    """Resistive heating sigma |grad V|^2 per voxel, evaluated per face and split
+    evenly between its two voxels: q_i = sum_nb sigma_f (V_nb - V_i)^2 / (2 h^2)
+    [W/m^3 per V^2]; sum_i q_i h^3 is then the network's dissipated power."""
+    q = np.zeros(V.shape)
+    for d in range(6):
+        nb, ok = _shift(V, d)
+        q += np.where(ok, sig_face[d] * (nb - V) ** 2, 0.0)
+    return q / (2.0 * h * h)
+
+
+def potential_source(case, m: Model):
+    """Linte's RF source for ``case``: electrode = voxels within r0 of the
+    needle's active segments (the geometry of or_source), ground = the outer
+    faces, sigma per label (Tissue.sigma) with harmonic-mean faces; the Joule
+    heating q is scaled so that sum_free q h^3 = P.  Returns (V, q, s) with
+    s = P q / (h^3 W) dt / (rho c) on the free voxels, W = sum_free q."""
+    nz, ny, nx = m.a.shape
+    lab = m.labels.astype(np.int64)
+    sig = np.array([t.sigma for t in case.table], dtype=np.float64)[lab]
+    sf = harmonic_faces(sig)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    ground = (x == 0) | (y == 0) | (z == 0) | (x == nx - 1) | (y == ny - 1) | (z == nz - 1)
+    electrode = (m.dist <= case.needle.r_clamp) & ~ground
+    V = potential_solve(sf, electrode, ground)
+    q = joule(V, sf, case.h)
+    free = m.isfixed == 0
+    W = float(np.sum(q[free]))
+    s = np.zeros(V.shape)
+    if W > 0.0:
+        s[free] = case.needle.power * q[free] / (case.h ** 3 * W) * case.dt / m.rhoc[free]
+    return V, q, s

@@ -53,6 +53,7 @@ class Tissue:
     Q_m: float = 0.0         # metabolic heat [W/m^3]
     fixed: int = 0           # 1: voxel held at T_fixed_C (vessel / hot tip)
     T_fixed_C: float = 37.0
+    sigma: float = 0.33      # electrical conductivity [S/m] (potential-solve source only)
 
     def as_tuple(self):
         return (self.k, self.rho, self.c, self.w_b, self.rho_b, self.c_b,
@@ -64,11 +65,11 @@ def liver() -> Tissue:
 
 
 def tumor() -> Tissue:
-    return Tissue(k=0.55, w_b=3e-3)
+    return Tissue(k=0.55, w_b=3e-3, sigma=0.45)
 
 
 def vessel() -> Tissue:
-    return Tissue(fixed=1, T_fixed_C=37.0)
+    return Tissue(fixed=1, T_fixed_C=37.0, sigma=0.7)
 
 
 def paper_liver() -> Tissue:
@@ -132,6 +133,7 @@ class Case:
     T_a_C: float = 37.0
     face_bc: int = DIRICHLET
     conduction: str = "centre"      # "centre" (K at the voxel) or "harmonic" (conservative)
+    source: str = "needle"          # "needle" (max(d, r0)^-4) or "potential" (sigma |grad V|^2)
 
     @property
     def nvox(self) -> int:
