@@ -260,6 +260,30 @@ rfa_status rfa_batch_autotune(rfa_batch *b, const char *cache_path);
 rfa_status rfa_batch_get_schedule(rfa_batch *b, int *tb_depth, int *tile_variant, int *uses_graph);
 
 /*
+ * RF source from the electric potential (Linte's resistive term sigma |grad V|^2
+ * of Eq. 2675-eq1_Linte) instead of the max(d, r0)^-4 weights of
+ * rfa_place_needle: div(sigma grad V) = 0 with the electrode -- the voxels within
+ * r_clamp_m of the needle's active segments -- at V = 1 and the outer faces at
+ * V = 0 (ground), face conductances the harmonic mean of the voxels' sigma.
+ * The heating q_i = sum_nb sigma_f (V_nb - V_i)^2 / (2 h^2) (each face's
+ * dissipation split between its voxels) is scaled so that the free voxels
+ * receive power_W, and written to the source field like rfa_place_needle.
+ *   sigma_S_per_m : host, n_sigma = number of labels, electrical conductivity.
+ *   max_iters, tol: preconditioned conjugate gradients (FP64) stop at
+ *                   ||r|| <= tol ||b|| or after max_iters iterations.
+ *   iters_out, rel_residual_out (may be NULL): iterations used, final ||r||/||b||
+ *                   (check it against tol: reaching max_iters is not an error).
+ * Synchronous.  rfa_set_tissue re-solves with the same settings.  rfa_backward
+ * returns RFA_E_UNSUPPORTED while this source is in use.
+ * Errors: RFA_E_STATE (no tissue), RFA_E_INVALID (needle, sigma, n_sigma,
+ * max_iters, tol), RFA_E_UNSUPPORTED (more than 16 labels), RFA_E_OOM,
+ * RFA_E_NONFINITE (the iteration diverged).
+ */
+rfa_status rfa_place_needle_potential(rfa_grid *g, const rfa_needle *needle, const double *sigma_S_per_m,
+                                      int n_sigma, int max_iters, double tol, int *iters_out,
+                                      double *rel_residual_out);
+
+/*
  * Conduction form.  RFA_COND_CENTRE (default): K taken at the voxel,
  * K_i * sum of second differences -- the paper's Eq. 2675-eq2 with scalar K,
  * applied voxel-wise.  RFA_COND_HARMONIC: the conservative div(K grad T) of Eq.

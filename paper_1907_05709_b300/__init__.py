@@ -34,7 +34,7 @@ EXPORTED = ("rfa_create_grid", "rfa_destroy_grid", "rfa_set_tissue", "rfa_place_
             "rfa_batch_step", "rfa_batch_destroy", "rfa_synchronize", "rfa_steps_done",
             "rfa_last_error", "rfa_necrosis_reduce_noalloc", "rfa_batch_autotune",
             "rfa_batch_get_schedule", "rfa_selftest_wait_timeout", "rfa_warp_temperature",
-            "rfa_set_conduction")
+            "rfa_set_conduction", "rfa_place_needle_potential")
 
 
 class RfaError(RuntimeError):
@@ -98,6 +98,8 @@ def lib():
         "rfa_selftest_wait_timeout": [ctypes.c_longlong],
         "rfa_warp_temperature": [P, P, P, I],
         "rfa_set_conduction": [P, I],
+        "rfa_place_needle_potential": [P, ctypes.POINTER(rfa_needle), ctypes.POINTER(D), I, I, D, ctypes.POINTER(I),
+                                       ctypes.POINTER(D)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -187,6 +189,17 @@ def rfa_set_tissue(g, labels, table: Sequence):
 def rfa_place_needle(g, needle):
     n = needle if isinstance(needle, rfa_needle) else make_needle(needle)
     _check(lib().rfa_place_needle(g, ctypes.byref(n)), "rfa_place_needle")
+
+
+def rfa_place_needle_potential(g, needle, sigma, max_iters: int = 20000, tol: float = 1e-12):
+    """Returns (iterations, relative residual) of the potential solve."""
+    n = needle if isinstance(needle, rfa_needle) else make_needle(needle)
+    s = np.ascontiguousarray(np.asarray(sigma, dtype=np.float64))
+    it, res = ctypes.c_int(0), ctypes.c_double(0.0)
+    _check(lib().rfa_place_needle_potential(g, ctypes.byref(n), s.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                            len(s), int(max_iters), float(tol), ctypes.byref(it),
+                                            ctypes.byref(res)), "rfa_place_needle_potential")
+    return it.value, res.value
 
 
 def rfa_set_damage(g, enable=1, A=7.39e39, Ea=2.577e5, R=8.31, T_thr_C=60.0):
@@ -336,7 +349,10 @@ class Grid:
         if getattr(case, "conduction", "centre") == "harmonic":
             rfa_set_conduction(g.handle, COND_HARMONIC)
         g.set_tissue(case.labels, case.table)
-        g.place_needle(case.needle)
+        if getattr(case, "source", "needle") == "potential":
+            rfa_place_needle_potential(g.handle, case.needle, [t.sigma for t in case.table])
+        else:
+            g.place_needle(case.needle)
         d = case.damage
         g.set_damage(int(bool(d.enable and damage)), d.A, d.Ea, d.R, d.T_thr_C)
         return g

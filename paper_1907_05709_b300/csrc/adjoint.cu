@@ -453,6 +453,10 @@ rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads)
         set_error("rfa_backward needs every step since rfa_set_tissue recorded (rfa_step(..., 1))");
         return RFA_E_STATE;
     }
+    if (g->src_mode != 0) {
+        set_error("rfa_backward supports the max(d, r0)^-4 needle source only");
+        return RFA_E_UNSUPPORTED;
+    }
     if (g->n_labels > kMaxGradLabels) {
         set_error("rfa_backward supports at most 8 labels");
         return RFA_E_UNSUPPORTED;

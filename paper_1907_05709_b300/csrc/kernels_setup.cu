@@ -85,21 +85,6 @@ __global__ void k_setup(const uint8_t *__restrict__ labels, const LabelCoef *__r
     }
 }
 
-// squared distance from a voxel centre to the nearest active segment
-__device__ double needle_dist2(const NeedleGeom &g, double px, double py, double pz)
-{
-    double best = 1e300;
-    for (int k = 0; k < g.nseg; ++k) {
-        const Segment &sg = g.seg[k];
-        double ux = sg.p1[0] - sg.p0[0], uy = sg.p1[1] - sg.p0[1], uz = sg.p1[2] - sg.p0[2];
-        double wx = px - sg.p0[0], wy = py - sg.p0[1], wz = pz - sg.p0[2];
-        double t = (wx * ux + wy * uy + wz * uz) * sg.inv_uu;
-        t = fmin(fmax(t, 0.0), 1.0);
-        double ex = wx - t * ux, ey = wy - t * uy, ez = wz - t * uz;
-        best = fmin(best, ex * ex + ey * ey + ez * ez);
-    }
-    return best;
-}
 
 // w = max(d, r0)^-4 = 1 / max(d^2, r0^2)^2
 __device__ inline double needle_weight2(const NeedleGeom &g, double d2)
@@ -208,6 +193,21 @@ cudaError_t launch_setup(rfa_grid *g, const uint8_t *labels_dense_dev, int n_lab
     SETUP_CASE(RFA_STATE_F64, RFA_PARAM_F32)
     SETUP_CASE(RFA_STATE_F64, RFA_PARAM_F64)
 #undef SETUP_CASE
+    return cudaGetLastError();
+}
+
+cudaError_t launch_source_write(rfa_grid *g, const double *partial, int npartial)
+{
+    double *W = (double *)g->red + kReduceBlocks;
+    k_sum_partials<<<1, 1024, 0, g->stream>>>(partial, npartial, W);
+    if (g->sp == RFA_STATE_F64)
+        k_source_write<RFA_STATE_F64><<<148 * 8, 256, 0, g->stream>>>(
+            g->geom, g->label, g->d_table, g->nx, g->ny, g->nz, g->pitch, g->h, g->dt, g->face, W,
+            (const double *)g->stage, g->s);
+    else
+        k_source_write<RFA_STATE_F32><<<148 * 8, 256, 0, g->stream>>>(
+            g->geom, g->label, g->d_table, g->nx, g->ny, g->nz, g->pitch, g->h, g->dt, g->face, W,
+            (const double *)g->stage, g->s);
     return cudaGetLastError();
 }
 

@@ -156,6 +156,10 @@ struct rfa_grid {
     rfa::Schedule sched;
     rfa::Record rec;
     int cond = 0;              // RFA_COND_CENTRE or RFA_COND_HARMONIC
+    int src_mode = 0;          // 0: max(d, r0)^-4 weights; 1: potential solve (sigma |grad V|^2)
+    std::vector<double> sigma; // electrical conductivity per label (potential solve)
+    int pot_max_iters = 0, pot_iters = 0;
+    double pot_tol = 0.0, pot_res = 0.0;
     void *d_wpair = nullptr;   // conservative form: label-pair weights (float, double for FP64 coefficients)
     float *d_wadj = nullptr;   // FP32 weights and their K derivatives for the adjoint (3 tables)
 
@@ -175,10 +179,32 @@ rfa_status cuda_fail(cudaError_t e, const char *what);
         if (e_ != cudaSuccess) return rfa::cuda_fail(e_, #call); \
     } while (0)
 
+// squared distance from a voxel centre to the nearest active segment
+__device__ inline double needle_dist2(const NeedleGeom &g, double px, double py, double pz)
+{
+    double best = 1e300;
+    for (int k = 0; k < g.nseg; ++k) {
+        const Segment &sg = g.seg[k];
+        double ux = sg.p1[0] - sg.p0[0], uy = sg.p1[1] - sg.p0[1], uz = sg.p1[2] - sg.p0[2];
+        double wx = px - sg.p0[0], wy = py - sg.p0[1], wz = pz - sg.p0[2];
+        double t = (wx * ux + wy * uy + wz * uz) * sg.inv_uu;
+        t = fmin(fmax(t, 0.0), 1.0);
+        double ex = wx - t * ux, ey = wy - t * uy, ez = wz - t * uz;
+        best = fmin(best, ex * ex + ey * ey + ez * ez);
+    }
+    return best;
+}
+
 // ---------------------------------------------------------------- launchers
 // setup / source (kernels_setup.cu)
 cudaError_t launch_setup(rfa_grid *g, const uint8_t *labels_dense_dev, int n_labels);
 cudaError_t launch_source(rfa_grid *g);
+// s from source weights already in g->stage (FP64 per padded voxel) and their
+// per-block partial sums over the free voxels
+cudaError_t launch_source_write(rfa_grid *g, const double *partial, int npartial);
+// the RF source from the electric potential (kernels_potential.cu); uses g->geom,
+// g->sigma, g->pot_max_iters, g->pot_tol; sets g->pot_iters, g->pot_res
+rfa_status potential_place(rfa_grid *g);
 // plain one-step-per-launch kernel (kernels_step.cu)
 struct DamageConst {
     float c0, c1, TK0;     // inc = exp2(c0 - c1 / (theta + TK0)), FP32 path

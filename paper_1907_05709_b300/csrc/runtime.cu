@@ -283,8 +283,17 @@ rfa_status rfa_set_tissue(rfa_grid *g, const uint8_t *labels, const rfa_tissue *
         return fail(RFA_E_INVALID, "label value >= n_labels");
     }
     if (g->have_needle) {
-        RFA_CUDA(launch_source(g));
-        RFA_CUDA(cudaStreamSynchronize(g->stream));
+        if (g->src_mode == 1) {
+            if ((int)g->sigma.size() != n_labels) {
+                g->have_needle = false;
+                return fail(RFA_E_STATE, "the potential-solve source needs one sigma per label: place the needle again");
+            }
+            const rfa_status st = potential_place(g);
+            if (st != RFA_OK) return st;
+        } else {
+            RFA_CUDA(launch_source(g));
+            RFA_CUDA(cudaStreamSynchronize(g->stream));
+        }
     }
     return RFA_OK;
 }
@@ -298,10 +307,40 @@ rfa_status rfa_place_needle(rfa_grid *g, const rfa_needle *needle)
     if (st != RFA_OK) return st;
     g->geom = geom;
     g->needle = *needle;
+    g->src_mode = 0;
     RFA_CUDA(launch_source(g));
     RFA_CUDA(cudaStreamSynchronize(g->stream));
     g->have_needle = true;
     if (g->steps > 0) g->rec.valid = false;  // the recorded trajectory used another source
+    return RFA_OK;
+}
+
+rfa_status rfa_place_needle_potential(rfa_grid *g, const rfa_needle *needle, const double *sigma_S_per_m,
+                                      int n_sigma, int max_iters, double tol, int *iters_out,
+                                      double *rel_residual_out)
+{
+    if (!g || !needle || !sigma_S_per_m) return fail(RFA_E_INVALID, "null argument");
+    if (!g->have_tissue) return fail(RFA_E_STATE, "rfa_set_tissue must come first");
+    if (n_sigma != g->n_labels) return fail(RFA_E_INVALID, "n_sigma must equal the number of labels");
+    if (max_iters < 1 || !(tol > 0.0)) return fail(RFA_E_INVALID, "max_iters >= 1 and tol > 0 are needed");
+    for (int l = 0; l < n_sigma; ++l)
+        if (!(sigma_S_per_m[l] >= 0.0) || !std::isfinite(sigma_S_per_m[l]))
+            return fail(RFA_E_INVALID, "sigma must be finite and >= 0");
+    NeedleGeom geom{};
+    rfa_status st = build_geometry(*needle, geom);
+    if (st != RFA_OK) return st;
+    g->geom = geom;
+    g->needle = *needle;
+    g->sigma.assign(sigma_S_per_m, sigma_S_per_m + n_sigma);
+    g->pot_max_iters = max_iters;
+    g->pot_tol = tol;
+    g->src_mode = 1;
+    st = potential_place(g);
+    if (st != RFA_OK) return st;
+    g->have_needle = true;
+    if (g->steps > 0) g->rec.valid = false;
+    if (iters_out) *iters_out = g->pot_iters;
+    if (rel_residual_out) *rel_residual_out = g->pot_res;
     return RFA_OK;
 }
 
