@@ -38,7 +38,7 @@ def lib():
                                _P_D, _P_D, _P_D, _P_D, _P_U8, _P_D]
         L.or_source.argtypes = [i, i, i, d, d, _P_D, _P_D, _P_U8, _P_D, _P_D, _P_D]
         L.or_run.argtypes = [i, i, i, i64, _P_D, _P_D, _P_D, _P_D, _P_U8, _P_D, _P_U8, d, d,
-                             i, d, d, d, d, _P_D, _P_D, i, _P_D]
+                             i, d, d, d, d, _P_D, _P_D, i, _P_D, i]
         L.or_adjoint.argtypes = [i, i, i, i64, d, d, _P_D, _P_D, _P_D, _P_D, _P_U8, _P_U8, i,
                                  _P_D, _P_D, _P_D, _P_D, _P_D, _P_D, _P_D, i, _P_D, _P_D, _P_D]
         L.or_source_grad.argtypes = [i, i, i, d, d, _P_D, _P_D, _P_U8, _P_D, _P_D]
@@ -109,6 +109,8 @@ class Model:
     wf: Optional[np.ndarray] = None
     dwa: Optional[np.ndarray] = None
     dwb: Optional[np.ndarray] = None
+    # perfusion weighted by the tissue state alpha = 1 / max(1, Omega) (0: constant)
+    alpha_perf: int = 0
 
 
 def face_weights(case, param_mode: str):
@@ -171,6 +173,7 @@ def setup(case, param_mode: str = "f64", conduction: Optional[str] = None) -> Mo
               labels, tab, nd, case.T_a_C)
     if getattr(case, "source", "needle") == "potential":
         _, _, m.s = potential_source(case, m)
+    m.alpha_perf = int(getattr(case, "perfusion", "constant") == "tissue_state")
     if conduction == "harmonic":
         m.wf, m.dwa, m.dwb = face_weights(case, param_mode)
     elif conduction != "centre":
@@ -205,7 +208,7 @@ def run(m: Model, st: State, nsteps: int, damage=None, T_thr_C: float = 60.0,
     _check(lib().or_run(m.nx, m.ny, m.nz, int(nsteps), _pd(m.a), _pd(m.b), _pd(m.s), _pd(m.qm),
                         _pu8(m.isfixed), _pd(st.theta), _pu8(st.latch), m.T_a, thr, en, m.dt,
                         A, Ea, R, _pd(st.omega), _pd(st.omega_c), int(nthreads),
-                        None if m.wf is None else _pd(m.wf)), "run")
+                        None if m.wf is None else _pd(m.wf), int(m.alpha_perf)), "run")
     st.steps += int(nsteps)
     return st
 

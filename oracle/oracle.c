@@ -270,7 +270,7 @@ int or_run(int nx, int ny, int nz, int64_t nsteps,
            const double *a, const double *b, const double *s, const double *qm,
            const uint8_t *isfixed, double *theta, uint8_t *latch, double T_a, double T_thr,
            int damage, double dt, double A, double Ea, double R, double *omega, double *omega_c,
-           int nthreads, const double *wf)
+           int nthreads, const double *wf, int alpha_perf)
 {
     size_t n = (size_t)nx * ny * nz;
     double *cur = theta;
@@ -291,8 +291,11 @@ int or_run(int nx, int ny, int nz, int64_t nsteps,
                     if (isfixed[i]) {
                         tn = t;   /* Alg. 1 else-branch: copy the input value */
                     } else {
-                        /* central second differences in x, y, z (Eq. 2675-eq3) */
-                        tn = t + conduction(nx, ny, nz, a, wf, cur, x, y, z) - b[i] * t + s[i] + qm[i];
+                        /* central second differences in x, y, z (Eq. 2675-eq3); with the
+                           tissue-state coupling the perfusion is weighted by
+                           alpha = 1 / max(1, Omega) (Eq. eq-tissState, capped at 1) */
+                        const double bi = alpha_perf ? b[i] / fmax(1.0, omega[i]) : b[i];
+                        tn = t + conduction(nx, ny, nz, a, wf, cur, x, y, z) - bi * t + s[i] + qm[i];
                     }
                     nxt[i] = tn;
                     if (tn + T_a >= T_thr) latch[i] = 1;

@@ -134,6 +134,7 @@ class Case:
     face_bc: int = DIRICHLET
     conduction: str = "centre"      # "centre" (K at the voxel) or "harmonic" (conservative)
     source: str = "needle"          # "needle" (max(d, r0)^-4) or "potential" (sigma |grad V|^2)
+    perfusion: str = "constant"     # "constant" or "tissue_state" (w_b weighted by 1/max(1, Omega))
 
     @property
     def nvox(self) -> int:
