@@ -260,6 +260,19 @@ rfa_status rfa_batch_autotune(rfa_batch *b, const char *cache_path);
 rfa_status rfa_batch_get_schedule(rfa_batch *b, int *tb_depth, int *tile_variant, int *uses_graph);
 
 /*
+ * Perfusion coupled to the tissue state (Linte's alpha(t) of Eq. 2675-eq1_Linte
+ * and Eq. eq-tissState): with RFA_PERF_TISSUE_STATE the perfusion term of a
+ * voxel is multiplied by alpha = 1 / max(1, Omega), Omega its Arrhenius
+ * integral at the start of the step (the inverse integral, capped at 1 below
+ * the damage threshold where it would be singular).  Needs the damage integral
+ * on (rfa_set_damage), else Omega = 0 and alpha = 1.  Runs one step per launch
+ * (no blocked or batched stepping); rfa_backward returns RFA_E_UNSUPPORTED
+ * while it is on.  Errors: RFA_E_INVALID (unknown mode).
+ */
+enum { RFA_PERF_CONSTANT = 0, RFA_PERF_TISSUE_STATE = 1 };
+rfa_status rfa_set_perfusion_coupling(rfa_grid *g, int mode);
+
+/*
  * RF source from the electric potential (Linte's resistive term sigma |grad V|^2
  * of Eq. 2675-eq1_Linte) instead of the max(d, r0)^-4 weights of
  * rfa_place_needle: div(sigma grad V) = 0 with the electrode -- the voxels within

@@ -34,7 +34,7 @@ EXPORTED = ("rfa_create_grid", "rfa_destroy_grid", "rfa_set_tissue", "rfa_place_
             "rfa_batch_step", "rfa_batch_destroy", "rfa_synchronize", "rfa_steps_done",
             "rfa_last_error", "rfa_necrosis_reduce_noalloc", "rfa_batch_autotune",
             "rfa_batch_get_schedule", "rfa_selftest_wait_timeout", "rfa_warp_temperature",
-            "rfa_set_conduction", "rfa_place_needle_potential")
+            "rfa_set_conduction", "rfa_place_needle_potential", "rfa_set_perfusion_coupling")
 
 
 class RfaError(RuntimeError):
@@ -98,6 +98,7 @@ def lib():
         "rfa_selftest_wait_timeout": [ctypes.c_longlong],
         "rfa_warp_temperature": [P, P, P, I],
         "rfa_set_conduction": [P, I],
+        "rfa_set_perfusion_coupling": [P, I],
         "rfa_place_needle_potential": [P, ctypes.POINTER(rfa_needle), ctypes.POINTER(D), I, I, D, ctypes.POINTER(I),
                                        ctypes.POINTER(D)],
     }
@@ -217,6 +218,13 @@ def rfa_get_temperature(g, dst, dst_is_device: bool, as_f64: bool = False):
 
 
 COND_CENTRE, COND_HARMONIC = 0, 1
+
+
+PERF_CONSTANT, PERF_TISSUE_STATE = 0, 1
+
+
+def rfa_set_perfusion_coupling(g, mode: int):
+    _check(lib().rfa_set_perfusion_coupling(g, int(mode)), "rfa_set_perfusion_coupling")
 
 
 def rfa_set_conduction(g, mode: int):
@@ -348,6 +356,8 @@ class Grid:
                 case.T_a_C, cuda_stream)
         if getattr(case, "conduction", "centre") == "harmonic":
             rfa_set_conduction(g.handle, COND_HARMONIC)
+        if getattr(case, "perfusion", "constant") == "tissue_state":
+            rfa_set_perfusion_coupling(g.handle, PERF_TISSUE_STATE)
         g.set_tissue(case.labels, case.table)
         if getattr(case, "source", "needle") == "potential":
             rfa_place_needle_potential(g.handle, case.needle, [t.sigma for t in case.table])

@@ -457,6 +457,10 @@ rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads)
         set_error("rfa_backward supports the max(d, r0)^-4 needle source only");
         return RFA_E_UNSUPPORTED;
     }
+    if (g->alpha_perf) {
+        set_error("rfa_backward does not differentiate the tissue-state perfusion coupling");
+        return RFA_E_UNSUPPORTED;
+    }
     if (g->n_labels > kMaxGradLabels) {
         set_error("rfa_backward supports at most 8 labels");
         return RFA_E_UNSUPPORTED;
@@ -525,7 +529,7 @@ rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads)
                                             sb + (size_t)(j + 2) * nvp, lout, sb + (size_t)(j + 1) * nvp));
                 j += 2;
             } else if (g->cond == RFA_COND_HARMONIC) {
-                RFA_CUDA(launch_step_cond(g, sb + (size_t)j * nvp, lin, sb + (size_t)(j + 1) * nvp, lout, false,
+                RFA_CUDA(launch_step_model(g, sb + (size_t)j * nvp, lin, sb + (size_t)(j + 1) * nvp, lout, false,
                                           false, false));
                 j += 1;
             } else {

@@ -187,8 +187,9 @@ rfa_status rfa_batch_create(rfa_grid *const *members, int n, rfa_batch **out)
         if (!g->have_tissue) return bfail(RFA_E_STATE, "every member needs rfa_set_tissue first");
         if (g->sp != RFA_STATE_F32C || g->pp != RFA_PARAM_BF16)
             return bfail(RFA_E_UNSUPPORTED, "batched stepping needs compensated FP32 state and BF16 coefficients");
-        if (g->face != RFA_FACE_DIRICHLET || g->cond != RFA_COND_CENTRE)
-            return bfail(RFA_E_UNSUPPORTED, "batched stepping needs Dirichlet faces and the centre conduction form");
+        if (g->face != RFA_FACE_DIRICHLET || g->cond != RFA_COND_CENTRE || g->alpha_perf)
+            return bfail(RFA_E_UNSUPPORTED,
+                         "batched stepping needs Dirichlet faces, the centre conduction form and constant perfusion");
         if (g->stream != members[0]->stream) return bfail(RFA_E_INVALID, "members must share one stream");
         if (g->dmg != members[0]->dmg) return bfail(RFA_E_INVALID, "members must share the damage setting");
         for (int k = 0; k < m; ++k)

@@ -10,8 +10,11 @@
 // and the usual b, s.  Fixed voxels (a = 0: fixed labels, Dirichlet faces) keep
 // their value and still set their neighbours' face conductances.
 //
-// One step per launch, one thread per voxel: this is the model option, not
-// the benchmarked path.  Latch and damage integral as in the one-step kernel.
+// One step per launch, one thread per voxel: the kernel of the model options
+// (this form, and the perfusion weighted by the tissue state alpha = 1 /
+// max(1, Omega) of Eq. eq-tissState with either form), not the benchmarked
+// path.  Latch and damage integral as in the one-step kernel; with the centre
+// form and alpha = 1 it performs the one-step kernel's operations exactly.
 //
 // The adjoint of the step: with lambda = dL/dtheta',
 //     (A^T lambda)_j = A_jj lambda_j + sum_{i nb of j, i free} w(l_i, l_j) lambda_i,
@@ -63,10 +66,12 @@ struct CondArgs {
     double thr;
     DamageConst dc;
     int damage, latch_on, fold;
+    int cond;   // 0: centre form (a_i * sum of differences), 1: harmonic face weights
+    int alpha;  // perfusion weighted by 1 / max(1, Omega) of the step's start
 };
 
 template <int SP, int PP>
-__global__ void __launch_bounds__(256) k_step_cond(const CondArgs A)
+__global__ void __launch_bounds__(256) k_step_model(const CondArgs A)
 {
     using T = typename std::conditional<SP == RFA_STATE_F64, double, float>::type;
     using W = typename std::conditional<PP == RFA_PARAM_F64, double, float>::type;
@@ -87,7 +92,7 @@ __global__ void __launch_bounds__(256) k_step_cond(const CondArgs A)
     }
     double ad, bd;
     cond_ab<PP>(A.ab, i, ad, bd);
-    const T c = hin[i];
+    const T c = hin[i];  // (ad, bd: the voxel's a and b as stored)
     const float cl = SP == RFA_STATE_F32C ? A.lo_in[i] : 0.f;
     T nh = c;
     float nl = cl;
@@ -99,7 +104,33 @@ __global__ void __launch_bounds__(256) k_step_cond(const CondArgs A)
         const long long off[6] = {-1, 1, -(long long)A.pitch, (long long)A.pitch, -(long long)A.plane,
                                   (long long)A.plane};
         const T sv = ((const T *)A.s)[i];
-        if (SP == RFA_STATE_F32C) {
+        if (A.alpha) {  // tissue state: alpha = 1 / max(1, Omega) with Omega before this step
+            const double om = A.omega[i] + (double)A.omega_c[i];
+            if (om > 1.0) bd = bd / om;
+        }
+        if (!A.cond) {
+            // centre form: the one-step kernel's operations (bit-identical to it when alpha = 1)
+            if (SP == RFA_STATE_F32C) {
+                float S = 0.f;
+#pragma unroll
+                for (int d = 0; d < 6; ++d) {
+                    const size_t j = (size_t)((long long)i + (in[d] ? off[d] : 0));
+                    S = acc(S, in[d] ? cdiff((float)hin[j], A.lo_in[j], (float)c, cl) : 0.f);
+                }
+                float h2, l2;
+                cupdate((float)c, cl, S, (float)ad, (float)bd, (float)sv, h2, l2);
+                nh = (T)h2;
+                nl = l2;
+            } else {
+                T S = T(0);
+#pragma unroll
+                for (int d = 0; d < 6; ++d) {
+                    const size_t j = (size_t)((long long)i + (in[d] ? off[d] : 0));
+                    S = acc(S, in[d] ? pdiff(hin[j], c) : T(0));
+                }
+                nh = pupdate(c, S, (T)ad, (T)bd, sv);
+            }
+        } else if (SP == RFA_STATE_F32C) {
             const float th = __fadd_rn((float)c, cl);
             float delta = __fmaf_rn(-(float)bd, th, (float)sv);
 #pragma unroll
@@ -290,10 +321,12 @@ rfa_status cond_build_tables(rfa_grid *g, const rfa_tissue *table, int L)
     return RFA_OK;
 }
 
-cudaError_t launch_step_cond(rfa_grid *g, const void *th_in, const void *lo_in, void *th_out, void *lo_out,
-                             bool damage, bool latch, bool fold)
+cudaError_t launch_step_model(rfa_grid *g, const void *th_in, const void *lo_in, void *th_out, void *lo_out,
+                              bool damage, bool latch, bool fold)
 {
     CondArgs A;
+    A.cond = g->cond == RFA_COND_HARMONIC ? 1 : 0;
+    A.alpha = g->alpha_perf;
     A.th_in = th_in;
     A.lo_in = (const float *)lo_in;
     A.th_out = th_out;
@@ -318,7 +351,7 @@ cudaError_t launch_step_cond(rfa_grid *g, const void *th_in, const void *lo_in, 
     A.fold = fold ? 1 : 0;
     const dim3 blk(32, 8), grd = cond_grid(g);
 #define COND_CASE(SPV, PPV) \
-    if (g->sp == SPV && g->pp == PPV) k_step_cond<SPV, PPV><<<grd, blk, 0, g->stream>>>(A);
+    if (g->sp == SPV && g->pp == PPV) k_step_model<SPV, PPV><<<grd, blk, 0, g->stream>>>(A);
     COND_CASE(RFA_STATE_F32, RFA_PARAM_BF16)
     COND_CASE(RFA_STATE_F32, RFA_PARAM_F32)
     COND_CASE(RFA_STATE_F32, RFA_PARAM_F64)
@@ -368,6 +401,21 @@ cudaError_t launch_adjoint_cond(rfa_grid *g, const float *lam_in, float *lam_out
 }  // namespace rfa
 
 using namespace rfa;
+
+extern "C" rfa_status rfa_set_perfusion_coupling(rfa_grid *g, int mode)
+{
+    if (!g) {
+        set_error("null grid");
+        return RFA_E_INVALID;
+    }
+    if (mode != RFA_PERF_CONSTANT && mode != RFA_PERF_TISSUE_STATE) {
+        set_error("unknown perfusion coupling");
+        return RFA_E_INVALID;
+    }
+    if (mode != g->alpha_perf && g->steps > 0) g->rec.valid = false;
+    g->alpha_perf = mode;
+    return RFA_OK;
+}
 
 extern "C" rfa_status rfa_set_conduction(rfa_grid *g, int mode)
 {

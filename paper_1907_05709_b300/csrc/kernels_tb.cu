@@ -742,7 +742,7 @@ bool tb_supported(const rfa_grid *g, int depth, int variant)
     if (g->sp != RFA_STATE_F32C || g->pp != RFA_PARAM_BF16) return false;
     if (variant < 0 || variant > 2) return false;
     if (g->face != RFA_FACE_DIRICHLET) return false;  // insulated faces: one-step kernel
-    if (g->cond != RFA_COND_CENTRE) return false;     // conservative form: its own one-step kernel
+    if (g->cond != RFA_COND_CENTRE || g->alpha_perf) return false;  // model options: their own kernel
     if (variant == 0 && (depth < 2 || depth > 3)) return false;
     if (variant >= 1 && depth != 2) return false;
     return encode_fn() != nullptr;

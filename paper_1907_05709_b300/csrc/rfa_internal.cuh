@@ -157,6 +157,7 @@ struct rfa_grid {
     rfa::Record rec;
     int cond = 0;              // RFA_COND_CENTRE or RFA_COND_HARMONIC
     int src_mode = 0;          // 0: max(d, r0)^-4 weights; 1: potential solve (sigma |grad V|^2)
+    int alpha_perf = 0;        // 1: perfusion weighted by 1 / max(1, Omega)
     std::vector<double> sigma; // electrical conductivity per label (potential solve)
     int pot_max_iters = 0, pot_iters = 0;
     double pot_tol = 0.0, pot_res = 0.0;
@@ -216,8 +217,9 @@ cudaError_t launch_step_plain(rfa_grid *g, const void *th_in, const void *lo_in,
 // conservative conduction (kernels_cond.cu): label-pair tables of at most kCondLabels labels
 constexpr int kCondLabels = 16;
 rfa_status cond_build_tables(rfa_grid *g, const rfa_tissue *table, int n_labels);
-cudaError_t launch_step_cond(rfa_grid *g, const void *th_in, const void *lo_in, void *th_out, void *lo_out,
-                             bool damage, bool latch, bool fold);
+// one step of the model options (harmonic conduction and/or tissue-state perfusion)
+cudaError_t launch_step_model(rfa_grid *g, const void *th_in, const void *lo_in, void *th_out, void *lo_out,
+                              bool damage, bool latch, bool fold);
 cudaError_t launch_adjoint_cond(rfa_grid *g, const float *lam_in, float *lam_out, float *Lam, const float *th,
                                 double *acc);
 // temporal-blocked TMA kernel (kernels_tb.cu)

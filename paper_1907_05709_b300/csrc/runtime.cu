@@ -124,9 +124,9 @@ rfa_status advance(rfa_grid *g, int64_t nsteps, bool damage, bool latch)
         if (use_tb) {
             e = launch_step_tb(g, m, g->sched.tile_variant, g->th[g->cur], g->lo[g->cur],
                                g->th[g->cur ^ 1], g->lo[g->cur ^ 1], damage, fold);
-        } else if (g->cond == RFA_COND_HARMONIC) {
-            e = launch_step_cond(g, g->th[g->cur], g->lo[g->cur], g->th[g->cur ^ 1], g->lo[g->cur ^ 1], damage,
-                                 latch, fold);
+        } else if (g->cond == RFA_COND_HARMONIC || g->alpha_perf) {
+            e = launch_step_model(g, g->th[g->cur], g->lo[g->cur], g->th[g->cur ^ 1], g->lo[g->cur ^ 1], damage,
+                                  latch, fold);
         } else {
             e = launch_step_plain(g, g->th[g->cur], g->lo[g->cur], g->th[g->cur ^ 1],
                                   g->lo[g->cur ^ 1], damage, latch, fold);
