@@ -317,6 +317,22 @@ def measure_batched(rfa, stream, args):
 
 
 # ------------------------------------------------------------------ our arm
+# ------------------------------------------------------------------ ranks
+def reduce_max(x: float, dist, device) -> float:
+    """Max over ranks (identity on one process); every rank gets the result."""
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(nvox: int, nsteps: int, bench_steps: int, world: int, ms_max: float) -> float:
+    """Whole-job GVox-steps/s: every rank advances its own replica (weak scaling),
+    divided by the slowest rank's time."""
+    return nvox * nsteps * bench_steps * world / (ms_max * 1e-3) / 1e9
+
+
 def run_ours(args):
     import torch
     import paper_1907_05709_b300 as rfa
@@ -403,12 +419,9 @@ def run_ours(args):
     clocks = clk.stop()
     ms = t_start.elapsed_time(t_end)
     kern_ms = sum(a.elapsed_time(b) for a, b in step_ms)
-    ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = reduce_max(ms, dist, dev)
     vox_steps = case.nvox * case.nsteps * args.steps * world
-    value = vox_steps / (ms_max * 1e-3) / 1e9
+    value = job_throughput(case.nvox, case.nsteps, args.steps, world, ms_max)
 
     # end to end from host buffers (labels in, temperature field out)
     e2e = None
@@ -420,10 +433,7 @@ def run_ours(args):
             one_step(True)
         barrier()
         wall = time.perf_counter() - t0
-        w_t = torch.tensor([wall], device=dev, dtype=torch.float64)
-        if dist is not None:
-            dist.all_reduce(w_t, op=dist.ReduceOp.MAX)
-        e2e = {"value": vox_steps / float(w_t.item()) / 1e9, "unit": UNIT,
+        e2e = {"value": vox_steps / reduce_max(wall, dist, dev) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(case.nvox + 256 * 9 * 8 + 104),
                "d2h_bytes_per_step": int(case.nvox * 4 + 32 + 4)}
 
@@ -492,7 +502,7 @@ def profile_case(name):
     return 0
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -507,11 +517,16 @@ def main():
     ap.add_argument("--no-secondary", action="store_true", help="skip the adjoint and batched measurements")
     ap.add_argument("--batch-steps", type=int, default=4000)
     ap.add_argument("--profile-case", default=None, help="batch16 | adjoint128: short case for ncu")
-    args = ap.parse_args()
-    if args.profile_case:
-        return profile_case(args.profile_case)
+    args = ap.parse_args(argv)
     if args.schedule == "plain":
         args.schedule = "tb1"
+    return args
+
+
+def main():
+    args = parse_args()
+    if args.profile_case:
+        return profile_case(args.profile_case)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
