@@ -282,6 +282,89 @@ def measure_adjoint(rfa, stream):
             "backward_over_forward": t_b / t_f, "schedule": sched}
 
 
+def measure_next_rows(rfa, stream, case, g, cpu_baseline_on: bool):
+    """The model options at the bench's size, each against its compulsory bytes
+    (HBM roofline), and -- the CPU-baseline leg, unless disabled -- the FP64
+    oracle timed on a bounded sample beside it: breathing resample (Eq.
+    breathing), conservative conduction step, step with tissue-state perfusion,
+    potential-solve source (CG iterations)."""
+    import torch
+    peak, _ = measured_peak_hbm()
+    out = {}
+    n = case.nvox
+    cores = os.cpu_count()
+
+    def roof(nbytes, ms):
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        return {"achieved_GBs": gbs, "peak_GBs": peak, "frac": gbs / peak, "bytes_per_voxel": nbytes / n}
+
+    def cpu(value, unit, sample):
+        return {"value": value, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample}
+
+    # breathing resample of the bench grid's current state: u 12 B, theta hi+lo 8 B, T 4 B
+    u = torch.from_numpy(ph.breathing_field(case, 1.0)).cuda()
+    dst = torch.empty((case.nz, case.ny, case.nx), dtype=torch.float32, device="cuda")
+    rfa.rfa_warp_temperature(g.handle, u, dst, False)
+    ms = _ms_between(torch, stream, lambda: [rfa.rfa_warp_temperature(g.handle, u, dst, False)
+                                             for _ in range(5)]) / 5
+    out["breathing_warp"] = dict(roof(24.0 * n, ms), ms=ms, gvox_s=n / (ms * 1e-3) / 1e9)
+    del u, dst
+    if cpu_baseline_on:
+        import oracle
+        sm = ph.single_needle_case(seed=1, n=96, nsteps=1)
+        mo = oracle.setup(sm, "bf16")
+        uo = ph.breathing_field(sm, 1.0)
+        t0 = time.perf_counter()
+        oracle.warp_temperature(mo.theta0, uo, sm.h, sm.T_a_C)
+        out["breathing_warp"]["cpu_baseline"] = cpu(sm.nvox / (time.perf_counter() - t0) / 1e9, "GVox/s",
+                                                    "96^3 resample, numpy FP64")
+    # conservative conduction / tissue-state perfusion, 20 steps on a second grid;
+    # bytes per voxel-step: theta hi+lo 16, a/b 4, s 4, label 1, latch 2, carry 8 (+ Omega 8)
+    for name, cond, perf, bpv in (("conservative_step", "harmonic", "constant", 35.0),
+                                  ("tissue_state_step", "centre", "tissue_state", 43.0)):
+        c2 = ph.umbrella_case_256(seed=0, nsteps=20)
+        c2.conduction, c2.perfusion = cond, perf
+        g2 = rfa.Grid.from_case(c2, cuda_stream=stream.cuda_stream)
+        g2.step(4)
+        ms = _ms_between(torch, stream, lambda: g2.step(20)) / 20
+        g2.close()
+        out[name] = dict(roof(bpv * n, ms), ms_per_step=ms, gvox_steps_s=n / (ms * 1e-3) / 1e9)
+        if cpu_baseline_on:
+            import oracle
+            sm = ph.single_needle_case(seed=1, n=96, nsteps=4)
+            sm.conduction, sm.perfusion = cond, perf
+            mo = oracle.setup(sm, "bf16")
+            st = oracle.initial_state(mo)
+            t0 = time.perf_counter()
+            oracle.run(mo, st, 4, damage=sm.damage)
+            out[name]["cpu_baseline"] = cpu(sm.nvox * 4 / (time.perf_counter() - t0) / 1e9, "GVox-steps/s",
+                                            "96^3, 4 steps, FP64 oracle (C, OpenMP)")
+    # potential-solve source: FP64 CG; per iteration ~117 B/voxel: spmv (cls, label, D, p, Ap: 26),
+    # update (cls, 1/D, x, r, p, Ap read, x, r, z written: 65), direction (cls, z, p, p: 25)
+    c3 = ph.umbrella_case_256(seed=0, nsteps=1)
+    g3 = rfa.Grid(c3.nx, c3.ny, c3.nz, c3.h, c3.dt, rfa.STATE_F32C, rfa.PARAM_BF16, c3.face_bc, c3.T_a_C,
+                  stream.cuda_stream)
+    g3.set_tissue(c3.labels, c3.table)
+    sig = [t.sigma for t in c3.table]
+    rfa.rfa_place_needle_potential(g3.handle, c3.needle, sig, 40, 1e-30)      # warm-up
+    res = {}
+    ms = _ms_between(torch, stream, lambda: res.setdefault(
+        "r", rfa.rfa_place_needle_potential(g3.handle, c3.needle, sig, 20000, 1e-10)))
+    g3.close()
+    it, rel = res["r"]
+    out["potential_source"] = dict(roof(117.0 * n * it, ms), ms=ms, cg_iterations=it, rel_residual=rel,
+                                   ms_per_iteration=ms / max(it, 1))
+    if cpu_baseline_on:
+        import oracle
+        sm = ph.single_needle_case(seed=1, n=32, nsteps=1)
+        sm.source = "potential"
+        t0 = time.perf_counter()
+        oracle.setup(sm, "bf16")
+        out["potential_source"]["cpu_baseline"] = cpu(time.perf_counter() - t0, "s",
+                                                      "32^3 set-up with a direct sparse solve (scipy)")
+    return out
+
+
 def measure_batched(rfa, stream, args):
     """64 needle configurations on {96,128,160,192}^3 grids, 4000 steps (or
     --batch-steps): one batched persistent launch per call vs the per-needle loop
@@ -453,7 +536,8 @@ def run_ours(args):
     secondary = None
     if rank == 0 and not args.no_secondary:
         secondary = {"adjoint": measure_adjoint(rfa, stream),
-                     "batched": measure_batched(rfa, stream, args)}
+                     "batched": measure_batched(rfa, stream, args),
+                     "next_rows": measure_next_rows(rfa, stream, case, g, not args.no_cpu_baseline)}
     if dist is not None:
         dist.barrier()
     if rank == 0:

@@ -11,8 +11,10 @@
 //
 // Solver: conjugate gradients with the Jacobi preconditioner, matrix-free, in
 // FP64 (the source sets the heating of every later step; FP64 keeps the solve
-// far below the FP32 state's resolution).  Scalars stay on the device; the
-// host reads the residual every kCheck iterations.
+// far below the FP32 state's resolution).  The diagonal and its inverse are
+// stored once (B300's FP64 pipe is narrow: no per-iteration division).
+// Scalars stay on the device; the host reads the residual every kCheck
+// iterations.
 //
 // Heating: q_i = sum_nb sigma_f (V_nb - V_i)^2 / (2 h^2), each face's
 // dissipation split between its two voxels, so that sum_i q_i h^3 equals the
@@ -89,7 +91,7 @@ __global__ void k_pot_class(NeedleGeom geom, PotGrid G, double h, uint8_t *cls)
 
 // x0 = V on fixed voxels, 0 on free ones; r = b; z = r / D; p = z; partials of r.z and b.b
 __global__ void __launch_bounds__(256) k_pot_init(PotGrid G, double *xv, double *r, double *zv, double *p,
-                                                 double *part)
+                                                 double *Dv, double *iDv, double *part)
 {
     __shared__ double S[kCondLabels * kCondLabels];
     for (int k = threadIdx.x; k < kCondLabels * kCondLabels; k += blockDim.x) S[k] = G.S[k];
@@ -111,9 +113,12 @@ __global__ void __launch_bounds__(256) k_pot_init(PotGrid G, double *xv, double 
                 if (G.cls[j] == CLS_ELECTRODE) b += sf;
             }
             ri = b;
-            zi = D > 0.0 ? b / D : 0.0;
+            const double iD = D > 0.0 ? 1.0 / D : 0.0;
+            zi = b * iD;
             rz += ri * zi;
             bb += b * b;
+            Dv[i] = D;
+            iDv[i] = iD;
         }
         xv[i] = xi;
         r[i] = ri;
@@ -129,7 +134,8 @@ __global__ void __launch_bounds__(256) k_pot_init(PotGrid G, double *xv, double 
 }
 
 // Ap = A p on the free voxels; partial sums of p.Ap
-__global__ void __launch_bounds__(256) k_pot_spmv(PotGrid G, const double *p, double *Ap, double *part)
+__global__ void __launch_bounds__(256) k_pot_spmv(PotGrid G, const double *Dv, const double *p, double *Ap,
+                                                 double *part)
 {
     __shared__ double S[kCondLabels * kCondLabels];
     for (int k = threadIdx.x; k < kCondLabels * kCondLabels; k += blockDim.x) S[k] = G.S[k];
@@ -142,12 +148,10 @@ __global__ void __launch_bounds__(256) k_pot_spmv(PotGrid G, const double *p, do
             pot_xyz(G, i, x, y, z);
             const int l = G.label[i];
             const double pi = p[i];
+            v = Dv[i] * pi;
             for (int d = 0; d < 6; ++d) {
                 size_t j;
-                if (!pot_nb(G, i, x, y, z, d, j)) continue;
-                const double sf = S[l * kCondLabels + G.label[j]];
-                v += sf * pi;
-                if (G.cls[j] == CLS_FREE) v -= sf * p[j];
+                if (pot_nb(G, i, x, y, z, d, j) && G.cls[j] == CLS_FREE) v -= S[l * kCondLabels + G.label[j]] * p[j];
             }
             acc += pi * v;
         }
@@ -187,27 +191,17 @@ __global__ void k_pot_scalars(const double *part, int nblk, int which, double *s
 }
 
 // x += alpha p; r -= alpha Ap; z = r / D; partial sums of r.z and r.r
-__global__ void __launch_bounds__(256) k_pot_update(PotGrid G, const double *sc, double *xv, double *r, double *zv,
-                                                   const double *p, const double *Ap, double *part)
+__global__ void __launch_bounds__(256) k_pot_update(PotGrid G, const double *sc, const double *iDv, double *xv,
+                                                   double *r, double *zv, const double *p, const double *Ap,
+                                                   double *part)
 {
-    __shared__ double S[kCondLabels * kCondLabels];
-    for (int k = threadIdx.x; k < kCondLabels * kCondLabels; k += blockDim.x) S[k] = G.S[k];
-    __syncthreads();
     const double alpha = sc[SC_ALPHA];
     double rz = 0.0, rr = 0.0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < G.nvp; i += (size_t)gridDim.x * blockDim.x) {
         if (G.cls[i] != CLS_FREE) continue;
-        int x, y, z;
-        pot_xyz(G, i, x, y, z);
-        const int l = G.label[i];
-        double D = 0.0;
-        for (int d = 0; d < 6; ++d) {
-            size_t j;
-            if (pot_nb(G, i, x, y, z, d, j)) D += S[l * kCondLabels + G.label[j]];
-        }
         xv[i] += alpha * p[i];
         const double ri = r[i] - alpha * Ap[i];
-        const double zi = D > 0.0 ? ri / D : 0.0;
+        const double zi = ri * iDv[i];
         r[i] = ri;
         zv[i] = zi;
         rz += ri * zi;
@@ -281,34 +275,34 @@ rfa_status potential_place(rfa_grid *g)
         }
     const size_t nvp = g->nvp;
     struct Bufs {
-        void *p[7] = {};
+        void *p[9] = {};
         ~Bufs()
         {
             for (void *q : p)
                 if (q) cudaFree(q);
         }
     } B;
-    for (int k = 0; k < 5; ++k)
+    for (int k = 0; k < 7; ++k)
         if (cudaMalloc(&B.p[k], nvp * 8) != cudaSuccess) {
             cudaGetLastError();
             set_error("potential solve workspace allocation failed");
             return RFA_E_OOM;
         }
-    if (cudaMalloc(&B.p[5], nvp) != cudaSuccess || cudaMalloc(&B.p[6], kCondLabels * kCondLabels * 8 + SC_N * 8) != cudaSuccess) {
+    if (cudaMalloc(&B.p[7], nvp) != cudaSuccess || cudaMalloc(&B.p[8], kCondLabels * kCondLabels * 8 + SC_N * 8) != cudaSuccess) {
         cudaGetLastError();
         set_error("potential solve workspace allocation failed");
         return RFA_E_OOM;
     }
     double *xv = (double *)B.p[0], *r = (double *)B.p[1], *zv = (double *)B.p[2], *p = (double *)B.p[3];
-    double *Ap = (double *)B.p[4];
-    uint8_t *cls = (uint8_t *)B.p[5];
-    double *dS = (double *)B.p[6], *sc = dS + kCondLabels * kCondLabels;
+    double *Ap = (double *)B.p[4], *Dv = (double *)B.p[5], *iDv = (double *)B.p[6];
+    uint8_t *cls = (uint8_t *)B.p[7];
+    double *dS = (double *)B.p[8], *sc = dS + kCondLabels * kCondLabels;
     double *part = (double *)g->red;  // 2 * kReduceBlocks doubles
     RFA_CUDA(cudaMemcpyAsync(dS, S.data(), S.size() * 8, cudaMemcpyHostToDevice, g->stream));
     PotGrid G{cls, g->label, dS, g->nx, g->ny, g->nz, g->pitch, g->plane, nvp};
     const unsigned nb = kReduceBlocks;
     k_pot_class<<<nb, 256, 0, g->stream>>>(g->geom, G, g->h, cls);
-    k_pot_init<<<nb, 256, 0, g->stream>>>(G, xv, r, zv, p, part);
+    k_pot_init<<<nb, 256, 0, g->stream>>>(G, xv, r, zv, p, Dv, iDv, part);
     k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, 2, sc);
     RFA_CUDA(cudaGetLastError());
     double host_sc[SC_N];
@@ -320,9 +314,9 @@ rfa_status potential_place(rfa_grid *g)
     while (rel > g->pot_tol && it < g->pot_max_iters) {
         const int n = std::min(kCheck, g->pot_max_iters - it);
         for (int k = 0; k < n; ++k) {
-            k_pot_spmv<<<nb, 256, 0, g->stream>>>(G, p, Ap, part);
+            k_pot_spmv<<<nb, 256, 0, g->stream>>>(G, Dv, p, Ap, part);
             k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, 0, sc);
-            k_pot_update<<<nb, 256, 0, g->stream>>>(G, sc, xv, r, zv, p, Ap, part);
+            k_pot_update<<<nb, 256, 0, g->stream>>>(G, sc, iDv, xv, r, zv, p, Ap, part);
             k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, 1, sc);
             k_pot_direction<<<nb, 256, 0, g->stream>>>(G, sc, zv, p);
         }
