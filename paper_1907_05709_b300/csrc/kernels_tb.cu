@@ -17,7 +17,11 @@
 // planes q-1, q, q+1 of stage k-1 from a 3-plane shared-memory ring.  The
 // valid region shrinks by one voxel per stage in x and y (trapezoid); stage
 // k < M covers tile rows k .. EY-1-k, the last stage only the output tile, and
-// writes it to HBM.  Two CTA barriers per plane for M = 2.
+// writes it to HBM.  CTA barriers follow stages 1 .. M-1 only (one per plane
+// at M = 2): the last stage's coefficients are taken to registers before the
+// last barrier and its input ring has a fourth slot, so the next plane's early
+// stages overlap it; the next stage-0 plane is requested two planes ahead, right
+// after the last barrier.
 //
 // Numerics.  Every stage uses the same update (rfa_update.cuh) and the same
 // neighbour order as the one-step kernel, so a launch of depth M produces
@@ -49,34 +53,34 @@ constexpr int TB_TX = 64;       // output tile width
 constexpr int TB_HX = 4;        // x halo (keeps the TMA x coordinate 16-byte aligned)
 constexpr int TB_QX = TB_EX / 4;  // quads (4 consecutive x voxels) per tile row
 
-// Tile variants: height EY of the loaded tile and prefetch distance PD (stage-0
-// planes requested ahead of the one being consumed).
-//   0: EY = 16, PD = 1 (2 CTAs per SM at depth 2)
-//   1: EY = 32, PD = 1 (1 CTA per SM)
-//   2: EY = 14, PD = 2 (2 CTAs per SM at depth 2)
-__host__ __device__ constexpr int tile_ey(int v) { return v == 1 ? 32 : v == 2 ? 14 : 16; }
-__host__ __device__ constexpr int tile_pd(int v) { return v == 2 ? 2 : 1; }
+// Tile variants (height EY of the loaded tile):
+//   0: EY = 16 (2 CTAs per SM at depth 2)
+//   1: EY = 32 (1 CTA per SM)
+__host__ __device__ constexpr int tile_ey(int v) { return v == 1 ? 32 : 16; }
 
 template <int M, int V>
 struct Cfg {
     static constexpr int EY = tile_ey(V);
-    static constexpr int PD = tile_pd(V);
     static constexpr int TY = EY - 2 * M;                 // output rows per tile
     static constexpr int NQ1 = (EY - 2) * TB_QX;          // quads of stage 1 (tile rows 1 .. EY-2)
     static constexpr int NQO = TY * (TB_QX - 2);          // quads of the last stage (the output tile)
     static constexpr int THREADS = (NQ1 + 31) / 32 * 32;  // one thread per stage-1 quad
-    static constexpr int S0 = M + 1 + PD;                 // stage-0 ring slots (planes p0-M .. p0+PD)
+    // stage-0 ring: planes p0-M .. p0+1, and p0+2 requested into the slot of p0-M
+    // once the last barrier of the plane has passed
+    static constexpr int S0 = M + 2;
     static constexpr int BOX = TB_EX * EY;                // floats of one TMA box (a tile plane)
     // stride of the planes in shared memory: TMA destinations need 128-byte alignment
     static constexpr int PLANE = (BOX + 31) / 32 * 32;
     static constexpr int SLOT0 = 4 * PLANE;               // stage-0 slot: hi, lo, ab, s planes
-    // ring of stage k (1 <= k < M): 3 slots of hi, lo; from stage 2 on also the
-    // running Arrhenius sum and the running maximum of the voxel's values
+    // ring of stage k (1 <= k < M): slots of hi, lo; from stage 2 on also the
+    // running Arrhenius sum and the running maximum of the voxel's values.  3 slots;
+    // the last ring (read by the last stage, after which there is no barrier) 4.
     __host__ __device__ static constexpr int ring_planes(int k) { return k >= 2 ? 4 : 2; }
+    __host__ __device__ static constexpr int ring_slots(int k) { return k == M - 1 ? 4 : 3; }
     __host__ __device__ static constexpr int ring_off(int k)
     {
         int o = S0 * SLOT0;
-        for (int j = 1; j < k; ++j) o += 3 * ring_planes(j) * PLANE;
+        for (int j = 1; j < k; ++j) o += ring_slots(j) * ring_planes(j) * PLANE;
         return o;
     }
     static constexpr int BAR_OFF = ring_off(M);
@@ -238,7 +242,7 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
     mid[0] = mxl[0] = mxh[0] = 0;
     mact[0] = false;
 
-    constexpr int PD = C::PD;
+    constexpr int PD = 2;  // stage-0 planes requested ahead of the one consumed
     int item = first;
     if (item < nitems && tid == 0) {  // the first PD planes of the first item
         int local;
@@ -262,32 +266,21 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
         const bool out_quad = mact[M] && yg < A.ny && xg0 < A.nx;
         const int nin = A.nx - xg0;      // voxels of the quad inside the grid (>= 4: all)
 
-        // ring-0 slot offsets of planes p0 - d (d = 0 .. S0-1) and stage-ring
-        // slots e[r] of planes p0 - d with d % 3 == r; both rotate once per plane
+        // ring-0 slot offsets of planes p0 - d (d = 0 .. S0-1); stage-ring slots of
+        // planes p0 - d: e[d % 3] (3-slot rings), f[d % 4] (the last ring); all
+        // rotate once per plane
         int s0_cur = (int)(P.nload % S0);
         uint32_t phase = (uint32_t)((P.nload / S0) & 1);
         int r0[S0];
 #pragma unroll
         for (int d = 0; d < S0; ++d) r0[d] = ((s0_cur - d + S0) % S0) * C::SLOT0;
         int e[3] = {0, 2, 1};
+        int f[4] = {0, 3, 2, 1};
         float4 k1ch = make_float4(0.f, 0.f, 0.f, 0.f), k1cl = k1ch, k1mh = k1ch, k1ml = k1ch;
 
         for (int it = 0; it < L; ++it, ++P.nload) {
             const int p0 = zb - M + it;
             const int s0_next = s0_cur + 1 == S0 ? 0 : s0_cur + 1;
-            if (tid == 0) {  // request plane p0 + PD (of this item, else of the next one)
-                const int s0_pd = s0_cur + PD >= S0 ? s0_cur + PD - S0 : s0_cur + PD;
-                if (it + PD < L) {
-                    tb_issue<M, V>(P, s0_pd, maps, X0, Y0, p0 + PD);
-                } else if (item + stride < nitems) {
-                    int local1;
-                    const CUtensorMap *maps1;
-                    decltype(auto) T1 = get(item + stride, local1, maps1);
-                    int X1, Y1, zb1, ze1;
-                    tb_item_geom<M, V>(T1, local1, X1, Y1, zb1, ze1);
-                    tb_issue<M, V>(P, s0_pd, maps1, X1, Y1, zb1 - M + (it + PD - L));
-                }
-            }
             // output-stage operands of plane p0 - M, loaded early to hide their latency
             const int qo = p0 - M;
             const bool out_now = out_quad && it >= 2 * M && qo >= 0 && qo < A.nz;
@@ -304,6 +297,14 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
                 }
             }
             const bool ok = mbar_wait(bar_base + 8u * s0_cur, phase);
+            // the last stage's coefficients (plane p0 - M) go to registers before the
+            // last barrier: its ring-0 slot is then refilled right after that barrier
+            uint4 wM = make_uint4(0u, 0u, 0u, 0u);
+            float4 sM = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (mact[M] && it >= 2 * M) {
+                wM = *reinterpret_cast<const uint4 *>(sm + r0[M] + 2 * PLANE + mid[M]);
+                sM = ld4(sm, r0[M] + 3 * PLANE + mid[M]);
+            }
 #pragma unroll
             for (int k = 1; k <= M; ++k) {
                 if (it >= 2 * k && mact[k]) {
@@ -316,9 +317,15 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
                         bp = r0[0];
                     } else {
                         const int rk = C::ring_off(k - 1), sl = C::ring_planes(k - 1) * PLANE;
-                        bc = rk + e[k % 3] * sl;
-                        bm = rk + e[(k + 1) % 3] * sl;
-                        bp = rk + e[(k - 1) % 3] * sl;
+                        if (k == M) {  // the last ring: 4 slots
+                            bc = rk + f[k % 4] * sl;
+                            bm = rk + f[(k + 1) % 4] * sl;
+                            bp = rk + f[(k - 1) % 4] * sl;
+                        } else {
+                            bc = rk + e[k % 3] * sl;
+                            bm = rk + e[(k + 1) % 3] * sl;
+                            bp = rk + e[(k - 1) % 3] * sl;
+                        }
                     }
                     float4 ch, cl, zmh, zml;
                     if (k == 1 && it > 2) {  // this column's planes p0-2, p0-1, kept from the last iteration
@@ -333,8 +340,8 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
                     if (k == 1) { k1mh = ch; k1ml = cl; k1ch = zph; k1cl = zpl; }
                     const float lh = sm[bc + id + mxl[k]], ll = sm[bc + PLANE + id + mxl[k]];
                     const float rh = sm[bc + id + mxh[k]], rl = sm[bc + PLANE + id + mxh[k]];
-                    const uint4 w4 = *reinterpret_cast<const uint4 *>(sm + cb + 2 * PLANE + id);
-                    const float4 s4 = ld4(sm, cb + 3 * PLANE + id);
+                    const uint4 w4 = k == M ? wM : *reinterpret_cast<const uint4 *>(sm + cb + 2 * PLANE + id);
+                    const float4 s4 = k == M ? sM : ld4(sm, cb + 3 * PLANE + id);
                     // voxel pairs (0,1) and (2,3) of the quad
                     const float2 C01 = make_float2(ch.x, ch.y), C23 = make_float2(ch.z, ch.w);
                     const float2 L01 = make_float2(cl.x, cl.y), L23 = make_float2(cl.z, cl.w);
@@ -383,7 +390,7 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
                     }
                     if (k < M) {
                         const int ro = C::ring_off(k), sl = C::ring_planes(k) * PLANE;
-                        const int bo = ro + e[k % 3] * sl;
+                        const int bo = ro + (k == M - 1 ? f[k % 4] : e[k % 3]) * sl;
                         *reinterpret_cast<float4 *>(sm + bo + id) = make_float4(H01.x, H01.y, H23.x, H23.y);
                         *reinterpret_cast<float4 *>(sm + bo + PLANE + id) = make_float4(N01.x, N01.y, N23.x, N23.y);
                         if (k >= 2) {
@@ -438,22 +445,37 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
                         }
                     }
                 }
+                // a barrier after every stage but the last: the next plane's stages
+                // 1 .. M-1 touch no slot the last stage still reads (4-slot last ring,
+                // its coefficients already in registers), so warps without a quad in
+                // the last stage go straight on to the next plane
                 if (k == 1) {
                     // the stage-1 barrier also agrees on the stage-0 wait: a CTA whose
                     // wait timed out leaves (stage 1 only wrote shared memory)
                     if (__syncthreads_or(!ok)) {
-                        if (tid == 0) {  // let the requests in flight land first (bounded)
+                        if (tid == 0) {  // let the request in flight land first (bounded)
                             atomicOr(status, kStatusTimeout);
-#pragma unroll
-                            for (int j = 1; j <= PD; ++j) {
-                                const int sj = s0_cur + j >= S0 ? s0_cur + j - S0 : s0_cur + j;
-                                mbar_wait(bar_base + 8u * sj, s0_cur + j >= S0 ? phase ^ 1u : phase);
-                            }
+                            mbar_wait(bar_base + 8u * s0_next, s0_next == 0 ? phase ^ 1u : phase);
                         }
                         return false;
                     }
-                } else {
+                } else if (k < M) {
                     __syncthreads();
+                }
+                if (k == M - 1 && tid == 0) {
+                    // every read of plane p0 - M's slot is done: request plane p0 + PD
+                    // into it (of this item, else of the next one)
+                    const int s0_pd = s0_cur + PD >= S0 ? s0_cur + PD - S0 : s0_cur + PD;
+                    if (it + PD < L) {
+                        tb_issue<M, V>(P, s0_pd, maps, X0, Y0, p0 + PD);
+                    } else if (item + stride < nitems) {
+                        int local1;
+                        const CUtensorMap *maps1;
+                        decltype(auto) T1 = get(item + stride, local1, maps1);
+                        int X1, Y1, zb1, ze1;
+                        tb_item_geom<M, V>(T1, local1, X1, Y1, zb1, ze1);
+                        tb_issue<M, V>(P, s0_pd, maps1, X1, Y1, zb1 - M + (it + PD - L));
+                    }
                 }
             }
             // rotate the ring slots by one plane
@@ -465,6 +487,11 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
             e[2] = e[1];
             e[1] = e[0];
             e[0] = t1;
+            const int t2 = f[3];
+            f[3] = f[2];
+            f[2] = f[1];
+            f[1] = f[0];
+            f[0] = t2;
             if (s0_next == 0) phase ^= 1u;
             s0_cur = s0_next;
         }
@@ -740,7 +767,7 @@ MapCache &map_cache()
 bool tb_supported(const rfa_grid *g, int depth, int variant)
 {
     if (g->sp != RFA_STATE_F32C || g->pp != RFA_PARAM_BF16) return false;
-    if (variant < 0 || variant > 2) return false;
+    if (variant < 0 || variant > 1) return false;
     if (g->face != RFA_FACE_DIRICHLET) return false;  // insulated faces: one-step kernel
     if (g->cond != RFA_COND_CENTRE || g->alpha_perf) return false;  // model options: their own kernel
     if (variant == 0 && (depth < 2 || depth > 3)) return false;
@@ -795,7 +822,6 @@ cudaError_t launch_step_tb(rfa_grid *g, int depth, int variant, const void *th_i
     TB_CASE(2, 0)
     TB_CASE(3, 0)
     TB_CASE(2, 1)
-    TB_CASE(2, 2)
 #undef TB_CASE
     return cudaErrorInvalidValue;
 }
@@ -813,7 +839,6 @@ cudaError_t launch_step_tb_rec(rfa_grid *g, int depth, int variant, const void *
     if (depth == 2 && variant == 0) return launch_inst<2, 0, false, false, true>(g, maps, T);
     if (depth == 3 && variant == 0) return launch_inst<3, 0, false, false, true>(g, maps, T);
     if (depth == 2 && variant == 1) return launch_inst<2, 1, false, false, true>(g, maps, T);
-    if (depth == 2 && variant == 2) return launch_inst<2, 2, false, false, true>(g, maps, T);
     return cudaErrorInvalidValue;
 }
 
@@ -864,7 +889,6 @@ cudaError_t prepare_batch_tb(int depth, int variant, bool damage, int nitems, in
     PREP_CASE(2, 0)
     PREP_CASE(3, 0)
     PREP_CASE(2, 1)
-    PREP_CASE(2, 2)
 #undef PREP_CASE
     return cudaErrorInvalidValue;
 }
@@ -921,7 +945,6 @@ cudaError_t graph_batch_tb(int depth, int variant, bool damage, const void *memb
     GRAPH_CASE(2, 0)
     GRAPH_CASE(3, 0)
     GRAPH_CASE(2, 1)
-    GRAPH_CASE(2, 2)
 #undef GRAPH_CASE
     return cudaErrorInvalidValue;
 }
@@ -938,7 +961,6 @@ cudaError_t launch_batch_tb(int depth, int variant, bool damage, const void *mem
     BATCH_CASE(2, 0)
     BATCH_CASE(3, 0)
     BATCH_CASE(2, 1)
-    BATCH_CASE(2, 2)
 #undef BATCH_CASE
     return cudaErrorInvalidValue;
 }
