@@ -11,6 +11,7 @@
 // not fill a block run as one-step launches per member afterwards.
 #include "rfa_internal.cuh"
 
+#include <algorithm>
 #include <cstdio>
 #include <fstream>
 #include <new>
@@ -37,6 +38,8 @@ struct rfa_batch {
 };
 
 namespace rfa {
+
+constexpr int64_t kMaxBlocksPerLaunch = 4096;  // time blocks of one batched launch
 
 namespace {
 
@@ -102,7 +105,8 @@ rfa_status upload_members(rfa_batch *b)
 
 cudaError_t enqueue_blocks(rfa_batch *b, int64_t ntime)
 {
-    cudaError_t e = cudaMemsetAsync(b->d_gbar, 0, 2 * sizeof(unsigned), b->stream);
+    // grid barrier (2 words) and the item counter of every time block
+    cudaError_t e = cudaMemsetAsync(b->d_gbar, 0, (2 + (size_t)ntime) * sizeof(unsigned), b->stream);
     if (e != cudaSuccess) return e;
     return launch_batch_tb(b->depth, b->variant, b->damage, b->d_members, (int)b->members.size(), b->nitems,
                            (int)ntime, b->d_gbar, b->members[0]->status, b->stream, b->grid);
@@ -138,15 +142,18 @@ rfa_status run_blocks(rfa_batch *b, int64_t ntime)
 rfa_status batch_step(rfa_batch *b, int64_t nsteps)
 {
     const int64_t ntime = nsteps / b->depth, rem = nsteps % b->depth;
-    if (ntime > 0) {
+    // at most kMaxBlocksPerLaunch time blocks per launch (one item counter each)
+    for (int64_t done = 0; done < ntime;) {
+        const int64_t n = std::min<int64_t>(ntime - done, kMaxBlocksPerLaunch);
         rfa_status st = upload_members(b);
         if (st != RFA_OK) return st;
-        st = run_blocks(b, ntime);
+        st = run_blocks(b, n);
         if (st != RFA_OK) return st;
         for (rfa_grid *g : b->members) {
-            g->cur ^= (int)(ntime & 1);
-            if (b->damage) g->carry_steps = 0;  // the last block folded the carry
+            g->cur ^= (int)(n & 1);
+            if (b->damage) g->carry_steps = 0;  // the last block of a launch folds the carry
         }
+        done += n;
     }
     for (rfa_grid *g : b->members) {
         if (rem > 0) {
@@ -200,7 +207,7 @@ rfa_status rfa_batch_create(rfa_grid *const *members, int n, rfa_batch **out)
     b->members.assign(members, members + n);
     b->stream = members[0]->stream;
     b->damage = members[0]->dmg != 0;
-    if (cudaMalloc((void **)&b->d_gbar, 256) != cudaSuccess) {
+    if (cudaMalloc((void **)&b->d_gbar, (2 + (size_t)kMaxBlocksPerLaunch) * sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
         delete b;
         return bfail(RFA_E_OOM, "batch barrier allocation failed");

@@ -177,7 +177,21 @@ __device__ __forceinline__ void tb_issue(const TBPipe &P, int j, const CUtensorM
     tma_load_3d(dst + 12u * C::PLANE, &maps[3], X0 - TB_HX, Y0 - M, z, bar);
 }
 
-// Advance work items first, first + stride, ... < nitems by M steps.
+// The work items a CTA advances: a fixed stride (items of one grid are alike),
+// or claimed from a counter (batch members differ in size, so CTAs that finish
+// early take more).  start() gives the first item, after(cur) the next one.
+struct StrideItems {
+    int first, stride;
+    __device__ int start() const { return first; }
+    __device__ int after(int cur) const { return cur + stride; }
+};
+struct ClaimedItems {
+    unsigned *ctr;
+    __device__ int start() const { return (int)atomicAdd(ctr, 1u); }
+    __device__ int after(int) const { return (int)atomicAdd(ctr, 1u); }
+};
+
+// Advance the work items of `items` (< nitems) by M steps.
 // get(item, local, maps) returns the item's TBTile (a reference to kernel
 // parameters for one grid; a register copy for the batch), its index in that
 // tile and the tensor maps of the tile's input state.
@@ -200,9 +214,8 @@ __device__ __forceinline__ void tb_issue(const TBPipe &P, int j, const CUtensorM
 // nothing is carried between planes; for M = 3 the running sum and maximum
 // travel with the values through the stage-2 ring.  The sums keep the order
 // ((inc_1 + inc_2) + ...) of the per-step evaluation.
-template <int M, int V, bool DMG, bool FOLD, bool REC, class Get>
-__device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &get, unsigned *status,
-                       bool &bad)
+template <int M, int V, bool DMG, bool FOLD, bool REC, class Items, class Get>
+__device__ bool tb_run(TBPipe &P, const Items &items, int nitems, const Get &get, unsigned *status, bool &bad)
 {
     static_assert(!(REC && DMG), "the replay has no damage integral");
     using C = Cfg<M, V>;
@@ -243,17 +256,29 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
     mact[0] = false;
 
     constexpr int PD = 2;  // stage-0 planes requested ahead of the one consumed
-    int item = first;
-    if (item < nitems && tid == 0) {  // the first PD planes of the first item
-        int local;
-        const CUtensorMap *mp;
-        const TBTile &T = get(item, local, mp);
-        int X0, Y0, zb, ze;
-        tb_item_geom<M, V>(T, local, X0, Y0, zb, ze);
+    // item queue: the current item and the next one, both known to every thread;
+    // thread 0 takes the one after next during the current item (after its first
+    // barrier, when every thread has read the current entry) and the next item's
+    // first planes are requested before the current one ends
+    __shared__ int s_q[2];
+    if (tid == 0) {
+        const int i0 = items.start();
+        s_q[0] = i0;
+        s_q[1] = i0 < nitems ? items.after(i0) : nitems;
+        if (i0 < nitems) {  // the first PD planes of the first item
+            int local;
+            const CUtensorMap *mp;
+            const TBTile &T = get(i0, local, mp);
+            int X0, Y0, zb, ze;
+            tb_item_geom<M, V>(T, local, X0, Y0, zb, ze);
 #pragma unroll
-        for (int j = 0; j < PD; ++j) tb_issue<M, V>(P, (int)((P.nload + j) % S0), mp, X0, Y0, zb - M + j);
+            for (int j = 0; j < PD; ++j) tb_issue<M, V>(P, (int)((P.nload + j) % S0), mp, X0, Y0, zb - M + j);
+        }
     }
-    for (; item < nitems; item += stride) {
+    __syncthreads();
+    int qk = 0;
+    int item = s_q[0], nxt = s_q[1];
+    while (item < nitems) {
         int local;
         const CUtensorMap *maps;
         decltype(auto) A = get(item, local, maps);
@@ -462,16 +487,17 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
                 } else if (k < M) {
                     __syncthreads();
                 }
+                if (k == 1 && it == 0 && tid == 0) s_q[qk] = nxt < nitems ? items.after(nxt) : nitems;
                 if (k == M - 1 && tid == 0) {
                     // every read of plane p0 - M's slot is done: request plane p0 + PD
                     // into it (of this item, else of the next one)
                     const int s0_pd = s0_cur + PD >= S0 ? s0_cur + PD - S0 : s0_cur + PD;
                     if (it + PD < L) {
                         tb_issue<M, V>(P, s0_pd, maps, X0, Y0, p0 + PD);
-                    } else if (item + stride < nitems) {
+                    } else if (nxt < nitems) {
                         int local1;
                         const CUtensorMap *maps1;
-                        decltype(auto) T1 = get(item + stride, local1, maps1);
+                        decltype(auto) T1 = get(nxt, local1, maps1);
                         int X1, Y1, zb1, ze1;
                         tb_item_geom<M, V>(T1, local1, X1, Y1, zb1, ze1);
                         tb_issue<M, V>(P, s0_pd, maps1, X1, Y1, zb1 - M + (it + PD - L));
@@ -495,6 +521,9 @@ __device__ bool tb_run(TBPipe &P, int first, int stride, int nitems, const Get &
             if (s0_next == 0) phase ^= 1u;
             s0_cur = s0_next;
         }
+        item = nxt;
+        nxt = s_q[qk];
+        qk ^= 1;
     }
     return true;
 }
@@ -539,7 +568,8 @@ __global__ void __launch_bounds__(Cfg<M, V>::THREADS, Cfg<M, V>::MINB)
         return T0;
     };
     bool bad = false;
-    tb_run<M, V, DMG, FOLD, REC>(P, blockIdx.x, gridDim.x, T0.xt * T0.yt * T0.zc, get, status, bad);
+    tb_run<M, V, DMG, FOLD, REC>(P, StrideItems{(int)blockIdx.x, (int)gridDim.x}, T0.xt * T0.yt * T0.zc, get,
+                                 status, bad);
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusNonfinite);
 }
 
@@ -607,8 +637,9 @@ __global__ void __launch_bounds__(Cfg<M, V>::THREADS, Cfg<M, V>::MINB)
             return T;
         };
         const bool fold = DMG && ((t + 1) % fold_every == 0 || t == ntime - 1);
-        const bool ok = fold ? tb_run<M, V, DMG, true, false>(P, blockIdx.x, gridDim.x, nitems, get, status, bad)
-                             : tb_run<M, V, DMG, false, false>(P, blockIdx.x, gridDim.x, nitems, get, status, bad);
+        const ClaimedItems items{gbar + 2 + t};  // one counter per time block, zeroed before the launch
+        const bool ok = fold ? tb_run<M, V, DMG, true, false>(P, items, nitems, get, status, bad)
+                             : tb_run<M, V, DMG, false, false>(P, items, nitems, get, status, bad);
         if (!ok) break;
         if (!grid_sync(gbar, gridDim.x)) {
             if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
@@ -908,7 +939,7 @@ cudaError_t graph_batch_inst(const TBMember *mem, int nmem, int nitems, int ntim
     mp.dst = gbar;
     mp.value = 0;
     mp.elementSize = sizeof(unsigned);
-    mp.width = 2;
+    mp.width = 2 + (size_t)ntime;  // grid barrier and one item counter per time block
     mp.height = 1;
     mp.pitch = 0;
     e = cudaGraphAddMemsetNode(&nmemset, graph, nullptr, 0, &mp);
