@@ -26,6 +26,7 @@ struct rfa_batch {
     bool damage = false;
     std::vector<rfa::TBMemberHost> hosts;
     std::vector<int> item_begin;
+    std::vector<int> order;  // descriptor slot -> member (costliest items first)
     int nitems = 0;
     void *d_members = nullptr;
     CUtensorMap *d_maps = nullptr;
@@ -68,11 +69,20 @@ rfa_status build_plan(rfa_batch *b)
     const int n = (int)b->members.size();
     b->hosts.assign(n, TBMemberHost{});
     b->item_begin.assign(n + 1, 0);
-    for (int m = 0; m < n; ++m) {
+    for (int m = 0; m < n; ++m)
         if (!tb_batch_member(b->members[m], b->depth, b->variant, 64, b->hosts[m]))
             return bfail(RFA_E_CUDA, "tensor map creation failed for a batch member");
-        b->item_begin[m + 1] = b->item_begin[m] + b->hosts[m].items;
-    }
+    // items are claimed in numbering order: number the costliest items (most
+    // planes per z chunk) first, so that a time block ends on the cheapest ones
+    b->order.resize(n);
+    for (int m = 0; m < n; ++m) b->order[m] = m;
+    auto cost = [&](int m) {
+        const rfa_grid *g = b->members[m];
+        const int zc = b->hosts[m].tile[0].zc;
+        return (g->nz + zc - 1) / zc + 2 * b->depth;
+    };
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    for (int j = 0; j < n; ++j) b->item_begin[j + 1] = b->item_begin[j] + b->hosts[b->order[j]].items;
     b->nitems = b->item_begin[n];
     const size_t mb = tb_member_bytes();
     if (cudaMalloc(&b->d_members, mb * n) != cudaSuccess ||
@@ -82,8 +92,8 @@ rfa_status build_plan(rfa_batch *b)
         return bfail(RFA_E_OOM, "batch descriptor allocation failed");
     }
     std::vector<CUtensorMap> maps(8 * (size_t)n);
-    for (int m = 0; m < n; ++m)
-        for (int k = 0; k < 8; ++k) maps[8 * (size_t)m + k] = b->hosts[m].maps[k];
+    for (int j = 0; j < n; ++j)
+        for (int k = 0; k < 8; ++k) maps[8 * (size_t)j + k] = b->hosts[b->order[j]].maps[k];
     RFA_CUDA(cudaMemcpyAsync(b->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
                              b->stream));
     RFA_CUDA(cudaStreamSynchronize(b->stream));
@@ -95,9 +105,11 @@ rfa_status build_plan(rfa_batch *b)
 rfa_status upload_members(rfa_batch *b)
 {
     const size_t mb = tb_member_bytes();
-    for (size_t m = 0; m < b->members.size(); ++m)
-        tb_pack_member(b->hosts[m], b->d_maps + 8 * m, b->item_begin[m], b->members[m]->cur,
-                       (char *)b->h_members + mb * m);
+    for (size_t j = 0; j < b->members.size(); ++j) {
+        const int m = b->order[j];
+        tb_pack_member(b->hosts[m], b->d_maps + 8 * j, b->item_begin[j], b->members[m]->cur,
+                       (char *)b->h_members + mb * j);
+    }
     RFA_CUDA(cudaMemcpyAsync(b->d_members, b->h_members, mb * b->members.size(), cudaMemcpyHostToDevice,
                              b->stream));
     return RFA_OK;
