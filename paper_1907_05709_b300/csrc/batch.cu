@@ -70,7 +70,7 @@ rfa_status build_plan(rfa_batch *b)
     b->hosts.assign(n, TBMemberHost{});
     b->item_begin.assign(n + 1, 0);
     for (int m = 0; m < n; ++m)
-        if (!tb_batch_member(b->members[m], b->depth, b->variant, 64, b->hosts[m]))
+        if (!tb_batch_member(b->members[m], b->depth, b->variant, 96, b->hosts[m]))
             return bfail(RFA_E_CUDA, "tensor map creation failed for a batch member");
     // items are claimed in numbering order: number the costliest items (most
     // planes per z chunk) first, so that a time block ends on the cheapest ones
