@@ -66,122 +66,297 @@ struct CondArgs {
     double thr;
     DamageConst dc;
     int damage, latch_on, fold;
+    int zchunk;
     int cond;   // 0: centre form (a_i * sum of differences), 1: harmonic face weights
     int alpha;  // perfusion weighted by 1 / max(1, Omega) of the step's start
 };
 
+template <typename T>
+struct MQ {
+    T v[4];
+};
+__device__ __forceinline__ MQ<float> mldq(const float *p)
+{
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    return {{t.x, t.y, t.z, t.w}};
+}
+__device__ __forceinline__ MQ<double> mldq(const double *p)
+{
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    return {{a.x, a.y, b.x, b.y}};
+}
+template <typename T>
+__device__ __forceinline__ MQ<T> mzq()
+{
+    return {{T(0), T(0), T(0), T(0)}};
+}
+// a and b of voxels i..i+3 (i a multiple of 4) in the parameter type's own
+// precision: float for BF16/FP32 storage, double for FP64
+template <int PP, typename W>
+__device__ __forceinline__ void mld_ab(const void *ab, size_t i, W a[4], W b[4])
+{
+    if (PP == RFA_PARAM_BF16) {
+        const uint4 w = *reinterpret_cast<const uint4 *>((const uint32_t *)ab + i);
+        const uint32_t v[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            a[q] = (W)bf16_to_float(v[q] & 0xffffu);
+            b[q] = (W)bf16_to_float(v[q] >> 16);
+        }
+    } else if (PP == RFA_PARAM_F32) {
+        const float4 u = reinterpret_cast<const float4 *>((const float2 *)ab + i)[0];
+        const float4 w = reinterpret_cast<const float4 *>((const float2 *)ab + i)[1];
+        a[0] = (W)u.x, b[0] = (W)u.y, a[1] = (W)u.z, b[1] = (W)u.w;
+        a[2] = (W)w.x, b[2] = (W)w.y, a[3] = (W)w.z, b[3] = (W)w.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double2 v = ((const double2 *)ab)[i + q];
+            a[q] = (W)v.x;
+            b[q] = (W)v.y;
+        }
+    }
+}
+
+// One step of the model options, a thread per quad of 4 consecutive x voxels
+// streaming z (planes z-1, z, z+1 and their labels in registers); x neighbours
+// and their labels by warp shuffles, y neighbours through L1.  Per voxel the
+// centre form performs the one-step kernel's operations; the harmonic form
+// weighs every neighbour difference with its face weight from the label-pair
+// table; with the tissue-state coupling b is divided by max(1, Omega).
 template <int SP, int PP>
 __global__ void __launch_bounds__(256) k_step_model(const CondArgs A)
 {
     using T = typename std::conditional<SP == RFA_STATE_F64, double, float>::type;
     using W = typename std::conditional<PP == RFA_PARAM_F64, double, float>::type;
+    using IT = typename std::conditional<SP == RFA_STATE_F64, double, float>::type;
+    // b after the tissue-state division: double where the state or the parameters are FP64
+    using BT = typename std::conditional<SP == RFA_STATE_F64 || PP == RFA_PARAM_F64, double, float>::type;
+    constexpr bool COMP = SP == RFA_STATE_F32C;
+    const unsigned FULL = 0xffffffffu;
     __shared__ W wt[kCondLabels * kCondLabels];
     for (int k = threadIdx.y * blockDim.x + threadIdx.x; k < kCondLabels * kCondLabels; k += blockDim.x * blockDim.y)
         wt[k] = ((const W *)A.wpair)[k];
     __syncthreads();
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= A.pitch || y >= A.ny) return;
-    const size_t i = (size_t)z * A.plane + (size_t)y * A.pitch + x;
+    const int lane = threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (y >= A.ny) return;  // whole warp (blockDim.x == 32), after the only barrier
+    const int x0 = 4 * (blockIdx.x * 32 + lane);
+    const bool inrow = x0 < A.pitch;
+    const int zb = blockIdx.z * A.zchunk, ze = min(A.nz, zb + A.zchunk);
     const T *hin = (const T *)A.th_in;
     T *hout = (T *)A.th_out;
-    if (x >= A.nx) {  // row padding stays zero
-        hout[i] = T(0);
-        if (SP == RFA_STATE_F32C) A.lo_out[i] = 0.f;
-        return;
-    }
-    double ad, bd;
-    cond_ab<PP>(A.ab, i, ad, bd);
-    const T c = hin[i];  // (ad, bd: the voxel's a and b as stored)
-    const float cl = SP == RFA_STATE_F32C ? A.lo_in[i] : 0.f;
-    T nh = c;
-    float nl = cl;
-    if (ad != 0.0) {
-        const int l = A.label[i];
-        const W *wl = wt + l * kCondLabels;
-        // neighbours in the fixed order x-, x+, y-, y+, z-, z+
-        const bool in[6] = {x > 0, x + 1 < A.nx, y > 0, y + 1 < A.ny, z > 0, z + 1 < A.nz};
-        const long long off[6] = {-1, 1, -(long long)A.pitch, (long long)A.pitch, -(long long)A.plane,
-                                  (long long)A.plane};
-        const T sv = ((const T *)A.s)[i];
-        if (A.alpha) {  // tissue state: alpha = 1 / max(1, Omega) with Omega before this step
-            const double om = A.omega[i] + (double)A.omega_c[i];
-            if (om > 1.0) bd = bd / om;
+    const T thr = (T)A.thr;
+    const size_t rowoff = (size_t)y * A.pitch + x0;
+    const bool hasYm = y > 0, hasYp = y < A.ny - 1, hasL = x0 > 0, hasR = x0 + 4 < A.nx;
+    MQ<T> hm = mzq<T>(), hc = mzq<T>(), hp = mzq<T>();
+    MQ<float> lm = mzq<float>(), lc = mzq<float>(), lp = mzq<float>();
+    uint32_t labm = 0, labc = 0, labp = 0;
+    if (inrow) {
+        const size_t ic = (size_t)zb * A.plane + rowoff;
+        hc = mldq(hin + ic);
+        if (COMP) lc = mldq(A.lo_in + ic);
+        labc = *reinterpret_cast<const uint32_t *>(A.label + ic);
+        if (zb > 0) {
+            hm = mldq(hin + ic - A.plane);
+            if (COMP) lm = mldq(A.lo_in + ic - A.plane);
+            labm = *reinterpret_cast<const uint32_t *>(A.label + ic - A.plane);
         }
-        if (!A.cond) {
-            // centre form: the one-step kernel's operations (bit-identical to it when alpha = 1)
-            if (SP == RFA_STATE_F32C) {
-                float S = 0.f;
+    }
+    bool bad = false;
+    for (int z = zb; z < ze; ++z) {
+        const size_t i = (size_t)z * A.plane + rowoff;
+        const bool hasZp = z + 1 < A.nz, hasZm = z > 0;
+        MQ<T> hym = mzq<T>(), hyp = mzq<T>();
+        MQ<float> lym = mzq<float>(), lyp = mzq<float>();
+        uint32_t labym = 0, labyp = 0;
+        W aq[4] = {0, 0, 0, 0}, bq[4] = {0, 0, 0, 0};
+        MQ<T> sq = mzq<T>();
+        if (inrow) {
+            if (hasZp) {
+                hp = mldq(hin + i + A.plane);
+                if (COMP) lp = mldq(A.lo_in + i + A.plane);
+                labp = *reinterpret_cast<const uint32_t *>(A.label + i + A.plane);
+            }
+            if (hasYm) {
+                hym = mldq(hin + i - A.pitch);
+                if (COMP) lym = mldq(A.lo_in + i - A.pitch);
+                labym = *reinterpret_cast<const uint32_t *>(A.label + i - A.pitch);
+            }
+            if (hasYp) {
+                hyp = mldq(hin + i + A.pitch);
+                if (COMP) lyp = mldq(A.lo_in + i + A.pitch);
+                labyp = *reinterpret_cast<const uint32_t *>(A.label + i + A.pitch);
+            }
+            mld_ab<PP, W>(A.ab, i, aq, bq);
+            sq = mldq((const T *)A.s + i);
+        }
+        // x neighbours across quads (value, lo part, label)
+        T left = __shfl_up_sync(FULL, hc.v[3], 1), right = __shfl_down_sync(FULL, hc.v[0], 1);
+        float lleft = 0.f, lright = 0.f;
+        if (COMP) {
+            lleft = __shfl_up_sync(FULL, lc.v[3], 1);
+            lright = __shfl_down_sync(FULL, lc.v[0], 1);
+        }
+        uint32_t labl = __shfl_up_sync(FULL, labc >> 24, 1), labr = __shfl_down_sync(FULL, labc & 0xffu, 1);
+        if (inrow && lane == 0 && hasL) {
+            left = hin[i - 1];
+            if (COMP) lleft = A.lo_in[i - 1];
+            labl = A.label[i - 1];
+        }
+        if (inrow && lane == 31 && hasR) {
+            right = hin[i + 4];
+            if (COMP) lright = A.lo_in[i + 4];
+            labr = A.label[i + 4];
+        }
+        if (inrow) {
+            MQ<double> om4 = mzq<double>();
+            float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (A.damage || A.alpha) {
+                cc = *reinterpret_cast<const float4 *>(A.omega_c + i);
+                if (A.alpha || A.fold || SP == RFA_STATE_F64) om4 = mldq(A.omega + i);
+            }
+            const float ccv[4] = {cc.x, cc.y, cc.z, cc.w};
+            MQ<T> ho;
+            MQ<float> lo;
+            uint32_t latch_bits = 0;
+            IT inc[4] = {0, 0, 0, 0};
 #pragma unroll
-                for (int d = 0; d < 6; ++d) {
-                    const size_t j = (size_t)((long long)i + (in[d] ? off[d] : 0));
-                    S = acc(S, in[d] ? cdiff((float)hin[j], A.lo_in[j], (float)c, cl) : 0.f);
+            for (int q = 0; q < 4; ++q) {
+                const int x = x0 + q;
+                const T c = hc.v[q];
+                const float cl = COMP ? lc.v[q] : 0.f;
+                T nh = c;
+                float nl = cl;
+                if (aq[q] != W(0) && x < A.nx) {
+                    BT bd = (BT)bq[q];
+                    // tissue state: b / max(1, Omega) with Omega at the start of the step.  Omega
+                    // below 0.5 (the high word of the double) and a carry below 0.5 give an FP64
+                    // sum below 1 exactly, so the FP64 sum and the division are skipped there.
+                    if (A.alpha && !(__double2hiint(om4.v[q]) < 0x3FE00000 && ccv[q] < 0.5f)) {
+                        const double om = om4.v[q] + (double)ccv[q];
+                        if (om > 1.0) bd = (BT)((double)bq[q] / om);
+                    }
+                    // neighbours in the fixed order x-, x+, y-, y+, z-, z+
+                    const bool in[6] = {x > 0, x + 1 < A.nx, hasYm, hasYp, hasZm, hasZp};
+                    const T nbh[6] = {q == 0 ? left : hc.v[q - 1], q == 3 ? right : hc.v[q + 1], hym.v[q], hyp.v[q],
+                                      hm.v[q], hp.v[q]};
+                    const float nbl[6] = {COMP ? (q == 0 ? lleft : lc.v[q - 1]) : 0.f,
+                                          COMP ? (q == 3 ? lright : lc.v[q + 1]) : 0.f, lym.v[q], lyp.v[q], lm.v[q],
+                                          lp.v[q]};
+                    const int l = (labc >> (8 * q)) & 0xff;
+                    const int nbl_lab[6] = {q == 0 ? (int)labl : (int)((labc >> (8 * (q - 1))) & 0xff),
+                                            q == 3 ? (int)labr : (int)((labc >> (8 * (q + 1))) & 0xff),
+                                            (int)((labym >> (8 * q)) & 0xff), (int)((labyp >> (8 * q)) & 0xff),
+                                            (int)((labm >> (8 * q)) & 0xff), (int)((labp >> (8 * q)) & 0xff)};
+                    if (COMP) {
+                        float h2, l2;
+                        if (!A.cond) {
+                            float S = 0.f;
+#pragma unroll
+                            for (int d = 0; d < 6; ++d)
+                                S = acc(S, in[d] ? cdiff((float)nbh[d], nbl[d], (float)c, cl) : 0.f);
+                            cupdate((float)c, cl, S, (float)aq[q], (float)bd, (float)sq.v[q], h2, l2);
+                        } else {
+                            const float th = __fadd_rn((float)c, cl);
+                            float delta = __fmaf_rn(-(float)bd, th, (float)sq.v[q]);
+#pragma unroll
+                            for (int d = 0; d < 6; ++d)
+                                if (in[d])
+                                    delta = __fmaf_rn((float)wt[l * kCondLabels + nbl_lab[d]],
+                                                      cdiff((float)nbh[d], nbl[d], (float)c, cl), delta);
+                            cadd((float)c, cl, delta, h2, l2);
+                        }
+                        nh = (T)h2;
+                        nl = l2;
+                    } else if (!A.cond) {
+                        T S = T(0);
+#pragma unroll
+                        for (int d = 0; d < 6; ++d) S = acc(S, in[d] ? pdiff(nbh[d], c) : T(0));
+                        nh = pupdate(c, S, (T)aq[q], (T)bd, sq.v[q]);
+                    } else {
+                        T delta;
+                        if (SP == RFA_STATE_F64) delta = (T)__fma_rn(-bd, (double)c, (double)sq.v[q]);
+                        else delta = (T)__fmaf_rn(-(float)bd, (float)c, (float)sq.v[q]);
+#pragma unroll
+                        for (int d = 0; d < 6; ++d)
+                            if (in[d]) {
+                                const T w = (T)wt[l * kCondLabels + nbl_lab[d]];
+                                if (SP == RFA_STATE_F64)
+                                    delta = (T)__fma_rn((double)w, __dsub_rn((double)nbh[d], (double)c), (double)delta);
+                                else
+                                    delta = (T)__fmaf_rn((float)w, __fsub_rn((float)nbh[d], (float)c), (float)delta);
+                            }
+                        nh = SP == RFA_STATE_F64 ? (T)__dadd_rn((double)c, (double)delta)
+                                                 : (T)__fadd_rn((float)c, (float)delta);
+                    }
                 }
-                float h2, l2;
-                cupdate((float)c, cl, S, (float)ad, (float)bd, (float)sv, h2, l2);
-                nh = (T)h2;
-                nl = l2;
+                if (x >= A.nx) {
+                    nh = T(0);
+                    nl = 0.f;
+                }
+                bad |= x < A.nx && !isfinite(nh);
+                ho.v[q] = nh;
+                lo.v[q] = nl;
+                if (A.latch_on && x < A.nx && nh + (T)nl >= thr) latch_bits |= 1u << (8 * q);
+                if (A.damage && x < A.nx) {
+                    if (SP == RFA_STATE_F64) inc[q] = exp2(A.dc.c0d - A.dc.c1d / ((double)nh + A.dc.TK0d));
+                    else inc[q] = arrhenius_inc(__fadd_rn((float)nh, nl), A.dc.c0, A.dc.c1, A.dc.TK0);
+                }
+            }
+            if (SP == RFA_STATE_F64) {
+                reinterpret_cast<double2 *>(hout + i)[0] = make_double2((double)ho.v[0], (double)ho.v[1]);
+                reinterpret_cast<double2 *>(hout + i)[1] = make_double2((double)ho.v[2], (double)ho.v[3]);
             } else {
-                T S = T(0);
-#pragma unroll
-                for (int d = 0; d < 6; ++d) {
-                    const size_t j = (size_t)((long long)i + (in[d] ? off[d] : 0));
-                    S = acc(S, in[d] ? pdiff(hin[j], c) : T(0));
-                }
-                nh = pupdate(c, S, (T)ad, (T)bd, sv);
+                *reinterpret_cast<float4 *>(hout + i) =
+                    make_float4((float)ho.v[0], (float)ho.v[1], (float)ho.v[2], (float)ho.v[3]);
             }
-        } else if (SP == RFA_STATE_F32C) {
-            const float th = __fadd_rn((float)c, cl);
-            float delta = __fmaf_rn(-(float)bd, th, (float)sv);
+            if (COMP) *reinterpret_cast<float4 *>(A.lo_out + i) = make_float4(lo.v[0], lo.v[1], lo.v[2], lo.v[3]);
+            if (A.latch_on && latch_bits) {
+                uint32_t *lp32 = reinterpret_cast<uint32_t *>(A.latch + i);
+                const uint32_t old = *lp32;
+                if ((old | latch_bits) != old) *lp32 = old | latch_bits;
+            }
+            if (A.damage) {
+                float P[4] = {cc.x, cc.y, cc.z, cc.w};
+                double om[4] = {om4.v[0], om4.v[1], om4.v[2], om4.v[3]};
+                if (SP == RFA_STATE_F64) {
 #pragma unroll
-            for (int d = 0; d < 6; ++d)
-                if (in[d]) {
-                    const size_t j = (size_t)((long long)i + off[d]);
-                    const float w = (float)wl[A.label[j]];
-                    delta = __fmaf_rn(w, cdiff((float)hin[j], A.lo_in[j], (float)c, cl), delta);
-                }
-            float h2, l2;
-            cadd((float)c, cl, delta, h2, l2);
-            nh = (T)h2;
-            nl = l2;
-        } else {
-            T delta;
-            if (SP == RFA_STATE_F64) delta = (T)__fma_rn(-bd, (double)c, (double)sv);
-            else delta = (T)__fmaf_rn(-(float)bd, (float)c, (float)sv);
+                    for (int q = 0; q < 4; ++q) {
+                        if (x0 + q >= A.nx) continue;
+                        const double sm = __dadd_rn(om[q], (double)inc[q]);
+                        const double bb = __dsub_rn(sm, om[q]);
+                        const double er =
+                            __dadd_rn(__dsub_rn(om[q], __dsub_rn(sm, bb)), __dsub_rn((double)inc[q], bb));
+                        om[q] = sm;
+                        P[q] = __fadd_rn(P[q], (float)er);
+                    }
+                } else {
 #pragma unroll
-            for (int d = 0; d < 6; ++d)
-                if (in[d]) {
-                    const size_t j = (size_t)((long long)i + off[d]);
-                    const T w = (T)wl[A.label[j]];
-                    if (SP == RFA_STATE_F64) delta = (T)__fma_rn((double)w, __dsub_rn((double)hin[j], (double)c), (double)delta);
-                    else delta = (T)__fmaf_rn((float)w, __fsub_rn((float)hin[j], (float)c), (float)delta);
+                    for (int q = 0; q < 4; ++q)
+                        if (x0 + q < A.nx) P[q] = __fadd_rn(P[q], (float)inc[q]);
+                    if (A.fold)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (x0 + q < A.nx) carry_fold(om[q], P[q]);
                 }
-            nh = SP == RFA_STATE_F64 ? (T)__dadd_rn((double)c, (double)delta) : (T)__fadd_rn((float)c, (float)delta);
+                if (SP == RFA_STATE_F64 || A.fold) {
+                    reinterpret_cast<double2 *>(A.omega + i)[0] = make_double2(om[0], om[1]);
+                    reinterpret_cast<double2 *>(A.omega + i)[1] = make_double2(om[2], om[3]);
+                }
+                *reinterpret_cast<float4 *>(A.omega_c + i) = make_float4(P[0], P[1], P[2], P[3]);
+            }
+        }
+        hm = hc;
+        hc = hp;
+        labm = labc;
+        labc = labp;
+        if (COMP) {
+            lm = lc;
+            lc = lp;
         }
     }
-    hout[i] = nh;
-    if (SP == RFA_STATE_F32C) A.lo_out[i] = nl;
-    if (!isfinite((double)nh)) atomicOr(A.status, kStatusNonfinite);
-    if (A.latch_on && nh + (T)nl >= (T)A.thr) A.latch[i] = 1;
-    if (A.damage) {
-        if (SP == RFA_STATE_F64) {
-            const double inc = exp2(A.dc.c0d - A.dc.c1d / ((double)nh + A.dc.TK0d));
-            const double om = A.omega[i];
-            const double sm = __dadd_rn(om, inc);
-            const double bb = __dsub_rn(sm, om);
-            const double er = __dadd_rn(__dsub_rn(om, __dsub_rn(sm, bb)), __dsub_rn(inc, bb));
-            A.omega[i] = sm;
-            A.omega_c[i] = __fadd_rn(A.omega_c[i], (float)er);
-        } else {
-            float P = __fadd_rn(A.omega_c[i], arrhenius_inc(__fadd_rn((float)nh, nl), A.dc.c0, A.dc.c1, A.dc.TK0));
-            if (A.fold) {
-                double om = A.omega[i];
-                carry_fold(om, P);
-                A.omega[i] = om;
-            }
-            A.omega_c[i] = P;
-        }
-    }
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(A.status, kStatusNonfinite);
 }
 
 struct CondAdjArgs {
@@ -349,7 +524,8 @@ cudaError_t launch_step_model(rfa_grid *g, const void *th_in, const void *lo_in,
     A.damage = damage ? 1 : 0;
     A.latch_on = latch ? 1 : 0;
     A.fold = fold ? 1 : 0;
-    const dim3 blk(32, 8), grd = cond_grid(g);
+    A.zchunk = choose_zchunk(g, 3);
+    const dim3 blk(32, 8), grd = plain_grid_dims(g, A.zchunk);
 #define COND_CASE(SPV, PPV) \
     if (g->sp == SPV && g->pp == PPV) k_step_model<SPV, PPV><<<grd, blk, 0, g->stream>>>(A);
     COND_CASE(RFA_STATE_F32, RFA_PARAM_BF16)
