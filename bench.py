@@ -339,8 +339,10 @@ def measure_next_rows(rfa, stream, case, g, cpu_baseline_on: bool):
             oracle.run(mo, st, 4, damage=sm.damage)
             out[name]["cpu_baseline"] = cpu(sm.nvox * 4 / (time.perf_counter() - t0) / 1e9, "GVox-steps/s",
                                             "96^3, 4 steps, FP64 oracle (C, OpenMP)")
-    # potential-solve source: FP64 CG; per iteration ~117 B/voxel: spmv (cls, label, D, p, Ap: 26),
-    # update (cls, 1/D, x, r, p, Ap read, x, r, z written: 65), direction (cls, z, p, p: 25)
+    # potential-solve source: FP32 CG iterations inside an FP64 defect correction; per FP32
+    # iteration 60 B/voxel: spmv (cls, label, D, p read, Ap written: 14), update (cls, 1/D, e, r,
+    # p, Ap read, e, r, z written: 33), direction (cls, z, p read, p written: 13).  The few FP64
+    # correction passes per solve (x += e, r = b - A x) are not counted: the figure is a floor.
     c3 = ph.umbrella_case_256(seed=0, nsteps=1)
     g3 = rfa.Grid(c3.nx, c3.ny, c3.nz, c3.h, c3.dt, rfa.STATE_F32C, rfa.PARAM_BF16, c3.face_bc, c3.T_a_C,
                   stream.cuda_stream)
@@ -352,7 +354,7 @@ def measure_next_rows(rfa, stream, case, g, cpu_baseline_on: bool):
         "r", rfa.rfa_place_needle_potential(g3.handle, c3.needle, sig, 20000, 1e-10)))
     g3.close()
     it, rel = res["r"]
-    out["potential_source"] = dict(roof(117.0 * n * it, ms), ms=ms, cg_iterations=it, rel_residual=rel,
+    out["potential_source"] = dict(roof(60.0 * n * it, ms), ms=ms, cg_iterations=it, rel_residual=rel,
                                    ms_per_iteration=ms / max(it, 1))
     if cpu_baseline_on:
         import oracle
@@ -580,6 +582,28 @@ def profile_case(name):
         seed = torch.full(case.labels.shape, 1e-6, dtype=torch.float32, device="cuda")
         for _ in range(2):
             g.backward(seed)
+    elif name == "model256":
+        # the model options at 256^3: breathing resample, conservative step,
+        # tissue-state step, 40 iterations of the potential solve
+        case = ph.umbrella_case_256(seed=0, nsteps=8)
+        g = rfa.Grid.from_case(case, cuda_stream=stream.cuda_stream)
+        g.step(8)
+        u = torch.from_numpy(ph.breathing_field(case, 1.0)).cuda()
+        dst = torch.empty((case.nz, case.ny, case.nx), dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            rfa.rfa_warp_temperature(g.handle, u, dst, False)
+        g.close()
+        for cond, perf in (("harmonic", "constant"), ("centre", "tissue_state")):
+            c2 = ph.umbrella_case_256(seed=0, nsteps=8)
+            c2.conduction, c2.perfusion = cond, perf
+            g2 = rfa.Grid.from_case(c2, cuda_stream=stream.cuda_stream)
+            g2.step(8)
+            g2.close()
+        g3 = rfa.Grid(case.nx, case.ny, case.nz, case.h, case.dt, rfa.STATE_F32C, rfa.PARAM_BF16, case.face_bc,
+                      case.T_a_C, stream.cuda_stream)
+        g3.set_tissue(case.labels, case.table)
+        rfa.rfa_place_needle_potential(g3.handle, case.needle, [t.sigma for t in case.table], 40, 1e-30)
+        g3.close()
     else:
         raise SystemExit(f"unknown profile case {name}")
     torch.cuda.synchronize()
@@ -600,7 +624,7 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-secondary", action="store_true", help="skip the adjoint and batched measurements")
     ap.add_argument("--batch-steps", type=int, default=4000)
-    ap.add_argument("--profile-case", default=None, help="batch16 | adjoint128: short case for ncu")
+    ap.add_argument("--profile-case", default=None, help="batch16 | adjoint128 | model256: short case for ncu")
     args = ap.parse_args(argv)
     if args.schedule == "plain":
         args.schedule = "tb1"

@@ -282,10 +282,15 @@ rfa_status rfa_set_perfusion_coupling(rfa_grid *g, int mode);
  * dissipation split between its voxels) is scaled so that the free voxels
  * receive power_W, and written to the source field like rfa_place_needle.
  *   sigma_S_per_m : host, n_sigma = number of labels, electrical conductivity.
- *   max_iters, tol: preconditioned conjugate gradients (FP64) stop at
- *                   ||r|| <= tol ||b|| or after max_iters iterations.
- *   iters_out, rel_residual_out (may be NULL): iterations used, final ||r||/||b||
- *                   (check it against tol: reaching max_iters is not an error).
+ *   max_iters, tol: Jacobi-preconditioned conjugate gradients stop when the
+ *                   FP64 residual ||b - A x|| <= tol ||b|| or after max_iters
+ *                   iterations.  The iterations run in FP32 inside an FP64
+ *                   defect correction (x and b - A x in FP64 after each FP32
+ *                   cycle); if a cycle gains less than 2x, FP64 conjugate
+ *                   gradients continue from the current x.
+ *   iters_out, rel_residual_out (may be NULL): iterations used (FP32 and FP64
+ *                   together), final FP64 ||b - A x||/||b|| (check it against
+ *                   tol: reaching max_iters is not an error).
  * Synchronous.  rfa_set_tissue re-solves with the same settings.  rfa_backward
  * returns RFA_E_UNSUPPORTED while this source is in use.
  * Errors: RFA_E_STATE (no tissue), RFA_E_INVALID (needle, sigma, n_sigma,
@@ -326,7 +331,9 @@ rfa_status rfa_set_conduction(rfa_grid *g, int mode);
  *   dst_dev   : device, nx*ny*nz values in degrees C, x fastest; float, or
  *               double when as_f64 != 0.  Caller-owned.
  * FP64 states interpolate in FP64; FP32 states in FP32 (hi and lo parts
- * separately).  Asynchronous on the grid's stream; the state is not changed.
+ * separately, then summed with the ambient temperature in FP64 for a double
+ * output, in FP32 for a float one).  Asynchronous on the grid's stream; the
+ * state is not changed.
  * Errors: RFA_E_INVALID (null pointer), RFA_E_STATE (no tissue yet).
  */
 rfa_status rfa_warp_temperature(rfa_grid *g, const float *u_inv_dev, void *dst_dev, int as_f64);

@@ -124,7 +124,7 @@ __device__ __forceinline__ void mld_ab(const void *ab, size_t i, W a[4], W b[4])
 // centre form performs the one-step kernel's operations; the harmonic form
 // weighs every neighbour difference with its face weight from the label-pair
 // table; with the tissue-state coupling b is divided by max(1, Omega).
-template <int SP, int PP>
+template <int SP, int PP, bool COND, bool ALPHA>
 __global__ void __launch_bounds__(256) k_step_model(const CondArgs A)
 {
     using T = typename std::conditional<SP == RFA_STATE_F64, double, float>::type;
@@ -209,12 +209,18 @@ __global__ void __launch_bounds__(256) k_step_model(const CondArgs A)
             if (COMP) lright = A.lo_in[i + 4];
             labr = A.label[i + 4];
         }
+        // the quad, its x neighbours and its y/z neighbour quads all of one label
+        const uint32_t l0 = labc & 0xffu;
+        const bool uni = labc == l0 * 0x01010101u && labym == labc && labyp == labc && labm == labc &&
+                         labp == labc && labl == l0 && labr == l0;
+        W wuni = W(0);
+        if (COND && uni) wuni = wt[l0 * (kCondLabels + 1)];
         if (inrow) {
             MQ<double> om4 = mzq<double>();
             float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (A.damage || A.alpha) {
+            if (A.damage || ALPHA) {
                 cc = *reinterpret_cast<const float4 *>(A.omega_c + i);
-                if (A.alpha || A.fold || SP == RFA_STATE_F64) om4 = mldq(A.omega + i);
+                if (ALPHA || A.fold || SP == RFA_STATE_F64) om4 = mldq(A.omega + i);
             }
             const float ccv[4] = {cc.x, cc.y, cc.z, cc.w};
             MQ<T> ho;
@@ -233,7 +239,7 @@ __global__ void __launch_bounds__(256) k_step_model(const CondArgs A)
                     // tissue state: b / max(1, Omega) with Omega at the start of the step.  Omega
                     // below 0.5 (the high word of the double) and a carry below 0.5 give an FP64
                     // sum below 1 exactly, so the FP64 sum and the division are skipped there.
-                    if (A.alpha && !(__double2hiint(om4.v[q]) < 0x3FE00000 && ccv[q] < 0.5f)) {
+                    if (ALPHA && !(__double2hiint(om4.v[q]) < 0x3FE00000 && ccv[q] < 0.5f)) {
                         const double om = om4.v[q] + (double)ccv[q];
                         if (om > 1.0) bd = (BT)((double)bq[q] / om);
                     }
@@ -244,14 +250,28 @@ __global__ void __launch_bounds__(256) k_step_model(const CondArgs A)
                     const float nbl[6] = {COMP ? (q == 0 ? lleft : lc.v[q - 1]) : 0.f,
                                           COMP ? (q == 3 ? lright : lc.v[q + 1]) : 0.f, lym.v[q], lyp.v[q], lm.v[q],
                                           lp.v[q]};
-                    const int l = (labc >> (8 * q)) & 0xff;
-                    const int nbl_lab[6] = {q == 0 ? (int)labl : (int)((labc >> (8 * (q - 1))) & 0xff),
-                                            q == 3 ? (int)labr : (int)((labc >> (8 * (q + 1))) & 0xff),
-                                            (int)((labym >> (8 * q)) & 0xff), (int)((labyp >> (8 * q)) & 0xff),
-                                            (int)((labm >> (8 * q)) & 0xff), (int)((labp >> (8 * q)) & 0xff)};
+                    // face weights w(l, m): one table entry where the quad and all its
+                    // neighbours share a label, else one look-up per face
+                    W wv[6];
+                    if (COND) {
+                        if (uni) {
+#pragma unroll
+                            for (int d = 0; d < 6; ++d) wv[d] = wuni;
+                        } else {
+                            const int l = (labc >> (8 * q)) & 0xff;
+                            const int nbl_lab[6] = {q == 0 ? (int)labl : (int)((labc >> (8 * (q - 1))) & 0xff),
+                                                    q == 3 ? (int)labr : (int)((labc >> (8 * (q + 1))) & 0xff),
+                                                    (int)((labym >> (8 * q)) & 0xff),
+                                                    (int)((labyp >> (8 * q)) & 0xff),
+                                                    (int)((labm >> (8 * q)) & 0xff),
+                                                    (int)((labp >> (8 * q)) & 0xff)};
+#pragma unroll
+                            for (int d = 0; d < 6; ++d) wv[d] = wt[l * kCondLabels + nbl_lab[d]];
+                        }
+                    }
                     if (COMP) {
                         float h2, l2;
-                        if (!A.cond) {
+                        if (!COND) {
                             float S = 0.f;
 #pragma unroll
                             for (int d = 0; d < 6; ++d)
@@ -263,13 +283,12 @@ __global__ void __launch_bounds__(256) k_step_model(const CondArgs A)
 #pragma unroll
                             for (int d = 0; d < 6; ++d)
                                 if (in[d])
-                                    delta = __fmaf_rn((float)wt[l * kCondLabels + nbl_lab[d]],
-                                                      cdiff((float)nbh[d], nbl[d], (float)c, cl), delta);
+                                    delta = __fmaf_rn((float)wv[d], cdiff((float)nbh[d], nbl[d], (float)c, cl), delta);
                             cadd((float)c, cl, delta, h2, l2);
                         }
                         nh = (T)h2;
                         nl = l2;
-                    } else if (!A.cond) {
+                    } else if (!COND) {
                         T S = T(0);
 #pragma unroll
                         for (int d = 0; d < 6; ++d) S = acc(S, in[d] ? pdiff(nbh[d], c) : T(0));
@@ -281,7 +300,7 @@ __global__ void __launch_bounds__(256) k_step_model(const CondArgs A)
 #pragma unroll
                         for (int d = 0; d < 6; ++d)
                             if (in[d]) {
-                                const T w = (T)wt[l * kCondLabels + nbl_lab[d]];
+                                const T w = (T)wv[d];
                                 if (SP == RFA_STATE_F64)
                                     delta = (T)__fma_rn((double)w, __dsub_rn((double)nbh[d], (double)c), (double)delta);
                                 else
@@ -502,6 +521,7 @@ cudaError_t launch_step_model(rfa_grid *g, const void *th_in, const void *lo_in,
     CondArgs A;
     A.cond = g->cond == RFA_COND_HARMONIC ? 1 : 0;
     A.alpha = g->alpha_perf;
+    if (!A.cond && !A.alpha) return cudaErrorInvalidValue;  // the one-step kernel serves this model
     A.th_in = th_in;
     A.lo_in = (const float *)lo_in;
     A.th_out = th_out;
@@ -526,8 +546,12 @@ cudaError_t launch_step_model(rfa_grid *g, const void *th_in, const void *lo_in,
     A.fold = fold ? 1 : 0;
     A.zchunk = choose_zchunk(g, 3);
     const dim3 blk(32, 8), grd = plain_grid_dims(g, A.zchunk);
-#define COND_CASE(SPV, PPV) \
-    if (g->sp == SPV && g->pp == PPV) k_step_model<SPV, PPV><<<grd, blk, 0, g->stream>>>(A);
+#define COND_CASE(SPV, PPV)                                                                                  \
+    if (g->sp == SPV && g->pp == PPV) {                                                                      \
+        if (A.cond && A.alpha) k_step_model<SPV, PPV, true, true><<<grd, blk, 0, g->stream>>>(A);            \
+        else if (A.cond) k_step_model<SPV, PPV, true, false><<<grd, blk, 0, g->stream>>>(A);                 \
+        else k_step_model<SPV, PPV, false, true><<<grd, blk, 0, g->stream>>>(A);                             \
+    }
     COND_CASE(RFA_STATE_F32, RFA_PARAM_BF16)
     COND_CASE(RFA_STATE_F32, RFA_PARAM_F32)
     COND_CASE(RFA_STATE_F32, RFA_PARAM_F64)

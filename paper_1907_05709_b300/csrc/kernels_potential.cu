@@ -9,12 +9,19 @@
 //   free voxel i:  sum_nb sigma_f (V_i - V_nb) = 0, a symmetric positive
 //   definite system in the free unknowns.
 //
-// Solver: conjugate gradients with the Jacobi preconditioner, matrix-free, in
-// FP64 (the source sets the heating of every later step; FP64 keeps the solve
-// far below the FP32 state's resolution).  The diagonal and its inverse are
-// stored once (B300's FP64 pipe is narrow: no per-iteration division).
-// Scalars stay on the device; the host reads the residual every kCheck
-// iterations.
+// Solver: conjugate gradients with the Jacobi preconditioner, matrix-free, to
+// an FP64 relative residual (the source sets the heating of every later step;
+// FP64 keeps the solve far below the FP32 state's resolution).  B300's FP64
+// pipe is narrow, so the iterations run in FP32 inside an FP64 defect
+// correction: each cycle solves A e = r in FP32 (reducing the FP32 residual
+// by kInnerEta, or as far as the tolerance still needs), adds e to the FP64
+// iterate x and forms the true residual r = b - A x in FP64.  A cycle that
+// gains less than a factor 2 (FP32 has stagnated at its attainable accuracy,
+// about cond(A) * 2^-24) hands over to plain FP64 conjugate gradients from
+// the current x.  The stopping rule is the FP64 one either way:
+// ||b - A x|| <= tol ||b||.  The diagonal and its inverse are stored once (no
+// per-iteration division).  Scalars stay on the device; the host reads the
+// residual every kCheck iterations.
 //
 // Heating: q_i = sum_nb sigma_f (V_nb - V_i)^2 / (2 h^2), each face's
 // dissipation split between its two voxels, so that sum_i q_i h^3 equals the
@@ -30,6 +37,7 @@ namespace rfa {
 namespace {
 
 constexpr int kCheck = 20;
+constexpr double kInnerEta = 1e-4;  // FP32 residual reduction per correction cycle
 enum { CLS_FREE = 0, CLS_ELECTRODE = 1, CLS_GROUND = 2, CLS_PAD = 3 };
 // scalars: rz, alpha, beta, rr, bb
 enum { SC_RZ = 0, SC_ALPHA, SC_BETA, SC_RR, SC_BB, SC_N };
@@ -74,6 +82,17 @@ __device__ __forceinline__ void pot_xyz(const PotGrid &G, size_t i, int &x, int 
     const size_t r = i / G.pitch;
     y = (int)(r % G.ny);
     z = (int)(r / G.ny);
+}
+
+// the per-iteration kernels: a warp per grid row (one 32-bit division per row
+// instead of 64-bit ones per voxel), lanes along x; padding voxels untouched
+#define POT_ROWS(G)                                                                                                 \
+    for (int row = blockIdx.x * 8 + (int)(threadIdx.x >> 5); row < (G).ny * (G).nz; row += gridDim.x * 8)         \
+        for (int y = row % (G).ny, z = row / (G).ny, x = threadIdx.x & 31; x < (G).nx; x += 32)
+
+__device__ __forceinline__ size_t pot_at(const PotGrid &G, int x, int y, int z)
+{
+    return (size_t)z * G.plane + (size_t)y * G.pitch + x;
 }
 
 __global__ void k_pot_class(NeedleGeom geom, PotGrid G, double h, uint8_t *cls)
@@ -141,32 +160,31 @@ __global__ void __launch_bounds__(256) k_pot_spmv(PotGrid G, const double *Dv, c
     for (int k = threadIdx.x; k < kCondLabels * kCondLabels; k += blockDim.x) S[k] = G.S[k];
     __syncthreads();
     double acc = 0.0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < G.nvp; i += (size_t)gridDim.x * blockDim.x) {
-        double v = 0.0;
-        if (G.cls[i] == CLS_FREE) {
-            int x, y, z;
-            pot_xyz(G, i, x, y, z);
-            const int l = G.label[i];
-            const double pi = p[i];
-            v = Dv[i] * pi;
-            for (int d = 0; d < 6; ++d) {
-                size_t j;
-                if (pot_nb(G, i, x, y, z, d, j) && G.cls[j] == CLS_FREE) v -= S[l * kCondLabels + G.label[j]] * p[j];
-            }
-            acc += pi * v;
+    POT_ROWS(G)
+    {
+        const size_t i = pot_at(G, x, y, z);
+        if (G.cls[i] != CLS_FREE) continue;
+        const int l = G.label[i];
+        const double pi = p[i];
+        double v = Dv[i] * pi;
+        for (int d = 0; d < 6; ++d) {
+            size_t j;
+            if (pot_nb(G, i, x, y, z, d, j) && G.cls[j] == CLS_FREE) v -= S[l * kCondLabels + G.label[j]] * p[j];
         }
         Ap[i] = v;
+        acc += pi * v;
     }
     acc = pot_block_sum(acc);
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
-// scalar steps on one block: which = 0 -> alpha = rz / sum(part); 1 -> rz_new, beta, rr
+// scalar steps on one block: which = 0 -> alpha = rz / sum(part); 1 -> rz_new,
+// beta, rr; 2 -> rz, rr (and b.b) at a start; 3 -> rr = sum(part)
 __global__ void k_pot_scalars(const double *part, int nblk, int which, double *sc)
 {
     double a = 0.0, b = 0.0;
     for (int k = threadIdx.x; k < nblk; k += blockDim.x) {
-        if (which == 0) {
+        if (which == 0 || which == 3) {
             a += part[k];
         } else {
             a += part[2 * k];
@@ -182,10 +200,12 @@ __global__ void k_pot_scalars(const double *part, int nblk, int which, double *s
             sc[SC_BETA] = sc[SC_RZ] != 0.0 ? a / sc[SC_RZ] : 0.0;
             sc[SC_RZ] = a;
             sc[SC_RR] = b;
-        } else {  // initial: rz and b.b
+        } else if (which == 2) {  // a start: rz and r.r (b.b at the first)
             sc[SC_RZ] = a;
             sc[SC_BB] = b;
             sc[SC_RR] = b;
+        } else {
+            sc[SC_RR] = a;
         }
     }
 }
@@ -197,7 +217,9 @@ __global__ void __launch_bounds__(256) k_pot_update(PotGrid G, const double *sc,
 {
     const double alpha = sc[SC_ALPHA];
     double rz = 0.0, rr = 0.0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < G.nvp; i += (size_t)gridDim.x * blockDim.x) {
+    POT_ROWS(G)
+    {
+        const size_t i = pot_at(G, x, y, z);
         if (G.cls[i] != CLS_FREE) continue;
         xv[i] += alpha * p[i];
         const double ri = r[i] - alpha * Ap[i];
@@ -215,12 +237,247 @@ __global__ void __launch_bounds__(256) k_pot_update(PotGrid G, const double *sc,
     }
 }
 
-__global__ void k_pot_direction(PotGrid G, const double *sc, const double *zv, double *p)
+__global__ void __launch_bounds__(256) k_pot_direction(PotGrid G, const double *sc, const double *zv, double *p)
 {
     const double beta = sc[SC_BETA];
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < G.nvp; i += (size_t)gridDim.x * blockDim.x)
+    POT_ROWS(G)
+    {
+        const size_t i = pot_at(G, x, y, z);
         if (G.cls[i] == CLS_FREE) p[i] = zv[i] + beta * p[i];
+    }
 }
+
+// ---- FP32 inner iterations and the FP64 correction
+
+// the FP32 face-conductance table in shared memory
+__device__ __forceinline__ void pot_table32(const PotGrid &G, float *S)
+{
+    for (int k = threadIdx.x; k < kCondLabels * kCondLabels; k += blockDim.x) S[k] = (float)G.S[k];
+    __syncthreads();
+}
+
+// true residual r = b - A x = sum_nb sigma_f (x_nb - x_i) in FP64 on the free
+// voxels (x holds 1 on the electrode and 0 on the ground); partials of r.r
+__global__ void __launch_bounds__(256) k_pot_resid64(PotGrid G, const double *xv, double *r, double *part)
+{
+    __shared__ double S[kCondLabels * kCondLabels];
+    for (int k = threadIdx.x; k < kCondLabels * kCondLabels; k += blockDim.x) S[k] = G.S[k];
+    __syncthreads();
+    double rr = 0.0;
+    POT_ROWS(G)
+    {
+        const size_t i = pot_at(G, x, y, z);
+        if (G.cls[i] != CLS_FREE) continue;
+        const int l = G.label[i];
+        const double xi = xv[i];
+        double v = 0.0;
+        for (int d = 0; d < 6; ++d) {
+            size_t j;
+            if (pot_nb(G, i, x, y, z, d, j)) v += S[l * kCondLabels + G.label[j]] * (xv[j] - xi);
+        }
+        r[i] = v;
+        rr += v * v;
+    }
+    rr = pot_block_sum(rr);
+    if (threadIdx.x == 0) part[blockIdx.x] = rr;
+}
+
+// The FP32 vectors keep an invariant: every entry off the free set (electrode,
+// ground, row padding) is exactly 0.  Then the update and direction steps
+// need no class test, and a non-free neighbour's term in A p is sigma_f * 0,
+// an exact no-op, so the operator is that of the free unknowns.  Each lane
+// takes a quad of 4 x voxels (16-byte vectors; rows are padded to 4).
+#define POT_QUADS(G)                                                                                                \
+    for (int row = blockIdx.x * 8 + (int)(threadIdx.x >> 5); row < (G).ny * (G).nz; row += gridDim.x * 8)         \
+        for (int y = row % (G).ny, z = row / (G).ny, x0 = 4 * (int)(threadIdx.x & 31); x0 < (G).nx; x0 += 128)
+
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ uchar4 ldb4(const uint8_t *p) { return *reinterpret_cast<const uchar4 *>(p); }
+__device__ __forceinline__ float f4at(const float4 &v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
+__device__ __forceinline__ int b4at(const uchar4 &v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
+
+// start of a cycle: r32 = r, e = 0, z = r32 / D, p = z on the free voxels, 0
+// elsewhere; FP32 diagonal from the FP64 one; partials of r32.z and r32.r32
+// (FP32 per thread, FP64 per block)
+__global__ void __launch_bounds__(256) k_pot_init32(PotGrid G, const double *r, const double *Dv, float *r32,
+                                                   float *e32, float *z32, float *p32, float *D32, float *iD32,
+                                                   double *part)
+{
+    float rz = 0.f, rr = 0.f;
+    POT_QUADS(G)
+    {
+        const size_t i = pot_at(G, x0, y, z);
+        const uchar4 c4 = ldb4(G.cls + i);
+        float D[4], iD[4], rv[4], zv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const bool fr = b4at(c4, q) == CLS_FREE;
+            D[q] = fr ? (float)Dv[i + q] : 0.f;
+            iD[q] = D[q] > 0.f ? 1.f / D[q] : 0.f;
+            rv[q] = fr ? (float)r[i + q] : 0.f;
+            zv[q] = rv[q] * iD[q];
+            rz = fmaf(rv[q], zv[q], rz);
+            rr = fmaf(rv[q], rv[q], rr);
+        }
+        st4(D32 + i, make_float4(D[0], D[1], D[2], D[3]));
+        st4(iD32 + i, make_float4(iD[0], iD[1], iD[2], iD[3]));
+        st4(r32 + i, make_float4(rv[0], rv[1], rv[2], rv[3]));
+        st4(e32 + i, make_float4(0.f, 0.f, 0.f, 0.f));
+        st4(z32 + i, make_float4(zv[0], zv[1], zv[2], zv[3]));
+        st4(p32 + i, make_float4(zv[0], zv[1], zv[2], zv[3]));
+    }
+    const double a = pot_block_sum((double)rz), b = pot_block_sum((double)rr);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+// Ap = A p in FP32 (0 off the free set); partials of p.Ap.  Neighbour terms in
+// the order x-, x+, y-, y+, z-, z+; where the quad and all its neighbours
+// share one label, one table entry serves every face.
+__global__ void __launch_bounds__(256) k_pot_spmv32(PotGrid G, const float *D32, const float *p, float *Ap,
+                                                   double *part)
+{
+    __shared__ float S[kCondLabels * kCondLabels];
+    pot_table32(G, S);
+    float acc = 0.f;
+    POT_QUADS(G)
+    {
+        const size_t i = pot_at(G, x0, y, z);
+        const uchar4 c4 = ldb4(G.cls + i), l4 = ldb4(G.label + i);
+        const float4 p4 = ld4(p + i), D4 = ld4(D32 + i);
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        const uchar4 bz = make_uchar4(0, 0, 0, 0);
+        const bool hasL = x0 > 0, hasR = x0 + 4 < G.pitch, hasYm = y > 0, hasYp = y + 1 < G.ny, hasZm = z > 0,
+                   hasZp = z + 1 < G.nz;
+        const float pL = hasL ? p[i - 1] : 0.f, pR = hasR ? p[i + 4] : 0.f;
+        const int lL = hasL ? G.label[i - 1] : 0, lR = hasR ? G.label[i + 4] : 0;
+        const float4 pym = hasYm ? ld4(p + i - G.pitch) : zero, pyp = hasYp ? ld4(p + i + G.pitch) : zero;
+        const float4 pzm = hasZm ? ld4(p + i - G.plane) : zero, pzp = hasZp ? ld4(p + i + G.plane) : zero;
+        const uchar4 lym = hasYm ? ldb4(G.label + i - G.pitch) : bz, lyp = hasYp ? ldb4(G.label + i + G.pitch) : bz;
+        const uchar4 lzm = hasZm ? ldb4(G.label + i - G.plane) : bz, lzp = hasZp ? ldb4(G.label + i + G.plane) : bz;
+        const int l0 = l4.x;
+        const bool uni = l4.y == l0 && l4.z == l0 && l4.w == l0 && lL == l0 && lR == l0 && lym.x == l0 &&
+                         lym.y == l0 && lym.z == l0 && lym.w == l0 && lyp.x == l0 && lyp.y == l0 && lyp.z == l0 &&
+                         lyp.w == l0 && lzm.x == l0 && lzm.y == l0 && lzm.z == l0 && lzm.w == l0 && lzp.x == l0 &&
+                         lzp.y == l0 && lzp.z == l0 && lzp.w == l0;
+        const float su = S[l0 * (kCondLabels + 1)];
+        float out[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float pq = f4at(p4, q);
+            const float nb[6] = {q == 0 ? pL : f4at(p4, q - 1), q == 3 ? pR : f4at(p4, q + 1), f4at(pym, q),
+                                 f4at(pyp, q), f4at(pzm, q), f4at(pzp, q)};
+            float w[6];
+            if (uni) {
+#pragma unroll
+                for (int d = 0; d < 6; ++d) w[d] = su;
+            } else {
+                const int l = b4at(l4, q);
+                const int ln[6] = {q == 0 ? lL : b4at(l4, q - 1), q == 3 ? lR : b4at(l4, q + 1), b4at(lym, q),
+                                   b4at(lyp, q), b4at(lzm, q), b4at(lzp, q)};
+#pragma unroll
+                for (int d = 0; d < 6; ++d) w[d] = S[l * kCondLabels + ln[d]];
+            }
+            float v = f4at(D4, q) * pq;
+#pragma unroll
+            for (int d = 0; d < 6; ++d) v = fmaf(-w[d], nb[d], v);
+            v = b4at(c4, q) == CLS_FREE ? v : 0.f;
+            out[q] = v;
+            acc = fmaf(pq, v, acc);
+        }
+        st4(Ap + i, make_float4(out[0], out[1], out[2], out[3]));
+    }
+    const double a = pot_block_sum((double)acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = a;
+}
+
+// e += alpha p; r32 -= alpha Ap; z = r32 / D; partials of r32.z and r32.r32
+// (off the free set every operand is 0 and stays 0)
+__global__ void __launch_bounds__(256) k_pot_update32(PotGrid G, const double *sc, const float *iD32, float *e32,
+                                                     float *r32, float *z32, const float *p, const float *Ap,
+                                                     double *part)
+{
+    const float alpha = (float)sc[SC_ALPHA];
+    float rz = 0.f, rr = 0.f;
+    POT_QUADS(G)
+    {
+        const size_t i = pot_at(G, x0, y, z);
+        const float4 e = ld4(e32 + i), r0 = ld4(r32 + i), p4 = ld4(p + i), a4 = ld4(Ap + i), iD = ld4(iD32 + i);
+        const float4 e1 = make_float4(fmaf(alpha, p4.x, e.x), fmaf(alpha, p4.y, e.y), fmaf(alpha, p4.z, e.z),
+                                      fmaf(alpha, p4.w, e.w));
+        const float4 r1 = make_float4(fmaf(-alpha, a4.x, r0.x), fmaf(-alpha, a4.y, r0.y), fmaf(-alpha, a4.z, r0.z),
+                                      fmaf(-alpha, a4.w, r0.w));
+        const float4 z1 = make_float4(r1.x * iD.x, r1.y * iD.y, r1.z * iD.z, r1.w * iD.w);
+        st4(e32 + i, e1);
+        st4(r32 + i, r1);
+        st4(z32 + i, z1);
+        rz = fmaf(r1.x, z1.x, fmaf(r1.y, z1.y, fmaf(r1.z, z1.z, fmaf(r1.w, z1.w, rz))));
+        rr = fmaf(r1.x, r1.x, fmaf(r1.y, r1.y, fmaf(r1.z, r1.z, fmaf(r1.w, r1.w, rr))));
+    }
+    const double a = pot_block_sum((double)rz), b = pot_block_sum((double)rr);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+// p = z + beta p
+__global__ void __launch_bounds__(256) k_pot_direction32(PotGrid G, const double *sc, const float *z32, float *p)
+{
+    const float beta = (float)sc[SC_BETA];
+    POT_QUADS(G)
+    {
+        const size_t i = pot_at(G, x0, y, z);
+        const float4 z4 = ld4(z32 + i), p4 = ld4(p + i);
+        st4(p + i, make_float4(fmaf(beta, p4.x, z4.x), fmaf(beta, p4.y, z4.y), fmaf(beta, p4.z, z4.z),
+                               fmaf(beta, p4.w, z4.w)));
+    }
+}
+
+// end of a cycle: x += e (e is 0 off the free set, so x keeps its fixed values)
+__global__ void __launch_bounds__(256) k_pot_correct(PotGrid G, const float *e32, double *xv)
+{
+    POT_QUADS(G)
+    {
+        const size_t i = pot_at(G, x0, y, z);
+        const float4 e = ld4(e32 + i);
+        double2 *xp = reinterpret_cast<double2 *>(xv + i);
+        const double2 a = xp[0], b = xp[1];
+        xp[0] = make_double2(a.x + (double)e.x, a.y + (double)e.y);
+        xp[1] = make_double2(b.x + (double)e.z, b.y + (double)e.w);
+    }
+}
+
+#undef POT_QUADS
+
+// hand-over to FP64 conjugate gradients from the current x: z = r / D, p = z;
+// partials of r.z and r.r
+__global__ void __launch_bounds__(256) k_pot_restart64(PotGrid G, const double *r, const double *iDv, double *zv,
+                                                      double *p, double *part)
+{
+    double rz = 0.0, rr = 0.0;
+    POT_ROWS(G)
+    {
+        const size_t i = pot_at(G, x, y, z);
+        if (G.cls[i] != CLS_FREE) continue;
+        const double ri = r[i], zi = ri * iDv[i];
+        zv[i] = zi;
+        p[i] = zi;
+        rz += ri * zi;
+        rr += ri * ri;
+    }
+    rz = pot_block_sum(rz);
+    rr = pot_block_sum(rr);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = rz;
+        part[2 * blockIdx.x + 1] = rr;
+    }
+}
+
+#undef POT_ROWS
 
 // q = sum_nb sigma_f (V_nb - V_i)^2 / (2 h^2) into wbuf on the thermally free
 // voxels (the 1/r^4 source's rule), per-block partial sums of q over them
@@ -275,7 +532,7 @@ rfa_status potential_place(rfa_grid *g)
         }
     const size_t nvp = g->nvp;
     struct Bufs {
-        void *p[9] = {};
+        void *p[10] = {};
         ~Bufs()
         {
             for (void *q : p)
@@ -288,7 +545,9 @@ rfa_status potential_place(rfa_grid *g)
             set_error("potential solve workspace allocation failed");
             return RFA_E_OOM;
         }
-    if (cudaMalloc(&B.p[7], nvp) != cudaSuccess || cudaMalloc(&B.p[8], kCondLabels * kCondLabels * 8 + SC_N * 8) != cudaSuccess) {
+    if (cudaMalloc(&B.p[7], nvp) != cudaSuccess ||
+        cudaMalloc(&B.p[8], kCondLabels * kCondLabels * 8 + SC_N * 8) != cudaSuccess ||
+        cudaMalloc(&B.p[9], 7 * nvp * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         set_error("potential solve workspace allocation failed");
         return RFA_E_OOM;
@@ -311,6 +570,57 @@ rfa_status potential_place(rfa_grid *g)
     const double bnorm = std::sqrt(host_sc[SC_BB]);
     double rel = bnorm > 0.0 ? 1.0 : 0.0;
     int it = 0;
+    auto read_scalars = [&]() -> rfa_status {
+        RFA_CUDA(cudaGetLastError());
+        RFA_CUDA(cudaMemcpyAsync(host_sc, sc, sizeof host_sc, cudaMemcpyDeviceToHost, g->stream));
+        RFA_CUDA(cudaStreamSynchronize(g->stream));
+        return RFA_OK;
+    };
+    // FP32 cycles inside the FP64 defect correction (r = b at the start, x = the fixed values)
+    float *r32 = (float *)B.p[9], *e32 = r32 + nvp, *z32 = e32 + nvp, *p32 = z32 + nvp, *Ap32 = p32 + nvp;
+    float *D32 = Ap32 + nvp, *iD32 = D32 + nvp;
+    bool fp64_cg = false;
+    while (rel > g->pot_tol && it < g->pot_max_iters && !fp64_cg) {
+        const double eta = std::max(kInnerEta, 0.25 * g->pot_tol / rel);
+        k_pot_init32<<<nb, 256, 0, g->stream>>>(G, r, Dv, r32, e32, z32, p32, D32, iD32, part);
+        k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, 2, sc);
+        if (rfa_status st = read_scalars()) return st;
+        const double r0 = std::sqrt(std::fmax(host_sc[SC_RR], 0.0));
+        double rin = r0;
+        while (rin > eta * r0 && it < g->pot_max_iters) {
+            const int n = std::min(kCheck, g->pot_max_iters - it);
+            for (int k = 0; k < n; ++k) {
+                k_pot_spmv32<<<nb, 256, 0, g->stream>>>(G, D32, p32, Ap32, part);
+                k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, 0, sc);
+                k_pot_update32<<<nb, 256, 0, g->stream>>>(G, sc, iD32, e32, r32, z32, p32, Ap32, part);
+                k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, 1, sc);
+                k_pot_direction32<<<nb, 256, 0, g->stream>>>(G, sc, z32, p32);
+            }
+            it += n;
+            if (rfa_status st = read_scalars()) return st;
+            rin = std::sqrt(std::fmax(host_sc[SC_RR], 0.0));
+            if (!std::isfinite(rin)) {
+                set_error("potential solve diverged");
+                return RFA_E_NONFINITE;
+            }
+        }
+        k_pot_correct<<<nb, 256, 0, g->stream>>>(G, e32, xv);
+        k_pot_resid64<<<nb, 256, 0, g->stream>>>(G, xv, r, part);
+        k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, 3, sc);
+        if (rfa_status st = read_scalars()) return st;
+        const double rel_new = std::sqrt(std::fmax(host_sc[SC_RR], 0.0)) / bnorm;
+        if (!std::isfinite(rel_new)) {
+            set_error("potential solve diverged");
+            return RFA_E_NONFINITE;
+        }
+        fp64_cg = !(rel_new <= 0.5 * rel);  // FP32 stagnated: FP64 from here
+        rel = rel_new;
+    }
+    // FP64 conjugate gradients from the current x (r already holds b - A x)
+    if (rel > g->pot_tol && it < g->pot_max_iters) {
+        k_pot_restart64<<<nb, 256, 0, g->stream>>>(G, r, iDv, zv, p, part);
+        k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, 2, sc);
+    }
     while (rel > g->pot_tol && it < g->pot_max_iters) {
         const int n = std::min(kCheck, g->pot_max_iters - it);
         for (int k = 0; k < n; ++k) {
@@ -321,9 +631,7 @@ rfa_status potential_place(rfa_grid *g)
             k_pot_direction<<<nb, 256, 0, g->stream>>>(G, sc, zv, p);
         }
         it += n;
-        RFA_CUDA(cudaGetLastError());
-        RFA_CUDA(cudaMemcpyAsync(host_sc, sc, sizeof host_sc, cudaMemcpyDeviceToHost, g->stream));
-        RFA_CUDA(cudaStreamSynchronize(g->stream));
+        if (rfa_status st = read_scalars()) return st;
         rel = std::sqrt(std::fmax(host_sc[SC_RR], 0.0)) / bnorm;
         if (!std::isfinite(rel)) {
             set_error("potential solve diverged");
