@@ -37,6 +37,7 @@ sys.path.insert(0, ROOT)
 import phantoms as ph  # noqa: E402
 
 METRIC = "bioheat GVox-steps/s and % HBM roofline; batched+adjoint vs plain @1e-3 K"
+NOMINAL_HBM_GBS = 7700.0
 UNIT = "GVox-steps/s"
 
 
@@ -173,31 +174,37 @@ def measured_peak_hbm():
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample(case, target_s=15.0, min_steps=2, max_steps=2000):
-    """Time the FP64 oracle on the full grid for a bounded number of steps."""
+def oracle_sample(case, target_s=15.0, min_steps=2, max_steps=2000, nthreads=0, model=None):
+    """Time the FP64 oracle on the full grid for a bounded number of steps
+    (nthreads 0: all cores)."""
     import oracle
     t0 = time.perf_counter()
-    m = oracle.setup(case, "bf16")
+    m = model if model is not None else oracle.setup(case, "bf16")
     t_setup = time.perf_counter() - t0
     st = oracle.initial_state(m)
     dmg = case.damage if case.damage.enable else None
     t0 = time.perf_counter()
-    oracle.run(m, st, min_steps, damage=dmg)
+    oracle.run(m, st, min_steps, damage=dmg, nthreads=nthreads)
     t_cal = (time.perf_counter() - t0) / min_steps
     n = int(max(min_steps, min(max_steps, target_s / max(t_cal, 1e-9))))
     t0 = time.perf_counter()
-    oracle.run(m, st, n, damage=dmg)
+    oracle.run(m, st, n, damage=dmg, nthreads=nthreads)
     t = time.perf_counter() - t0
-    return n, t, t_setup
+    return n, t, t_setup, m
 
 
 def cpu_baseline(case, target_s=15.0):
-    n, t, _ = oracle_sample(case, target_s)
+    """The oracle on all host cores, and on one thread beside it (a shorter
+    sample): the per-step cost is fixed, so a few steps give the rate."""
+    n, t, _, m = oracle_sample(case, target_s)
+    n1, t1, _, _ = oracle_sample(case, max(2.0, target_s / 5), min_steps=1, nthreads=1, model=m)
     return {"value": case.nvox * n / t / 1e9, "unit": UNIT, "cores": os.cpu_count(),
             "kind": "oracle",
             "sample": f"FP64 oracle (C, OpenMP over z, {os.cpu_count()} threads), full "
                       f"{case.nx}x{case.ny}x{case.nz} phantom, {n} of {case.nsteps} time steps"
-                      f"{' with Arrhenius' if case.damage.enable else ''}, set-up excluded"}
+                      f"{' with Arrhenius' if case.damage.enable else ''}, set-up excluded",
+            "single_thread": {"value": case.nvox * n1 / t1 / 1e9, "unit": UNIT, "cores": 1,
+                              "sample": f"the same, 1 thread, {n1} time steps"}}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -208,7 +215,7 @@ def run_reference(args):
     case = workload(args.workload, 0, args.sim_steps)
     import oracle
     # one step = oracle set-up + a bounded sample of time steps on the full grid
-    n, t_cal, t_setup = oracle_sample(case, target_s=4.0, min_steps=2)
+    n, t_cal, t_setup, _ = oracle_sample(case, target_s=4.0, min_steps=2)
     per_step_target = 12.0
     n = max(2, int(n * per_step_target / max(4.0, 1e-9)))
     dmg = case.damage if case.damage.enable else None
@@ -462,9 +469,13 @@ def run_ours(args):
     depth, variant = rfa.rfa_get_schedule(g.handle)
 
     step_ms = []
+    whole_ms = []
 
     def one_step(host: bool):
         lab = labels_pin if host else labels_dev
+        w0 = torch.cuda.Event(enable_timing=True)
+        w1 = torch.cuda.Event(enable_timing=True)
+        w0.record(stream)
         g.set_tissue(lab, case.table)       # S1, and S2 (the placed needle is placed again)
         g.set_damage(int(d.enable), d.A, d.Ea, d.R, d.T_thr_C)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -475,7 +486,9 @@ def run_ours(args):
         _, counts, vols, sv = g.necrosis(want_mask=False)
         if host:
             rfa.rfa_get_temperature(g.handle, T_host, False, False)
+        w1.record(stream)
         step_ms.append((e0, e1))
+        whole_ms.append((w0, w1))
         return counts
 
     def barrier():
@@ -487,6 +500,7 @@ def run_ours(args):
         one_step(False)
     barrier()
     step_ms.clear()
+    whole_ms.clear()
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
@@ -504,6 +518,9 @@ def run_ours(args):
     clocks = clk.stop()
     ms = t_start.elapsed_time(t_end)
     kern_ms = sum(a.elapsed_time(b) for a, b in step_ms)
+    per_step = sorted(case.nvox * case.nsteps / (a.elapsed_time(b) * 1e-3) / 1e9 for a, b in whole_ms)
+    step_stats = {"best": per_step[-1], "median": statistics.median(per_step), "worst": per_step[0],
+                  "n": len(per_step), "unit": UNIT}
     ms_max = reduce_max(ms, dist, dev)
     vox_steps = case.nvox * case.nsteps * args.steps * world
     value = job_throughput(case.nvox, case.nsteps, args.steps, world, ms_max)
@@ -533,7 +550,9 @@ def run_ours(args):
             "frac": achieved / peak, "traffic": load_traffic(kname, case.nvox),
             "kernel": kname, "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
             "algorithmic_bytes_per_launch": nbytes, "avg_launch_us": avg_launch_ms * 1e3,
-            "steps_per_launch": depth}
+            "steps_per_launch": depth,
+            "nominal": {"peak": NOMINAL_HBM_GBS, "frac": achieved / NOMINAL_HBM_GBS,
+                        "note": "B300 HBM3e nominal 7.7 TB/s; the frac above is of measured"}}
     kernels_per_step = 2 + 3 + launches_per_step + 2   # setup (2), source (3), steps, necrosis (2)
     secondary = None
     if rank == 0 and not args.no_secondary:
@@ -551,6 +570,7 @@ def run_ours(args):
                                parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                                schedule={"tb_depth": depth, "tile_variant": variant}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "per_step": step_stats,
                 "gpu_launches": kernels_per_step * args.steps,
                 "necrosis_voxels": [int(counts[0]), int(counts[1])],
                 "secondary": secondary}
