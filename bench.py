@@ -308,13 +308,14 @@ def measure_next_rows(rfa, stream, case, g, cpu_baseline_on: bool):
     def cpu(value, unit, sample):
         return {"value": value, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample}
 
-    # breathing resample of the bench grid's current state: u 12 B, theta hi+lo 8 B, T 4 B
+    # breathing resample of the bench grid's current state to an FP32 field: u 12 B,
+    # theta hi 4 B (a float output reads hi alone), T 4 B
     u = torch.from_numpy(ph.breathing_field(case, 1.0)).cuda()
     dst = torch.empty((case.nz, case.ny, case.nx), dtype=torch.float32, device="cuda")
     rfa.rfa_warp_temperature(g.handle, u, dst, False)
     ms = _ms_between(torch, stream, lambda: [rfa.rfa_warp_temperature(g.handle, u, dst, False)
                                              for _ in range(5)]) / 5
-    out["breathing_warp"] = dict(roof(24.0 * n, ms), ms=ms, gvox_s=n / (ms * 1e-3) / 1e9)
+    out["breathing_warp"] = dict(roof(20.0 * n, ms), ms=ms, gvox_s=n / (ms * 1e-3) / 1e9)
     del u, dst
     if cpu_baseline_on:
         import oracle
@@ -347,8 +348,8 @@ def measure_next_rows(rfa, stream, case, g, cpu_baseline_on: bool):
             out[name]["cpu_baseline"] = cpu(sm.nvox * 4 / (time.perf_counter() - t0) / 1e9, "GVox-steps/s",
                                             "96^3, 4 steps, FP64 oracle (C, OpenMP)")
     # potential-solve source: FP32 CG iterations inside an FP64 defect correction; per FP32
-    # iteration 60 B/voxel: spmv (cls, label, D, p read, Ap written: 14), update (cls, 1/D, e, r,
-    # p, Ap read, e, r, z written: 33), direction (cls, z, p read, p written: 13).  The few FP64
+    # iteration 54 B/voxel: direction + spmv (cls, label, D, z, previous p read, p and Ap
+    # written: 22), update (1/D, e, r, p, Ap read, e, r, z written: 32).  The few FP64
     # correction passes per solve (x += e, r = b - A x) are not counted: the figure is a floor.
     c3 = ph.umbrella_case_256(seed=0, nsteps=1)
     g3 = rfa.Grid(c3.nx, c3.ny, c3.nz, c3.h, c3.dt, rfa.STATE_F32C, rfa.PARAM_BF16, c3.face_bc, c3.T_a_C,
@@ -361,7 +362,7 @@ def measure_next_rows(rfa, stream, case, g, cpu_baseline_on: bool):
         "r", rfa.rfa_place_needle_potential(g3.handle, c3.needle, sig, 20000, 1e-10)))
     g3.close()
     it, rel = res["r"]
-    out["potential_source"] = dict(roof(60.0 * n * it, ms), ms=ms, cg_iterations=it, rel_residual=rel,
+    out["potential_source"] = dict(roof(54.0 * n * it, ms), ms=ms, cg_iterations=it, rel_residual=rel,
                                    ms_per_iteration=ms / max(it, 1))
     if cpu_baseline_on:
         import oracle

@@ -330,10 +330,11 @@ rfa_status rfa_set_conduction(rfa_grid *g, int mode);
  *               components, metres), caller-owned, read only.
  *   dst_dev   : device, nx*ny*nz values in degrees C, x fastest; float, or
  *               double when as_f64 != 0.  Caller-owned.
- * FP64 states interpolate in FP64; FP32 states in FP32 (hi and lo parts
- * separately, then summed with the ambient temperature in FP64 for a double
- * output, in FP32 for a float one).  Asynchronous on the grid's stream; the
- * state is not changed.
+ * FP64 states interpolate in FP64; FP32 states in FP32.  A compensated state
+ * interpolates hi and lo separately and sums them with the ambient
+ * temperature in FP64 for a double output; a float output interpolates hi
+ * alone (|lo| <= ulp(hi)/2, below its resolution) and sums in FP32.
+ * Asynchronous on the grid's stream; the state is not changed.
  * Errors: RFA_E_INVALID (null pointer), RFA_E_STATE (no tissue yet).
  */
 rfa_status rfa_warp_temperature(rfa_grid *g, const float *u_inv_dev, void *dst_dev, int as_f64);

@@ -178,36 +178,63 @@ __global__ void __launch_bounds__(256) k_pot_spmv(PotGrid G, const double *Dv, c
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
-// scalar steps on one block: which = 0 -> alpha = rz / sum(part); 1 -> rz_new,
-// beta, rr; 2 -> rz, rr (and b.b) at a start; 3 -> rr = sum(part)
-__global__ void k_pot_scalars(const double *part, int nblk, int which, double *sc)
+// the scalar steps from the summed partials a (and b): which = 0 -> alpha =
+// rz / a; 1 -> beta = a / rz, rz = a, rr = b; 2 -> a start: rz = a, rr = b
+// (and b.b), beta = 0; 3 -> rr = a
+__device__ void pot_scalars_apply(int which, double a, double b, double *sc)
 {
-    double a = 0.0, b = 0.0;
+    if (which == 0) {
+        sc[SC_ALPHA] = a != 0.0 ? sc[SC_RZ] / a : 0.0;
+    } else if (which == 1) {
+        sc[SC_BETA] = sc[SC_RZ] != 0.0 ? a / sc[SC_RZ] : 0.0;
+        sc[SC_RZ] = a;
+        sc[SC_RR] = b;
+    } else if (which == 2) {
+        sc[SC_RZ] = a;
+        sc[SC_BB] = b;
+        sc[SC_RR] = b;
+        sc[SC_BETA] = 0.0;
+    } else {
+        sc[SC_RR] = a;
+    }
+}
+
+// sum of the per-block partials (one or two per block) in a fixed order, on one block
+__device__ void pot_sum_partials(const double *part, int nblk, bool pairs, double &a, double &b)
+{
+    a = 0.0;
+    b = 0.0;
     for (int k = threadIdx.x; k < nblk; k += blockDim.x) {
-        if (which == 0 || which == 3) {
-            a += part[k];
+        if (!pairs) {
+            a += __ldcg(part + k);
         } else {
-            a += part[2 * k];
-            b += part[2 * k + 1];
+            a += __ldcg(part + 2 * k);
+            b += __ldcg(part + 2 * k + 1);
         }
     }
     a = pot_block_sum(a);
     b = pot_block_sum(b);
-    if (threadIdx.x == 0) {
-        if (which == 0) {
-            sc[SC_ALPHA] = a != 0.0 ? sc[SC_RZ] / a : 0.0;
-        } else if (which == 1) {
-            sc[SC_BETA] = sc[SC_RZ] != 0.0 ? a / sc[SC_RZ] : 0.0;
-            sc[SC_RZ] = a;
-            sc[SC_RR] = b;
-        } else if (which == 2) {  // a start: rz and r.r (b.b at the first)
-            sc[SC_RZ] = a;
-            sc[SC_BB] = b;
-            sc[SC_RR] = b;
-        } else {
-            sc[SC_RR] = a;
-        }
-    }
+}
+
+// scalar steps on one block (which as in pot_scalars_apply)
+__global__ void k_pot_scalars(const double *part, int nblk, int which, double *sc)
+{
+    double a, b;
+    pot_sum_partials(part, nblk, which == 1 || which == 2, a, b);
+    if (threadIdx.x == 0) pot_scalars_apply(which, a, b, sc);
+}
+
+// after every block has written its partials: true in the last block to finish
+// (the classic fence-and-count hand-over); that block then applies the scalar
+// step itself and re-arms the counter, which saves a launch per reduction
+__device__ bool pot_last_block(unsigned *ctr)
+{
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ctr, 1u) == gridDim.x - 1;
+    __syncthreads();
+    return last;
 }
 
 // x += alpha p; r -= alpha Ap; z = r / D; partial sums of r.z and r.r
@@ -297,9 +324,10 @@ __device__ __forceinline__ uchar4 ldb4(const uint8_t *p) { return *reinterpret_c
 __device__ __forceinline__ float f4at(const float4 &v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
 __device__ __forceinline__ int b4at(const uchar4 &v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
 
-// start of a cycle: r32 = r, e = 0, z = r32 / D, p = z on the free voxels, 0
-// elsewhere; FP32 diagonal from the FP64 one; partials of r32.z and r32.r32
-// (FP32 per thread, FP64 per block)
+// start of a cycle: r32 = r, e = 0, z = r32 / D on the free voxels, 0
+// elsewhere, and the previous direction 0 (with beta = 0 the first direction
+// is z); FP32 diagonal from the FP64 one; partials of r32.z and r32.r32 (FP32
+// per thread, FP64 per block)
 __global__ void __launch_bounds__(256) k_pot_init32(PotGrid G, const double *r, const double *Dv, float *r32,
                                                    float *e32, float *z32, float *p32, float *D32, float *iD32,
                                                    double *part)
@@ -325,7 +353,7 @@ __global__ void __launch_bounds__(256) k_pot_init32(PotGrid G, const double *r, 
         st4(r32 + i, make_float4(rv[0], rv[1], rv[2], rv[3]));
         st4(e32 + i, make_float4(0.f, 0.f, 0.f, 0.f));
         st4(z32 + i, make_float4(zv[0], zv[1], zv[2], zv[3]));
-        st4(p32 + i, make_float4(zv[0], zv[1], zv[2], zv[3]));
+        st4(p32 + i, make_float4(0.f, 0.f, 0.f, 0.f));
     }
     const double a = pot_block_sum((double)rz), b = pot_block_sum((double)rr);
     if (threadIdx.x == 0) {
@@ -334,35 +362,47 @@ __global__ void __launch_bounds__(256) k_pot_init32(PotGrid G, const double *r, 
     }
 }
 
-// Ap = A p in FP32 (0 off the free set); partials of p.Ap.  Neighbour terms in
-// the order x-, x+, y-, y+, z-, z+; where the quad and all its neighbours
-// share one label, one table entry serves every face.
-__global__ void __launch_bounds__(256) k_pot_spmv32(PotGrid G, const float *D32, const float *p, float *Ap,
-                                                   double *part)
+// The search direction and the operator in one pass: p = z + beta p_prev on
+// the quad and its six neighbour points (p_prev and p are separate buffers,
+// swapped every iteration), p written for the quad, Ap = A p in FP32 (0 off
+// the free set); partials of p.Ap, and alpha = rz / (p.Ap) by the last block.
+// Neighbour terms in the order x-, x+, y-, y+, z-, z+; where the quad and all
+// its neighbours share one label, one table entry serves every face.
+__global__ void __launch_bounds__(256) k_pot_spmv32(PotGrid G, double *sc, const float *D32, const float *z32,
+                                                   const float *pprev, float *p, float *Ap, double *part,
+                                                   unsigned *ctr)
 {
     __shared__ float S[kCondLabels * kCondLabels];
     pot_table32(G, S);
+    const float beta = (float)sc[SC_BETA];
+    auto dir = [&](float zv, float pv) { return fmaf(beta, pv, zv); };
+    auto dir4 = [&](const float4 &zv, const float4 &pv) {
+        return make_float4(dir(zv.x, pv.x), dir(zv.y, pv.y), dir(zv.z, pv.z), dir(zv.w, pv.w));
+    };
     float acc = 0.f;
     POT_QUADS(G)
     {
         const size_t i = pot_at(G, x0, y, z);
         const uchar4 c4 = ldb4(G.cls + i), l4 = ldb4(G.label + i);
-        const float4 p4 = ld4(p + i), D4 = ld4(D32 + i);
+        const float4 p4 = dir4(ld4(z32 + i), ld4(pprev + i)), D4 = ld4(D32 + i);
         const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
         const uchar4 bz = make_uchar4(0, 0, 0, 0);
         const bool hasL = x0 > 0, hasR = x0 + 4 < G.pitch, hasYm = y > 0, hasYp = y + 1 < G.ny, hasZm = z > 0,
                    hasZp = z + 1 < G.nz;
-        const float pL = hasL ? p[i - 1] : 0.f, pR = hasR ? p[i + 4] : 0.f;
+        const float pL = hasL ? dir(z32[i - 1], pprev[i - 1]) : 0.f;
+        const float pR = hasR ? dir(z32[i + 4], pprev[i + 4]) : 0.f;
         const int lL = hasL ? G.label[i - 1] : 0, lR = hasR ? G.label[i + 4] : 0;
-        const float4 pym = hasYm ? ld4(p + i - G.pitch) : zero, pyp = hasYp ? ld4(p + i + G.pitch) : zero;
-        const float4 pzm = hasZm ? ld4(p + i - G.plane) : zero, pzp = hasZp ? ld4(p + i + G.plane) : zero;
-        const uchar4 lym = hasYm ? ldb4(G.label + i - G.pitch) : bz, lyp = hasYp ? ldb4(G.label + i + G.pitch) : bz;
-        const uchar4 lzm = hasZm ? ldb4(G.label + i - G.plane) : bz, lzp = hasZp ? ldb4(G.label + i + G.plane) : bz;
-        const int l0 = l4.x;
-        const bool uni = l4.y == l0 && l4.z == l0 && l4.w == l0 && lL == l0 && lR == l0 && lym.x == l0 &&
-                         lym.y == l0 && lym.z == l0 && lym.w == l0 && lyp.x == l0 && lyp.y == l0 && lyp.z == l0 &&
-                         lyp.w == l0 && lzm.x == l0 && lzm.y == l0 && lzm.z == l0 && lzm.w == l0 && lzp.x == l0 &&
-                         lzp.y == l0 && lzp.z == l0 && lzp.w == l0;
+        const size_t oy = G.pitch, oz = G.plane;
+        const float4 pym = hasYm ? dir4(ld4(z32 + i - oy), ld4(pprev + i - oy)) : zero;
+        const float4 pyp = hasYp ? dir4(ld4(z32 + i + oy), ld4(pprev + i + oy)) : zero;
+        const float4 pzm = hasZm ? dir4(ld4(z32 + i - oz), ld4(pprev + i - oz)) : zero;
+        const float4 pzp = hasZp ? dir4(ld4(z32 + i + oz), ld4(pprev + i + oz)) : zero;
+        const uchar4 lym = hasYm ? ldb4(G.label + i - oy) : bz, lyp = hasYp ? ldb4(G.label + i + oy) : bz;
+        const uchar4 lzm = hasZm ? ldb4(G.label + i - oz) : bz, lzp = hasZp ? ldb4(G.label + i + oz) : bz;
+        const uint32_t l0 = l4.x, rep4 = l0 * 0x01010101u;
+        auto w32 = [](const uchar4 &v) { return (uint32_t)v.x | (uint32_t)v.y << 8 | (uint32_t)v.z << 16 | (uint32_t)v.w << 24; };
+        const bool uni = w32(l4) == rep4 && (uint32_t)lL == l0 && (uint32_t)lR == l0 && w32(lym) == rep4 &&
+                         w32(lyp) == rep4 && w32(lzm) == rep4 && w32(lzp) == rep4;
         const float su = S[l0 * (kCondLabels + 1)];
         float out[4];
 #pragma unroll
@@ -388,17 +428,26 @@ __global__ void __launch_bounds__(256) k_pot_spmv32(PotGrid G, const float *D32,
             out[q] = v;
             acc = fmaf(pq, v, acc);
         }
+        st4(p + i, p4);
         st4(Ap + i, make_float4(out[0], out[1], out[2], out[3]));
     }
     const double a = pot_block_sum((double)acc);
     if (threadIdx.x == 0) part[blockIdx.x] = a;
+    if (pot_last_block(ctr)) {
+        double s0, s1;
+        pot_sum_partials(part, gridDim.x, false, s0, s1);
+        if (threadIdx.x == 0) {
+            pot_scalars_apply(0, s0, s1, sc);
+            *ctr = 0u;
+        }
+    }
 }
 
 // e += alpha p; r32 -= alpha Ap; z = r32 / D; partials of r32.z and r32.r32
 // (off the free set every operand is 0 and stays 0)
-__global__ void __launch_bounds__(256) k_pot_update32(PotGrid G, const double *sc, const float *iD32, float *e32,
+__global__ void __launch_bounds__(256) k_pot_update32(PotGrid G, double *sc, const float *iD32, float *e32,
                                                      float *r32, float *z32, const float *p, const float *Ap,
-                                                     double *part)
+                                                     double *part, unsigned *ctr)
 {
     const float alpha = (float)sc[SC_ALPHA];
     float rz = 0.f, rr = 0.f;
@@ -422,18 +471,13 @@ __global__ void __launch_bounds__(256) k_pot_update32(PotGrid G, const double *s
         part[2 * blockIdx.x] = a;
         part[2 * blockIdx.x + 1] = b;
     }
-}
-
-// p = z + beta p
-__global__ void __launch_bounds__(256) k_pot_direction32(PotGrid G, const double *sc, const float *z32, float *p)
-{
-    const float beta = (float)sc[SC_BETA];
-    POT_QUADS(G)
-    {
-        const size_t i = pot_at(G, x0, y, z);
-        const float4 z4 = ld4(z32 + i), p4 = ld4(p + i);
-        st4(p + i, make_float4(fmaf(beta, p4.x, z4.x), fmaf(beta, p4.y, z4.y), fmaf(beta, p4.z, z4.z),
-                               fmaf(beta, p4.w, z4.w)));
+    if (pot_last_block(ctr)) {
+        double s0, s1;
+        pot_sum_partials(part, gridDim.x, true, s0, s1);
+        if (threadIdx.x == 0) {
+            pot_scalars_apply(1, s0, s1, sc);
+            *ctr = 0u;
+        }
     }
 }
 
@@ -546,8 +590,8 @@ rfa_status potential_place(rfa_grid *g)
             return RFA_E_OOM;
         }
     if (cudaMalloc(&B.p[7], nvp) != cudaSuccess ||
-        cudaMalloc(&B.p[8], kCondLabels * kCondLabels * 8 + SC_N * 8) != cudaSuccess ||
-        cudaMalloc(&B.p[9], 7 * nvp * sizeof(float)) != cudaSuccess) {
+        cudaMalloc(&B.p[8], kCondLabels * kCondLabels * 8 + SC_N * 8 + 8) != cudaSuccess ||
+        cudaMalloc(&B.p[9], 8 * nvp * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         set_error("potential solve workspace allocation failed");
         return RFA_E_OOM;
@@ -556,8 +600,10 @@ rfa_status potential_place(rfa_grid *g)
     double *Ap = (double *)B.p[4], *Dv = (double *)B.p[5], *iDv = (double *)B.p[6];
     uint8_t *cls = (uint8_t *)B.p[7];
     double *dS = (double *)B.p[8], *sc = dS + kCondLabels * kCondLabels;
+    unsigned *ctr = (unsigned *)(sc + SC_N);  // last-block counter of the fused reductions
     double *part = (double *)g->red;  // 2 * kReduceBlocks doubles
     RFA_CUDA(cudaMemcpyAsync(dS, S.data(), S.size() * 8, cudaMemcpyHostToDevice, g->stream));
+    RFA_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned), g->stream));
     PotGrid G{cls, g->label, dS, g->nx, g->ny, g->nz, g->pitch, g->plane, nvp};
     const unsigned nb = kReduceBlocks;
     k_pot_class<<<nb, 256, 0, g->stream>>>(g->geom, G, g->h, cls);
@@ -577,12 +623,13 @@ rfa_status potential_place(rfa_grid *g)
         return RFA_OK;
     };
     // FP32 cycles inside the FP64 defect correction (r = b at the start, x = the fixed values)
-    float *r32 = (float *)B.p[9], *e32 = r32 + nvp, *z32 = e32 + nvp, *p32 = z32 + nvp, *Ap32 = p32 + nvp;
-    float *D32 = Ap32 + nvp, *iD32 = D32 + nvp;
+    float *r32 = (float *)B.p[9], *e32 = r32 + nvp, *z32 = e32 + nvp, *Ap32 = z32 + nvp;
+    float *D32 = Ap32 + nvp, *iD32 = D32 + nvp, *pbuf[2] = {iD32 + nvp, iD32 + 2 * nvp};
     bool fp64_cg = false;
     while (rel > g->pot_tol && it < g->pot_max_iters && !fp64_cg) {
         const double eta = std::max(kInnerEta, 0.25 * g->pot_tol / rel);
-        k_pot_init32<<<nb, 256, 0, g->stream>>>(G, r, Dv, r32, e32, z32, p32, D32, iD32, part);
+        int pk = 0;  // pbuf[pk]: the previous direction
+        k_pot_init32<<<nb, 256, 0, g->stream>>>(G, r, Dv, r32, e32, z32, pbuf[pk], D32, iD32, part);
         k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, 2, sc);
         if (rfa_status st = read_scalars()) return st;
         const double r0 = std::sqrt(std::fmax(host_sc[SC_RR], 0.0));
@@ -590,11 +637,10 @@ rfa_status potential_place(rfa_grid *g)
         while (rin > eta * r0 && it < g->pot_max_iters) {
             const int n = std::min(kCheck, g->pot_max_iters - it);
             for (int k = 0; k < n; ++k) {
-                k_pot_spmv32<<<nb, 256, 0, g->stream>>>(G, D32, p32, Ap32, part);
-                k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, 0, sc);
-                k_pot_update32<<<nb, 256, 0, g->stream>>>(G, sc, iD32, e32, r32, z32, p32, Ap32, part);
-                k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, 1, sc);
-                k_pot_direction32<<<nb, 256, 0, g->stream>>>(G, sc, z32, p32);
+                k_pot_spmv32<<<nb, 256, 0, g->stream>>>(G, sc, D32, z32, pbuf[pk], pbuf[pk ^ 1], Ap32, part, ctr);
+                k_pot_update32<<<nb, 256, 0, g->stream>>>(G, sc, iD32, e32, r32, z32, pbuf[pk ^ 1], Ap32, part,
+                                                          ctr);
+                pk ^= 1;
             }
             it += n;
             if (rfa_status st = read_scalars()) return st;

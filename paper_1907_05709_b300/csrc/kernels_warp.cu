@@ -9,8 +9,9 @@
 // Precision: the fractional sample offset is formed from the displacement in
 // voxels alone (x + d with x integer: floor(x + d) = x + floor(d)), so FP32
 // keeps it to a few 1e-7 of the displacement.  Compensated states interpolate hi and lo
-// separately in FP32 and add them at the end (in FP64 for an FP64 output, in
-// FP32 for an FP32 one); FP64 states interpolate in FP64.
+// separately in FP32 and add them in FP64 for an FP64 output; an FP32 output
+// interpolates hi alone (|lo| <= ulp(hi)/2 is below its resolution).  FP64
+// states interpolate in FP64.
 #include "rfa_internal.cuh"
 
 namespace rfa {
@@ -106,8 +107,11 @@ __global__ void __launch_bounds__(256) k_warp(const void *th, const float *lo, c
             const int dx = ax.i1 - ax.i0;
             const size_t dy = (size_t)(ay.i1 - ay.i0) * pitch, dz = (size_t)(az.i1 - az.i0) * plane;
             const float vh = trilinear_at<float>((const float *)th + o, dx, dy, dz, ax.f, ay.f, az.f);
+            // the lo part of a compensated state is at most half an ulp of hi, below
+            // the resolution of an FP32 temperature (theta >= 0 near the needle, so
+            // ulp(hi) <= ulp(T)): only a double output interpolates it
             float vl = 0.f;
-            if (SP == RFA_STATE_F32C) vl = trilinear_at<float>(lo + o, dx, dy, dz, ax.f, ay.f, az.f);
+            if (SP == RFA_STATE_F32C && as_f64) vl = trilinear_at<float>(lo + o, dx, dy, dz, ax.f, ay.f, az.f);
             if (as_f64) ((double *)dst)[j] = ((double)vh + (double)vl) + T_a;
             else ((float *)dst)[j] = __fadd_rn(__fadd_rn(vh, vl), T_af);
         }
