@@ -14,6 +14,8 @@
 // states interpolate in FP64.
 #include "rfa_internal.cuh"
 
+#include <climits>
+
 namespace rfa {
 namespace {
 
@@ -47,21 +49,36 @@ __device__ __forceinline__ Axis<R> axis_sample(int c, R d, int n)
     return a;
 }
 
+// the same sample for FP32, without branches: a clamped axis samples one voxel
+// (step 0) with weight 0, exactly as above (i1 = i0, f = 0)
+struct AxisF {
+    int i0, step;
+    float f;
+};
+__device__ __forceinline__ AxisF axis_sample_f(int c, float d, int n, float lo, float hi)
+{
+    d = fminf(fmaxf(d, lo), hi);  // lo = -(n+1), hi = n+1; also maps NaN to the low face
+    const float fl = floorf(d);
+    const int i = c + (int)fl;
+    const bool in = i >= 0 && i < n - 1;
+    return {min(max(i, 0), n - 1), in ? 1 : 0, in ? d - fl : 0.f};
+}
+
 template <class R>
 __device__ __forceinline__ R lerp_(R a, R b, R f)
 {
     return a + f * (b - a);
 }
 
-// the 8 corners from one base pointer and the three axis steps (0 where an
-// axis is clamped)
-template <class R>
-__device__ __forceinline__ R trilinear_at(const R *p, int dx, size_t dy, size_t dz, R fx, R fy, R fz)
+// the 8 corners at offsets o (+ dx, dy, dz: the axis steps, 0 where an axis is
+// clamped) from a base pointer, in the index type I
+template <class R, class I>
+__device__ __forceinline__ R trilinear_at(const R *p, I o, I dx, I dy, I dz, R fx, R fy, R fz)
 {
-    const R c00 = lerp_(__ldg(p), __ldg(p + dx), fx);
-    const R c10 = lerp_(__ldg(p + dy), __ldg(p + dy + dx), fx);
-    const R c01 = lerp_(__ldg(p + dz), __ldg(p + dz + dx), fx);
-    const R c11 = lerp_(__ldg(p + dz + dy), __ldg(p + dz + dy + dx), fx);
+    const R c00 = lerp_(__ldg(p + o), __ldg(p + o + dx), fx);
+    const R c10 = lerp_(__ldg(p + o + dy), __ldg(p + o + dy + dx), fx);
+    const R c01 = lerp_(__ldg(p + o + dz), __ldg(p + o + dz + dx), fx);
+    const R c11 = lerp_(__ldg(p + o + dz + dy), __ldg(p + o + dz + dy + dx), fx);
     return lerp_(lerp_(c00, c10, fy), lerp_(c01, c11, fy), fz);
 }
 
@@ -76,17 +93,21 @@ __device__ __forceinline__ R trilinear(const Axis<R> &ax, const Axis<R> &ay, con
 }
 
 // a thread per output voxel: x across the 32 lanes, y across the block's 8
-// rows, z across the grid (looping past 65535 planes); u is [3][nz][ny][nx]
-template <int SP>
+// rows, z across the grid (looping past 65535 planes); u is [3][nz][ny][nx].
+// I: the index type of the FP32 path (int where every index fits, which
+// saves the 64-bit address arithmetic)
+template <int SP, class I>
 __global__ void __launch_bounds__(256) k_warp(const void *th, const float *lo, const float *u, int nx, int ny,
                                               int nz, int pitch, size_t plane, double h, double T_a, float rh,
                                               float T_af, void *dst, int as_f64)
 {
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
     if (x >= nx || y >= ny) return;
-    const size_t n = (size_t)nx * ny * nz;
+    const I n = (I)nx * ny * nz;
+    const float lx = -(float)(nx + 1), hx = (float)(nx + 1), ly = -(float)(ny + 1), hy = (float)(ny + 1);
+    const float lz = -(float)(nz + 1), hz = (float)(nz + 1);
     for (int z = blockIdx.z; z < nz; z += gridDim.z) {
-        const size_t j = ((size_t)z * ny + y) * nx + x;
+        const I j = ((I)z * ny + y) * nx + x;
         if (SP == RFA_STATE_F64) {
             const Axis<double> ax = axis_sample<double>(x, (double)u[j] / h, nx);
             const Axis<double> ay = axis_sample<double>(y, (double)u[j + n] / h, ny);
@@ -100,18 +121,17 @@ __global__ void __launch_bounds__(256) k_warp(const void *th, const float *lo, c
         } else {
             // displacement in voxels: u * rh with rh = 1/h rounded to FP32 on the
             // host (within 2 ulp of u/h: ~2e-7 relative)
-            const Axis<float> ax = axis_sample<float>(x, __fmul_rn(__ldg(u + j), rh), nx);
-            const Axis<float> ay = axis_sample<float>(y, __fmul_rn(__ldg(u + j + n), rh), ny);
-            const Axis<float> az = axis_sample<float>(z, __fmul_rn(__ldg(u + j + 2 * n), rh), nz);
-            const size_t o = (size_t)az.i0 * plane + (size_t)ay.i0 * pitch + ax.i0;
-            const int dx = ax.i1 - ax.i0;
-            const size_t dy = (size_t)(ay.i1 - ay.i0) * pitch, dz = (size_t)(az.i1 - az.i0) * plane;
-            const float vh = trilinear_at<float>((const float *)th + o, dx, dy, dz, ax.f, ay.f, az.f);
+            const AxisF ax = axis_sample_f(x, __fmul_rn(__ldg(u + j), rh), nx, lx, hx);
+            const AxisF ay = axis_sample_f(y, __fmul_rn(__ldg(u + j + n), rh), ny, ly, hy);
+            const AxisF az = axis_sample_f(z, __fmul_rn(__ldg(u + j + 2 * n), rh), nz, lz, hz);
+            const I o = (I)az.i0 * (I)plane + (I)ay.i0 * (I)pitch + ax.i0;
+            const I dx = ax.step, dy = ay.step ? (I)pitch : I(0), dz = az.step ? (I)plane : I(0);
+            const float vh = trilinear_at<float, I>((const float *)th, o, dx, dy, dz, ax.f, ay.f, az.f);
             // the lo part of a compensated state is at most half an ulp of hi, below
             // the resolution of an FP32 temperature (theta >= 0 near the needle, so
             // ulp(hi) <= ulp(T)): only a double output interpolates it
             float vl = 0.f;
-            if (SP == RFA_STATE_F32C && as_f64) vl = trilinear_at<float>(lo + o, dx, dy, dz, ax.f, ay.f, az.f);
+            if (SP == RFA_STATE_F32C && as_f64) vl = trilinear_at<float, I>(lo, o, dx, dy, dz, ax.f, ay.f, az.f);
             if (as_f64) ((double *)dst)[j] = ((double)vh + (double)vl) + T_a;
             else ((float *)dst)[j] = __fadd_rn(__fadd_rn(vh, vl), T_af);
         }
@@ -137,15 +157,17 @@ extern "C" rfa_status rfa_warp_temperature(rfa_grid *g, const float *u_inv_dev, 
     const float *lo = (const float *)g->lo[g->cur];
     const float rh = (float)(1.0 / g->h), T_af = (float)g->T_a;
     const dim3 blk(32, 8), grd((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz < 65535 ? g->nz : 65535);
-    if (g->sp == RFA_STATE_F64)
-        k_warp<RFA_STATE_F64><<<grd, blk, 0, g->stream>>>(th, lo, u_inv_dev, g->nx, g->ny, g->nz, g->pitch, g->plane,
-                                                         g->h, g->T_a, rh, T_af, dst_dev, as_f64);
-    else if (g->sp == RFA_STATE_F32C)
-        k_warp<RFA_STATE_F32C><<<grd, blk, 0, g->stream>>>(th, lo, u_inv_dev, g->nx, g->ny, g->nz, g->pitch, g->plane,
-                                                          g->h, g->T_a, rh, T_af, dst_dev, as_f64);
-    else
-        k_warp<RFA_STATE_F32><<<grd, blk, 0, g->stream>>>(th, lo, u_inv_dev, g->nx, g->ny, g->nz, g->pitch, g->plane,
-                                                         g->h, g->T_a, rh, T_af, dst_dev, as_f64);
+    // 32-bit indices where u (3 nx ny nz values) and the padded state fit
+    const size_t nvox = (size_t)g->nx * g->ny * g->nz;
+    const bool idx32 = 3 * nvox <= (size_t)INT_MAX && g->nvp <= (size_t)INT_MAX;
+#define WARP_ARGS                                                                                                  \
+    th, lo, u_inv_dev, g->nx, g->ny, g->nz, g->pitch, g->plane, g->h, g->T_a, rh, T_af, dst_dev, as_f64
+    if (g->sp == RFA_STATE_F64) k_warp<RFA_STATE_F64, size_t><<<grd, blk, 0, g->stream>>>(WARP_ARGS);
+    else if (g->sp == RFA_STATE_F32C && idx32) k_warp<RFA_STATE_F32C, int><<<grd, blk, 0, g->stream>>>(WARP_ARGS);
+    else if (g->sp == RFA_STATE_F32C) k_warp<RFA_STATE_F32C, size_t><<<grd, blk, 0, g->stream>>>(WARP_ARGS);
+    else if (idx32) k_warp<RFA_STATE_F32, int><<<grd, blk, 0, g->stream>>>(WARP_ARGS);
+    else k_warp<RFA_STATE_F32, size_t><<<grd, blk, 0, g->stream>>>(WARP_ARGS);
+#undef WARP_ARGS
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "rfa_warp_temperature launch");
     return RFA_OK;
