@@ -124,8 +124,11 @@ __device__ __forceinline__ void mld_ab(const void *ab, size_t i, W a[4], W b[4])
 // centre form performs the one-step kernel's operations; the harmonic form
 // weighs every neighbour difference with its face weight from the label-pair
 // table; with the tissue-state coupling b is divided by max(1, Omega).
+// The conservative form alone (FP32 states) runs faster at 3 CTAs/SM (a few spilled
+// registers, more warps to hide its load latency); the tissue-state forms run
+// faster at 2 (measured at 256^3).
 template <int SP, int PP, bool COND, bool ALPHA>
-__global__ void __launch_bounds__(256) k_step_model(const CondArgs A)
+__global__ void __launch_bounds__(256, (COND && !ALPHA && SP != RFA_STATE_F64) ? 3 : 2) k_step_model(const CondArgs A)
 {
     using T = typename std::conditional<SP == RFA_STATE_F64, double, float>::type;
     using W = typename std::conditional<PP == RFA_PARAM_F64, double, float>::type;
