@@ -136,10 +136,6 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-// x - n or x + n for x one period out of [0, n)
-__device__ __forceinline__ int wrap_lo(int x, int n) { return x < 0 ? x + n : x; }
-__device__ __forceinline__ int wrap_hi(int x, int n) { return x >= n ? x - n : x; }
-
 __device__ __forceinline__ float4 ld4(const float *sm, int off)
 {
     return *reinterpret_cast<const float4 *>(sm + off);
@@ -561,12 +557,18 @@ __global__ void __launch_bounds__(Cfg<M, V>::THREADS, Cfg<M, V>::MINB)
 {
     TBPipe P;
     if (!tb_setup<M, V>(P, status)) return;
-    // the descriptor stays in kernel-parameter space (constant-bank operands)
+    // the descriptor stays in kernel-parameter space (constant-bank operands).
+    // The reference returned is to the kernel's own parameter, which outlives
+    // every call of the lambda; the compiler's "reference to local" note does
+    // not apply (a pointer to a __grid_constant__ copy instead cost 3 % more
+    // instructions).
+#pragma nv_diag_suppress 836
     auto get = [&](int item, int &local, const CUtensorMap *&mp) -> const TBTile & {
         local = item;
         mp = maps.m;
         return T0;
     };
+#pragma nv_diag_default 836
     bool bad = false;
     tb_run<M, V, DMG, FOLD, REC>(P, StrideItems{(int)blockIdx.x, (int)gridDim.x}, T0.xt * T0.yt * T0.zc, get,
                                  status, bad);
