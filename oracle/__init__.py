@@ -29,23 +29,26 @@ _P_U8 = ctypes.POINTER(ctypes.c_uint8)
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = ctypes.CDLL(path)
-        i, d, i64 = ctypes.c_int, ctypes.c_double, ctypes.c_int64
-        L.or_round_bf16.argtypes = [d]
-        L.or_round_bf16.restype = d
-        L.or_setup.argtypes = [i, i, i, d, d, i, d, i, _P_U8, i, _P_D,
-                               _P_D, _P_D, _P_D, _P_D, _P_U8, _P_D]
-        L.or_source.argtypes = [i, i, i, d, d, _P_D, _P_D, _P_U8, _P_D, _P_D, _P_D]
-        L.or_run.argtypes = [i, i, i, i64, _P_D, _P_D, _P_D, _P_D, _P_U8, _P_D, _P_U8, d, d,
-                             i, d, d, d, d, _P_D, _P_D, i, _P_D, i]
-        L.or_adjoint.argtypes = [i, i, i, i64, d, d, _P_D, _P_D, _P_D, _P_D, _P_U8, _P_U8, i,
-                                 _P_D, _P_D, _P_D, _P_D, _P_D, _P_D, _P_D, i, _P_D, _P_D, _P_D]
-        L.or_source_grad.argtypes = [i, i, i, d, d, _P_D, _P_D, _P_U8, _P_D, _P_D]
-        for f in ("or_setup", "or_source", "or_run", "or_adjoint", "or_source_grad"):
-            getattr(L, f).restype = ctypes.c_int
-        _lib = L
+        _lib = bind(ctypes.CDLL(_build.build()))
     return _lib
+
+
+def bind(L):
+    """Declare the C entry points' argument types on a loaded oracle library."""
+    i, d, i64 = ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    L.or_round_bf16.argtypes = [d]
+    L.or_round_bf16.restype = d
+    L.or_setup.argtypes = [i, i, i, d, d, i, d, i, _P_U8, i, _P_D,
+                           _P_D, _P_D, _P_D, _P_D, _P_U8, _P_D]
+    L.or_source.argtypes = [i, i, i, d, d, _P_D, _P_D, _P_U8, _P_D, _P_D, _P_D]
+    L.or_run.argtypes = [i, i, i, i64, _P_D, _P_D, _P_D, _P_D, _P_U8, _P_D, _P_U8, d, d,
+                         i, d, d, d, d, _P_D, _P_D, i, _P_D, i]
+    L.or_adjoint.argtypes = [i, i, i, i64, d, d, _P_D, _P_D, _P_D, _P_D, _P_U8, _P_U8, i,
+                             _P_D, _P_D, _P_D, _P_D, _P_D, _P_D, _P_D, i, _P_D, _P_D, _P_D]
+    L.or_source_grad.argtypes = [i, i, i, d, d, _P_D, _P_D, _P_U8, _P_D, _P_D]
+    for f in ("or_setup", "or_source", "or_run", "or_adjoint", "or_source_grad"):
+        getattr(L, f).restype = ctypes.c_int
+    return L
 
 
 def _pd(a):

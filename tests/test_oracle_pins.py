@@ -314,6 +314,28 @@ def test_dense_brute_force_latch_and_damage():
     assert np.allclose(st.omega.ravel(), om, rtol=1e-12, atol=0)
 
 
+def test_latch_after_each_step_tests_the_new_temperature():
+    """The latch after n steps is max_{k=1..n} T^k >= T_thr (the step's new
+    temperature, not the one it started from): checked against brute force at
+    every step where the brute-force latch set grows, and the step before."""
+    case = ph.random_small_case(11, 6, 7, 5, nsteps=0, power=2.0, damage=ph.Damage(enable=0, T_thr_C=45.0))
+    m = oracle.setup(case, "f64")
+    A, c = brute.step_matrix(m.a, m.b, m.s + m.qm, m.isfixed)
+    th = m.theta0.ravel().copy()
+    latch = np.zeros(th.size, bool)
+    sets = [latch.copy()]
+    for _ in range(150):
+        th = A @ th + c
+        latch |= th + case.T_a_C >= 45.0
+        sets.append(latch.copy())
+    grow = [n for n in range(1, len(sets)) if sets[n].sum() > sets[n - 1].sum()]
+    assert len(grow) >= 3
+    for n in sorted(set(grow) | {g - 1 for g in grow if g > 1}):
+        st = oracle.initial_state(m)
+        oracle.run(m, st, n, T_thr_C=45.0)
+        assert np.array_equal(st.latch.ravel() != 0, sets[n]), n
+
+
 # ------------------------------------------------------------------ paper set-up
 def test_paper_fixed_tip_experiment_properties():
     """Sec. 'Evaluation Methods' / 'Simulation of Heat Propagation': a 5x5x3-voxel
