@@ -3,13 +3,17 @@
 Each case plants one mistake -- a dropped term, a wrong sign, a transposed or
 shifted index, an off-by-one face test, a missing unit offset, a skipped
 compensation, the step matrix instead of its transpose -- into a copy of the
-oracle's C source, compiles the copy with the oracle's own flags, binds it in
-place of the oracle library and runs the pins (closed forms, invariants, brute
-force, finite differences).  At least one pin must fail for every mistake; an
-unmodified copy must pass them all.  The oracle source itself is never changed.
+oracle's C source (compiled with the oracle's own flags and bound in place of
+the oracle library), or into a copy of one of its numpy functions (bound in
+place of that function), and runs the pins (closed forms, invariants, brute
+force, finite differences).  At least one pin must fail (or stop with an
+error) for every mistake; an unmodified copy must pass them all.  The oracle
+source itself is never changed.
 """
 import ctypes
+import inspect
 import os
+import textwrap
 
 import pytest
 
@@ -20,6 +24,8 @@ from tests import test_oracle_adjoint as ADJ
 from tests import test_oracle_alpha as ALPHA
 from tests import test_oracle_cond as COND
 from tests import test_oracle_pins as PINS
+from tests import test_oracle_potential as POT
+from tests import test_oracle_warp as WARP
 
 # the pins, fastest first (a mutant stops at the first pin that fails)
 CHECKS = [
@@ -47,6 +53,15 @@ CHECKS = [
     ("conservative: adjoint transpose", COND.test_adjoint_matches_dense_transpose),
     ("tissue state: scalar recurrence", ALPHA.test_uniform_field_follows_the_scalar_recurrence),
     ("tissue state: below threshold", ALPHA.test_no_effect_below_the_damage_threshold_and_hotter_above),
+    ("potential: two-material resistor", POT.test_two_material_resistor),
+    ("potential: power balance, maximum principle", POT.test_tellegen_power_balance_and_maximum_principle),
+    ("potential: symmetry", POT.test_symmetry_of_a_centred_needle),
+    ("resample: zero field", WARP.test_zero_field_is_identity),
+    ("resample: shift x", lambda: WARP.test_integer_shift_with_clamp(0, 3)),
+    ("resample: shift y", lambda: WARP.test_integer_shift_with_clamp(1, -2)),
+    ("resample: shift z", lambda: WARP.test_integer_shift_with_clamp(2, 4)),
+    ("resample: affine field", WARP.test_affine_field_reproduced_exactly),
+    ("resample: scipy", WARP.test_matches_scipy_map_coordinates),
     ("paper hot tip", PINS.test_paper_fixed_tip_experiment_properties),
     ("steady point source", PINS.test_steady_point_source_fixed_point_and_refinement),
 ]
@@ -98,11 +113,34 @@ def _bind_copy(tmp_path, old, new):
     return oracle.bind(ctypes.CDLL(lib))
 
 
+# (name, oracle function, text in its source, planted replacement)
+PY_MUTANTS = [
+    ("face weights: arithmetic mean", "face_weights", "W[l, m] = g * (2.0 * tl.k * tm.k / Ks)",
+     "W[l, m] = g * (0.5 * Ks)"),
+    ("face weights: the neighbour's rho c", "face_weights", "W[l, m] = g * (2.0 * tl.k * tm.k / Ks)",
+     "W[l, m] = case.dt / (tm.rho * tm.c * case.h * case.h) * (2.0 * tl.k * tm.k / Ks)"),
+    ("face weights: x- and x+ swapped", "face_weights", "((2, -1), (2, 1), (1, -1)", "((2, 1), (2, -1), (1, -1)"),
+    ("resample: weights of the two z corners swapped", "warp_temperature",
+     "((z0, 1.0 - fz), (z1, fz))", "((z0, fz), (z1, 1.0 - fz))"),
+    ("resample: nearest instead of floor", "warp_temperature", "fl = np.floor(dd)", "fl = np.round(dd)"),
+    ("resample: clamp one voxel late", "warp_temperature", "low, high = i < 0, i >= n - 1",
+     "low, high = i < 0, i >= n"),
+    ("potential faces: arithmetic mean", "harmonic_faces", "hm = np.divide(2.0 * vals * nb, s, out=np.zeros_like(s), where=s > 0)",
+     "hm = 0.5 * s"),
+    ("potential: electrode and ground swapped", "potential_solve", "Vfix = electrode.astype(np.float64)",
+     "Vfix = ground.astype(np.float64)"),
+    ("potential: boundary term sign", "potential_solve", "np.add.at(rhs, i[~jf], sf[~jf] * nb_fix[m][~jf])",
+     "np.add.at(rhs, i[~jf], -sf[~jf] * nb_fix[m][~jf])"),
+    ("Joule heating: |dV| not squared", "joule", "(nb - V) ** 2", "np.abs(nb - V)"),
+    ("Joule heating: face not split", "joule", "return q / (2.0 * h * h)", "return q / (h * h)"),
+]
+
+
 def _failing_check():
     for name, check in CHECKS:
         try:
             check()
-        except AssertionError:
+        except Exception:  # an assertion, or an error the mistake provoked
             return name
     return None
 
@@ -115,5 +153,16 @@ def test_unmodified_copy_passes_every_pin(tmp_path, monkeypatch):
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
 def test_pins_catch_planted_mistake(name, old, new, tmp_path, monkeypatch):
     monkeypatch.setattr(oracle, "_lib", _bind_copy(str(tmp_path), old, new))
+    caught = _failing_check()
+    assert caught is not None, f"no pin catches: {name}"
+
+
+@pytest.mark.parametrize("name,fname,old,new", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_pins_catch_planted_mistake_in_numpy_parts(name, fname, old, new, monkeypatch):
+    src = textwrap.dedent(inspect.getsource(getattr(oracle, fname)))
+    assert src.count(old) == 1, f"mutation site not unique: {old!r}"
+    ns = dict(vars(oracle))
+    exec(compile(src.replace(old, new), f"<{fname} with a planted mistake>", "exec"), ns)
+    monkeypatch.setattr(oracle, fname, ns[fname])
     caught = _failing_check()
     assert caught is not None, f"no pin catches: {name}"
