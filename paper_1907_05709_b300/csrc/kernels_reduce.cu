@@ -7,6 +7,7 @@
 // (warp shuffles, then shared memory), and one block sums the partials in a
 // fixed order, so the counts and the FP64 smoothed volume are bit-reproducible.
 #include "rfa_internal.cuh"
+#include "necrosis.cuh"
 
 namespace rfa {
 
@@ -25,6 +26,21 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
+template <typename T>
+__device__ __forceinline__ T block_sum256(T v)
+{
+    // fixed order: warp tree, then the 8 warp sums in order
+    __shared__ T sh[8];
+    v = warp_sum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    T t = T(0);
+    for (int k = 0; k < 8; ++k) t += sh[k];
+    return t;
+}
+
+// a warp per grid row, lanes along x in quads
 template <int SP>
 __global__ void __launch_bounds__(256) k_necrosis(const void *th, const float *lo,
                                                   const uint8_t *latch, const double *omega,
@@ -33,65 +49,39 @@ __global__ void __launch_bounds__(256) k_necrosis(const void *th, const float *l
                                                   double T_thr, double inv_width,
                                                   uint8_t *mask_dense, NecroPartial *part)
 {
-    using T = typename std::conditional<SP == RFA_STATE_F64, double, float>::type;
-    size_t nvp = (size_t)pitch * ny * nz;
-    unsigned long long c0 = 0, c1 = 0;
+    unsigned n0 = 0, n1 = 0;
     double sm = 0.0;
     const double off = T_thr - T_a;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nvp;
-         i += (size_t)gridDim.x * blockDim.x) {
-        int x = (int)(i % pitch);
-        if (x >= nx) continue;
-        uint8_t m = (latch[i] ? 1 : 0) | (omega[i] + (double)carry[i] >= 1.0 ? 2 : 0);
-        c0 += m & 1;
-        c1 += (m >> 1) & 1;
-        if (SP == RFA_STATE_F64) {
-            double u = (((const double *)th)[i] - off) * inv_width;
-            sm += 1.0 / (1.0 + exp(-u));
-        } else {
-            float v = ((const float *)th)[i];
-            if (SP == RFA_STATE_F32C) v += lo[i];
-            float u = (v - (float)off) * (float)inv_width;
-            sm += (double)(1.0f / (1.0f + __expf(-u)));
-        }
-        if (mask_dense) {
-            size_t r = i / pitch;
-            mask_dense[r * nx + x] = m;
+    const float offf = (float)off, iwf = (float)inv_width;
+    for (int row = blockIdx.x * 8 + (int)(threadIdx.x >> 5); row < ny * nz; row += gridDim.x * 8) {
+        const size_t rb = (size_t)row * pitch;
+        for (int x0 = 4 * (int)(threadIdx.x & 31); x0 < nx; x0 += 128) {
+            const int nin = nx - x0 < 4 ? nx - x0 : 4;
+            uint8_t m[4];
+            necro_quad<SP>(th, lo, latch, omega, carry, rb + x0, nin, off, inv_width, offf, iwf, n0, n1, sm, m);
+            if (mask_dense)
+                for (int q = 0; q < nin; ++q) mask_dense[(size_t)row * nx + x0 + q] = m[q];
         }
     }
-    __shared__ unsigned long long s0[8], s1[8];
-    __shared__ double s2[8];
-    c0 = warp_sum(c0);
-    c1 = warp_sum(c1);
-    sm = warp_sum(sm);
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) {
-        s0[w] = c0;
-        s1[w] = c1;
-        s2[w] = sm;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        NecroPartial p{0, 0, 0.0, 0.0};
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-            p.n_thermal += s0[k];
-            p.n_arrh += s1[k];
-            p.smooth += s2[k];
-        }
-        part[blockIdx.x] = p;
-    }
+    const unsigned long long c0 = block_sum256((unsigned long long)n0), c1 = block_sum256((unsigned long long)n1);
+    const double s = block_sum256(sm);
+    if (threadIdx.x == 0) part[blockIdx.x] = NecroPartial{c0, c1, s, 0.0};
 }
 
-__global__ void k_necrosis_final(const NecroPartial *part, int n, NecroPartial *out)
+// the partials in a fixed order on one block of 256 threads
+__global__ void __launch_bounds__(256) k_necrosis_final(const NecroPartial *part, int n, NecroPartial *out)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    NecroPartial p{0, 0, 0.0, 0.0};
-    for (int k = 0; k < n; ++k) {
-        p.n_thermal += part[k].n_thermal;
-        p.n_arrh += part[k].n_arrh;
-        p.smooth += part[k].smooth;
+    unsigned long long a = 0, b = 0;
+    double c = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        a += part[k].n_thermal;
+        b += part[k].n_arrh;
+        c += part[k].smooth;
     }
-    *out = p;
+    a = block_sum256(a);
+    b = block_sum256(b);
+    c = block_sum256(c);
+    if (threadIdx.x == 0) *out = NecroPartial{a, b, c, 0.0};
 }
 
 template <int SP>
@@ -190,7 +180,7 @@ cudaError_t launch_necrosis(rfa_grid *g, uint8_t *mask_dense_dev, double width_K
         k_necrosis<RFA_STATE_F32><<<kReduceBlocks, 256, 0, g->stream>>>(
             th, lo, g->latch, g->omega, g->omega_c, g->nx, g->ny, g->nz, g->pitch, g->T_a, g->T_thr, iw,
             mask_dense_dev, part);
-    k_necrosis_final<<<1, 32, 0, g->stream>>>(part, kReduceBlocks, (NecroPartial *)result_dev);
+    k_necrosis_final<<<1, 256, 0, g->stream>>>(part, kReduceBlocks, (NecroPartial *)result_dev);
     return cudaGetLastError();
 }
 

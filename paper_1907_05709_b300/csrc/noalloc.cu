@@ -22,6 +22,7 @@
 // reads, so nothing has to be cleared, but calls whose work overlaps on the GPU
 // (different streams, or different host threads) race on the records.
 #include "rfa_internal.cuh"
+#include "necrosis.cuh"
 
 #include <mutex>
 
@@ -38,12 +39,30 @@ struct NaRecord {
     double pad;
 };
 
+// block of 256 threads: warp trees, then the 8 warp sums in order (fixed order)
+template <typename T>
+__device__ __forceinline__ T na_block_sum(T v)
+{
+    __shared__ T sh[8];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    T t = T(0);
+    for (int k = 0; k < 8; ++k) t += sh[k];
+    return t;
+}
+
 static __device__ __align__(256) NaRecord g_noalloc_scratch[kNoAllocRecords];
 
 std::mutex g_na_mu;
 void *g_na_ptr[64] = {};  // device address of the scratch array, per device ordinal
 
-// per-block partials: thermal latch, Arrhenius (Omega + carry >= 1), smoothed sigmoid sum
+// per-record partials over padded voxels [65536 r, 65536 (r + 1)): thermal
+// latch, Arrhenius (Omega + carry >= 1), smoothed sigmoid sum, in the quads of
+// rfa_necrosis_mask (4 x voxels from a multiple of 4: the same FP32 quad sums;
+// records start at multiples of 4 and the padded pitch is one).  The grid
+// limit keeps every padded index below 2^32.
 template <int SP>
 __global__ void __launch_bounds__(256) k_na_partials(const void *th, const float *lo,
                                                      const uint8_t *latch, const double *omega,
@@ -51,66 +70,45 @@ __global__ void __launch_bounds__(256) k_na_partials(const void *th, const float
                                                      int pitch, double off, double inv_width,
                                                      NaRecord *rec)
 {
-    const size_t nvp = (size_t)pitch * ny * nz;
-    const size_t begin = (size_t)blockIdx.x * kNoAllocVoxelsPerRecord;
-    const size_t end = begin + kNoAllocVoxelsPerRecord < nvp ? begin + kNoAllocVoxelsPerRecord : nvp;
-    unsigned long long c0 = 0, c1 = 0;
+    const unsigned nvp = (unsigned)((size_t)pitch * ny * nz);
+    const unsigned begin = blockIdx.x * (unsigned)kNoAllocVoxelsPerRecord;
+    const unsigned end = nvp - begin > (unsigned)kNoAllocVoxelsPerRecord ? begin + (unsigned)kNoAllocVoxelsPerRecord : nvp;
+    const float offf = (float)off, iwf = (float)inv_width;
+    unsigned n0 = 0, n1 = 0;
     double sm = 0.0;
-    for (size_t i = begin + threadIdx.x; i < end; i += blockDim.x) {
-        if ((int)(i % pitch) >= nx) continue;
-        c0 += latch[i] ? 1 : 0;
-        c1 += (omega[i] + (double)carry[i] >= 1.0) ? 1 : 0;
-        if (SP == RFA_STATE_F64) {
-            const double u = (((const double *)th)[i] - off) * inv_width;
-            sm += 1.0 / (1.0 + exp(-u));
-        } else {
-            float v = ((const float *)th)[i];
-            if (SP == RFA_STATE_F32C) v += lo[i];
-            const float u = (v - (float)off) * (float)inv_width;
-            sm += (double)(1.0f / (1.0f + __expf(-u)));
-        }
+    for (unsigned i = begin + 4u * threadIdx.x; i < end; i += 4u * blockDim.x) {
+        const int x0 = (int)(i % (unsigned)pitch);
+        if (x0 >= nx) continue;
+        const int nin = nx - x0 < 4 ? nx - x0 : 4;
+        uint8_t m[4];
+        necro_quad<SP>(th, lo, latch, omega, carry, i, nin, off, inv_width, offf, iwf, n0, n1, sm, m);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        c0 += __shfl_xor_sync(0xffffffffu, c0, o);
-        c1 += __shfl_xor_sync(0xffffffffu, c1, o);
-        sm += __shfl_xor_sync(0xffffffffu, sm, o);
-    }
-    __shared__ unsigned long long s0[8], s1[8];
-    __shared__ double s2[8];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) {
-        s0[w] = c0;
-        s1[w] = c1;
-        s2[w] = sm;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        NaRecord r{0, 0, 0.0, 0.0};
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-            r.n_thermal += s0[k];
-            r.n_arrh += s1[k];
-            r.smooth += s2[k];
-        }
-        rec[blockIdx.x] = r;
-    }
+    const unsigned long long c0 = na_block_sum((unsigned long long)n0), c1 = na_block_sum((unsigned long long)n1);
+    const double s = na_block_sum(sm);
+    if (threadIdx.x == 0) rec[blockIdx.x] = NaRecord{c0, c1, s, 0.0};
 }
 
-// sum the records in a fixed order; out = {count_thermal, count_arrhenius, smooth_volume_m3, 0}
-__global__ void k_na_final(const NaRecord *rec, int n, double h3, void *out)
+// sum the records in a fixed order on one block of 256 threads;
+// out = {count_thermal, count_arrhenius, smooth_volume_m3, 0}
+__global__ void __launch_bounds__(256) k_na_final(const NaRecord *rec, int n, double h3, void *out)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     unsigned long long c0 = 0, c1 = 0;
     double sm = 0.0;
-    for (int k = 0; k < n; ++k) {
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
         c0 += rec[k].n_thermal;
         c1 += rec[k].n_arrh;
         sm += rec[k].smooth;
     }
-    int64_t *o = (int64_t *)out;
-    o[0] = (int64_t)c0;
-    o[1] = (int64_t)c1;
-    ((double *)out)[2] = h3 * sm;
-    ((double *)out)[3] = 0.0;
+    c0 = na_block_sum(c0);
+    c1 = na_block_sum(c1);
+    sm = na_block_sum(sm);
+    if (threadIdx.x == 0) {
+        int64_t *o = (int64_t *)out;
+        o[0] = (int64_t)c0;
+        o[1] = (int64_t)c1;
+        ((double *)out)[2] = h3 * sm;
+        ((double *)out)[3] = 0.0;
+    }
 }
 
 }  // namespace
@@ -168,7 +166,7 @@ extern "C" rfa_status rfa_necrosis_reduce_noalloc(rfa_grid *g, double smooth_wid
     else
         k_na_partials<RFA_STATE_F32><<<nb, 256, 0, g->stream>>>(th, lo, g->latch, g->omega, g->omega_c, g->nx,
                                                                 g->ny, g->nz, g->pitch, off, iw, rec);
-    k_na_final<<<1, 32, 0, g->stream>>>(rec, (int)nrec, g->h * g->h * g->h, result_dev);
+    k_na_final<<<1, 256, 0, g->stream>>>(rec, (int)nrec, g->h * g->h * g->h, result_dev);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "rfa_necrosis_reduce_noalloc launch");
     return RFA_OK;
