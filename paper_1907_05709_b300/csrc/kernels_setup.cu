@@ -25,6 +25,7 @@ __global__ void k_label_coef(LabelCoef *tab, int n_labels, double dt, double h, 
     LabelCoef t = tab[l];
     t.a = t.fixed ? 0.0 : round_coef(coef_a(t, dt, h), pp);
     t.b = t.fixed ? 0.0 : round_coef(coef_b(t, dt), pp);
+    t.dt_rhoc = dt / (t.rho * t.c);
     tab[l] = t;
 }
 
@@ -132,42 +133,52 @@ __global__ void k_source_sum(NeedleGeom geom, const uint8_t *__restrict__ label,
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
-// pass 2 (fused with pass 3's input): W = sum of the partials in fixed order
-__global__ void k_sum_partials(const double *partial, int n, double *out)
+// pass 2: W = sum of the partials in fixed order (out[0]) and the scale
+// P / (h^3 W) of the weights (out[1]; 0 without a needle or weight)
+__global__ void k_source_scale(const double *partial, int n, double P, double h, int nseg, double *out)
 {
     double acc = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partial[i];
     acc = block_sum(acc);
-    if (threadIdx.x == 0) *out = acc;
+    if (threadIdx.x == 0) {
+        out[0] = acc;
+        out[1] = (acc > 0.0 && nseg > 0) ? P / (h * h * h * acc) : 0.0;
+    }
 }
 
-// pass 3: s_i = (P w_i / (h^3 W) + Q_m) dt / (rho c)_i on free voxels
+// pass 3: s_i = (P w_i / (h^3 W) + Q_m) dt / (rho c)_i on free voxels, 0
+// elsewhere; a warp per grid row, the per-label values in shared memory
 template <int SP>
-__global__ void k_source_write(NeedleGeom geom, const uint8_t *__restrict__ label,
-                               const LabelCoef *__restrict__ tab, int nx, int ny, int nz,
-                               int pitch, double h, double dt, int face, const double *Wp,
-                               const double *wbuf, void *s)
+__global__ void __launch_bounds__(256) k_source_write(const uint8_t *__restrict__ label,
+                                                      const LabelCoef *__restrict__ tab, int n_labels, int nx,
+                                                      int ny, int nz, int pitch, int face, const double *Wp,
+                                                      const double *wbuf, void *s)
 {
     using T = typename std::conditional<SP == RFA_STATE_F64, double, float>::type;
-    size_t nvp = (size_t)pitch * ny * nz;
-    const double W = *Wp;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nvp;
-         i += (size_t)gridDim.x * blockDim.x) {
-        int x = (int)(i % pitch);
-        double v = 0.0;
-        if (x < nx) {
-            size_t r = i / pitch;
-            int y = (int)(r % ny);
-            int z = (int)(r / ny);
-            bool face_vox = (x == 0 || y == 0 || z == 0 || x == nx - 1 || y == ny - 1 || z == nz - 1);
-            const LabelCoef t = tab[label[i]];
-            if (!(t.fixed || (face == RFA_FACE_DIRICHLET && face_vox))) {
-                double rhoc = t.rho * t.c;
-                double q = (W > 0.0 && geom.nseg > 0) ? geom.P * wbuf[i] / (h * h * h * W) : 0.0;
-                v = q * dt / rhoc + t.Q_m * dt / rhoc;
+    __shared__ double qm[256], dtrc[256];
+    __shared__ uint8_t fixed[256];
+    for (int l = threadIdx.x; l < n_labels; l += blockDim.x) {
+        qm[l] = tab[l].Q_m;
+        dtrc[l] = tab[l].dt_rhoc;
+        fixed[l] = tab[l].fixed ? 1 : 0;
+    }
+    __syncthreads();
+    const double scale = Wp[1];
+    for (int row = blockIdx.x * 8 + (int)(threadIdx.x >> 5); row < ny * nz; row += gridDim.x * 8) {
+        const int y = row % ny, z = row / ny;
+        const bool face_row = y == 0 || z == 0 || y == ny - 1 || z == nz - 1;
+        const size_t rb = (size_t)row * pitch;
+        for (int x = threadIdx.x & 31; x < pitch; x += 32) {
+            const size_t i = rb + x;
+            double v = 0.0;
+            if (x < nx) {
+                const int l = label[i];
+                const bool face_vox = face_row || x == 0 || x == nx - 1;
+                if (!(fixed[l] || (face == RFA_FACE_DIRICHLET && face_vox)))
+                    v = fma(scale, wbuf[i], qm[l]) * dtrc[l];
             }
+            ((T *)s)[i] = (T)v;
         }
-        ((T *)s)[i] = (T)v;
     }
 }
 
@@ -199,15 +210,15 @@ cudaError_t launch_setup(rfa_grid *g, const uint8_t *labels_dense_dev, int n_lab
 cudaError_t launch_source_write(rfa_grid *g, const double *partial, int npartial)
 {
     double *W = (double *)g->red + kReduceBlocks;
-    k_sum_partials<<<1, 1024, 0, g->stream>>>(partial, npartial, W);
+    k_source_scale<<<1, 1024, 0, g->stream>>>(partial, npartial, g->geom.P, g->h, g->geom.nseg, W);
     if (g->sp == RFA_STATE_F64)
         k_source_write<RFA_STATE_F64><<<148 * 8, 256, 0, g->stream>>>(
-            g->geom, g->label, g->d_table, g->nx, g->ny, g->nz, g->pitch, g->h, g->dt, g->face, W,
-            (const double *)g->stage, g->s);
+            g->label, g->d_table, g->n_labels, g->nx, g->ny, g->nz, g->pitch, g->face, W, (const double *)g->stage,
+            g->s);
     else
         k_source_write<RFA_STATE_F32><<<148 * 8, 256, 0, g->stream>>>(
-            g->geom, g->label, g->d_table, g->nx, g->ny, g->nz, g->pitch, g->h, g->dt, g->face, W,
-            (const double *)g->stage, g->s);
+            g->label, g->d_table, g->n_labels, g->nx, g->ny, g->nz, g->pitch, g->face, W, (const double *)g->stage,
+            g->s);
     return cudaGetLastError();
 }
 
@@ -218,16 +229,7 @@ cudaError_t launch_source(rfa_grid *g)
     k_source_sum<<<kReduceBlocks, 256, 0, g->stream>>>(g->geom, g->label, g->d_table, g->nx,
                                                        g->ny, g->nz, g->pitch, g->h, g->face,
                                                        partial, (double *)g->stage);
-    k_sum_partials<<<1, 1024, 0, g->stream>>>(partial, kReduceBlocks, W);
-    if (g->sp == RFA_STATE_F64)
-        k_source_write<RFA_STATE_F64><<<148 * 8, 256, 0, g->stream>>>(
-            g->geom, g->label, g->d_table, g->nx, g->ny, g->nz, g->pitch, g->h, g->dt, g->face, W,
-            (const double *)g->stage, g->s);
-    else
-        k_source_write<RFA_STATE_F32><<<148 * 8, 256, 0, g->stream>>>(
-            g->geom, g->label, g->d_table, g->nx, g->ny, g->nz, g->pitch, g->h, g->dt, g->face, W,
-            (const double *)g->stage, g->s);
-    return cudaGetLastError();
+    return launch_source_write(g, partial, kReduceBlocks);
 }
 
 }  // namespace rfa

@@ -38,7 +38,8 @@ constexpr int kCarrySteps = 128;   // fold the FP32 damage carry into the FP64 i
 struct LabelCoef {
     double k, rho, c, w_b, rho_b, c_b, Q_m, T_fixed;
     int fixed;
-    double a, b;  // stored (rounded) update coefficients, filled on the device by k_label_coef
+    double a, b;   // stored (rounded) update coefficients, filled on the device by k_label_coef
+    double dt_rhoc;  // dt / (rho c), filled there too
 };
 
 struct Segment {
