@@ -26,6 +26,18 @@ def test_setup_and_source_fields_match_oracle():
         assert np.array_equal(gpu["theta"], m.theta0)
 
 
+def test_source_field_nine_tines_larger_grid():
+    """The source weights on a 72 x 64 x 56 grid at h = 0.5 mm around a 9-tine
+    umbrella (many voxels nearly equidistant from two tines): every voxel to
+    1e-12 of the oracle's FP64 source."""
+    case = ph.random_small_case(3, 72, 64, 56, h=0.5e-3, kind=ph.UMBRELLA)
+    assert case.needle.n_tines == 8 and case.needle.tine_axial == 1
+    gpu = run_gpu(case, rfa.STATE_F64, rfa.PARAM_F64, 0)
+    m = oracle.setup(case, "f64")
+    s_ref = m.s + m.qm
+    assert np.max(np.abs(gpu["s"] - s_ref) / np.maximum(s_ref, 1e-300)) <= 1e-12
+
+
 def test_homogeneous_64_fp64_2000_steps():
     """64^3, h = 1 mm, homogeneous liver, straight 15 mm needle at 15 W,
     dt = 0.05 s, 2000 steps, FP64 state: <= 1e-9 K."""
