@@ -32,63 +32,83 @@ __global__ void k_label_coef(LabelCoef *tab, int n_labels, double dt, double h, 
     tab[l] = t;
 }
 
+// Every value k_setup writes follows from the voxel's label (or is 0 on a
+// Dirichlet face voxel of a free label), so each block first forms, per label,
+// the stored coefficient pair and the start value (hi, and for compensated
+// states the exact lo) with the per-voxel expressions, then a warp per grid row
+// writes them (no per-voxel FP64 and no 64-bit index division).
 template <int SP, int PP>
-__global__ void k_setup(const uint8_t *__restrict__ labels, const LabelCoef *__restrict__ tab,
-                        int nx, int ny, int nz, int pitch, double h, double dt, double T_a,
-                        int face, void *th0, void *th1, void *lo0, void *lo1, void *ab,
-                        void *s, uint8_t *label_pad, uint8_t *latch, double *omega,
-                        float *omega_c, int n_labels, unsigned *status)
+__global__ void __launch_bounds__(256) k_setup(const uint8_t *__restrict__ labels,
+                                               const LabelCoef *__restrict__ tab, int nx, int ny, int nz,
+                                               int pitch, double h, double dt, double T_a, int face, void *th0,
+                                               void *th1, void *lo0, void *lo1, void *ab, void *s,
+                                               uint8_t *label_pad, uint8_t *latch, double *omega,
+                                               float *omega_c, int n_labels, unsigned *status)
 {
     using T = typename std::conditional<SP == RFA_STATE_F64, double, float>::type;
-    size_t nvp = (size_t)pitch * ny * nz;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nvp;
-         i += (size_t)gridDim.x * blockDim.x) {
-        int x = (int)(i % pitch);
-        size_t r = i / pitch;
-        int y = (int)(r % ny);
-        int z = (int)(r / ny);
-        double a = 0.0, b = 0.0, th = 0.0;
-        uint8_t l = 0;
-        if (x < nx) {
-            l = labels[((size_t)z * ny + y) * nx + x];
-            if (l >= n_labels) {
-                atomicOr(status, kStatusBadLabel);
-                l = 0;
-            }
-            const LabelCoef t = tab[l];
-            bool face_vox = (x == 0 || y == 0 || z == 0 || x == nx - 1 || y == ny - 1 || z == nz - 1);
-            if (t.fixed) {
-                th = t.T_fixed - T_a;
-            } else if (face == RFA_FACE_DIRICHLET && face_vox) {
-                th = 0.0;
-            } else {
-                a = t.a;
-                b = t.b;
-            }
-        }
-        ((T *)th0)[i] = (T)th;
-        ((T *)th1)[i] = (T)th;
-        if (SP == RFA_STATE_F32C) {
-            // the pair (hi, lo) represents th exactly
-            float hi = (float)th;
-            ((float *)lo0)[i] = (float)(th - (double)hi);
-            ((float *)lo1)[i] = (float)(th - (double)hi);
-        }
+    using AB = typename std::conditional<PP == RFA_PARAM_BF16, uint32_t,
+                                         typename std::conditional<PP == RFA_PARAM_F32, float2, double2>::type>::type;
+    __shared__ AB sab[256];
+    __shared__ T sth[256];
+    __shared__ float slo[256];
+    __shared__ uint8_t sfixed[256];
+    for (int l = threadIdx.x; l < n_labels; l += blockDim.x) {
+        const LabelCoef t = tab[l];
+        const double a = t.fixed ? 0.0 : t.a, b = t.fixed ? 0.0 : t.b;
+        const double th = t.fixed ? t.T_fixed - T_a : 0.0;
         if (PP == RFA_PARAM_BF16) {
-            ((uint32_t *)ab)[i] = (uint32_t)bf16_bits_rne(a) | ((uint32_t)bf16_bits_rne(b) << 16);
+            *reinterpret_cast<uint32_t *>(&sab[l]) = (uint32_t)bf16_bits_rne(a) | ((uint32_t)bf16_bits_rne(b) << 16);
         } else if (PP == RFA_PARAM_F32) {
-            ((float2 *)ab)[i] = make_float2((float)a, (float)b);
+            *reinterpret_cast<float2 *>(&sab[l]) = make_float2((float)a, (float)b);
         } else {
-            ((double2 *)ab)[i] = make_double2(a, b);
+            *reinterpret_cast<double2 *>(&sab[l]) = make_double2(a, b);
         }
-        ((T *)s)[i] = (T)0;
-        label_pad[i] = l;
-        latch[i] = 0;
-        omega[i] = 0.0;
-        omega_c[i] = 0.0f;
+        sth[l] = (T)th;
+        // the pair (hi, lo) represents th exactly
+        slo[l] = SP == RFA_STATE_F32C ? (float)(th - (double)(float)th) : 0.f;
+        sfixed[l] = t.fixed ? 1 : 0;
+    }
+    __syncthreads();
+    const AB zero_ab{};
+    for (int row = blockIdx.x * 8 + (int)(threadIdx.x >> 5); row < ny * nz; row += gridDim.x * 8) {
+        const int y = row % ny, z = row / ny;
+        const bool face_row = y == 0 || z == 0 || y == ny - 1 || z == nz - 1;
+        const size_t rb = (size_t)row * pitch;
+        for (int x = threadIdx.x & 31; x < pitch; x += 32) {
+            const size_t i = rb + x;
+            AB abv = zero_ab;
+            T th = T(0);
+            float lo = 0.f;
+            uint8_t l = 0;
+            if (x < nx) {
+                l = labels[(size_t)row * nx + x];
+                if (l >= n_labels) {
+                    atomicOr(status, kStatusBadLabel);
+                    l = 0;
+                }
+                const bool face_vox = face_row || x == 0 || x == nx - 1;
+                if (sfixed[l]) {
+                    th = sth[l];
+                    lo = slo[l];
+                } else if (!(face == RFA_FACE_DIRICHLET && face_vox)) {
+                    abv = sab[l];
+                }
+            }
+            ((T *)th0)[i] = th;
+            ((T *)th1)[i] = th;
+            if (SP == RFA_STATE_F32C) {
+                ((float *)lo0)[i] = lo;
+                ((float *)lo1)[i] = lo;
+            }
+            ((AB *)ab)[i] = abv;
+            ((T *)s)[i] = T(0);
+            label_pad[i] = l;
+            latch[i] = 0;
+            omega[i] = 0.0;
+            omega_c[i] = 0.0f;
+        }
     }
 }
-
 
 // w = max(d, r0)^-4 = 1 / max(d^2, r0^2)^2
 __device__ inline double needle_weight2(const NeedleGeom &g, double d2)
