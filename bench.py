@@ -375,6 +375,32 @@ def measure_next_rows(rfa, stream, case, g, cpu_baseline_on: bool):
     return out
 
 
+def measure_path_rows(rfa, stream, case, g, labels_dev):
+    """The path's steps outside the time loop at the bench's size, on the bench
+    grid after its timed steps: S6, the necrosis counts and smoothed volume
+    (the allocation-free entry point: device result, no host copy), against its
+    bytes (latch 1, Omega 8, carry 4, theta hi+lo 8 = 21 B/voxel); S1 + S2,
+    rfa_set_tissue (coefficients, start state, and the needle placed again),
+    and S2 alone, rfa_place_needle (FP64 distances to the needle's segments,
+    FP64 sum of the weights: bound by B300's FP64 pipe, once per placement)."""
+    import torch
+    peak, _ = measured_peak_hbm()
+    n = case.nvox
+    out = {}
+    res = torch.zeros(4, dtype=torch.float64, device="cuda")
+    rfa.rfa_necrosis_reduce_noalloc(g.handle, res, 1.0)
+    ms = _ms_between(torch, stream, lambda: [rfa.rfa_necrosis_reduce_noalloc(g.handle, res, 1.0)
+                                             for _ in range(10)]) / 10
+    gbs = 21.0 * n / (ms * 1e-3) / 1e9
+    out["necrosis_reduce"] = {"ms": ms, "bytes_per_voxel": 21.0, "achieved_GBs": gbs, "peak_GBs": peak,
+                              "frac": gbs / peak, "gvox_s": n / (ms * 1e-3) / 1e9}
+    ms = _ms_between(torch, stream, lambda: [g.set_tissue(labels_dev, case.table) for _ in range(3)]) / 3
+    out["tissue_setup_and_source"] = {"ms": ms, "gvox_s": n / (ms * 1e-3) / 1e9}
+    ms = _ms_between(torch, stream, lambda: [g.place_needle(case.needle) for _ in range(3)]) / 3
+    out["source_place"] = {"ms": ms, "gvox_s": n / (ms * 1e-3) / 1e9}
+    return out
+
+
 def measure_batched(rfa, stream, args):
     """64 needle configurations on {96,128,160,192}^3 grids, 4000 steps (or
     --batch-steps): one batched persistent launch per call vs the per-needle loop
@@ -560,6 +586,7 @@ def run_ours(args):
         secondary = {"adjoint": measure_adjoint(rfa, stream),
                      "batched": measure_batched(rfa, stream, args),
                      "next_rows": measure_next_rows(rfa, stream, case, g, not args.no_cpu_baseline)}
+        secondary["path_rows"] = measure_path_rows(rfa, stream, case, g, labels_dev)
     if dist is not None:
         dist.barrier()
     if rank == 0:
@@ -604,8 +631,8 @@ def profile_case(name):
         for _ in range(2):
             g.backward(seed)
     elif name == "model256":
-        # the model options at 256^3: breathing resample, conservative step,
-        # tissue-state step, 40 iterations of the potential solve
+        # the model options at 256^3: breathing resample, necrosis reduction,
+        # conservative step, tissue-state step, 40 iterations of the potential solve
         case = ph.umbrella_case_256(seed=0, nsteps=8)
         g = rfa.Grid.from_case(case, cuda_stream=stream.cuda_stream)
         g.step(8)
@@ -613,6 +640,9 @@ def profile_case(name):
         dst = torch.empty((case.nz, case.ny, case.nx), dtype=torch.float32, device="cuda")
         for _ in range(3):
             rfa.rfa_warp_temperature(g.handle, u, dst, False)
+        res = torch.zeros(4, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            rfa.rfa_necrosis_reduce_noalloc(g.handle, res, 1.0)
         g.close()
         for cond, perf in (("harmonic", "constant"), ("centre", "tissue_state")):
             c2 = ph.umbrella_case_256(seed=0, nsteps=8)
