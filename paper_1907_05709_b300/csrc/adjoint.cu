@@ -493,7 +493,7 @@ rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads)
     A.nz = g->nz;
     A.pitch = g->pitch;
     A.plane = g->plane;
-    A.zchunk = choose_zchunk(g, 2);
+    A.zchunk = choose_zchunk_waves(g, 2);
     A.face = g->face;
     A.acc = accd;
     for (int l = 0; l < kMaxGradLabels; ++l) {
