@@ -12,13 +12,16 @@
 // Solver: conjugate gradients with the Jacobi preconditioner, matrix-free, to
 // an FP64 relative residual (the source sets the heating of every later step;
 // FP64 keeps the solve far below the FP32 state's resolution).  B300's FP64
-// pipe is narrow, so the iterations run in FP32 inside an FP64 defect
-// correction: each cycle solves A e = r in FP32 (reducing the FP32 residual
-// by kInnerEta, or as far as the tolerance still needs), adds e to the FP64
-// iterate x and forms the true residual r = b - A x in FP64.  A cycle that
-// gains less than a factor 2 (FP32 has stagnated at its attainable accuracy,
-// about cond(A) * 2^-24) hands over to plain FP64 conjugate gradients from
-// the current x.  The stopping rule is the FP64 one either way:
+// pipe is narrow, so the iterations run in FP32, with the residual replaced
+// by the true FP64 one every time the FP32 residual has fallen by kInnerEta
+// (CG with residual replacement, "reliable updates": van der Vorst and Ye's
+// residual replacement for Krylov methods).  At a replacement the FP32
+// correction e is added to the FP64 iterate x, r = b - A x is formed in FP64,
+// and the iteration goes on from the kept search direction with beta =
+// (r.z)_new / (r.z)_old, so it keeps its Krylov information instead of
+// restarting.  A cycle that gains less than a factor 2 (FP32 at its attainable
+// accuracy, about cond(A) * 2^-24) hands over to plain FP64 conjugate
+// gradients from the current x.  The stopping rule is the FP64 one either way:
 // ||b - A x|| <= tol ||b||.  The diagonal and its inverse are stored once (no
 // per-iteration division).  Scalars stay on the device; the host reads the
 // residual every kCheck iterations.
@@ -37,7 +40,7 @@ namespace rfa {
 namespace {
 
 constexpr int kCheck = 20;
-constexpr double kInnerEta = 1e-4;  // FP32 residual reduction per correction cycle
+constexpr double kInnerEta = 1e-2;  // FP32 residual reduction between residual replacements
 enum { CLS_FREE = 0, CLS_ELECTRODE = 1, CLS_GROUND = 2, CLS_PAD = 3 };
 // scalars: rz, alpha, beta, rr, bb
 enum { SC_RZ = 0, SC_ALPHA, SC_BETA, SC_RR, SC_BB, SC_N };
@@ -325,12 +328,13 @@ __device__ __forceinline__ float f4at(const float4 &v, int q) { return q == 0 ? 
 __device__ __forceinline__ int b4at(const uchar4 &v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
 
 // start of a cycle: r32 = r, e = 0, z = r32 / D on the free voxels, 0
-// elsewhere, and the previous direction 0 (with beta = 0 the first direction
-// is z); FP32 diagonal from the FP64 one; partials of r32.z and r32.r32 (FP32
-// per thread, FP64 per block)
+// elsewhere; FP32 diagonal from the FP64 one; partials of r32.z and r32.r32
+// (FP32 per thread, FP64 per block).  The previous direction is set to 0 at the
+// first cycle (with beta = 0 the first direction is z) and kept at a residual
+// replacement (beta = (r.z)_new / (r.z)_old continues the iteration).
 __global__ void __launch_bounds__(256) k_pot_init32(PotGrid G, const double *r, const double *Dv, float *r32,
                                                    float *e32, float *z32, float *p32, float *D32, float *iD32,
-                                                   double *part)
+                                                   int keep_direction, double *part)
 {
     float rz = 0.f, rr = 0.f;
     POT_QUADS(G)
@@ -353,7 +357,7 @@ __global__ void __launch_bounds__(256) k_pot_init32(PotGrid G, const double *r, 
         st4(r32 + i, make_float4(rv[0], rv[1], rv[2], rv[3]));
         st4(e32 + i, make_float4(0.f, 0.f, 0.f, 0.f));
         st4(z32 + i, make_float4(zv[0], zv[1], zv[2], zv[3]));
-        st4(p32 + i, make_float4(0.f, 0.f, 0.f, 0.f));
+        if (!keep_direction) st4(p32 + i, make_float4(0.f, 0.f, 0.f, 0.f));
     }
     const double a = pot_block_sum((double)rz), b = pot_block_sum((double)rr);
     if (threadIdx.x == 0) {
@@ -626,11 +630,13 @@ rfa_status potential_place(rfa_grid *g)
     float *r32 = (float *)B.p[9], *e32 = r32 + nvp, *z32 = e32 + nvp, *Ap32 = z32 + nvp;
     float *D32 = Ap32 + nvp, *iD32 = D32 + nvp, *pbuf[2] = {iD32 + nvp, iD32 + 2 * nvp};
     bool fp64_cg = false;
+    int pk = 0;     // pbuf[pk]: the previous direction (kept across replacements)
+    int cycle = 0;  // 0: the first cycle starts from direction 0
     while (rel > g->pot_tol && it < g->pot_max_iters && !fp64_cg) {
         const double eta = std::max(kInnerEta, 0.25 * g->pot_tol / rel);
-        int pk = 0;  // pbuf[pk]: the previous direction
-        k_pot_init32<<<nb, 256, 0, g->stream>>>(G, r, Dv, r32, e32, z32, pbuf[pk], D32, iD32, part);
-        k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, 2, sc);
+        k_pot_init32<<<nb, 256, 0, g->stream>>>(G, r, Dv, r32, e32, z32, pbuf[pk], D32, iD32, cycle > 0, part);
+        k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, cycle > 0 ? 1 : 2, sc);
+        ++cycle;
         if (rfa_status st = read_scalars()) return st;
         const double r0 = std::sqrt(std::fmax(host_sc[SC_RR], 0.0));
         double rin = r0;
