@@ -259,12 +259,14 @@ def _ms_between(torch, stream, fn):
     return e0.elapsed_time(e1)
 
 
-def measure_adjoint(rfa, stream):
+def measure_adjoint(rfa, stream, conduction="centre"):
     """128^3, h = 0.75 mm, straight 20 W needle, 2000 steps: recorded forward
     (sqrt(N) checkpoints) vs rfa_backward (recompute + adjoint + contractions),
-    seed = the C3 loss gradient of an arbitrary target."""
+    seed = the C3 loss gradient of an arbitrary target.  conduction="harmonic"
+    runs the conservative form (its own forward and adjoint kernels)."""
     import torch
     case = ph.adjoint_case_128()
+    case.conduction = conduction
     g = rfa.Grid.from_case(case, damage=False, cuda_stream=stream.cuda_stream)
     rfa.rfa_autotune(g.handle, None)      # the forward runs with the tuned schedule
     seed = torch.full(case.labels.shape, 1e-6, dtype=torch.float32, device="cuda")
@@ -362,6 +364,9 @@ def measure_next_rows(rfa, stream, case, g, cpu_baseline_on: bool):
         "r", rfa.rfa_place_needle_potential(g3.handle, c3.needle, sig, 20000, 1e-10)))
     g3.close()
     it, rel = res["r"]
+    adj = measure_adjoint(rfa, stream, conduction="harmonic")
+    out["conservative_adjoint"] = {k: adj[k] for k in ("workload", "grid", "time_steps", "forward_recorded_ms",
+                                                       "backward_ms", "backward_over_forward")}
     out["potential_source"] = dict(roof(54.0 * n * it, ms), ms=ms, cg_iterations=it, rel_residual=rel,
                                    ms_per_iteration=ms / max(it, 1))
     if cpu_baseline_on:

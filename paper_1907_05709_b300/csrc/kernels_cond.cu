@@ -386,75 +386,217 @@ struct CondAdjArgs {
     float *lam_out, *Lam;
     const void *ab;
     const uint8_t *label;
+    const LabelCoef *tab;          // a != 0 marks the labels whose voxels are updated
     const float *wpair, *dA, *dB;  // [kCondLabels][kCondLabels]: w, dw/dK_l, dw/dK_m
     float gw[kCondLabels];         // d b / d w_b of each label
-    int nx, ny, nz, pitch;
+    int nx, ny, nz, pitch, zchunk, face, n_labels;
     size_t plane;
     double *acc;                   // [0..7] dL/dK, [8..15] dL/dw_b
 };
 
+__device__ __forceinline__ int byte_at(uint32_t w, int q) { return (int)((w >> (8 * q)) & 0xffu); }
+
+// One adjoint step of the conservative form: lam_out = A^T lam_in, Lam +=
+// lam_in, and the contractions dL/dK (through both labels of every face of a
+// free voxel) and dL/dw_b.  A thread per quad of 4 x voxels streaming z
+// (lambda, theta and labels of planes z-1, z, z+1 in registers), x neighbours
+// by warp shuffles.  A voxel is updated by the forward step exactly when its
+// stored a is nonzero, i.e. when its label's a is nonzero and it is not a
+// Dirichlet face voxel: the voxel itself is tested on its stored a, its
+// neighbours on their label and position (no coefficient loads for them).
+// Row j of the step matrix holds w(l_j, l_i) for its neighbour i, so
+// lam_out_i = diag_i lam_i + sum over free neighbours j of w(l_j, l_i) lam_j,
+// diag_i = 1 - b_i - sum_j w(l_i, l_j) for a free i (1 otherwise).  The label
+// sums stay in registers and leave the block with one FP64 atomic per label.
 template <int PP>
-__global__ void __launch_bounds__(256) k_adjoint_cond(const CondAdjArgs A)
+__global__ void __launch_bounds__(256, 2) k_adjoint_cond(const CondAdjArgs A)
 {
+    constexpr int NL = 8;  // the backward pass admits at most 8 labels
+    const unsigned FULL = 0xffffffffu;
     __shared__ float wt[kCondLabels * kCondLabels], da[kCondLabels * kCondLabels], db[kCondLabels * kCondLabels];
-    __shared__ float sK[kCondLabels], sW[kCondLabels];
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
-    for (int k = tid; k < kCondLabels * kCondLabels; k += nthr) {
+    __shared__ uint8_t afree[kCondLabels];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int k = tid; k < kCondLabels * kCondLabels; k += blockDim.x * blockDim.y) {
         wt[k] = A.wpair[k];
         da[k] = A.dA[k];
         db[k] = A.dB[k];
     }
-    if (tid < kCondLabels) sK[tid] = sW[tid] = 0.f;
+    if (tid < kCondLabels) afree[tid] = tid < A.n_labels && A.tab[tid].a != 0.0;
     __syncthreads();
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x < A.pitch && y < A.ny) {
-        const size_t j = (size_t)z * A.plane + (size_t)y * A.pitch + x;
-        if (x >= A.nx) {
-            A.lam_out[j] = 0.f;
-        } else {
-            double ad, bd;
-            cond_ab<PP>(A.ab, j, ad, bd);
-            const bool free_j = ad != 0.0;
-            const int lj = A.label[j];
-            const float lam = A.lam_in[j], tj = A.th[j];
-            const bool in[6] = {x > 0, x + 1 < A.nx, y > 0, y + 1 < A.ny, z > 0, z + 1 < A.nz};
-            const long long off[6] = {-1, 1, -(long long)A.pitch, (long long)A.pitch, -(long long)A.plane,
-                                      (long long)A.plane};
-            float diag = 1.f, nsum = 0.f, gk_own = 0.f;
-            if (free_j) diag = 1.f - (float)bd;
+    float accK[NL], accW[NL];
 #pragma unroll
-            for (int d = 0; d < 6; ++d)
-                if (in[d]) {
-                    const size_t i = (size_t)((long long)j + off[d]);
-                    const int li = A.label[i];
-                    double ai, bi;
-                    cond_ab<PP>(A.ab, i, ai, bi);
-                    if (ai != 0.0) nsum += wt[li * kCondLabels + lj] * A.lam_in[i];  // row i of A holds w(l_i, l_j)
-                    if (free_j) {
-                        diag -= wt[lj * kCondLabels + li];
-                        const float v = lam * (A.th[i] - tj);
-                        gk_own += da[lj * kCondLabels + li] * v;
-                        if (li == lj) gk_own += db[lj * kCondLabels + li] * v;
-                        else atomicAdd(&sK[li], db[lj * kCondLabels + li] * v);
+    for (int L = 0; L < NL; ++L) accK[L] = accW[L] = 0.f;
+    auto add_label = [&](float (&acc)[NL], int lab, float v) {
+#pragma unroll
+        for (int L = 0; L < NL; ++L) acc[L] += lab == L ? v : 0.f;
+    };
+    const int lane = threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (y < A.ny) {  // whole warp (blockDim.x == 32)
+        const int x0 = 4 * (blockIdx.x * 32 + lane);
+        const bool inrow = x0 < A.pitch;
+        const int zb = blockIdx.z * A.zchunk, ze = min(A.nz, zb + A.zchunk);
+        const size_t rowoff = (size_t)y * A.pitch + x0;
+        const bool hasYm = y > 0, hasYp = y + 1 < A.ny;
+        const bool dir = A.face == RFA_FACE_DIRICHLET;
+        auto face = [&](int xx, int yy, int zz) {
+            return dir && (xx == 0 || xx == A.nx - 1 || yy == 0 || yy == A.ny - 1 || zz == 0 || zz == A.nz - 1);
+        };
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 lm = z4, lc = z4, lp = z4, tm = z4, tc = z4, tp = z4;
+        uint32_t labm = 0, labc = 0, labp = 0;
+        if (inrow) {
+            const size_t i = (size_t)zb * A.plane + rowoff;
+            lc = *reinterpret_cast<const float4 *>(A.lam_in + i);
+            tc = *reinterpret_cast<const float4 *>(A.th + i);
+            labc = *reinterpret_cast<const uint32_t *>(A.label + i);
+            if (zb > 0) {
+                lm = *reinterpret_cast<const float4 *>(A.lam_in + i - A.plane);
+                tm = *reinterpret_cast<const float4 *>(A.th + i - A.plane);
+                labm = *reinterpret_cast<const uint32_t *>(A.label + i - A.plane);
+            }
+        }
+        for (int z = zb; z < ze; ++z) {
+            const size_t i = (size_t)z * A.plane + rowoff;
+            const bool hasZm = z > 0, hasZp = z + 1 < A.nz;
+            float4 lym = z4, lyp = z4, tym = z4, typ = z4, Lc = z4;
+            uint32_t labym = 0, labyp = 0;
+            float aq[4] = {0.f, 0.f, 0.f, 0.f}, bq[4] = {0.f, 0.f, 0.f, 0.f};
+            if (inrow) {
+                lp = tp = z4;
+                labp = 0;
+                if (hasZp) {
+                    lp = *reinterpret_cast<const float4 *>(A.lam_in + i + A.plane);
+                    tp = *reinterpret_cast<const float4 *>(A.th + i + A.plane);
+                    labp = *reinterpret_cast<const uint32_t *>(A.label + i + A.plane);
+                }
+                if (hasYm) {
+                    lym = *reinterpret_cast<const float4 *>(A.lam_in + i - A.pitch);
+                    tym = *reinterpret_cast<const float4 *>(A.th + i - A.pitch);
+                    labym = *reinterpret_cast<const uint32_t *>(A.label + i - A.pitch);
+                }
+                if (hasYp) {
+                    lyp = *reinterpret_cast<const float4 *>(A.lam_in + i + A.pitch);
+                    typ = *reinterpret_cast<const float4 *>(A.th + i + A.pitch);
+                    labyp = *reinterpret_cast<const uint32_t *>(A.label + i + A.pitch);
+                }
+                mld_ab<PP, float>(A.ab, i, aq, bq);
+                Lc = *reinterpret_cast<const float4 *>(A.Lam + i);
+            }
+            // x neighbours across quads: lambda, theta, label
+            float lamL = __shfl_up_sync(FULL, lc.w, 1), lamR = __shfl_down_sync(FULL, lc.x, 1);
+            float thL = __shfl_up_sync(FULL, tc.w, 1), thR = __shfl_down_sync(FULL, tc.x, 1);
+            int labL = (int)__shfl_up_sync(FULL, labc >> 24, 1), labR = (int)__shfl_down_sync(FULL, labc & 0xffu, 1);
+            if (inrow && lane == 0 && x0 > 0) {
+                lamL = A.lam_in[i - 1];
+                thL = A.th[i - 1];
+                labL = A.label[i - 1];
+            }
+            if (inrow && lane == 31 && x0 + 4 < A.nx) {
+                lamR = A.lam_in[i + 4];
+                thR = A.th[i + 4];
+                labR = A.label[i + 4];
+            }
+            if (inrow) {
+                const float lcv[4] = {lc.x, lc.y, lc.z, lc.w}, tcv[4] = {tc.x, tc.y, tc.z, tc.w};
+                const float lmv[4] = {lm.x, lm.y, lm.z, lm.w}, tmv[4] = {tm.x, tm.y, tm.z, tm.w};
+                const float lpv[4] = {lp.x, lp.y, lp.z, lp.w}, tpv[4] = {tp.x, tp.y, tp.z, tp.w};
+                const float lymv[4] = {lym.x, lym.y, lym.z, lym.w}, tymv[4] = {tym.x, tym.y, tym.z, tym.w};
+                const float lypv[4] = {lyp.x, lyp.y, lyp.z, lyp.w}, typv[4] = {typ.x, typ.y, typ.z, typ.w};
+                const float Lcv[4] = {Lc.x, Lc.y, Lc.z, Lc.w};
+                float lo_[4], Lo_[4], gkq[4], gwq[4];
+                // only quads within a voxel of a Dirichlet face test their neighbours' position
+                const bool near_face = dir && (x0 <= 1 || x0 + 5 >= A.nx || y <= 1 || y + 2 >= A.ny || z <= 1 ||
+                                               z + 2 >= A.nz);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int x = x0 + q;
+                    const bool valid = x < A.nx;
+                    const int l = byte_at(labc, q);
+                    const float lam = lcv[q], t = tcv[q];
+                    const bool fr = valid && aq[q] != 0.f;  // the forward's own test on the stored a
+                    // neighbours in the order x-, x+, y-, y+, z-, z+
+                    const bool in[6] = {x > 0, x + 1 < A.nx, hasYm, hasYp, hasZm, hasZp};
+                    const float nl[6] = {q == 0 ? lamL : lcv[q - 1], q == 3 ? lamR : lcv[q + 1], lymv[q], lypv[q],
+                                         lmv[q], lpv[q]};
+                    const float nt[6] = {q == 0 ? thL : tcv[q - 1], q == 3 ? thR : tcv[q + 1], tymv[q], typv[q],
+                                         tmv[q], tpv[q]};
+                    const int nlab[6] = {q == 0 ? labL : byte_at(labc, q - 1), q == 3 ? labR : byte_at(labc, q + 1),
+                                         byte_at(labym, q), byte_at(labyp, q), byte_at(labm, q), byte_at(labp, q)};
+                    const int nx_[6] = {x - 1, x + 1, x, x, x, x}, ny_[6] = {y, y, y - 1, y + 1, y, y};
+                    const int nz_[6] = {z, z, z, z, z - 1, z + 1};
+                    // dL/dK: the face (i, j) of a free voxel i gives da[l_i][l_j] lam_i (theta_j -
+                    // theta_i) to label l_i and db[l_i][l_j] lam_i (theta_j - theta_i) to label
+                    // l_j; the second is collected here by the receiving voxel, so every term
+                    // lands on this voxel's own label
+                    float diag = fr ? 1.f - bq[q] : 1.f, nsum = 0.f, gk = 0.f;
+#pragma unroll
+                    for (int d = 0; d < 6; ++d) {
+                        if (!in[d]) continue;
+                        const int m = nlab[d];
+                        const bool frn = afree[m] && !(near_face && face(nx_[d], ny_[d], nz_[d]));
+                        if (frn) {
+                            nsum += wt[m * kCondLabels + l] * nl[d];
+                            gk += db[m * kCondLabels + l] * (nl[d] * (t - nt[d]));
+                        }
+                        if (fr) {
+                            diag -= wt[l * kCondLabels + m];
+                            gk += da[l * kCondLabels + m] * (lam * (nt[d] - t));
+                        }
+                    }
+                    lo_[q] = valid ? diag * lam + nsum : 0.f;
+                    Lo_[q] = valid ? Lcv[q] + lam : 0.f;
+                    gkq[q] = valid ? gk : 0.f;
+                    gwq[q] = fr ? lam * t : 0.f;
+                }
+                // label sums: once per quad where its voxels share a label
+                if (labc == (labc & 0xffu) * 0x01010101u) {
+                    add_label(accK, (int)(labc & 0xffu), (gkq[0] + gkq[1]) + (gkq[2] + gkq[3]));
+                    add_label(accW, (int)(labc & 0xffu), (gwq[0] + gwq[1]) + (gwq[2] + gwq[3]));
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        add_label(accK, byte_at(labc, q), gkq[q]);
+                        add_label(accW, byte_at(labc, q), gwq[q]);
                     }
                 }
-            A.lam_out[j] = diag * lam + nsum;
-            A.Lam[j] += lam;
-            if (free_j) {
-                atomicAdd(&sK[lj], gk_own);
-                atomicAdd(&sW[lj], lam * tj);
+                *reinterpret_cast<float4 *>(A.lam_out + i) = make_float4(lo_[0], lo_[1], lo_[2], lo_[3]);
+                *reinterpret_cast<float4 *>(A.Lam + i) = make_float4(Lo_[0], Lo_[1], Lo_[2], Lo_[3]);
             }
+            lm = lc;
+            lc = lp;
+            tm = tc;
+            tc = tp;
+            labm = labc;
+            labc = labp;
+        }
+    }
+    // block reduction of the label sums, then one FP64 atomic per label and block
+    __shared__ float sK[8][NL], sW[8][NL];
+    const int w = threadIdx.y;
+#pragma unroll
+    for (int L = 0; L < NL; ++L) {
+        float k = accK[L], v = accW[L];
+        for (int o = 16; o > 0; o >>= 1) {
+            k += __shfl_xor_sync(FULL, k, o);
+            v += __shfl_xor_sync(FULL, v, o);
+        }
+        if (lane == 0) {
+            sK[w][L] = k;
+            sW[w][L] = v;
         }
     }
     __syncthreads();
-    if (tid < 8) {  // the backward pass admits at most 8 labels (acc: [0..7] K, [8..15] w_b)
-        if (sK[tid] != 0.f) atomicAdd(&A.acc[tid], (double)sK[tid]);
-        if (sW[tid] != 0.f) atomicAdd(&A.acc[8 + tid], -(double)sW[tid] * (double)A.gw[tid]);
+    if (w == 0 && lane < NL) {
+        double k = 0.0, v = 0.0;
+        for (int j = 0; j < (int)blockDim.y; ++j) {
+            k += sK[j][lane];
+            v += sW[j][lane];
+        }
+        if (k != 0.0) atomicAdd(&A.acc[lane], k);
+        if (v != 0.0) atomicAdd(&A.acc[8 + lane], -v * (double)A.gw[lane]);
     }
 }
-
-dim3 cond_grid(const rfa_grid *g) { return dim3((unsigned)((g->pitch + 31) / 32), (unsigned)((g->ny + 7) / 8), (unsigned)g->nz); }
 
 }  // namespace
 
@@ -594,7 +736,11 @@ cudaError_t launch_adjoint_cond(rfa_grid *g, const float *lam_in, float *lam_out
     A.pitch = g->pitch;
     A.plane = g->plane;
     A.acc = acc;
-    const dim3 blk(32, 8), grd = cond_grid(g);
+    A.tab = g->d_table;
+    A.face = g->face;
+    A.n_labels = g->n_labels;
+    A.zchunk = choose_zchunk_waves(g, 2);
+    const dim3 blk(32, 8), grd = plain_grid_dims(g, A.zchunk);
     if (g->pp == RFA_PARAM_BF16) k_adjoint_cond<RFA_PARAM_BF16><<<grd, blk, 0, g->stream>>>(A);
     else if (g->pp == RFA_PARAM_F32) k_adjoint_cond<RFA_PARAM_F32><<<grd, blk, 0, g->stream>>>(A);
     else k_adjoint_cond<RFA_PARAM_F64><<<grd, blk, 0, g->stream>>>(A);
