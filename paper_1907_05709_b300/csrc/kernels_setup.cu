@@ -294,7 +294,6 @@ cudaError_t launch_source_write(rfa_grid *g, const double *partial, int npartial
 cudaError_t launch_source(rfa_grid *g)
 {
     double *partial = (double *)g->red;
-    double *W = partial + kReduceBlocks;
     // With coordinates of magnitude at most L, the FP32 squared distance is off
     // by at most ~110 u L d + 3 u d^2 <= 2.3e-5 L^2 (u = 2^-24, d <= 2 sqrt(3) L:
     // roundings of the coordinates, the projection t and the difference e).  The
