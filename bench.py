@@ -491,8 +491,8 @@ def run_ours(args):
     depth, variant = 1, 0
     if args.schedule == "auto":
         try:
-            rfa.rfa_autotune(g.handle, os.path.join(ROOT, "gpurun_out", "autotune.json")
-                             if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+            # RFA_AUTOTUNE_CACHE: optional JSON file the autotuner reads and updates
+            rfa.rfa_autotune(g.handle, os.environ.get("RFA_AUTOTUNE_CACHE") or None)
         except rfa.RfaError:
             pass
     elif args.schedule.startswith("tb"):        # tbN or tbNvV: depth N, tile variant V
