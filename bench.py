@@ -131,8 +131,8 @@ def algorithmic_bytes_per_voxel(arrhenius: bool, depth: int) -> float:
     (compensated FP32 state, BF16 coefficients): theta hi+lo read and written
     (16), packed a/b (4), source (4), latch read+write (2); with the damage
     integral its FP32 carry read and written (8) and the FP64 value read and
-    written (16) on the launches that fold the carry (every 128 steps)."""
-    fold = 16.0 * depth / 128.0
+    written (16) on the launches that fold the carry (every 256 steps)."""
+    fold = 16.0 * depth / 256.0
     return 16 + 4 + 4 + 2 + ((8 + fold) if arrhenius else 0)
 
 

@@ -33,7 +33,7 @@ constexpr unsigned kStatusTimeout = 2u;
 constexpr unsigned kStatusBadLabel = 4u;
 constexpr int kMaxSegments = 17;
 constexpr int kReduceBlocks = 592;  // 4 per SM on 148 SMs; fixed => deterministic reductions
-constexpr int kCarrySteps = 128;   // fold the FP32 damage carry into the FP64 integral every 128 steps
+constexpr int kCarrySteps = 256;   // fold the FP32 damage carry into the FP64 integral every 256 steps
 
 struct LabelCoef {
     double k, rho, c, w_b, rho_b, c_b, Q_m, T_fixed;

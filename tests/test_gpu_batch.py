@@ -52,9 +52,9 @@ def test_batch_equals_members_stepped_alone(damage, sched):
         tg, lg, og = _state(g)
         assert np.array_equal(ta, tg)
         assert np.array_equal(la, lg)
-        # the FP32 damage carry holds up to 128 steps before it is folded into FP64:
-        # runs that fold at different steps differ by <= ~128 * 2^-24 relative
-        assert np.allclose(oa, og, rtol=2e-5, atol=0)
+        # the FP32 damage carry holds up to 256 steps before it is folded into FP64:
+        # runs that fold at different steps differ by <= ~256 * 2^-24 relative
+        assert np.allclose(oa, og, rtol=3e-5, atol=0)
         assert g.steps_done == n1 + n2
     rfa.rfa_batch_destroy(b)
     for g in alone + grids:

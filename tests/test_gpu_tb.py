@@ -24,7 +24,7 @@ def test_blocked_equals_one_step(sched, dims):
     assert np.array_equal(a["T"], b["T"])
     assert np.array_equal(a["latch"], b["latch"])
     # the blocked kernel sums a block's increments in FP32 before adding them to the
-    # FP32 carry of the FP64 integral; both carries hold <= 128 steps (~128 * 2^-24)
+    # FP32 carry of the FP64 integral; both carries hold <= 256 steps (~256 * 2^-24)
     rel = np.abs(a["omega"] - b["omega"]) / np.maximum(a["omega"], 1e-300)
     assert rel.max() <= 2e-5
 
