@@ -109,3 +109,38 @@ def test_batch_rejects_unsupported_members():
         rfa.rfa_batch_create([g.handle, g.handle])
     g.close()
     g64.close()
+
+
+def test_batch64_full_configuration():
+    """The benchmark's batch as bench.py times it: 64 members on 96^3 .. 192^3
+    grids, 4000 steps, the autotuned schedule in one graph-replayed persistent
+    launch.  Sampled members (the smallest, the largest, a 9-tine umbrella)
+    equal the same member stepped alone, bit for bit; the smallest also matches
+    the FP64 oracle."""
+    cases = ph.batch_members(0, 64, 4000)
+    grids = [rfa.Grid.from_case(c, damage=False) for c in cases]
+    b = rfa.rfa_batch_create([g.handle for g in grids])
+    rfa.rfa_batch_autotune(b, None)
+    rfa.rfa_batch_step(b, 4000)
+    for g in grids:
+        g.synchronize()
+    nvox = [c.nvox for c in cases]
+    nine = [k for k, c in enumerate(cases) if c.needle.kind == ph.UMBRELLA and c.needle.tine_axial == 1]
+    sample = sorted({int(np.argmin(nvox)), int(np.argmax(nvox)), nine[0]})
+    for k in sample:
+        alone = rfa.Grid.from_case(cases[k], damage=False)
+        alone.step(4000)
+        ta, la, _ = _state(alone)
+        tb, lb, _ = _state(grids[k])
+        assert np.array_equal(ta, tb) and np.array_equal(la, lb), k
+        alone.close()
+    k = int(np.argmin(nvox))
+    g = grids[k]
+    gpu = dict(T=g.temperature(as_f64=True), theta=g.field(rfa.FIELD_THETA), omega=g.field(rfa.FIELD_OMEGA))
+    mask, counts, vols, sv = g.necrosis()
+    gpu.update(mask=mask, counts=counts, vols=vols, smooth=sv)
+    orc = run_oracle(cases[k], rfa.PARAM_BF16, 4000, damage=False)
+    compare(cases[k], gpu, orc, rfa.STATE_F32C, damage=False)
+    rfa.rfa_batch_destroy(b)
+    for g in grids:
+        g.close()
