@@ -158,8 +158,11 @@ rfa_status rfa_set_damage(rfa_grid *g, int enable, double A, double Ea, double R
  * after every step.  Asynchronous on the grid's stream.
  * record_for_backward != 0 stores sqrt(N) checkpoints so that rfa_backward can
  * differentiate the state after this call; recording is only valid when
- * every step since rfa_set_tissue was recorded.
- * Errors: RFA_E_STATE (no tissue or needle), RFA_E_INVALID (nsteps < 0).
+ * every step since rfa_set_tissue was recorded.  Checkpoint buffers come from
+ * a pool owned by the grid: a recording reuses the buffers of earlier ones and
+ * allocates only when it needs more (they are freed with the grid).
+ * Errors: RFA_E_STATE (no tissue or needle), RFA_E_INVALID (nsteps < 0),
+ * RFA_E_OOM (a checkpoint buffer could not be allocated).
  */
 rfa_status rfa_step(rfa_grid *g, int64_t nsteps, int record_for_backward);
 

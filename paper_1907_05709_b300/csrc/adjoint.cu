@@ -28,6 +28,14 @@
 namespace rfa {
 
 // ------------------------------------------------------------------ recording
+void record_reset(rfa_grid *g)
+{
+    g->rec.used = 0;
+    g->rec.valid = false;
+    g->rec.seg = 0;
+    g->rec.nsteps = 0;
+}
+
 void record_free(rfa_grid *g)
 {
     for (void *p : g->rec.ck_hi) cudaFree(p);
@@ -35,14 +43,12 @@ void record_free(rfa_grid *g)
         if (p) cudaFree(p);
     g->rec.ck_hi.clear();
     g->rec.ck_lo.clear();
-    g->rec.valid = false;
-    g->rec.seg = 0;
-    g->rec.nsteps = 0;
+    record_reset(g);
 }
 
 rfa_status record_begin(rfa_grid *g, int64_t nsteps)
 {
-    record_free(g);
+    record_reset(g);
     g->rec.seg = (int64_t)std::ceil(std::sqrt((double)nsteps));
     if (g->rec.seg < 1) g->rec.seg = 1;
     g->rec.valid = true;
@@ -52,23 +58,27 @@ rfa_status record_begin(rfa_grid *g, int64_t nsteps)
 rfa_status record_checkpoint(rfa_grid *g, int64_t step_index)
 {
     (void)step_index;
-    void *hi = nullptr, *lo = nullptr;
-    size_t bytes = g->nvp * g->state_elem();
-    if (cudaMalloc(&hi, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        set_error("checkpoint allocation failed");
-        return RFA_E_OOM;
+    const size_t bytes = g->nvp * g->state_elem();
+    if (g->rec.used == g->rec.ck_hi.size()) {  // the pool grows by one
+        void *hi = nullptr, *lo = nullptr;
+        if (cudaMalloc(&hi, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("checkpoint allocation failed");
+            return RFA_E_OOM;
+        }
+        if (g->sp == RFA_STATE_F32C && cudaMalloc(&lo, g->nvp * 4) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(hi);
+            set_error("checkpoint allocation failed");
+            return RFA_E_OOM;
+        }
+        g->rec.ck_hi.push_back(hi);
+        g->rec.ck_lo.push_back(lo);
     }
-    if (g->sp == RFA_STATE_F32C && cudaMalloc(&lo, g->nvp * 4) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(hi);
-        set_error("checkpoint allocation failed");
-        return RFA_E_OOM;
-    }
+    void *hi = g->rec.ck_hi[g->rec.used], *lo = g->rec.ck_lo[g->rec.used];
     RFA_CUDA(cudaMemcpyAsync(hi, g->th[g->cur], bytes, cudaMemcpyDeviceToDevice, g->stream));
     if (lo) RFA_CUDA(cudaMemcpyAsync(lo, g->lo[g->cur], g->nvp * 4, cudaMemcpyDeviceToDevice, g->stream));
-    g->rec.ck_hi.push_back(hi);
-    g->rec.ck_lo.push_back(lo);
+    ++g->rec.used;
     return RFA_OK;
 }
 
@@ -449,7 +459,7 @@ rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads)
         set_error("rfa_backward supports FP32 and compensated FP32 states");
         return RFA_E_UNSUPPORTED;
     }
-    if (!g->have_tissue || !g->rec.valid || g->rec.nsteps != g->steps || g->rec.ck_hi.empty()) {
+    if (!g->have_tissue || !g->rec.valid || g->rec.nsteps != g->steps || g->rec.used == 0) {
         set_error("rfa_backward needs every step since rfa_set_tissue recorded (rfa_step(..., 1))");
         return RFA_E_STATE;
     }
@@ -509,7 +519,7 @@ rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads)
     if (g->sched.tb_depth == 2 && tb_supported(g, 2, g->sched.tile_variant)) replay_variant = g->sched.tile_variant;
     else if (tb_supported(g, 2, 0)) replay_variant = 0;
     int lcur = 0;  // lambda ping-pong index holding lambda^{n+1}
-    const int64_t nck = (int64_t)g->rec.ck_hi.size();
+    const int64_t nck = (int64_t)g->rec.used;
     for (int64_t c = nck - 1; c >= 0; --c) {
         const int64_t s0 = c * seg, s1 = (s0 + seg < N) ? s0 + seg : N;
         // recompute theta^{s0} .. theta^{s1-1}; hi parts land in the segment buffer

@@ -111,8 +111,12 @@ struct Record {
     bool valid = false;        // every step since set-up was recorded
     int64_t seg = 0;           // checkpoint spacing
     int64_t nsteps = 0;        // steps recorded
-    std::vector<void *> ck_hi; // checkpoint states (hi, lo) every seg steps
+    // checkpoint states (hi, lo) every seg steps: the first `used` of a pool of
+    // buffers that later recordings reuse (freed with the grid), so recording
+    // allocates nothing once the pool is large enough
+    std::vector<void *> ck_hi;
     std::vector<void *> ck_lo;
+    size_t used = 0;
 };
 
 // Schedules of the step
@@ -270,7 +274,8 @@ cudaError_t launch_get_field(rfa_grid *g, int field, double *dst_dense_dev);
 
 // adjoint (adjoint.cu)
 rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads);
-void record_free(rfa_grid *g);
+void record_free(rfa_grid *g);   // release the checkpoint pool (grid destruction)
+void record_reset(rfa_grid *g);  // forget the recording, keep the pool
 rfa_status record_begin(rfa_grid *g, int64_t nsteps);
 rfa_status record_checkpoint(rfa_grid *g, int64_t step_index);
 

@@ -275,7 +275,7 @@ rfa_status rfa_set_tissue(rfa_grid *g, const uint8_t *labels, const rfa_tissue *
     g->steps = 0;
     g->carry_steps = 0;
     g->have_tissue = true;
-    record_free(g);
+    record_reset(g);
     RFA_CUDA(cudaMemcpyAsync(g->status_host, g->status, sizeof(unsigned), cudaMemcpyDeviceToHost, g->stream));
     RFA_CUDA(cudaStreamSynchronize(g->stream));
     if (*g->status_host & kStatusBadLabel) {
@@ -521,7 +521,7 @@ rfa_status rfa_set_state(rfa_grid *g, const void *blob, size_t n)
     RFA_CUDA(cudaMemcpyAsync(g->omega_c, p, nvp * 4, cudaMemcpyHostToDevice, g->stream));
     RFA_CUDA(cudaStreamSynchronize(g->stream));
     g->steps = hd.steps;
-    record_free(g);  // a restored state has no recorded history
+    record_reset(g);  // a restored state has no recorded history
     return RFA_OK;
 }
 
