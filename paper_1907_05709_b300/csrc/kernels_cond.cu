@@ -413,13 +413,14 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_cond(const CondAdjArgs A)
 {
     constexpr int NL = 8;  // the backward pass admits at most 8 labels
     const unsigned FULL = 0xffffffffu;
-    __shared__ float wt[kCondLabels * kCondLabels], da[kCondLabels * kCondLabels], db[kCondLabels * kCondLabels];
+    // per label pair (l, m) of a voxel and its neighbour, the four weights a face
+    // uses, in one 16-byte entry: w(l, m), dw(l, m)/dK_l, w(m, l), dw(m, l)/dK_l
+    __shared__ float4 pair[kCondLabels * kCondLabels];
     __shared__ uint8_t afree[kCondLabels];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     for (int k = tid; k < kCondLabels * kCondLabels; k += blockDim.x * blockDim.y) {
-        wt[k] = A.wpair[k];
-        da[k] = A.dA[k];
-        db[k] = A.dB[k];
+        const int l = k / kCondLabels, m = k % kCondLabels, km = m * kCondLabels + l;
+        pair[k] = make_float4(A.wpair[k], A.dA[k], A.wpair[km], A.dB[km]);
     }
     if (tid < kCondLabels) afree[tid] = tid < A.n_labels && A.tab[tid].a != 0.0;
     __syncthreads();
@@ -439,9 +440,6 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_cond(const CondAdjArgs A)
         const size_t rowoff = (size_t)y * A.pitch + x0;
         const bool hasYm = y > 0, hasYp = y + 1 < A.ny;
         const bool dir = A.face == RFA_FACE_DIRICHLET;
-        auto face = [&](int xx, int yy, int zz) {
-            return dir && (xx == 0 || xx == A.nx - 1 || yy == 0 || yy == A.ny - 1 || zz == 0 || zz == A.nz - 1);
-        };
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 lm = z4, lc = z4, lp = z4, tm = z4, tc = z4, tp = z4;
         uint32_t labm = 0, labc = 0, labp = 0;
@@ -505,9 +503,13 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_cond(const CondAdjArgs A)
                 const float lypv[4] = {lyp.x, lyp.y, lyp.z, lyp.w}, typv[4] = {typ.x, typ.y, typ.z, typ.w};
                 const float Lcv[4] = {Lc.x, Lc.y, Lc.z, Lc.w};
                 float lo_[4], Lo_[4], gkq[4], gwq[4];
-                // only quads within a voxel of a Dirichlet face test their neighbours' position
-                const bool near_face = dir && (x0 <= 1 || x0 + 5 >= A.nx || y <= 1 || y + 2 >= A.ny || z <= 1 ||
-                                               z + 2 >= A.nz);
+                // the neighbours on a Dirichlet face: the y- / y+ / z- / z+ neighbour rows
+                // are fixed for the quad; the x neighbours share the quad's row and plane
+                const bool rowface = dir && (y == 0 || y == A.ny - 1 || z == 0 || z == A.nz - 1);
+                const bool fyz[4] = {dir && (y - 1 == 0 || z == 0 || z == A.nz - 1),
+                                     dir && (y + 1 == A.ny - 1 || z == 0 || z == A.nz - 1),
+                                     dir && (z - 1 == 0 || y == 0 || y == A.ny - 1),
+                                     dir && (z + 1 == A.nz - 1 || y == 0 || y == A.ny - 1)};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int x = x0 + q;
@@ -523,8 +525,12 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_cond(const CondAdjArgs A)
                                          tmv[q], tpv[q]};
                     const int nlab[6] = {q == 0 ? labL : byte_at(labc, q - 1), q == 3 ? labR : byte_at(labc, q + 1),
                                          byte_at(labym, q), byte_at(labyp, q), byte_at(labm, q), byte_at(labp, q)};
-                    const int nx_[6] = {x - 1, x + 1, x, x, x, x}, ny_[6] = {y, y, y - 1, y + 1, y, y};
-                    const int nz_[6] = {z, z, z, z, z - 1, z + 1};
+                    const bool nface[6] = {rowface || (dir && (x - 1 == 0 || x - 1 == A.nx - 1)),
+                                           rowface || (dir && (x + 1 == 0 || x + 1 == A.nx - 1)),
+                                           fyz[0] || (dir && (x == 0 || x == A.nx - 1)),
+                                           fyz[1] || (dir && (x == 0 || x == A.nx - 1)),
+                                           fyz[2] || (dir && (x == 0 || x == A.nx - 1)),
+                                           fyz[3] || (dir && (x == 0 || x == A.nx - 1))};
                     // dL/dK: the face (i, j) of a free voxel i gives da[l_i][l_j] lam_i (theta_j -
                     // theta_i) to label l_i and db[l_i][l_j] lam_i (theta_j - theta_i) to label
                     // l_j; the second is collected here by the receiving voxel, so every term
@@ -534,14 +540,14 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_cond(const CondAdjArgs A)
                     for (int d = 0; d < 6; ++d) {
                         if (!in[d]) continue;
                         const int m = nlab[d];
-                        const bool frn = afree[m] && !(near_face && face(nx_[d], ny_[d], nz_[d]));
-                        if (frn) {
-                            nsum += wt[m * kCondLabels + l] * nl[d];
-                            gk += db[m * kCondLabels + l] * (nl[d] * (t - nt[d]));
+                        const float4 c = pair[l * kCondLabels + m];
+                        if (afree[m] && !nface[d]) {
+                            nsum += c.z * nl[d];
+                            gk += c.w * (nl[d] * (t - nt[d]));
                         }
                         if (fr) {
-                            diag -= wt[l * kCondLabels + m];
-                            gk += da[l * kCondLabels + m] * (lam * (nt[d] - t));
+                            diag -= c.x;
+                            gk += c.y * (lam * (nt[d] - t));
                         }
                     }
                     lo_[q] = valid ? diag * lam + nsum : 0.f;
