@@ -259,7 +259,7 @@ def _ms_between(torch, stream, fn):
     return e0.elapsed_time(e1)
 
 
-def measure_adjoint(rfa, stream, conduction="centre"):
+def measure_adjoint(rfa, stream, conduction="centre", cpu_baseline_on: bool = False):
     """128^3, h = 0.75 mm, straight 20 W needle, 2000 steps: recorded forward
     (sqrt(N) checkpoints) vs rfa_backward (recompute + adjoint + contractions),
     seed = the C3 loss gradient of an arbitrary target.  conduction="harmonic"
@@ -286,9 +286,21 @@ def measure_adjoint(rfa, stream, conduction="centre"):
     sched = rfa.rfa_get_schedule(g.handle)
     t_plain = _ms_between(torch, stream, lambda: g.step(case.nsteps))
     g.close()
-    return {"workload": "adjoint128", "grid": [case.nx, case.ny, case.nz], "time_steps": case.nsteps,
-            "forward_recorded_ms": t_f, "backward_ms": t_b, "forward_unrecorded_ms": t_plain,
-            "backward_over_forward": t_b / t_f, "schedule": sched}
+    res = {"workload": "adjoint128", "grid": [case.nx, case.ny, case.nz], "time_steps": case.nsteps,
+           "forward_recorded_ms": t_f, "backward_ms": t_b, "forward_unrecorded_ms": t_plain,
+           "backward_over_forward": t_b / t_f, "schedule": sched}
+    if cpu_baseline_on:
+        # the oracle's discrete adjoint beside it: 20 reverse steps of the same 128^3 case
+        import oracle
+        mo = oracle.setup(case, "f64")
+        seed_np = np.full((case.nz, case.ny, case.nx), 1e-6)
+        t0 = time.perf_counter()
+        oracle.adjoint(mo, 20, seed_np)
+        t = time.perf_counter() - t0
+        res["cpu_baseline"] = {"value": case.nvox * 20 / t / 1e9, "unit": "GVox-steps/s (backward)",
+                               "cores": os.cpu_count(), "kind": "oracle",
+                               "sample": "128^3, 20 steps of the FP64 oracle's adjoint (recompute and reverse)"}
+    return res
 
 
 def measure_next_rows(rfa, stream, case, g, cpu_baseline_on: bool):
@@ -380,7 +392,7 @@ def measure_next_rows(rfa, stream, case, g, cpu_baseline_on: bool):
     return out
 
 
-def measure_path_rows(rfa, stream, case, g, labels_dev):
+def measure_path_rows(rfa, stream, case, g, labels_dev, cpu_baseline_on: bool = True):
     """The path's steps outside the time loop at the bench's size, on the bench
     grid after its timed steps: S6, the necrosis counts and smoothed volume
     (the allocation-free entry point: device result, no host copy), against its
@@ -403,6 +415,23 @@ def measure_path_rows(rfa, stream, case, g, labels_dev):
     out["tissue_setup_and_source"] = {"ms": ms, "gvox_s": n / (ms * 1e-3) / 1e9}
     ms = _ms_between(torch, stream, lambda: [g.place_needle(case.needle) for _ in range(3)]) / 3
     out["source_place"] = {"ms": ms, "gvox_s": n / (ms * 1e-3) / 1e9}
+    if cpu_baseline_on:
+        # the oracle beside them, on a 96^3 sample of the same phantom generator
+        import oracle
+        cores = os.cpu_count()
+        sm = ph.single_needle_case(seed=1, n=96, nsteps=4)
+        t0 = time.perf_counter()
+        mo = oracle.setup(sm, "bf16")
+        t_setup = time.perf_counter() - t0
+        st = oracle.initial_state(mo)
+        oracle.run(mo, st, 4, damage=sm.damage)
+        t0 = time.perf_counter()
+        oracle.necrosis(mo, st)
+        t_nec = time.perf_counter() - t0
+        for key, t, what in (("tissue_setup_and_source", t_setup, "set-up and 1/r^4 source"),
+                             ("necrosis_reduce", t_nec, "necrosis mask, counts and smoothed volume")):
+            out[key]["cpu_baseline"] = {"value": sm.nvox / t / 1e9, "unit": "GVox/s", "cores": cores,
+                                        "kind": "oracle", "sample": f"96^3, {what}, FP64 oracle"}
     return out
 
 
@@ -588,10 +617,10 @@ def run_ours(args):
     kernels_per_step = 2 + 3 + launches_per_step + 2   # setup (2), source (3), steps, necrosis (2)
     secondary = None
     if rank == 0 and not args.no_secondary:
-        secondary = {"adjoint": measure_adjoint(rfa, stream),
+        secondary = {"adjoint": measure_adjoint(rfa, stream, cpu_baseline_on=not args.no_cpu_baseline),
                      "batched": measure_batched(rfa, stream, args),
                      "next_rows": measure_next_rows(rfa, stream, case, g, not args.no_cpu_baseline)}
-        secondary["path_rows"] = measure_path_rows(rfa, stream, case, g, labels_dev)
+        secondary["path_rows"] = measure_path_rows(rfa, stream, case, g, labels_dev, not args.no_cpu_baseline)
     if dist is not None:
         dist.barrier()
     if rank == 0:
