@@ -198,13 +198,24 @@ def cpu_baseline(case, target_s=15.0):
     sample): the per-step cost is fixed, so a few steps give the rate."""
     n, t, _, m = oracle_sample(case, target_s)
     n1, t1, _, _ = oracle_sample(case, max(2.0, target_s / 5), min_steps=1, nthreads=1, model=m)
+    # the 64^3 homogeneous case run entirely (2000 steps), all cores
+    import oracle
+    c0 = ph.homogeneous_case()
+    m0 = oracle.setup(c0, "bf16")
+    st0 = oracle.initial_state(m0)
+    t0 = time.perf_counter()
+    oracle.run(m0, st0, c0.nsteps)
+    t_c0 = time.perf_counter() - t0
     return {"value": case.nvox * n / t / 1e9, "unit": UNIT, "cores": os.cpu_count(),
             "kind": "oracle",
             "sample": f"FP64 oracle (C, OpenMP over z, {os.cpu_count()} threads), full "
                       f"{case.nx}x{case.ny}x{case.nz} phantom, {n} of {case.nsteps} time steps"
                       f"{' with Arrhenius' if case.damage.enable else ''}, set-up excluded",
             "single_thread": {"value": case.nvox * n1 / t1 / 1e9, "unit": UNIT, "cores": 1,
-                              "sample": f"the same, 1 thread, {n1} time steps"}}
+                              "sample": f"the same, 1 thread, {n1} time steps"},
+            "homogeneous64_full": {"value": c0.nvox * c0.nsteps / t_c0 / 1e9, "unit": UNIT,
+                                   "cores": os.cpu_count(),
+                                   "sample": f"64^3 homogeneous liver, all {c0.nsteps} steps"}}
 
 
 # ------------------------------------------------------------------ reference arm

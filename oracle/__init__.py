@@ -51,6 +51,14 @@ def bind(L):
     return L
 
 
+def _threads(nthreads: int) -> int:
+    """The OpenMP thread count to pass: nthreads, or every core for 0.  The
+    count is always passed explicitly because omp_set_num_threads is
+    process-wide: a one-thread call would otherwise leave later calls on one
+    thread.  Results do not depend on it (OpenMP over z only)."""
+    return int(nthreads) if nthreads and nthreads > 0 else (os.cpu_count() or 1)
+
+
 def _pd(a):
     assert a.dtype == np.float64 and a.flags.c_contiguous
     return a.ctypes.data_as(_P_D)
@@ -210,7 +218,7 @@ def run(m: Model, st: State, nsteps: int, damage=None, T_thr_C: float = 60.0,
     thr = dmg.T_thr_C if dmg is not None else T_thr_C
     _check(lib().or_run(m.nx, m.ny, m.nz, int(nsteps), _pd(m.a), _pd(m.b), _pd(m.s), _pd(m.qm),
                         _pu8(m.isfixed), _pd(st.theta), _pu8(st.latch), m.T_a, thr, en, m.dt,
-                        A, Ea, R, _pd(st.omega), _pd(st.omega_c), int(nthreads),
+                        A, Ea, R, _pd(st.omega), _pd(st.omega_c), _threads(nthreads),
                         None if m.wf is None else _pd(m.wf), int(m.alpha_perf)), "run")
     st.steps += int(nsteps)
     return st
@@ -226,7 +234,7 @@ def adjoint(m: Model, nsteps: int, lam_N: np.ndarray, nthreads: int = 0):
     _check(lib().or_adjoint(m.nx, m.ny, m.nz, int(nsteps), m.h, m.dt, _pd(m.a), _pd(m.b),
                             _pd(m.s), _pd(m.qm), _pu8(m.isfixed), _pu8(m.labels), nl, _pd(m.tab),
                             _pd(m.rhoc), _pd(m.theta0), _pd(lam), _pd(Lam), _pd(gk), _pd(gw),
-                            int(nthreads), None if m.wf is None else _pd(m.wf),
+                            _threads(nthreads), None if m.wf is None else _pd(m.wf),
                             None if m.wf is None else _pd(m.dwa),
                             None if m.wf is None else _pd(m.dwb)), "adjoint")
     g = np.zeros(4)
