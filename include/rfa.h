@@ -169,13 +169,17 @@ rfa_status rfa_step(rfa_grid *g, int64_t nsteps, int record_for_backward);
 /*
  * Copy the temperature T = theta + T_a in Celsius to dst (nx*ny*nz, x fastest)
  * as float (as_f64 = 0) or double (as_f64 = 1).  dst_is_device selects a
- * device (stream-ordered, asynchronous) or host (synchronous) destination.
- * Reports RFA_E_NONFINITE if a previous step produced a non-finite value.
+ * device (stream-ordered, asynchronous) or host (synchronous) destination;
+ * dst is caller-owned.  Reports RFA_E_NONFINITE if a previous step produced a
+ * non-finite value.  Errors: RFA_E_INVALID (null argument), RFA_E_OOM (host
+ * staging), RFA_E_NONFINITE, RFA_E_TIMEOUT (a device wait that ran out).
  */
 rfa_status rfa_get_temperature(rfa_grid *g, void *dst, int dst_is_device, int as_f64);
 
-/* Diagnostic copy of one field (RFA_FIELD_*) to host doubles, nx*ny*nz.
- * THETA is theta = T - T_a (hi + lo for the compensated state). */
+/* Diagnostic copy of one field (RFA_FIELD_*) to host doubles, nx*ny*nz (x
+ * fastest, caller-owned), synchronous.  THETA is theta = T - T_a (hi + lo for
+ * the compensated state); OMEGA is the FP64 integral plus its FP32 carry.
+ * Errors: RFA_E_INVALID (null argument, unknown field), RFA_E_OOM. */
 rfa_status rfa_get_field(rfa_grid *g, int field, double *dst_host);
 
 /*
@@ -183,7 +187,9 @@ rfa_status rfa_get_field(rfa_grid *g, int field, double *dst_host);
  * (Omega >= 1).  mask_or_null: host nx*ny*nz bytes or NULL.  counts[2] and
  * volumes_m3[2] (h^3 * count) for the two criteria; smooth_volume_m3 =
  * h^3 * sum_i sigmoid((T_i - T_thr) / smooth_width_K) on the current state.
- * Any output pointer may be NULL.  Deterministic two-pass reduction on device.
+ * Any output pointer may be NULL (host, caller-owned).  Deterministic two-pass
+ * reduction on device; synchronous.  Errors: RFA_E_INVALID (null grid,
+ * smooth_width_K <= 0), RFA_E_OOM, RFA_E_NONFINITE, RFA_E_TIMEOUT.
  */
 rfa_status rfa_necrosis_mask(rfa_grid *g, uint8_t *mask_or_null, int64_t *counts,
                              double *volumes_m3, double *smooth_volume_m3,
@@ -212,15 +218,21 @@ rfa_status rfa_necrosis_reduce_noalloc(rfa_grid *g, double smooth_width_K, void 
  * state.  grads (host, 4 + 2*n_labels doubles) receives
  *   [dL/dP, dL/dtip_x, dL/dtip_y, dL/dtip_z, dL/dk[0..L-1], dL/dw_b[0..L-1]].
  * Recomputes the trajectory from the sqrt(N) checkpoints.  Synchronous.
- * Errors: RFA_E_STATE (nothing recorded, or unrecorded steps since set-up),
- * RFA_E_UNSUPPORTED (FP64 state).
+ * Differentiates the centre and the conservative (RFA_COND_HARMONIC) forms.
+ * Errors: RFA_E_INVALID (null argument), RFA_E_STATE (nothing recorded, or
+ * unrecorded steps since set-up), RFA_E_UNSUPPORTED (FP64 state, the
+ * potential-solve source, the tissue-state perfusion coupling, more than 8
+ * labels), RFA_E_OOM (workspace).
  */
 rfa_status rfa_backward(rfa_grid *g, const float *dLdT_final_dev, double *grads);
 
 /*
  * Serialise the evolving state (theta, lo, latch, Omega and its compensation,
  * step counter) to blob.  With blob == NULL, *n receives the required size.
- * rfa_set_state restores a blob made by a grid of the same shape/precision.
+ * rfa_set_state restores a blob made by a grid of the same shape/precision
+ * (it needs rfa_set_tissue first; the restored state has no recorded history).
+ * blob is host memory owned by the caller.  Errors: RFA_E_INVALID (null
+ * argument, blob too small or from another grid), RFA_E_STATE (no tissue).
  */
 rfa_status rfa_get_state(rfa_grid *g, void *blob, size_t *n);
 rfa_status rfa_set_state(rfa_grid *g, const void *blob, size_t n);
@@ -234,6 +246,7 @@ rfa_status rfa_set_state(rfa_grid *g, const void *blob, size_t n);
  * the autotuner keeps one step per launch.
  * rfa_autotune times the candidates on a scratch copy of the grid's state and
  * keeps the fastest; cache_path (may be NULL) is a JSON file read and updated.
+ * Errors: RFA_E_INVALID (null grid, tb_depth outside 1..8), RFA_E_UNSUPPORTED.
  */
 rfa_status rfa_set_schedule(rfa_grid *g, int tb_depth, int tile_variant);
 rfa_status rfa_get_schedule(rfa_grid *g, int *tb_depth, int *tile_variant);
@@ -250,6 +263,10 @@ rfa_status rfa_autotune(rfa_grid *g, const char *cache_path);
  * block count), the remainder as one-step launches.  States are bit-identical
  * to stepping each member alone.  Device-side faults of the batched launch are
  * reported by rfa_synchronize on the first member.
+ * Errors: RFA_E_INVALID (null or repeated members, mixed streams or damage
+ * settings, nsteps < 0), RFA_E_STATE (a member without tissue),
+ * RFA_E_UNSUPPORTED (a member the blocked kernel cannot step), RFA_E_OOM,
+ * RFA_E_CUDA (tensor maps, graph).
  */
 rfa_status rfa_batch_create(rfa_grid *const *members, int n, rfa_batch **out);
 rfa_status rfa_batch_step(rfa_batch *b, int64_t nsteps);
