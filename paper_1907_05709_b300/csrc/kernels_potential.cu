@@ -47,6 +47,7 @@ enum { SC_RZ = 0, SC_ALPHA, SC_BETA, SC_RR, SC_BB, SC_N };
 
 struct PotGrid {
     const uint8_t *cls, *label;
+    const uint8_t *quni;  // per quad: 1 + the label shared by the quad and its neighbours, 0 if mixed
     const double *S;  // [kCondLabels][kCondLabels] face conductances
     int nx, ny, nz, pitch;
     size_t plane, nvp;
@@ -366,6 +367,29 @@ __global__ void __launch_bounds__(256) k_pot_init32(PotGrid G, const double *r, 
     }
 }
 
+// per quad, once per solve: 1 + the label when the quad and its six
+// neighbour sets (x edges, y and z neighbour quads) share one label, else 0
+__global__ void __launch_bounds__(256) k_pot_quni(PotGrid G, uint8_t *quni)
+{
+    POT_QUADS(G)
+    {
+        const size_t i = pot_at(G, x0, y, z);
+        const uchar4 bz = make_uchar4(0, 0, 0, 0);
+        const bool hasL = x0 > 0, hasR = x0 + 4 < G.pitch, hasYm = y > 0, hasYp = y + 1 < G.ny, hasZm = z > 0,
+                   hasZp = z + 1 < G.nz;
+        const size_t oy = G.pitch, oz = G.plane;
+        const uchar4 l4 = ldb4(G.label + i);
+        const int lL = hasL ? G.label[i - 1] : 0, lR = hasR ? G.label[i + 4] : 0;
+        const uchar4 lym = hasYm ? ldb4(G.label + i - oy) : bz, lyp = hasYp ? ldb4(G.label + i + oy) : bz;
+        const uchar4 lzm = hasZm ? ldb4(G.label + i - oz) : bz, lzp = hasZp ? ldb4(G.label + i + oz) : bz;
+        const uint32_t l0 = l4.x, rep4 = l0 * 0x01010101u;
+        auto w32 = [](const uchar4 &v) { return (uint32_t)v.x | (uint32_t)v.y << 8 | (uint32_t)v.z << 16 | (uint32_t)v.w << 24; };
+        const bool uni = w32(l4) == rep4 && (uint32_t)lL == l0 && (uint32_t)lR == l0 && w32(lym) == rep4 &&
+                         w32(lyp) == rep4 && w32(lzm) == rep4 && w32(lzp) == rep4;
+        quni[i >> 2] = uni ? (uint8_t)(l0 + 1) : 0;
+    }
+}
+
 // The search direction and the operator in one pass: p = z + beta p_prev on
 // the quad and its six neighbour points (p_prev and p are separate buffers,
 // swapped every iteration), p written for the quad, Ap = A p in FP32 (0 off
@@ -387,7 +411,8 @@ __global__ void __launch_bounds__(256) k_pot_spmv32(PotGrid G, double *sc, const
     POT_QUADS(G)
     {
         const size_t i = pot_at(G, x0, y, z);
-        const uchar4 c4 = ldb4(G.cls + i), l4 = ldb4(G.label + i);
+        const uchar4 c4 = ldb4(G.cls + i);
+        const int fl = G.quni[i >> 2];
         const float4 p4 = dir4(ld4(z32 + i), ld4(pprev + i)), D4 = ld4(D32 + i);
         const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
         const uchar4 bz = make_uchar4(0, 0, 0, 0);
@@ -395,19 +420,25 @@ __global__ void __launch_bounds__(256) k_pot_spmv32(PotGrid G, double *sc, const
                    hasZp = z + 1 < G.nz;
         const float pL = hasL ? dir(z32[i - 1], pprev[i - 1]) : 0.f;
         const float pR = hasR ? dir(z32[i + 4], pprev[i + 4]) : 0.f;
-        const int lL = hasL ? G.label[i - 1] : 0, lR = hasR ? G.label[i + 4] : 0;
         const size_t oy = G.pitch, oz = G.plane;
         const float4 pym = hasYm ? dir4(ld4(z32 + i - oy), ld4(pprev + i - oy)) : zero;
         const float4 pyp = hasYp ? dir4(ld4(z32 + i + oy), ld4(pprev + i + oy)) : zero;
         const float4 pzm = hasZm ? dir4(ld4(z32 + i - oz), ld4(pprev + i - oz)) : zero;
         const float4 pzp = hasZp ? dir4(ld4(z32 + i + oz), ld4(pprev + i + oz)) : zero;
-        const uchar4 lym = hasYm ? ldb4(G.label + i - oy) : bz, lyp = hasYp ? ldb4(G.label + i + oy) : bz;
-        const uchar4 lzm = hasZm ? ldb4(G.label + i - oz) : bz, lzp = hasZp ? ldb4(G.label + i + oz) : bz;
-        const uint32_t l0 = l4.x, rep4 = l0 * 0x01010101u;
-        auto w32 = [](const uchar4 &v) { return (uint32_t)v.x | (uint32_t)v.y << 8 | (uint32_t)v.z << 16 | (uint32_t)v.w << 24; };
-        const bool uni = w32(l4) == rep4 && (uint32_t)lL == l0 && (uint32_t)lR == l0 && w32(lym) == rep4 &&
-                         w32(lyp) == rep4 && w32(lzm) == rep4 && w32(lzp) == rep4;
-        const float su = S[l0 * (kCondLabels + 1)];
+        // labels only where the quad's neighbourhood is not of one label (the flag)
+        uchar4 l4 = bz, lym = bz, lyp = bz, lzm = bz, lzp = bz;
+        int lL = 0, lR = 0;
+        if (fl == 0) {
+            l4 = ldb4(G.label + i);
+            lL = hasL ? G.label[i - 1] : 0;
+            lR = hasR ? G.label[i + 4] : 0;
+            if (hasYm) lym = ldb4(G.label + i - oy);
+            if (hasYp) lyp = ldb4(G.label + i + oy);
+            if (hasZm) lzm = ldb4(G.label + i - oz);
+            if (hasZp) lzp = ldb4(G.label + i + oz);
+        }
+        const bool uni = fl != 0;
+        const float su = uni ? S[(fl - 1) * (kCondLabels + 1)] : 0.f;
         float out[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -580,7 +611,7 @@ rfa_status potential_place(rfa_grid *g)
         }
     const size_t nvp = g->nvp;
     struct Bufs {
-        void *p[10] = {};
+        void *p[11] = {};
         ~Bufs()
         {
             for (void *q : p)
@@ -595,7 +626,7 @@ rfa_status potential_place(rfa_grid *g)
         }
     if (cudaMalloc(&B.p[7], nvp) != cudaSuccess ||
         cudaMalloc(&B.p[8], kCondLabels * kCondLabels * 8 + SC_N * 8 + 8) != cudaSuccess ||
-        cudaMalloc(&B.p[9], 8 * nvp * sizeof(float)) != cudaSuccess) {
+        cudaMalloc(&B.p[9], 8 * nvp * sizeof(float)) != cudaSuccess || cudaMalloc(&B.p[10], nvp / 4 + 1) != cudaSuccess) {
         cudaGetLastError();
         set_error("potential solve workspace allocation failed");
         return RFA_E_OOM;
@@ -608,9 +639,11 @@ rfa_status potential_place(rfa_grid *g)
     double *part = (double *)g->red;  // 2 * kReduceBlocks doubles
     RFA_CUDA(cudaMemcpyAsync(dS, S.data(), S.size() * 8, cudaMemcpyHostToDevice, g->stream));
     RFA_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned), g->stream));
-    PotGrid G{cls, g->label, dS, g->nx, g->ny, g->nz, g->pitch, g->plane, nvp};
+    uint8_t *quni = (uint8_t *)B.p[10];
+    PotGrid G{cls, g->label, quni, dS, g->nx, g->ny, g->nz, g->pitch, g->plane, nvp};
     const unsigned nb = kReduceBlocks;
     k_pot_class<<<nb, 256, 0, g->stream>>>(g->geom, G, g->h, cls);
+    k_pot_quni<<<nb, 256, 0, g->stream>>>(G, quni);
     k_pot_init<<<nb, 256, 0, g->stream>>>(G, xv, r, zv, p, Dv, iDv, part);
     k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, 2, sc);
     RFA_CUDA(cudaGetLastError());
