@@ -228,7 +228,9 @@ rfa_status rfa_backward(rfa_grid *g, const float *dLdT_final_dev, double *grads)
 
 /*
  * Serialise the evolving state (theta, lo, latch, Omega and its compensation,
- * step counter) to blob.  With blob == NULL, *n receives the required size.
+ * step counter, steps since the last fold of the damage carry) to blob, so
+ * that a resumed run ends in the same bits as an uninterrupted one.  With
+ * blob == NULL, *n receives the required size.
  * rfa_set_state restores a blob made by a grid of the same shape/precision
  * (it needs rfa_set_tissue first; the restored state has no recorded history).
  * blob is host memory owned by the caller.  Errors: RFA_E_INVALID (null

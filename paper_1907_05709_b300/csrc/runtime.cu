@@ -459,13 +459,16 @@ rfa_status rfa_necrosis_mask(rfa_grid *g, uint8_t *mask_or_null, int64_t *counts
     return st;
 }
 
-// blob: header | theta | lo | latch | omega | omega_c
+// blob: header | theta | lo | latch | omega | omega_c.  The header keeps the
+// steps since the damage carry was last folded, so a resumed run folds at the
+// same steps as an uninterrupted one and ends in the same bits.
 struct StateHeader {
     uint64_t magic;
     int32_t nx, ny, nz, sp;
     int64_t steps;
+    int64_t carry_steps;
 };
-static const uint64_t kStateMagic = 0x3130353730394646ull;
+static const uint64_t kStateMagic = 0x3230353730394646ull;  // format 2 (with carry_steps)
 
 rfa_status rfa_get_state(rfa_grid *g, void *blob, size_t *n)
 {
@@ -475,7 +478,7 @@ rfa_status rfa_get_state(rfa_grid *g, void *blob, size_t *n)
                   (g->sp == RFA_STATE_F32C ? nvp * 4 : 0) + nvp + nvp * 8 + nvp * 4;
     if (!blob) { *n = need; return RFA_OK; }
     if (*n < need) return fail(RFA_E_INVALID, "blob too small");
-    StateHeader hd{kStateMagic, g->nx, g->ny, g->nz, g->sp, g->steps};
+    StateHeader hd{kStateMagic, g->nx, g->ny, g->nz, g->sp, g->steps, (int64_t)g->carry_steps};
     char *p = (char *)blob;
     std::memcpy(p, &hd, sizeof hd);
     p += sizeof hd;
@@ -521,6 +524,7 @@ rfa_status rfa_set_state(rfa_grid *g, const void *blob, size_t n)
     RFA_CUDA(cudaMemcpyAsync(g->omega_c, p, nvp * 4, cudaMemcpyHostToDevice, g->stream));
     RFA_CUDA(cudaStreamSynchronize(g->stream));
     g->steps = hd.steps;
+    g->carry_steps = hd.carry_steps;
     record_reset(g);  // a restored state has no recorded history
     return RFA_OK;
 }

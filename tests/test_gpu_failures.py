@@ -46,8 +46,8 @@ def test_nonfinite_state_reported():
     g = rfa.Grid.from_case(case)
     g.step(3)
     blob = bytearray(rfa.rfa_get_state(g.handle))
-    # header is 32 bytes, then theta hi (float32, padded rows of 24 voxels)
-    off = 32 + 4 * (5 * 20 * 24 + 7 * 24 + 9)
+    # header is 40 bytes, then theta hi (float32, padded rows of 24 voxels)
+    off = 40 + 4 * (5 * 20 * 24 + 7 * 24 + 9)
     blob[off:off + 4] = np.array([np.nan], np.float32).tobytes()
     rfa.rfa_set_state(g.handle, bytes(blob))
     g.step(2)
