@@ -204,7 +204,7 @@ rfa_status rfa_necrosis_mask(rfa_grid *g, uint8_t *mask_or_null, int64_t *counts
  * {int64 count_thermal, int64 count_arrhenius, double smooth_volume_m3, 0.0},
  * the same quantities rfa_necrosis_mask reports.  Asynchronous on the grid's
  * stream; calls no allocator and does not synchronise.  Scratch is one fixed
- * 128 KiB device array inside the library (4096 records, one per 65536 padded
+ * 512 KiB device array inside the library (16384 records, one per 16384 padded
  * voxels), so grids above 268,435,456 padded voxels are rejected with
  * RFA_E_INVALID.  The first call with a device current looks up that array's
  * address; make it before any stream capture.  Calls share the array: each

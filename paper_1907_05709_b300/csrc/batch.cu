@@ -82,9 +82,9 @@ rfa_status build_plan(rfa_batch *b)
         return (g->nz + zc - 1) / zc + 2 * b->depth;
     };
     std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) { return cost(x) > cost(y); });
-    // guided: the members numbered last (a quarter of them) get finer chunks, so a
+    // guided: the members numbered last (an eighth of them) get finer chunks, so a
     // time block ends on small items
-    for (int j = n - n / 4; j < n; ++j)
+    for (int j = n - n / 8; j < n; ++j)
         if (!tb_batch_member(b->members[b->order[j]], b->depth, b->variant, 32, b->hosts[b->order[j]]))
             return bfail(RFA_E_CUDA, "tensor map creation failed for a batch member");
     std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) { return cost(x) > cost(y); });

@@ -14,54 +14,36 @@
 // states interpolate in FP64.
 #include "rfa_internal.cuh"
 
+#include <algorithm>
 #include <climits>
 
 namespace rfa {
 namespace {
 
+// sample coordinate c + d (c integer voxel index, d displacement in voxels),
+// clamped to [0, n-1], without branches: i = c + floor(d); below 0 -> voxel 0,
+// at or past n-1 -> voxel n-1 (both: one voxel, step 0, weight 0), else
+// between i and i + 1 (step 1) with weight f = d - floor(d)
 template <class R>
-struct Axis {
-    int i0, i1;
+struct AxisS {
+    int i0, step;
     R f;
 };
-
-// sample coordinate c + d (c integer voxel index, d displacement in voxels),
-// clamped to [0, n-1]: i = c + floor(d); below 0 -> voxel 0, at or past n-1 ->
-// voxel n-1, else between i and i+1 with weight f = d - floor(d)
-template <class R>
-__device__ __forceinline__ Axis<R> axis_sample(int c, R d, int n)
-{
-    Axis<R> a;
-    d = fmin(fmax(d, -(R)(n + 1)), (R)(n + 1));  // also maps NaN to the low face
-    const R fl = floor(d);
-    const int i = c + (int)fl;  // |fl| <= n + 1: no overflow
-    if (i < 0) {
-        a.i0 = a.i1 = 0;
-        a.f = R(0);
-    } else if (i >= n - 1) {
-        a.i0 = a.i1 = n - 1;
-        a.f = R(0);
-    } else {
-        a.i0 = i;
-        a.i1 = i + 1;
-        a.f = d - fl;
-    }
-    return a;
-}
-
-// the same sample for FP32, without branches: a clamped axis samples one voxel
-// (step 0) with weight 0, exactly as above (i1 = i0, f = 0)
-struct AxisF {
-    int i0, step;
-    float f;
-};
-__device__ __forceinline__ AxisF axis_sample_f(int c, float d, int n, float lo, float hi)
+__device__ __forceinline__ AxisS<float> axis_sample_f(int c, float d, int n, float lo, float hi)
 {
     d = fminf(fmaxf(d, lo), hi);  // lo = -(n+1), hi = n+1; also maps NaN to the low face
     const float fl = floorf(d);
-    const int i = c + (int)fl;
+    const int i = c + (int)fl;    // |fl| <= n + 1: no overflow
     const bool in = i >= 0 && i < n - 1;
     return {min(max(i, 0), n - 1), in ? 1 : 0, in ? d - fl : 0.f};
+}
+__device__ __forceinline__ AxisS<double> axis_sample_d(int c, double d, int n)
+{
+    d = fmin(fmax(d, -(double)(n + 1)), (double)(n + 1));
+    const double fl = floor(d);
+    const int i = c + (int)fl;
+    const bool in = i >= 0 && i < n - 1;
+    return {min(max(i, 0), n - 1), in ? 1 : 0, in ? d - fl : 0.0};
 }
 
 template <class R>
@@ -82,48 +64,56 @@ __device__ __forceinline__ R trilinear_at(const R *p, I o, I dx, I dy, I dz, R f
     return lerp_(lerp_(c00, c10, fy), lerp_(c01, c11, fy), fz);
 }
 
-template <class R, class Load>
-__device__ __forceinline__ R trilinear(const Axis<R> &ax, const Axis<R> &ay, const Axis<R> &az, const Load &v)
-{
-    const R c00 = lerp_(v(ax.i0, ay.i0, az.i0), v(ax.i1, ay.i0, az.i0), ax.f);
-    const R c10 = lerp_(v(ax.i0, ay.i1, az.i0), v(ax.i1, ay.i1, az.i0), ax.f);
-    const R c01 = lerp_(v(ax.i0, ay.i0, az.i1), v(ax.i1, ay.i0, az.i1), ax.f);
-    const R c11 = lerp_(v(ax.i0, ay.i1, az.i1), v(ax.i1, ay.i1, az.i1), ax.f);
-    return lerp_(lerp_(c00, c10, ay.f), lerp_(c01, c11, ay.f), az.f);
-}
-
-// a thread per output voxel: x across the 32 lanes, y across the block's 8
-// rows, z across the grid (looping past 65535 planes); u is [3][nz][ny][nx].
-// I: the index type of the FP32 path (int where every index fits, which
-// saves the 64-bit address arithmetic)
+// a thread per output voxel and plane: x across the 32 lanes, y across the
+// block's 8 rows, z across the grid (planes z, z + gridDim.z, ...); u is
+// [3][nz][ny][nx].  The FP32 path loads the displacement of its next plane
+// before it gathers the current one, so the DRAM latency of u overlaps the
+// corner loads.  I: the index type of the FP32 path (int where every index
+// fits, which saves the 64-bit address arithmetic)
 template <int SP, class I>
 __global__ void __launch_bounds__(256) k_warp(const void *th, const float *lo, const float *u, int nx, int ny,
-                                              int nz, int pitch, size_t plane, double h, double T_a, float rh,
+                                              int nz, int pitch, size_t plane, double rhd, double T_a, float rh,
                                               float T_af, void *dst, int as_f64)
 {
     const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
     if (x >= nx || y >= ny) return;
     const I n = (I)nx * ny * nz;
-    const float lx = -(float)(nx + 1), hx = (float)(nx + 1), ly = -(float)(ny + 1), hy = (float)(ny + 1);
-    const float lz = -(float)(nz + 1), hz = (float)(nz + 1);
-    for (int z = blockIdx.z; z < nz; z += gridDim.z) {
-        const I j = ((I)z * ny + y) * nx + x;
-        if (SP == RFA_STATE_F64) {
-            const Axis<double> ax = axis_sample<double>(x, (double)u[j] / h, nx);
-            const Axis<double> ay = axis_sample<double>(y, (double)u[j + n] / h, ny);
-            const Axis<double> az = axis_sample<double>(z, (double)u[j + 2 * n] / h, nz);
-            const double *t = (const double *)th;
-            const double T = trilinear<double>(ax, ay, az, [&](int i, int k, int l) {
-                                 return t[(size_t)l * plane + (size_t)k * pitch + i];
-                             }) + T_a;
+    if constexpr (SP == RFA_STATE_F64) {
+        for (int z = blockIdx.z; z < nz; z += gridDim.z) {
+            const I j = ((I)z * ny + y) * nx + x;
+            // displacement in voxels: u times 1/h in FP64 (within an ulp of u/h)
+            const AxisS<double> ax = axis_sample_d(x, (double)__ldg(u + j) * rhd, nx);
+            const AxisS<double> ay = axis_sample_d(y, (double)__ldg(u + j + n) * rhd, ny);
+            const AxisS<double> az = axis_sample_d(z, (double)__ldg(u + j + 2 * n) * rhd, nz);
+            const size_t o = (size_t)az.i0 * plane + (size_t)ay.i0 * (size_t)pitch + ax.i0;
+            const size_t dx = ax.step, dy = ay.step ? (size_t)pitch : 0, dz = az.step ? plane : 0;
+            const double T = trilinear_at<double, size_t>((const double *)th, o, dx, dy, dz, ax.f, ay.f, az.f) + T_a;
             if (as_f64) ((double *)dst)[j] = T;
             else ((float *)dst)[j] = (float)T;
-        } else {
+        }
+    } else {
+        const float lx = -(float)(nx + 1), hx = (float)(nx + 1), ly = -(float)(ny + 1), hy = (float)(ny + 1);
+        const float lz = -(float)(nz + 1), hz = (float)(nz + 1);
+        const I pstep = (I)gridDim.z * ny * nx;  // index step between this thread's planes
+        int z = blockIdx.z;
+        if (z >= nz) return;
+        I j = ((I)z * ny + y) * nx + x;
+        float u0 = __ldg(u + j), u1 = __ldg(u + j + n), u2 = __ldg(u + j + 2 * n);
+        for (;;) {
+            const int zn = z + gridDim.z;
+            const bool more = zn < nz;
+            const I jn = j + pstep;
+            float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+            if (more) {
+                v0 = __ldg(u + jn);
+                v1 = __ldg(u + jn + n);
+                v2 = __ldg(u + jn + 2 * n);
+            }
             // displacement in voxels: u * rh with rh = 1/h rounded to FP32 on the
             // host (within 2 ulp of u/h: ~2e-7 relative)
-            const AxisF ax = axis_sample_f(x, __fmul_rn(__ldg(u + j), rh), nx, lx, hx);
-            const AxisF ay = axis_sample_f(y, __fmul_rn(__ldg(u + j + n), rh), ny, ly, hy);
-            const AxisF az = axis_sample_f(z, __fmul_rn(__ldg(u + j + 2 * n), rh), nz, lz, hz);
+            const AxisS<float> ax = axis_sample_f(x, __fmul_rn(u0, rh), nx, lx, hx);
+            const AxisS<float> ay = axis_sample_f(y, __fmul_rn(u1, rh), ny, ly, hy);
+            const AxisS<float> az = axis_sample_f(z, __fmul_rn(u2, rh), nz, lz, hz);
             const I o = (I)az.i0 * (I)plane + (I)ay.i0 * (I)pitch + ax.i0;
             const I dx = ax.step, dy = ay.step ? (I)pitch : I(0), dz = az.step ? (I)plane : I(0);
             const float vh = trilinear_at<float, I>((const float *)th, o, dx, dy, dz, ax.f, ay.f, az.f);
@@ -134,6 +124,12 @@ __global__ void __launch_bounds__(256) k_warp(const void *th, const float *lo, c
             if (SP == RFA_STATE_F32C && as_f64) vl = trilinear_at<float, I>(lo, o, dx, dy, dz, ax.f, ay.f, az.f);
             if (as_f64) ((double *)dst)[j] = ((double)vh + (double)vl) + T_a;
             else ((float *)dst)[j] = __fadd_rn(__fadd_rn(vh, vl), T_af);
+            if (!more) break;
+            z = zn;
+            j = jn;
+            u0 = v0;
+            u1 = v1;
+            u2 = v2;
         }
     }
 }
@@ -155,13 +151,22 @@ extern "C" rfa_status rfa_warp_temperature(rfa_grid *g, const float *u_inv_dev, 
     }
     const void *th = g->th[g->cur];
     const float *lo = (const float *)g->lo[g->cur];
-    const float rh = (float)(1.0 / g->h), T_af = (float)g->T_a;
-    const dim3 blk(32, 8), grd((g->nx + 31) / 32, (g->ny + 7) / 8, g->nz < 65535 ? g->nz : 65535);
+    const double rhd = 1.0 / g->h;
+    const float rh = (float)rhd, T_af = (float)g->T_a;
+    // planes per thread: about four where the grid still has four waves of
+    // blocks at 8 blocks per SM (the FP32 path prefetches the next plane's u)
+    const int bxy = ((g->nx + 31) / 32) * ((g->ny + 7) / 8);
+    const int waves4 = 4 * 8 * 148;
+    int gz = (g->nz + 3) / 4;
+    if ((long long)gz * bxy < waves4) gz = (int)std::min<long long>(g->nz, (waves4 + bxy - 1) / bxy);
+    if (g->sp == RFA_STATE_F64) gz = g->nz;
+    gz = std::min(gz, 65535);
+    const dim3 blk(32, 8), grd((g->nx + 31) / 32, (g->ny + 7) / 8, gz);
     // 32-bit indices where u (3 nx ny nz values) and the padded state fit
     const size_t nvox = (size_t)g->nx * g->ny * g->nz;
     const bool idx32 = 3 * nvox <= (size_t)INT_MAX && g->nvp <= (size_t)INT_MAX;
 #define WARP_ARGS                                                                                                  \
-    th, lo, u_inv_dev, g->nx, g->ny, g->nz, g->pitch, g->plane, g->h, g->T_a, rh, T_af, dst_dev, as_f64
+    th, lo, u_inv_dev, g->nx, g->ny, g->nz, g->pitch, g->plane, rhd, g->T_a, rh, T_af, dst_dev, as_f64
     if (g->sp == RFA_STATE_F64) k_warp<RFA_STATE_F64, size_t><<<grd, blk, 0, g->stream>>>(WARP_ARGS);
     else if (g->sp == RFA_STATE_F32C && idx32) k_warp<RFA_STATE_F32C, int><<<grd, blk, 0, g->stream>>>(WARP_ARGS);
     else if (g->sp == RFA_STATE_F32C) k_warp<RFA_STATE_F32C, size_t><<<grd, blk, 0, g->stream>>>(WARP_ARGS);

@@ -11,13 +11,15 @@
 //
 // How: the per-block partial sums of the two-pass reduction live in one
 // file-scope device array of fixed size (kNoAllocRecords records of 32 bytes,
-// 128 KiB), which every GPU that loads the library holds until the process
+// 512 KiB), which every GPU that loads the library holds until the process
 // exits.  Host code must not use the array's name as a device pointer; its
 // device address is looked up once per device with cudaGetSymbolAddress, on
 // the first call made with that device current.
 //
-// Limits: one record per 65536 padded voxels, so grids of more than
-// kNoAllocRecords * 65536 padded voxels (268,435,456; e.g. 640^3) are rejected.
+// Limits: one record (and one block) per 16384 padded voxels, so grids of
+// more than kNoAllocRecords * 16384 padded voxels (268,435,456; e.g. 640^3)
+// are rejected.  Records of 16384 voxels give a 256^3 grid 1024 blocks, about
+// seven per SM, so the streaming loads have enough warps in flight.
 // Every call shares the array: each call overwrites all the records it later
 // reads, so nothing has to be cleared, but calls whose work overlaps on the GPU
 // (different streams, or different host threads) race on the records.
@@ -30,8 +32,8 @@ namespace rfa {
 
 namespace {
 
-constexpr int kNoAllocRecords = 4096;
-constexpr size_t kNoAllocVoxelsPerRecord = 65536;
+constexpr int kNoAllocRecords = 16384;
+constexpr size_t kNoAllocVoxelsPerRecord = 16384;
 
 struct NaRecord {
     unsigned long long n_thermal, n_arrh;
@@ -58,7 +60,7 @@ static __device__ __align__(256) NaRecord g_noalloc_scratch[kNoAllocRecords];
 std::mutex g_na_mu;
 void *g_na_ptr[64] = {};  // device address of the scratch array, per device ordinal
 
-// per-record partials over padded voxels [65536 r, 65536 (r + 1)): thermal
+// per-record partials over padded voxels [16384 r, 16384 (r + 1)): thermal
 // latch, Arrhenius (Omega + carry >= 1), smoothed sigmoid sum, in the quads of
 // rfa_necrosis_mask (4 x voxels from a multiple of 4: the same FP32 quad sums;
 // records start at multiples of 4 and the padded pitch is one).  The grid
@@ -130,7 +132,7 @@ extern "C" rfa_status rfa_necrosis_reduce_noalloc(rfa_grid *g, double smooth_wid
     const size_t nrec = (g->nvp + kNoAllocVoxelsPerRecord - 1) / kNoAllocVoxelsPerRecord;
     if (nrec > (size_t)kNoAllocRecords) {
         set_error("grid too large for rfa_necrosis_reduce_noalloc: at most 268435456 padded voxels "
-                  "(4096 scratch records of 65536 voxels)");
+                  "(16384 scratch records of 16384 voxels)");
         return RFA_E_INVALID;
     }
     int dev = 0;
