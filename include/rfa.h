@@ -304,7 +304,8 @@ rfa_status rfa_set_perfusion_coupling(rfa_grid *g, int mode);
  * dissipation split between its voxels) is scaled so that the free voxels
  * receive power_W, and written to the source field like rfa_place_needle.
  *   sigma_S_per_m : host, n_sigma = number of labels, electrical conductivity.
- *   max_iters, tol: Jacobi-preconditioned conjugate gradients stop when the
+ *   max_iters, tol: preconditioned conjugate gradients (the preconditioner is
+ *                   chosen by rfa_set_potential_preconditioner) stop when the
  *                   FP64 residual ||b - A x|| <= tol ||b|| or after max_iters
  *                   iterations.  The iterations run in FP32 with residual
  *                   replacement: whenever the FP32 residual has fallen 100x,
@@ -323,6 +324,27 @@ rfa_status rfa_set_perfusion_coupling(rfa_grid *g, int mode);
 rfa_status rfa_place_needle_potential(rfa_grid *g, const rfa_needle *needle, const double *sigma_S_per_m,
                                       int n_sigma, int max_iters, double tol, int *iters_out,
                                       double *rel_residual_out);
+
+/*
+ * Preconditioner of the potential solve's FP32 iterations (the FP64 hand-over
+ * always uses Jacobi).  Linear solves of this kind are the standard numerical
+ * step behind the resistive source of Eq. 2675-eq1_Linte; the paper names no
+ * solver.
+ *   RFA_PRECOND_MULTIGRID (default): one symmetric V-cycle per iteration --
+ *     coarse levels of 2x2x2 aggregated cells with Galerkin operators (7-point:
+ *     summed face conductances), two damped-Jacobi sweeps (weight 0.8) before
+ *     and after each coarse correction, and the exact inverse of the coarsest
+ *     level (at most 128 cells, FP64 Cholesky on the host once per solve).
+ *     Grids of at most 128 voxels, or a coarsest matrix that is not positive
+ *     definite, fall back to Jacobi.  Device workspace: about 10/7 FP32 values
+ *     per voxel for the levels plus two FP32 fine vectors.
+ *   RFA_PRECOND_JACOBI: the inverse diagonal.
+ * Takes effect at the next potential solve (rfa_place_needle_potential, or
+ * rfa_set_tissue with that source in use).  Errors: RFA_E_INVALID (null grid,
+ * unknown mode).
+ */
+enum { RFA_PRECOND_MULTIGRID = 0, RFA_PRECOND_JACOBI = 1 };
+rfa_status rfa_set_potential_preconditioner(rfa_grid *g, int mode);
 
 /*
  * Conduction form.  RFA_COND_CENTRE (default): K taken at the voxel,

@@ -34,7 +34,8 @@ EXPORTED = ("rfa_create_grid", "rfa_destroy_grid", "rfa_set_tissue", "rfa_place_
             "rfa_batch_step", "rfa_batch_destroy", "rfa_synchronize", "rfa_steps_done",
             "rfa_last_error", "rfa_necrosis_reduce_noalloc", "rfa_batch_autotune",
             "rfa_batch_get_schedule", "rfa_selftest_wait_timeout", "rfa_warp_temperature",
-            "rfa_set_conduction", "rfa_place_needle_potential", "rfa_set_perfusion_coupling")
+            "rfa_set_conduction", "rfa_place_needle_potential", "rfa_set_perfusion_coupling",
+            "rfa_set_potential_preconditioner")
 
 
 class RfaError(RuntimeError):
@@ -99,6 +100,7 @@ def lib():
         "rfa_warp_temperature": [P, P, P, I],
         "rfa_set_conduction": [P, I],
         "rfa_set_perfusion_coupling": [P, I],
+        "rfa_set_potential_preconditioner": [P, I],
         "rfa_place_needle_potential": [P, ctypes.POINTER(rfa_needle), ctypes.POINTER(D), I, I, D, ctypes.POINTER(I),
                                        ctypes.POINTER(D)],
     }
@@ -201,6 +203,13 @@ def rfa_place_needle_potential(g, needle, sigma, max_iters: int = 20000, tol: fl
                                             len(s), int(max_iters), float(tol), ctypes.byref(it),
                                             ctypes.byref(res)), "rfa_place_needle_potential")
     return it.value, res.value
+
+
+PRECOND_MULTIGRID, PRECOND_JACOBI = 0, 1
+
+
+def rfa_set_potential_preconditioner(g, mode: int):
+    _check(lib().rfa_set_potential_preconditioner(g, int(mode)), "rfa_set_potential_preconditioner")
 
 
 def rfa_set_damage(g, enable=1, A=7.39e39, Ea=2.577e5, R=8.31, T_thr_C=60.0):

@@ -19,9 +19,10 @@
 // correction e is added to the FP64 iterate x, r = b - A x is formed in FP64,
 // and the iteration goes on from the kept search direction with beta =
 // (r.z)_new / (r.z)_old, so it keeps its Krylov information instead of
-// restarting.  A cycle that gains less than a factor 2 (FP32 at its attainable
-// accuracy, about cond(A) * 2^-24) hands over to plain FP64 conjugate
-// gradients from the current x.  The stopping rule is the FP64 one either way:
+// restarting.  A cycle also ends when its FP32 residual has made no new 1 %
+// low for kFlatChecks reads (FP32 stagnation).  A cycle that gains less than a
+// factor 2 (FP32 at its attainable accuracy, about cond(A) * 2^-24) hands over
+// to plain FP64 conjugate gradients from the current x.  The stopping rule is the FP64 one either way:
 // ||b - A x|| <= tol ||b||.  The diagonal and its inverse are stored once (no
 // per-iteration division).  Scalars stay on the device; the host reads the
 // residual every kCheck iterations.
@@ -32,6 +33,7 @@
 // the needle power P, exactly like the 1/r^4 weights (launch_source_write).
 #include "rfa_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -39,7 +41,9 @@ namespace rfa {
 
 namespace {
 
-constexpr int kCheck = 20;
+constexpr int kCheck = 20;       // Jacobi iterations between host reads of the residual
+constexpr int kCheckMg = 4;      // multigrid iterations between host reads (each costs several Jacobi ones)
+constexpr int kFlatChecks = 10;  // a cycle ends early after this many reads without a 1 % lower FP32 residual
 constexpr double kInnerEta = 1e-2;  // FP32 residual reduction between residual replacements
 enum { CLS_FREE = 0, CLS_ELECTRODE = 1, CLS_GROUND = 2, CLS_PAD = 3 };
 // scalars: rz, alpha, beta, rr, bb
@@ -184,22 +188,32 @@ __global__ void __launch_bounds__(256) k_pot_spmv(PotGrid G, const double *Dv, c
 
 // the scalar steps from the summed partials a (and b): which = 0 -> alpha =
 // rz / a; 1 -> beta = a / rz, rz = a, rr = b; 2 -> a start: rz = a, rr = b
-// (and b.b), beta = 0; 3 -> rr = a
+// (and b.b), beta = 0; 3 -> rr = a; 4 -> beta = a / rz, rz = a; 5 -> a start
+// from r.z alone: rz = a, beta = 0; 6 -> rr = b
+enum { SCW_ALPHA = 0, SCW_BETA_RR, SCW_START, SCW_RR, SCW_BETA, SCW_START_RZ, SCW_RR_B };
 __device__ void pot_scalars_apply(int which, double a, double b, double *sc)
 {
-    if (which == 0) {
+    if (which == SCW_ALPHA) {
         sc[SC_ALPHA] = a != 0.0 ? sc[SC_RZ] / a : 0.0;
-    } else if (which == 1) {
+    } else if (which == SCW_BETA_RR) {
         sc[SC_BETA] = sc[SC_RZ] != 0.0 ? a / sc[SC_RZ] : 0.0;
         sc[SC_RZ] = a;
         sc[SC_RR] = b;
-    } else if (which == 2) {
+    } else if (which == SCW_START) {
         sc[SC_RZ] = a;
         sc[SC_BB] = b;
         sc[SC_RR] = b;
         sc[SC_BETA] = 0.0;
-    } else {
+    } else if (which == SCW_RR) {
         sc[SC_RR] = a;
+    } else if (which == SCW_BETA) {
+        sc[SC_BETA] = sc[SC_RZ] != 0.0 ? a / sc[SC_RZ] : 0.0;
+        sc[SC_RZ] = a;
+    } else if (which == SCW_START_RZ) {
+        sc[SC_RZ] = a;
+        sc[SC_BETA] = 0.0;
+    } else {
+        sc[SC_RR] = b;
     }
 }
 
@@ -224,7 +238,7 @@ __device__ void pot_sum_partials(const double *part, int nblk, bool pairs, doubl
 __global__ void k_pot_scalars(const double *part, int nblk, int which, double *sc)
 {
     double a, b;
-    pot_sum_partials(part, nblk, which == 1 || which == 2, a, b);
+    pot_sum_partials(part, nblk, which == SCW_BETA_RR || which == SCW_START || which == SCW_RR_B, a, b);
     if (threadIdx.x == 0) pot_scalars_apply(which, a, b, sc);
 }
 
@@ -530,6 +544,370 @@ __global__ void __launch_bounds__(256) k_pot_correct(PotGrid G, const float *e32
     }
 }
 
+// ---- multigrid preconditioner (FP32)
+//
+// z = M r for the FP32 conjugate gradients: one symmetric V-cycle of
+// unsmoothed aggregation.  Level l+1 has a cell per 2 x 2 x 2 cells of level l
+// (a grid's odd last cell pairs with nothing); prolongation P copies a cell's
+// value to its free children, restriction is P^T (the children's sum), and the
+// coarse operator is the Galerkin product P^T A P, which for these aggregates
+// is again a 7-point operator: the conductance between two cells is the sum
+// of the fine face conductances between their free children, and the
+// diagonal is that sum over the cell's six faces plus the couplings of its
+// free children to fixed voxels (G, kept separately so every diagonal is a
+// sum of positive terms).  Smoother: damped Jacobi, kMgNu sweeps before and
+// after the coarse correction (the first from zero); the coarsest level
+// (at most kMgCoarsest cells) applies its exact inverse, formed once per
+// solve on the host by Cholesky in FP64.  Same sweeps before and after, a
+// symmetric smoother and an exact coarsest solve make M symmetric positive
+// definite, as conjugate gradients need.  Every vector stays 0 off the free
+// set (the diagonal there is 0, so Jacobi and the prolongation leave it).
+// The coarse correction is scaled by kMgGamma = 1.5 (piecewise-constant
+// prolongation undershoots smooth errors; any positive scale keeps M symmetric
+// positive definite).
+constexpr int kMgCoarsest = 128;
+constexpr float kMgOmega = 0.8f;
+constexpr int kMgNu = 2;
+constexpr float kMgGamma = 1.5f;
+
+struct MgLevel {
+    int nx, ny, nz, n;
+    float *D, *iD, *Wx, *Wy, *Wz, *G;  // operator: diagonal, its inverse, +x/+y/+z conductances, fixed couplings
+    float *b, *x, *t, *r;              // right side, two iterates, residual
+};
+
+// A v on a quad of the fine grid (0 off the free set; v is 0 there)
+__device__ __forceinline__ float4 pot_av4(const PotGrid &G, const float *S, const float *v, const float *D32,
+                                          size_t i, int x0, int y, int z, float4 &v4)
+{
+    const uchar4 c4 = ldb4(G.cls + i);
+    const int fl = G.quni[i >> 2];
+    v4 = ld4(v + i);
+    const float4 D4 = ld4(D32 + i);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const uchar4 bz = make_uchar4(0, 0, 0, 0);
+    const bool hasL = x0 > 0, hasR = x0 + 4 < G.pitch, hasYm = y > 0, hasYp = y + 1 < G.ny, hasZm = z > 0,
+               hasZp = z + 1 < G.nz;
+    const size_t oy = G.pitch, oz = G.plane;
+    const float pL = hasL ? v[i - 1] : 0.f, pR = hasR ? v[i + 4] : 0.f;
+    const float4 pym = hasYm ? ld4(v + i - oy) : zero, pyp = hasYp ? ld4(v + i + oy) : zero;
+    const float4 pzm = hasZm ? ld4(v + i - oz) : zero, pzp = hasZp ? ld4(v + i + oz) : zero;
+    uchar4 l4 = bz, lym = bz, lyp = bz, lzm = bz, lzp = bz;
+    int lL = 0, lR = 0;
+    if (fl == 0) {
+        l4 = ldb4(G.label + i);
+        lL = hasL ? G.label[i - 1] : 0;
+        lR = hasR ? G.label[i + 4] : 0;
+        if (hasYm) lym = ldb4(G.label + i - oy);
+        if (hasYp) lyp = ldb4(G.label + i + oy);
+        if (hasZm) lzm = ldb4(G.label + i - oz);
+        if (hasZp) lzp = ldb4(G.label + i + oz);
+    }
+    const bool uni = fl != 0;
+    const float su = uni ? S[(fl - 1) * (kCondLabels + 1)] : 0.f;
+    float out[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float pq = f4at(v4, q);
+        const float nb[6] = {q == 0 ? pL : f4at(v4, q - 1), q == 3 ? pR : f4at(v4, q + 1), f4at(pym, q),
+                             f4at(pyp, q), f4at(pzm, q), f4at(pzp, q)};
+        float w[6];
+        if (uni) {
+#pragma unroll
+            for (int d = 0; d < 6; ++d) w[d] = su;
+        } else {
+            const int l = b4at(l4, q);
+            const int ln[6] = {q == 0 ? lL : b4at(l4, q - 1), q == 3 ? lR : b4at(l4, q + 1), b4at(lym, q),
+                               b4at(lyp, q), b4at(lzm, q), b4at(lzp, q)};
+#pragma unroll
+            for (int d = 0; d < 6; ++d) w[d] = S[l * kCondLabels + ln[d]];
+        }
+        float a = f4at(D4, q) * pq;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) a = fmaf(-w[d], nb[d], a);
+        out[q] = b4at(c4, q) == CLS_FREE ? a : 0.f;
+    }
+    return make_float4(out[0], out[1], out[2], out[3]);
+}
+
+// fine level: x = omega b / D (the first sweep, from zero)
+__global__ void __launch_bounds__(256) k_mg0_first(PotGrid G, const float *iD32, const float *b, float *x)
+{
+    POT_QUADS(G)
+    {
+        const size_t i = pot_at(G, x0, y, z);
+        const float4 b4 = ld4(b + i), d4 = ld4(iD32 + i);
+        st4(x + i, make_float4(kMgOmega * d4.x * b4.x, kMgOmega * d4.y * b4.y, kMgOmega * d4.z * b4.z,
+                               kMgOmega * d4.w * b4.w));
+    }
+}
+
+// fine level: out = in + omega (b - A in) / D (RESID: out = b - A in)
+template <bool RESID>
+__global__ void __launch_bounds__(256) k_mg0_sweep(PotGrid G, const float *D32, const float *iD32, const float *b,
+                                                  const float *in, float *out)
+{
+    __shared__ float S[kCondLabels * kCondLabels];
+    pot_table32(G, S);
+    POT_QUADS(G)
+    {
+        const size_t i = pot_at(G, x0, y, z);
+        float4 v4;
+        const float4 a4 = pot_av4(G, S, in, D32, i, x0, y, z, v4);
+        const float4 b4 = ld4(b + i);
+        const float4 r4 = make_float4(b4.x - a4.x, b4.y - a4.y, b4.z - a4.z, b4.w - a4.w);
+        if (RESID) {
+            st4(out + i, r4);
+        } else {
+            const float4 d4 = ld4(iD32 + i);
+            st4(out + i, make_float4(fmaf(kMgOmega * d4.x, r4.x, v4.x), fmaf(kMgOmega * d4.y, r4.y, v4.y),
+                                     fmaf(kMgOmega * d4.z, r4.z, v4.z), fmaf(kMgOmega * d4.w, r4.w, v4.w)));
+        }
+    }
+}
+
+// fine level: coarse right side bc = P^T r (sum of the up to 8 fine children)
+__global__ void __launch_bounds__(256) k_mg0_restrict(PotGrid G, const float *r, MgLevel C, float *bc)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C.n; c += gridDim.x * blockDim.x) {
+        const int X = c % C.nx, Y = (c / C.nx) % C.ny, Z = c / (C.nx * C.ny);
+        float s = 0.f;
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int x = 2 * X + dx, y = 2 * Y + dy, z = 2 * Z + dz;
+                    if (x < G.nx && y < G.ny && z < G.nz) s += r[pot_at(G, x, y, z)];
+                }
+        bc[c] = s;
+    }
+}
+
+// fine level: x += gamma P xc on the free voxels (those with a nonzero diagonal)
+__global__ void __launch_bounds__(256) k_mg0_prolong(PotGrid G, const float *iD32, MgLevel C, const float *xc,
+                                                    float *x)
+{
+    POT_QUADS(G)
+    {
+        const size_t i = pot_at(G, x0, y, z);
+        const float4 d4 = ld4(iD32 + i);
+        float4 x4 = ld4(x + i);
+        const size_t cb = ((size_t)(z >> 1) * C.ny + (y >> 1)) * C.nx;
+        const int X0 = x0 >> 1;  // children x0, x0+1 of cell X0; x0+2, x0+3 of X0+1
+        if (d4.x > 0.f) x4.x = fmaf(kMgGamma, xc[cb + X0], x4.x);
+        if (d4.y > 0.f) x4.y = fmaf(kMgGamma, xc[cb + X0], x4.y);
+        if (d4.z > 0.f) x4.z = fmaf(kMgGamma, xc[cb + X0 + 1], x4.z);
+        if (d4.w > 0.f) x4.w = fmaf(kMgGamma, xc[cb + X0 + 1], x4.w);
+        st4(x + i, x4);
+    }
+}
+
+// A v at cell c of a coarse level
+__device__ __forceinline__ float mg_av(const MgLevel &L, const float *v, int c, int X, int Y, int Z)
+{
+    const int sy = L.nx, sz = L.nx * L.ny;
+    float a = L.D[c] * v[c];
+    if (X > 0) a = fmaf(-L.Wx[c - 1], v[c - 1], a);
+    if (X + 1 < L.nx) a = fmaf(-L.Wx[c], v[c + 1], a);
+    if (Y > 0) a = fmaf(-L.Wy[c - sy], v[c - sy], a);
+    if (Y + 1 < L.ny) a = fmaf(-L.Wy[c], v[c + sy], a);
+    if (Z > 0) a = fmaf(-L.Wz[c - sz], v[c - sz], a);
+    if (Z + 1 < L.nz) a = fmaf(-L.Wz[c], v[c + sz], a);
+    return a;
+}
+
+#define MG_CELLS(L)                                                                                           \
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x, X, Y, Z; c < (L).n; c += gridDim.x * blockDim.x)     \
+        if ((X = c % (L).nx), (Y = (c / (L).nx) % (L).ny), (Z = c / ((L).nx * (L).ny)), true)
+
+// coarse level: x = omega b / D
+__global__ void __launch_bounds__(256) k_mg_first(MgLevel L, const float *b, float *x)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < L.n; c += gridDim.x * blockDim.x)
+        x[c] = kMgOmega * L.iD[c] * b[c];
+}
+
+// coarse level: out = in + omega (b - A in) / D (RESID: out = b - A in)
+template <bool RESID>
+__global__ void __launch_bounds__(256) k_mg_sweep(MgLevel L, const float *b, const float *in, float *out)
+{
+    MG_CELLS(L)
+    {
+        const float r = b[c] - mg_av(L, in, c, X, Y, Z);
+        out[c] = RESID ? r : fmaf(kMgOmega * L.iD[c], r, in[c]);
+    }
+}
+
+// coarse level l -> l+1: bc = P^T r
+__global__ void __launch_bounds__(256) k_mg_restrict(MgLevel F, const float *r, MgLevel C, float *bc)
+{
+    MG_CELLS(C)
+    {
+        float s = 0.f;
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int x = 2 * X + dx, y = 2 * Y + dy, z = 2 * Z + dz;
+                    if (x < F.nx && y < F.ny && z < F.nz) s += r[(z * F.ny + y) * F.nx + x];
+                }
+        bc[c] = s;
+    }
+}
+
+// coarse level l+1 -> l: x += gamma P xc on the cells with free children
+__global__ void __launch_bounds__(256) k_mg_prolong(MgLevel F, MgLevel C, const float *xc, float *x)
+{
+    MG_CELLS(F)
+    {
+        if (F.iD[c] > 0.f) x[c] = fmaf(kMgGamma, xc[((Z >> 1) * C.ny + (Y >> 1)) * C.nx + (X >> 1)], x[c]);
+    }
+}
+
+// coarsest level: x = A^-1 b with the dense inverse (n <= kMgCoarsest, one block)
+__global__ void __launch_bounds__(kMgCoarsest) k_mg_coarsest(int n, const float *Ainv, const float *b, float *x)
+{
+    __shared__ float sb[kMgCoarsest];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) sb[k] = b[k];
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        float s = 0.f;
+        for (int k = 0; k < n; ++k) s = fmaf(Ainv[(size_t)k * n + t], sb[k], s);
+        x[t] = s;
+    }
+}
+
+// level 1 from the fine grid: +x/+y/+z conductances between the free children of
+// neighbouring cells, and G, the couplings of the free children to fixed voxels
+__global__ void __launch_bounds__(256) k_mg0_build(PotGrid G, MgLevel C)
+{
+    __shared__ float S[kCondLabels * kCondLabels];
+    pot_table32(G, S);
+    MG_CELLS(C)
+    {
+        float wx = 0.f, wy = 0.f, wz = 0.f, gf = 0.f;
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int x = 2 * X + dx, y = 2 * Y + dy, z = 2 * Z + dz;
+                    if (x >= G.nx || y >= G.ny || z >= G.nz) continue;
+                    const size_t i = pot_at(G, x, y, z);
+                    if (G.cls[i] != CLS_FREE) continue;
+                    const int l = G.label[i];
+                    for (int d = 0; d < 6; ++d) {
+                        size_t j;
+                        if (!pot_nb(G, i, x, y, z, d, j)) continue;
+                        const float sf = S[l * kCondLabels + G.label[j]];
+                        if (G.cls[j] != CLS_FREE) {
+                            gf += sf;
+                        } else if (d == 1 && dx == 1) {
+                            wx += sf;
+                        } else if (d == 3 && dy == 1) {
+                            wy += sf;
+                        } else if (d == 5 && dz == 1) {
+                            wz += sf;
+                        }
+                    }
+                }
+        C.Wx[c] = wx;
+        C.Wy[c] = wy;
+        C.Wz[c] = wz;
+        C.G[c] = gf;
+    }
+}
+
+// level l+1 from level l: sums over the children
+__global__ void __launch_bounds__(256) k_mg_build(MgLevel F, MgLevel C)
+{
+    MG_CELLS(C)
+    {
+        float wx = 0.f, wy = 0.f, wz = 0.f, gf = 0.f;
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int x = 2 * X + dx, y = 2 * Y + dy, z = 2 * Z + dz;
+                    if (x >= F.nx || y >= F.ny || z >= F.nz) continue;
+                    const int f = (z * F.ny + y) * F.nx + x;
+                    gf += F.G[f];
+                    if (dx == 1 && x + 1 < F.nx) wx += F.Wx[f];
+                    if (dy == 1 && y + 1 < F.ny) wy += F.Wy[f];
+                    if (dz == 1 && z + 1 < F.nz) wz += F.Wz[f];
+                }
+        C.Wx[c] = wx;
+        C.Wy[c] = wy;
+        C.Wz[c] = wz;
+        C.G[c] = gf;
+    }
+}
+
+// diagonal of a level: G plus the six face conductances; its inverse (0 where 0)
+__global__ void __launch_bounds__(256) k_mg_diag(MgLevel L)
+{
+    MG_CELLS(L)
+    {
+        const int sy = L.nx, sz = L.nx * L.ny;
+        float d = L.G[c] + L.Wx[c] + L.Wy[c] + L.Wz[c];
+        if (X > 0) d += L.Wx[c - 1];
+        if (Y > 0) d += L.Wy[c - sy];
+        if (Z > 0) d += L.Wz[c - sz];
+        L.D[c] = d;
+        L.iD[c] = d > 0.f ? 1.f / d : 0.f;
+    }
+}
+
+#undef MG_CELLS
+
+// CG steps around the preconditioner: e += alpha p; r32 -= alpha Ap; partials of
+// r32.r32, rr by the last block
+__global__ void __launch_bounds__(256) k_pot_update32_mg(PotGrid G, double *sc, float *e32, float *r32,
+                                                        const float *p, const float *Ap, double *part, unsigned *ctr)
+{
+    const float alpha = (float)sc[SC_ALPHA];
+    float rr = 0.f;
+    POT_QUADS(G)
+    {
+        const size_t i = pot_at(G, x0, y, z);
+        const float4 e = ld4(e32 + i), r0 = ld4(r32 + i), p4 = ld4(p + i), a4 = ld4(Ap + i);
+        st4(e32 + i, make_float4(fmaf(alpha, p4.x, e.x), fmaf(alpha, p4.y, e.y), fmaf(alpha, p4.z, e.z),
+                                 fmaf(alpha, p4.w, e.w)));
+        const float4 r1 = make_float4(fmaf(-alpha, a4.x, r0.x), fmaf(-alpha, a4.y, r0.y), fmaf(-alpha, a4.z, r0.z),
+                                      fmaf(-alpha, a4.w, r0.w));
+        st4(r32 + i, r1);
+        rr = fmaf(r1.x, r1.x, fmaf(r1.y, r1.y, fmaf(r1.z, r1.z, fmaf(r1.w, r1.w, rr))));
+    }
+    const double a = pot_block_sum((double)rr);
+    if (threadIdx.x == 0) part[blockIdx.x] = a;
+    if (pot_last_block(ctr)) {
+        double s0, s1;
+        pot_sum_partials(part, gridDim.x, false, s0, s1);
+        if (threadIdx.x == 0) {
+            pot_scalars_apply(SCW_RR, s0, s1, sc);
+            *ctr = 0u;
+        }
+    }
+}
+
+// partials of r.z; the last block applies the scalar step `which` (SCW_BETA or SCW_START_RZ)
+__global__ void __launch_bounds__(256) k_pot_dot32(PotGrid G, const float *r32, const float *zv, int which,
+                                                  double *sc, double *part, unsigned *ctr)
+{
+    float rz = 0.f;
+    POT_QUADS(G)
+    {
+        const size_t i = pot_at(G, x0, y, z);
+        const float4 r4 = ld4(r32 + i), z4 = ld4(zv + i);
+        rz = fmaf(r4.x, z4.x, fmaf(r4.y, z4.y, fmaf(r4.z, z4.z, fmaf(r4.w, z4.w, rz))));
+    }
+    const double a = pot_block_sum((double)rz);
+    if (threadIdx.x == 0) part[blockIdx.x] = a;
+    if (pot_last_block(ctr)) {
+        double s0, s1;
+        pot_sum_partials(part, gridDim.x, false, s0, s1);
+        if (threadIdx.x == 0) {
+            pot_scalars_apply(which, s0, s1, sc);
+            *ctr = 0u;
+        }
+    }
+}
+
 #undef POT_QUADS
 
 // hand-over to FP64 conjugate gradients from the current x: z = r / D, p = z;
@@ -590,6 +968,134 @@ __global__ void __launch_bounds__(256) k_pot_joule(PotGrid G, const double *V, c
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
+// the multigrid hierarchy of the FP32 iterations: levels 1 .. nl (L[0] is the
+// fine grid, unused here) and the dense inverse of the coarsest level
+struct MgHost {
+    std::vector<MgLevel> L;
+    float *mem = nullptr, *Ainv = nullptr;
+    ~MgHost()
+    {
+        if (mem) cudaFree(mem);
+        if (Ainv) cudaFree(Ainv);
+    }
+};
+
+inline unsigned mg_blocks(int n) { return (unsigned)std::min((n + 255) / 256, 148 * 8); }
+
+// Builds the levels and the coarsest inverse.  ok = false (and RFA_OK) where the
+// grid needs no coarse level or the coarsest matrix is not positive definite:
+// the caller then uses the Jacobi preconditioner.
+rfa_status mg_setup(rfa_grid *g, const PotGrid &G, MgHost &H, bool &ok)
+{
+    ok = false;
+    int nx = g->nx, ny = g->ny, nz = g->nz;
+    H.L.assign(1, MgLevel{});
+    while ((long long)nx * ny * nz > kMgCoarsest) {
+        nx = (nx + 1) / 2;
+        ny = (ny + 1) / 2;
+        nz = (nz + 1) / 2;
+        MgLevel l{};
+        l.nx = nx;
+        l.ny = ny;
+        l.nz = nz;
+        l.n = nx * ny * nz;
+        H.L.push_back(l);
+    }
+    const int nl = (int)H.L.size() - 1;
+    if (nl == 0) return RFA_OK;
+    size_t total = 0;
+    for (int l = 1; l <= nl; ++l) total += 10 * (((size_t)H.L[l].n + 63) / 64 * 64);
+    if (cudaMalloc(&H.mem, total * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&H.Ainv, (size_t)kMgCoarsest * kMgCoarsest * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("potential solve multigrid allocation failed");
+        return RFA_E_OOM;
+    }
+    float *q = H.mem;
+    for (int l = 1; l <= nl; ++l) {
+        MgLevel &L = H.L[l];
+        const size_t m = ((size_t)L.n + 63) / 64 * 64;
+        float **arr[10] = {&L.D, &L.iD, &L.Wx, &L.Wy, &L.Wz, &L.G, &L.b, &L.x, &L.t, &L.r};
+        for (float **a : arr) {
+            *a = q;
+            q += m;
+        }
+    }
+    k_mg0_build<<<mg_blocks(H.L[1].n), 256, 0, g->stream>>>(G, H.L[1]);
+    k_mg_diag<<<mg_blocks(H.L[1].n), 256, 0, g->stream>>>(H.L[1]);
+    for (int l = 2; l <= nl; ++l) {
+        k_mg_build<<<mg_blocks(H.L[l].n), 256, 0, g->stream>>>(H.L[l - 1], H.L[l]);
+        k_mg_diag<<<mg_blocks(H.L[l].n), 256, 0, g->stream>>>(H.L[l]);
+    }
+    RFA_CUDA(cudaGetLastError());
+    // the coarsest operator on the host: Cholesky in FP64 over its cells with a
+    // nonzero diagonal, then the inverse (zero rows and columns elsewhere)
+    const MgLevel &C = H.L[nl];
+    const int n = C.n;
+    std::vector<float> hD(n), hx(n), hy(n), hz(n);
+    RFA_CUDA(cudaMemcpyAsync(hD.data(), C.D, n * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+    RFA_CUDA(cudaMemcpyAsync(hx.data(), C.Wx, n * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+    RFA_CUDA(cudaMemcpyAsync(hy.data(), C.Wy, n * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+    RFA_CUDA(cudaMemcpyAsync(hz.data(), C.Wz, n * sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+    RFA_CUDA(cudaStreamSynchronize(g->stream));
+    std::vector<int> cid(n, -1), cell;
+    for (int c = 0; c < n; ++c)
+        if (hD[c] > 0.f) {
+            cid[c] = (int)cell.size();
+            cell.push_back(c);
+        }
+    const int m = (int)cell.size();
+    std::vector<double> A((size_t)m * m, 0.0);
+    const int sy = C.nx, sz = C.nx * C.ny;
+    for (int a = 0; a < m; ++a) {
+        const int c = cell[a];
+        const int X = c % C.nx, Y = (c / C.nx) % C.ny, Z = c / sz;
+        A[(size_t)a * m + a] = hD[c];
+        auto couple = [&](int o, float w) {
+            if (cid[o] >= 0) {
+                A[(size_t)a * m + cid[o]] -= w;
+                A[(size_t)cid[o] * m + a] -= w;
+            }
+        };
+        if (X + 1 < C.nx) couple(c + 1, hx[c]);
+        if (Y + 1 < C.ny) couple(c + sy, hy[c]);
+        if (Z + 1 < C.nz) couple(c + sz, hz[c]);
+    }
+    // A = L L^T in place (lower triangle)
+    for (int j = 0; j < m; ++j) {
+        double d = A[(size_t)j * m + j];
+        for (int k = 0; k < j; ++k) d -= A[(size_t)j * m + k] * A[(size_t)j * m + k];
+        if (!(d > 0.0)) return RFA_OK;  // not positive definite: Jacobi instead
+        d = std::sqrt(d);
+        A[(size_t)j * m + j] = d;
+        for (int i = j + 1; i < m; ++i) {
+            double v = A[(size_t)i * m + j];
+            for (int k = 0; k < j; ++k) v -= A[(size_t)i * m + k] * A[(size_t)j * m + k];
+            A[(size_t)i * m + j] = v / d;
+        }
+    }
+    // columns of A^-1: L y = e_k, then L^T x = y
+    std::vector<float> inv((size_t)n * n, 0.f);
+    std::vector<double> y(m);
+    for (int k = 0; k < m; ++k) {
+        for (int i = 0; i < m; ++i) {
+            double v = i == k ? 1.0 : 0.0;
+            for (int j = 0; j < i; ++j) v -= A[(size_t)i * m + j] * y[j];
+            y[i] = v / A[(size_t)i * m + i];
+        }
+        for (int i = m - 1; i >= 0; --i) {
+            double v = y[i];
+            for (int j = i + 1; j < m; ++j) v -= A[(size_t)j * m + i] * y[j];
+            y[i] = v / A[(size_t)i * m + i];
+        }
+        for (int i = 0; i < m; ++i) inv[(size_t)cell[k] * n + cell[i]] = (float)y[i];
+    }
+    RFA_CUDA(cudaMemcpyAsync(H.Ainv, inv.data(), inv.size() * sizeof(float), cudaMemcpyHostToDevice, g->stream));
+    RFA_CUDA(cudaStreamSynchronize(g->stream));
+    ok = true;
+    return RFA_OK;
+}
+
 }  // namespace
 
 rfa_status potential_place(rfa_grid *g)
@@ -626,7 +1132,7 @@ rfa_status potential_place(rfa_grid *g)
         }
     if (cudaMalloc(&B.p[7], nvp) != cudaSuccess ||
         cudaMalloc(&B.p[8], kCondLabels * kCondLabels * 8 + SC_N * 8 + 8) != cudaSuccess ||
-        cudaMalloc(&B.p[9], 8 * nvp * sizeof(float)) != cudaSuccess || cudaMalloc(&B.p[10], nvp / 4 + 1) != cudaSuccess) {
+        cudaMalloc(&B.p[9], 10 * nvp * sizeof(float)) != cudaSuccess || cudaMalloc(&B.p[10], nvp / 4 + 1) != cudaSuccess) {
         cudaGetLastError();
         set_error("potential solve workspace allocation failed");
         return RFA_E_OOM;
@@ -645,7 +1151,7 @@ rfa_status potential_place(rfa_grid *g)
     k_pot_class<<<nb, 256, 0, g->stream>>>(g->geom, G, g->h, cls);
     k_pot_quni<<<nb, 256, 0, g->stream>>>(G, quni);
     k_pot_init<<<nb, 256, 0, g->stream>>>(G, xv, r, zv, p, Dv, iDv, part);
-    k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, 2, sc);
+    k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, SCW_START, sc);
     RFA_CUDA(cudaGetLastError());
     double host_sc[SC_N];
     RFA_CUDA(cudaMemcpyAsync(host_sc, sc, sizeof host_sc, cudaMemcpyDeviceToHost, g->stream));
@@ -662,23 +1168,91 @@ rfa_status potential_place(rfa_grid *g)
     // FP32 cycles inside the FP64 defect correction (r = b at the start, x = the fixed values)
     float *r32 = (float *)B.p[9], *e32 = r32 + nvp, *z32 = e32 + nvp, *Ap32 = z32 + nvp;
     float *D32 = Ap32 + nvp, *iD32 = D32 + nvp, *pbuf[2] = {iD32 + nvp, iD32 + 2 * nvp};
+    float *zB = pbuf[1] + nvp, *rt = zB + nvp;  // the V-cycle's second fine iterate and residual
+    MgHost H;
+    bool use_mg = false;
+    if (g->pot_precond == RFA_PRECOND_MULTIGRID)
+        if (rfa_status st = mg_setup(g, G, H, use_mg)) return st;
+    const int nl = (int)H.L.size() - 1;
+    // z = M b: one V-cycle (the fine iterates alternate between z32 and zB)
+    auto vcycle = [&](const float *b0) -> float * {
+        float *cur0 = z32, *oth0 = zB;
+        k_mg0_first<<<nb, 256, 0, g->stream>>>(G, iD32, b0, cur0);
+        for (int s = 1; s < kMgNu; ++s) {
+            k_mg0_sweep<false><<<nb, 256, 0, g->stream>>>(G, D32, iD32, b0, cur0, oth0);
+            std::swap(cur0, oth0);
+        }
+        k_mg0_sweep<true><<<nb, 256, 0, g->stream>>>(G, D32, iD32, b0, cur0, rt);
+        k_mg0_restrict<<<mg_blocks(H.L[1].n), 256, 0, g->stream>>>(G, rt, H.L[1], H.L[1].b);
+        std::vector<float *> cur(nl + 1), oth(nl + 1);
+        for (int l = 1; l < nl; ++l) {
+            const MgLevel &L = H.L[l];
+            const unsigned bl = mg_blocks(L.n);
+            cur[l] = L.x;
+            oth[l] = L.t;
+            k_mg_first<<<bl, 256, 0, g->stream>>>(L, L.b, cur[l]);
+            for (int s = 1; s < kMgNu; ++s) {
+                k_mg_sweep<false><<<bl, 256, 0, g->stream>>>(L, L.b, cur[l], oth[l]);
+                std::swap(cur[l], oth[l]);
+            }
+            k_mg_sweep<true><<<bl, 256, 0, g->stream>>>(L, L.b, cur[l], L.r);
+            k_mg_restrict<<<mg_blocks(H.L[l + 1].n), 256, 0, g->stream>>>(L, L.r, H.L[l + 1], H.L[l + 1].b);
+        }
+        cur[nl] = H.L[nl].x;
+        k_mg_coarsest<<<1, kMgCoarsest, 0, g->stream>>>(H.L[nl].n, H.Ainv, H.L[nl].b, cur[nl]);
+        for (int l = nl - 1; l >= 1; --l) {
+            const MgLevel &L = H.L[l];
+            const unsigned bl = mg_blocks(L.n);
+            k_mg_prolong<<<bl, 256, 0, g->stream>>>(L, H.L[l + 1], cur[l + 1], cur[l]);
+            for (int s = 0; s < kMgNu; ++s) {
+                k_mg_sweep<false><<<bl, 256, 0, g->stream>>>(L, L.b, cur[l], oth[l]);
+                std::swap(cur[l], oth[l]);
+            }
+        }
+        k_mg0_prolong<<<nb, 256, 0, g->stream>>>(G, iD32, H.L[1], cur[1], cur0);
+        for (int s = 0; s < kMgNu; ++s) {
+            k_mg0_sweep<false><<<nb, 256, 0, g->stream>>>(G, D32, iD32, b0, cur0, oth0);
+            std::swap(cur0, oth0);
+        }
+        return cur0;
+    };
+    float *zfin = z32;  // the preconditioned residual of the current iteration
     bool fp64_cg = false;
     int pk = 0;     // pbuf[pk]: the previous direction (kept across replacements)
     int cycle = 0;  // 0: the first cycle starts from direction 0
     while (rel > g->pot_tol && it < g->pot_max_iters && !fp64_cg) {
         const double eta = std::max(kInnerEta, 0.25 * g->pot_tol / rel);
-        k_pot_init32<<<nb, 256, 0, g->stream>>>(G, r, Dv, r32, e32, z32, pbuf[pk], D32, iD32, cycle > 0, part);
-        k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, cycle > 0 ? 1 : 2, sc);
+        // Jacobi keeps the search direction across a replacement; the multigrid
+        // iteration restarts from direction 0 (with its strong preconditioner a
+        // kept direction is no longer conjugate to the new residual's Krylov
+        // space, and convergence stalls)
+        k_pot_init32<<<nb, 256, 0, g->stream>>>(G, r, Dv, r32, e32, z32, pbuf[pk], D32, iD32, !use_mg && cycle > 0,
+                                               part);
+        if (use_mg) {
+            k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, SCW_RR_B, sc);
+            zfin = vcycle(r32);
+            k_pot_dot32<<<nb, 256, 0, g->stream>>>(G, r32, zfin, SCW_START_RZ, sc, part, ctr);
+        } else {
+            k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, cycle > 0 ? SCW_BETA_RR : SCW_START, sc);
+            zfin = z32;
+        }
         ++cycle;
         if (rfa_status st = read_scalars()) return st;
         const double r0 = std::sqrt(std::fmax(host_sc[SC_RR], 0.0));
-        double rin = r0;
-        while (rin > eta * r0 && it < g->pot_max_iters) {
-            const int n = std::min(kCheck, g->pot_max_iters - it);
+        double rin = r0, best = r0;
+        int flat = 0;  // checks without a new minimum of the FP32 residual
+        while (rin > eta * r0 && it < g->pot_max_iters && flat < kFlatChecks) {
+            const int n = std::min(use_mg ? kCheckMg : kCheck, g->pot_max_iters - it);
             for (int k = 0; k < n; ++k) {
-                k_pot_spmv32<<<nb, 256, 0, g->stream>>>(G, sc, D32, z32, pbuf[pk], pbuf[pk ^ 1], Ap32, part, ctr);
-                k_pot_update32<<<nb, 256, 0, g->stream>>>(G, sc, iD32, e32, r32, z32, pbuf[pk ^ 1], Ap32, part,
-                                                          ctr);
+                k_pot_spmv32<<<nb, 256, 0, g->stream>>>(G, sc, D32, zfin, pbuf[pk], pbuf[pk ^ 1], Ap32, part, ctr);
+                if (use_mg) {
+                    k_pot_update32_mg<<<nb, 256, 0, g->stream>>>(G, sc, e32, r32, pbuf[pk ^ 1], Ap32, part, ctr);
+                    zfin = vcycle(r32);
+                    k_pot_dot32<<<nb, 256, 0, g->stream>>>(G, r32, zfin, SCW_BETA, sc, part, ctr);
+                } else {
+                    k_pot_update32<<<nb, 256, 0, g->stream>>>(G, sc, iD32, e32, r32, z32, pbuf[pk ^ 1], Ap32, part,
+                                                              ctr);
+                }
                 pk ^= 1;
             }
             it += n;
@@ -688,10 +1262,16 @@ rfa_status potential_place(rfa_grid *g)
                 set_error("potential solve diverged");
                 return RFA_E_NONFINITE;
             }
+            if (rin < 0.99 * best) {
+                best = rin;
+                flat = 0;
+            } else {
+                ++flat;
+            }
         }
         k_pot_correct<<<nb, 256, 0, g->stream>>>(G, e32, xv);
         k_pot_resid64<<<nb, 256, 0, g->stream>>>(G, xv, r, part);
-        k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, 3, sc);
+        k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, SCW_RR, sc);
         if (rfa_status st = read_scalars()) return st;
         const double rel_new = std::sqrt(std::fmax(host_sc[SC_RR], 0.0)) / bnorm;
         if (!std::isfinite(rel_new)) {
@@ -704,15 +1284,15 @@ rfa_status potential_place(rfa_grid *g)
     // FP64 conjugate gradients from the current x (r already holds b - A x)
     if (rel > g->pot_tol && it < g->pot_max_iters) {
         k_pot_restart64<<<nb, 256, 0, g->stream>>>(G, r, iDv, zv, p, part);
-        k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, 2, sc);
+        k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, SCW_START, sc);
     }
     while (rel > g->pot_tol && it < g->pot_max_iters) {
         const int n = std::min(kCheck, g->pot_max_iters - it);
         for (int k = 0; k < n; ++k) {
             k_pot_spmv<<<nb, 256, 0, g->stream>>>(G, Dv, p, Ap, part);
-            k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, 0, sc);
+            k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, SCW_ALPHA, sc);
             k_pot_update<<<nb, 256, 0, g->stream>>>(G, sc, iDv, xv, r, zv, p, Ap, part);
-            k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, 1, sc);
+            k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, SCW_BETA_RR, sc);
             k_pot_direction<<<nb, 256, 0, g->stream>>>(G, sc, zv, p);
         }
         it += n;

@@ -165,6 +165,7 @@ struct rfa_grid {
     int alpha_perf = 0;        // 1: perfusion weighted by 1 / max(1, Omega)
     std::vector<double> sigma; // electrical conductivity per label (potential solve)
     int pot_max_iters = 0, pot_iters = 0;
+    int pot_precond = 0;       // RFA_PRECOND_MULTIGRID or RFA_PRECOND_JACOBI
     double pot_tol = 0.0, pot_res = 0.0;
     void *d_wpair = nullptr;   // conservative form: label-pair weights (float, double for FP64 coefficients)
     float *d_wadj = nullptr;   // FP32 weights and their K derivatives for the adjoint (3 tables)

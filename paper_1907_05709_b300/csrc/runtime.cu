@@ -344,6 +344,15 @@ rfa_status rfa_place_needle_potential(rfa_grid *g, const rfa_needle *needle, con
     return RFA_OK;
 }
 
+rfa_status rfa_set_potential_preconditioner(rfa_grid *g, int mode)
+{
+    if (!g) return fail(RFA_E_INVALID, "null grid");
+    if (mode != RFA_PRECOND_MULTIGRID && mode != RFA_PRECOND_JACOBI)
+        return fail(RFA_E_INVALID, "unknown preconditioner");
+    g->pot_precond = mode;
+    return RFA_OK;
+}
+
 rfa_status rfa_set_damage(rfa_grid *g, int enable, double A, double Ea, double R, double T_thr_C)
 {
     if (!g) return fail(RFA_E_INVALID, "null grid");

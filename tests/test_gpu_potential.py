@@ -1,5 +1,6 @@
 """RF source from the electric potential (rfa_place_needle_potential, sigma
-|grad V|^2 of Eq. 2675-eq1_Linte) against the oracle's direct sparse solve.
+|grad V|^2 of Eq. 2675-eq1_Linte) against the oracle's direct sparse solve,
+with the multigrid (default) and the Jacobi preconditioner.
 
 The GPU solves by conjugate gradients to a relative residual of 1e-12; with a
 condition number of ~2e3 on these grids the source is within ~1e-8 relative
@@ -22,12 +23,14 @@ def _case(seed, dims, kind=ph.UMBRELLA):
     return c
 
 
+@pytest.mark.parametrize("precond", [rfa.PRECOND_MULTIGRID, rfa.PRECOND_JACOBI])
 @pytest.mark.parametrize("kind", [ph.STRAIGHT, ph.UMBRELLA])
-def test_source_field_matches_direct_solve(kind):
+def test_source_field_matches_direct_solve(kind, precond):
     case = _case(80, (41, 34, 29), kind)
     m = oracle.setup(case, "bf16")
     g = rfa.Grid(case.nx, case.ny, case.nz, case.h, case.dt, state_prec=rfa.STATE_F64)
     g.set_tissue(case.labels, case.table)
+    rfa.rfa_set_potential_preconditioner(g.handle, precond)
     it, res = rfa.rfa_place_needle_potential(g.handle, case.needle, [t.sigma for t in case.table])
     assert 0 < it < 20000 and res <= 1e-12
     s = g.field(rfa.FIELD_S)
@@ -64,4 +67,38 @@ def test_retissue_resolves_and_backward_declines():
     with pytest.raises(rfa.RfaError) as e:
         g.backward(torch.zeros(lab.shape, dtype=torch.float32, device="cuda"))
     assert e.value.status == 8
+    g.close()
+
+
+def test_multigrid_takes_far_fewer_iterations_than_jacobi():
+    case = _case(83, (64, 57, 49))
+    m = oracle.setup(case, "bf16")
+    g = rfa.Grid(case.nx, case.ny, case.nz, case.h, case.dt, state_prec=rfa.STATE_F64)
+    g.set_tissue(case.labels, case.table)
+    sig = [t.sigma for t in case.table]
+    got = {}
+    for pc in (rfa.PRECOND_JACOBI, rfa.PRECOND_MULTIGRID):
+        rfa.rfa_set_potential_preconditioner(g.handle, pc)
+        it, res = rfa.rfa_place_needle_potential(g.handle, case.needle, sig, 20000, 1e-12)
+        assert res <= 1e-12
+        s = g.field(rfa.FIELD_S)
+        assert np.max(np.abs(s - m.s)) <= 1e-7 * np.max(np.abs(m.s))
+        got[pc] = it
+    assert 5 * got[rfa.PRECOND_MULTIGRID] <= got[rfa.PRECOND_JACOBI]
+    with pytest.raises(rfa.RfaError) as e:
+        rfa.rfa_set_potential_preconditioner(g.handle, 7)
+    assert e.value.status == 1
+    g.close()
+
+
+def test_grid_without_coarse_level_falls_back_to_jacobi():
+    # 6 x 5 x 4 = 120 voxels: no coarse level, the multigrid setting solves with Jacobi
+    case = _case(84, (6, 5, 4), kind=ph.STRAIGHT)
+    m = oracle.setup(case, "bf16")
+    g = rfa.Grid(case.nx, case.ny, case.nz, case.h, case.dt, state_prec=rfa.STATE_F64)
+    g.set_tissue(case.labels, case.table)
+    it, res = rfa.rfa_place_needle_potential(g.handle, case.needle, [t.sigma for t in case.table])
+    assert res <= 1e-12
+    s = g.field(rfa.FIELD_S)
+    assert np.max(np.abs(s - m.s)) <= 1e-7 * max(np.max(np.abs(m.s)), 1e-300)
     g.close()
