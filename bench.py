@@ -372,10 +372,15 @@ def measure_next_rows(rfa, stream, case, g, cpu_baseline_on: bool):
             oracle.run(mo, st, 4, damage=sm.damage)
             out[name]["cpu_baseline"] = cpu(sm.nvox * 4 / (time.perf_counter() - t0) / 1e9, "GVox-steps/s",
                                             "96^3, 4 steps, FP64 oracle (C, OpenMP)")
-    # potential-solve source: FP32 CG iterations inside an FP64 defect correction; per FP32
-    # iteration 54 B/voxel: direction + spmv (cls, label, D, z, previous p read, p and Ap
-    # written: 22), update (1/D, e, r, p, Ap read, e, r, z written: 32).  The few FP64
-    # correction passes per solve (x += e, r = b - A x) are not counted: the figure is a floor.
+    # potential-solve source: FP32 CG iterations inside an FP64 defect correction, with the
+    # multigrid preconditioner (default) and, beside it, Jacobi.  Fine-grid bytes per voxel
+    # and iteration -- Jacobi 54: direction + spmv (cls, label, D, z, previous p read, p and
+    # Ap written: 22), update (1/D, e, r, p, Ap read, e, r, z written: 32).  Multigrid 164:
+    # direction + spmv 22, update (e, r, p, Ap read, e, r written) 24, r.z 8, and the
+    # V-cycle's fine passes 110 (first sweep b, 1/D read, x written 12; three sweeps and the
+    # residual, each x, b, D, 1/D or the residual, cls, label ~21 / 17.5; restriction 4.5;
+    # prolongation 12.5).  Coarse levels (about 1/7 more), the set-up and the FP64
+    # correction passes are not counted: the figures are floors.
     c3 = ph.umbrella_case_256(seed=0, nsteps=1)
     g3 = rfa.Grid(c3.nx, c3.ny, c3.nz, c3.h, c3.dt, rfa.STATE_F32C, rfa.PARAM_BF16, c3.face_bc, c3.T_a_C,
                   stream.cuda_stream)
@@ -385,13 +390,20 @@ def measure_next_rows(rfa, stream, case, g, cpu_baseline_on: bool):
     res = {}
     ms = _ms_between(torch, stream, lambda: res.setdefault(
         "r", rfa.rfa_place_needle_potential(g3.handle, c3.needle, sig, 20000, 1e-10)))
+    rfa.rfa_set_potential_preconditioner(g3.handle, rfa.PRECOND_JACOBI)
+    ms_j = _ms_between(torch, stream, lambda: res.setdefault(
+        "j", rfa.rfa_place_needle_potential(g3.handle, c3.needle, sig, 20000, 1e-10)))
     g3.close()
     it, rel = res["r"]
+    it_j, rel_j = res["j"]
     adj = measure_adjoint(rfa, stream, conduction="harmonic")
     out["conservative_adjoint"] = {k: adj[k] for k in ("workload", "grid", "time_steps", "forward_recorded_ms",
                                                        "backward_ms", "backward_over_forward")}
-    out["potential_source"] = dict(roof(54.0 * n * it, ms), ms=ms, cg_iterations=it, rel_residual=rel,
-                                   ms_per_iteration=ms / max(it, 1))
+    out["potential_source"] = dict(roof(164.0 * n * it, ms), ms=ms, preconditioner="multigrid", cg_iterations=it,
+                                   rel_residual=rel, ms_per_iteration=ms / max(it, 1),
+                                   jacobi={"ms": ms_j, "cg_iterations": it_j, "rel_residual": rel_j,
+                                           "frac": roof(54.0 * n * it_j, ms_j)["frac"]},
+                                   multigrid_over_jacobi=ms_j / ms)
     if cpu_baseline_on:
         import oracle
         sm = ph.single_needle_case(seed=1, n=32, nsteps=1)
@@ -700,6 +712,14 @@ def profile_case(name):
         g3.set_tissue(case.labels, case.table)
         rfa.rfa_place_needle_potential(g3.handle, case.needle, [t.sigma for t in case.table], 40, 1e-30)
         g3.close()
+    elif name == "potential256":
+        # the potential-solve source at 256^3 with the multigrid preconditioner, to 1e-10
+        case = ph.umbrella_case_256(seed=0, nsteps=1)
+        g3 = rfa.Grid(case.nx, case.ny, case.nz, case.h, case.dt, rfa.STATE_F32C, rfa.PARAM_BF16, case.face_bc,
+                      case.T_a_C, stream.cuda_stream)
+        g3.set_tissue(case.labels, case.table)
+        rfa.rfa_place_needle_potential(g3.handle, case.needle, [t.sigma for t in case.table], 20000, 1e-10)
+        g3.close()
     else:
         raise SystemExit(f"unknown profile case {name}")
     torch.cuda.synchronize()
@@ -720,7 +740,7 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-secondary", action="store_true", help="skip the adjoint and batched measurements")
     ap.add_argument("--batch-steps", type=int, default=4000)
-    ap.add_argument("--profile-case", default=None, help="batch16 | adjoint128 | model256: short case for ncu")
+    ap.add_argument("--profile-case", default=None, help="batch16 | adjoint128 | model256 | potential256: short case for ncu")
     args = ap.parse_args(argv)
     if args.schedule == "plain":
         args.schedule = "tb1"
