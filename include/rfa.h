@@ -308,10 +308,12 @@ rfa_status rfa_set_perfusion_coupling(rfa_grid *g, int mode);
  *                   chosen by rfa_set_potential_preconditioner) stop when the
  *                   FP64 residual ||b - A x|| <= tol ||b|| or after max_iters
  *                   iterations.  The iterations run in FP32 with residual
- *                   replacement: whenever the FP32 residual has fallen 100x,
- *                   x and b - A x are formed in FP64 and the iteration goes on
- *                   from its kept direction; if a cycle gains less than 2x,
- *                   FP64 conjugate gradients continue from the current x.
+ *                   replacement: whenever the FP32 residual has fallen 100x
+ *                   (or stagnates), x and b - A x are formed in FP64 and the
+ *                   iteration goes on (Jacobi: from its kept direction;
+ *                   multigrid: restarted); if a cycle gains less than 2x,
+ *                   Jacobi-preconditioned FP64 conjugate gradients continue
+ *                   from the current x.
  *   iters_out, rel_residual_out (may be NULL): iterations used (FP32 and FP64
  *                   together), final FP64 ||b - A x||/||b|| (check it against
  *                   tol: reaching max_iters is not an error).

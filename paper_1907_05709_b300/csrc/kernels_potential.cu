@@ -9,23 +9,23 @@
 //   free voxel i:  sum_nb sigma_f (V_i - V_nb) = 0, a symmetric positive
 //   definite system in the free unknowns.
 //
-// Solver: conjugate gradients with the Jacobi preconditioner, matrix-free, to
-// an FP64 relative residual (the source sets the heating of every later step;
+// Solver: preconditioned conjugate gradients (a multigrid V-cycle, below, or
+// the inverse diagonal), matrix-free, to an FP64 relative residual (the source sets the heating of every later step;
 // FP64 keeps the solve far below the FP32 state's resolution).  B300's FP64
 // pipe is narrow, so the iterations run in FP32, with the residual replaced
 // by the true FP64 one every time the FP32 residual has fallen by kInnerEta
 // (CG with residual replacement, "reliable updates": van der Vorst and Ye's
 // residual replacement for Krylov methods).  At a replacement the FP32
 // correction e is added to the FP64 iterate x, r = b - A x is formed in FP64,
-// and the iteration goes on from the kept search direction with beta =
+// and the Jacobi iteration goes on from the kept search direction with beta =
 // (r.z)_new / (r.z)_old, so it keeps its Krylov information instead of
-// restarting.  A cycle also ends when its FP32 residual has made no new 1 %
+// restarting (the multigrid iteration restarts: see the host loop).  A cycle also ends when its FP32 residual has made no new 1 %
 // low for kFlatChecks reads (FP32 stagnation).  A cycle that gains less than a
 // factor 2 (FP32 at its attainable accuracy, about cond(A) * 2^-24) hands over
-// to plain FP64 conjugate gradients from the current x.  The stopping rule is the FP64 one either way:
-// ||b - A x|| <= tol ||b||.  The diagonal and its inverse are stored once (no
+// to Jacobi-preconditioned FP64 conjugate gradients from the current x.  The
+// stopping rule is the FP64 one either way: ||b - A x|| <= tol ||b||.  The diagonal and its inverse are stored once (no
 // per-iteration division).  Scalars stay on the device; the host reads the
-// residual every kCheck iterations.
+// residual every kCheck (Jacobi) or kCheckMg (multigrid) iterations.
 //
 // Heating: q_i = sum_nb sigma_f (V_nb - V_i)^2 / (2 h^2), each face's
 // dissipation split between its two voxels, so that sum_i q_i h^3 equals the
