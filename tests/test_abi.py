@@ -61,3 +61,7 @@ def test_invalid_arguments_rejected_without_gpu():
     with pytest.raises(rfa.RfaError) as e:
         rfa.rfa_create_grid(4, 4, 4, 1e-3, 0.05, state_prec=7)
     assert e.value.status == 1
+    # setters check their grid before touching it
+    with pytest.raises(rfa.RfaError) as e:
+        rfa.rfa_set_potential_preconditioner(None, rfa.PRECOND_MULTIGRID)
+    assert e.value.status == 1 and "null grid" in str(e.value)
