@@ -34,6 +34,7 @@ CHECKS = [
     ("energy balance, straight", lambda: PINS.test_energy_balance_insulated_no_perfusion(ph.STRAIGHT)),
     ("energy balance, umbrella", lambda: PINS.test_energy_balance_insulated_no_perfusion(ph.UMBRELLA)),
     ("source shape", PINS.test_source_shape_hand_picked),
+    ("necrosis read-out", PINS.test_necrosis_counts_volumes_and_smoothed_volume_closed_forms),
     ("monotone heating", PINS.test_monotone_heating_in_time_and_distance),
     ("monotone phantom", PINS.test_random_phantom_monotone_in_time),
     ("Arrhenius closed form", PINS.test_arrhenius_constant_temperature_kahan),
@@ -133,6 +134,14 @@ PY_MUTANTS = [
      "np.add.at(rhs, i[~jf], -sf[~jf] * nb_fix[m][~jf])"),
     ("Joule heating: |dV| not squared", "joule", "(nb - V) ** 2", "np.abs(nb - V)"),
     ("Joule heating: face not split", "joule", "return q / (2.0 * h * h)", "return q / (h * h)"),
+    ("necrosis: sigmoid exponent sign flipped", "necrosis", "np.exp(-(T - thr_C) / width_K)",
+     "np.exp((T - thr_C) / width_K)"),
+    ("necrosis: h^3 dropped from the smoothed volume", "necrosis", "vs = h3 * float(", "vs = float("),
+    ("necrosis: width multiplied, not divided", "necrosis", "np.exp(-(T - thr_C) / width_K)",
+     "np.exp(-(T - thr_C) * width_K)"),
+    ("necrosis: Arrhenius criterion strict", "necrosis", "(st.omega >= 1.0)", "(st.omega > 1.0)"),
+    ("necrosis: volumes without h^3", "necrosis", "(h3 * n_th, h3 * n_ar)", "(n_th, n_ar)"),
+    ("necrosis: ambient temperature dropped", "necrosis", "T = st.theta + Ta", "T = st.theta"),
 ]
 
 

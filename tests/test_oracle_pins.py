@@ -356,3 +356,72 @@ def test_paper_fixed_tip_experiment_properties():
         prev = (t25, t50)
         if k == 5:      # t = 60 s
             assert t50 < 42.5
+
+
+# ------------------------------------------------------------------ necrosis read-out
+def _necrosis_model(nx=6, ny=5, nz=4, h=2e-3):
+    case = _case(nx, ny, nz, [ph.liver()], _no_source(), h=h)
+    return oracle.setup(case, "f64")
+
+
+def test_necrosis_counts_volumes_and_smoothed_volume_closed_forms():
+    """The necrosis read-out (the 60 C criterion of Sec. "Introduction" and the
+    Arrhenius criterion Omega >= 1 of Eq. eq-tissState), against values the
+    definitions fix exactly:
+      - sigma(0) = 1/2, so a field uniformly at the threshold has the smoothed
+        volume h^3 N / 2;
+      - sigma(ln 3) = 3/4 and sigma(-ln 3) = 1/4, at any width w when the field
+        sits at thr +- w ln 3 (a width applied as a product, a flipped exponent
+        or a missing h^3 changes these);
+      - counts of a hand-set latch and Omega pattern (Omega exactly 1 counts,
+        the double just below it does not), volumes h^3 * count."""
+    h = 2e-3
+    m = _necrosis_model(h=h)
+    st = oracle.initial_state(m)
+    N = st.theta.size
+    h3 = h ** 3
+    Ta = m.T_a
+
+    # uniform at the threshold: sigma(0) = 1/2 everywhere
+    st.theta[...] = 60.0 - Ta
+    _, counts, vols, vs = oracle.necrosis(m, st)
+    assert counts == (0, 0) and vols == (0.0, 0.0)
+    assert math.isclose(vs, h3 * N / 2, rel_tol=1e-14)
+
+    # thr + w ln 3 (sigma = 3/4) and thr - w ln 3 (sigma = 1/4), several widths and thresholds
+    for w, thr in ((1.0, 60.0), (2.0, 60.0), (0.25, 42.5), (3.0, 50.0)):
+        st.theta[...] = thr + w * math.log(3.0) - Ta
+        vs_hi = oracle.necrosis(m, st, width_K=w, thr_C=thr)[3]
+        assert math.isclose(vs_hi, 0.75 * h3 * N, rel_tol=1e-12), (w, thr)
+        st.theta[...] = thr - w * math.log(3.0) - Ta
+        vs_lo = oracle.necrosis(m, st, width_K=w, thr_C=thr)[3]
+        assert math.isclose(vs_lo, 0.25 * h3 * N, rel_tol=1e-12), (w, thr)
+    # half the voxels each way: 3/4 + 1/4 per pair
+    flat = st.theta.reshape(-1)
+    flat[0::2] = 60.0 + math.log(3.0) - Ta
+    flat[1::2] = 60.0 - math.log(3.0) - Ta
+    assert math.isclose(oracle.necrosis(m, st)[3], h3 * N / 2, rel_tol=1e-12)
+    # far above and far below: sigma -> 1 and 0
+    st.theta[...] = 60.0 + 200.0 - Ta
+    assert math.isclose(oracle.necrosis(m, st)[3], h3 * N, rel_tol=1e-14)
+    st.theta[...] = 60.0 - 200.0 - Ta
+    assert oracle.necrosis(m, st)[3] < h3 * N * 1e-80
+
+    # hand-set latch and Omega: counts, bits and volumes
+    rng = np.random.default_rng(5)
+    latch = (rng.random(st.latch.shape) < 0.3).astype(np.uint8)
+    om = np.zeros(st.omega.shape)
+    sel = rng.random(om.shape)
+    om[sel < 0.2] = 1.0                               # exactly at the criterion: dead
+    om[(sel >= 0.2) & (sel < 0.4)] = np.nextafter(1.0, 0.0)  # just below: alive
+    om[(sel >= 0.4) & (sel < 0.5)] = 7.5              # well above: dead
+    st.latch[...] = latch
+    st.omega[...] = om
+    mask, counts, vols, _ = oracle.necrosis(m, st)
+    n_th = int(latch.sum())
+    n_ar = int(np.count_nonzero(sel < 0.2) + np.count_nonzero((sel >= 0.4) & (sel < 0.5)))
+    assert counts == (n_th, n_ar)
+    assert vols == (h3 * n_th, h3 * n_ar)
+    assert np.array_equal(mask & 1, latch)
+    assert np.array_equal((mask >> 1) & 1, ((sel < 0.2) | ((sel >= 0.4) & (sel < 0.5))).astype(np.uint8))
+    assert not (mask & ~np.uint8(3)).any()
