@@ -57,13 +57,17 @@ def workload(name: str, seed: int, sim_steps):
     return c
 
 
-def workload_config(c, name):
+def workload_config(c, name, oracle_arm: bool = False):
+    """The workload of a bench line; ``oracle_arm`` describes the FP64 oracle's
+    arithmetic (the reference arm) instead of the GPU path's."""
+    gb = 46.0 * c.nvox / 1e9
     return {"workload": name, "grid": [c.nx, c.ny, c.nz], "h_mm": c.h * 1e3, "dt_s": c.dt,
-            "time_steps": c.nsteps, "needle": {0: "straight", 1: "umbrella"}[c.needle.kind],
+            "time_steps": c.nsteps, "needle": {0: "straight", 1: "umbrella", 2: "fixed tip"}[c.needle.kind],
             "n_tines": c.needle.n_tines if c.needle.kind == 1 else 0,
             "power_W": c.needle.power, "arrhenius": bool(c.damage.enable),
-            "state": "fp32 hi+lo compensated", "coefficients": "bf16",
-            "l2": "inputs larger than L2 (working set ~46 B/voxel, 0.8 GB)"}
+            "state": "fp64 (oracle)" if oracle_arm else "fp32 hi+lo compensated",
+            "coefficients": "bf16 (rounded, fed to the FP64 oracle)" if oracle_arm else "bf16",
+            "l2": f"inputs larger than L2 (working set ~46 B/voxel, {gb:.1f} GB)"}
 
 
 # ------------------------------------------------------------------ clocks
@@ -249,7 +253,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(case, args.workload),
+            "config": workload_config(case, args.workload, oracle_arm=True),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,

@@ -10,7 +10,9 @@
  *   - voxels held at a fixed temperature (vessels, Eq. 2675-eq6 and the
  *     else-branch of Alg. 1),
  *   - a 60 C necrosis latch (Sec. "Introduction") and the Arrhenius damage
- *     integral of Eq. eq-tissState, accumulated in FP64,
+ *     integral of Eq. eq-tissState (FP32 increments summed in an FP32 carry
+ *     that is folded into an FP64 integral every 256 steps; FP64 throughout
+ *     for the FP64 state),
  *   - a hand-written discrete adjoint for gradients (the paper has none).
  *
  * Conventions shared by every call:
@@ -62,7 +64,7 @@ enum { RFA_PARAM_BF16 = 0, RFA_PARAM_F32 = 1, RFA_PARAM_F64 = 2 };
 /* Outer faces: Dirichlet = the outer voxel layer is held at T_a; insulated =
  * zero flux (a neighbour outside the grid contributes nothing). */
 enum { RFA_FACE_DIRICHLET = 0, RFA_FACE_INSULATED = 1 };
-enum { RFA_NEEDLE_STRAIGHT = 0, RFA_NEEDLE_UMBRELLA = 1 };
+enum { RFA_NEEDLE_STRAIGHT = 0, RFA_NEEDLE_UMBRELLA = 1, RFA_NEEDLE_FIXED_TIP = 2 };
 /* Field ids for rfa_get_field. */
 enum { RFA_FIELD_THETA = 0, RFA_FIELD_A = 1, RFA_FIELD_B = 2, RFA_FIELD_S = 3,
        RFA_FIELD_LATCH = 4, RFA_FIELD_OMEGA = 5, RFA_FIELD_THETA_LO = 6 };
@@ -86,7 +88,21 @@ typedef struct {
  * the axis.  Source: q_i = P w_i / (h^3 sum_free w), w_i = max(d_i, r_clamp)^-4
  * with d_i the distance from the voxel centre to the nearest active segment
  * (the 1/r^4 fall-off of the resistive term sigma|grad V|^2 of Eq.
- * 2675-eq1_Linte around a point electrode). */
+ * 2675-eq1_Linte around a point electrode).
+ * FIXED_TIP: the paper's own set-up (Sec. "Evaluation Methods"): no RF source;
+ * the needle tip is a voxel hemisphere held at T_tip_C (the paper uses 90 and
+ * 60 C).  With (i, j, k) the voxel nearest tip_m and axis one of +-x, +-y, +-z,
+ * the hemisphere is the voxels at offsets u, v in -2..2 across the axis and
+ * w = 0, 1, 2 along it with 36 u^2 + 36 v^2 + 25 w^2 <= 225, i.e.
+ * (u/2.5)^2 + (v/2.5)^2 + (w/3)^2 <= 1: 5 x 5 voxels across, 3 deep, the flat
+ * face through tip_m and the dome toward +axis.  Its voxels get a = b = s = 0
+ * and the temperature T_tip_C (those outside the grid are skipped); placing
+ * another needle, or rfa_set_tissue, gives them back what their labels define
+ * (free voxels keep their current temperature).  power_W, the lengths, the
+ * tine fields and r_clamp_m are ignored; Q_m still heats the free voxels.
+ * Runs with the centre conduction form only; rfa_backward returns
+ * RFA_E_UNSUPPORTED while such a needle is placed.  T_tip_C is read for
+ * FIXED_TIP only. */
 typedef struct {
     int kind;
     double tip_m[3];
@@ -98,6 +114,7 @@ typedef struct {
     int tine_axial;
     double power_W;
     double r_clamp_m;
+    double T_tip_C;
 } rfa_needle;
 
 /*
@@ -136,16 +153,23 @@ rfa_status rfa_set_tissue(rfa_grid *g, const uint8_t *labels, const rfa_tissue *
  * Place the needle: builds the per-voxel source term
  * s_i = (q_i + Q_m,i) dt / (rho c)_i on the device (FP64 geometry and
  * normalisation sum, stored in the state precision).  Fixed voxels get no
- * source.  Does not reset the state.  Errors: RFA_E_STATE (no tissue yet),
- * RFA_E_INVALID (zero axis, n_tines outside 0..16, negative lengths).
+ * source.  Does not reset the state (a FIXED_TIP needle sets its tip voxels'
+ * temperature).  Errors: RFA_E_STATE (no tissue yet), RFA_E_INVALID (zero
+ * axis, n_tines outside 0..16, negative lengths, r_clamp_m <= 0; FIXED_TIP: an
+ * axis that is not a coordinate axis, a non-finite T_tip_C),
+ * RFA_E_UNSUPPORTED (FIXED_TIP with the conservative conduction form).
  */
 rfa_status rfa_place_needle(rfa_grid *g, const rfa_needle *needle);
 
 /*
  * Damage model.  enable != 0 accumulates, after every step,
  * Omega_i += dt * A * exp(-Ea / (R * T_K)) with T_K = T + 273.15 (Eq.
- * eq-tissState's integral, right-rectangle rule), in FP64 with Kahan
- * compensation.  T_thr_C is the necrosis-latch threshold used whether or not
+ * eq-tissState's integral, right-rectangle rule).  FP32 and compensated FP32
+ * states evaluate the increment in FP32 and add it to an FP32 carry, which is
+ * folded into the FP64 integral with an error-free sum every 256 steps (the
+ * carry keeps the fold's rounding error; at most 256 increments, about
+ * 1.5e-5 relative, sit in FP32); the FP64 state adds every increment to the
+ * FP64 integral with an error-free sum whose rounding error joins the carry.  T_thr_C is the necrosis-latch threshold used whether or not
  * the integral is enabled (default 60 C).  Defaults: disabled, A = 7.39e39,
  * Ea = 2.577e5, R = 8.31 (the paper's printed gas constant).
  */
@@ -200,15 +224,20 @@ rfa_status rfa_necrosis_mask(rfa_grid *g, uint8_t *mask_or_null, int64_t *counts
  * no counterpart; this exists for callers that may not allocate device memory
  * once running (a per-frame real-time loop where an allocation would stall the
  * device, or an application that pre-reserves its whole memory budget).
- * result_dev: caller-owned device buffer of 32 bytes receiving
+ * result_dev: caller-owned device buffer of 32 bytes, 8-byte aligned, receiving
  * {int64 count_thermal, int64 count_arrhenius, double smooth_volume_m3, 0.0},
  * the same quantities rfa_necrosis_mask reports.  Asynchronous on the grid's
  * stream; calls no allocator and does not synchronise.  Scratch is one fixed
  * 512 KiB device array inside the library (16384 records, one per 16384 padded
  * voxels), so grids above 268,435,456 padded voxels are rejected with
  * RFA_E_INVALID.  The first call with a device current looks up that array's
- * address; make it before any stream capture.  Calls share the array: each
- * call rewrites every record it reads, but calls that overlap on the GPU race.
+ * address; if the CUDA runtime loads device code lazily (the default), that
+ * look-up loads the library's code on the device and may allocate and block
+ * then, so make the first call during set-up, before any stream capture.
+ * Calls share the array: each call rewrites every record it reads, but calls
+ * that overlap on the GPU race.
+ * Errors: RFA_E_INVALID (null grid or result_dev, result_dev not 8-byte
+ * aligned, smooth_width_K <= 0, grid too large), RFA_E_CUDA (launch).
  */
 rfa_status rfa_necrosis_reduce_noalloc(rfa_grid *g, double smooth_width_K, void *result_dev);
 
@@ -221,8 +250,8 @@ rfa_status rfa_necrosis_reduce_noalloc(rfa_grid *g, double smooth_width_K, void 
  * Differentiates the centre and the conservative (RFA_COND_HARMONIC) forms.
  * Errors: RFA_E_INVALID (null argument), RFA_E_STATE (nothing recorded, or
  * unrecorded steps since set-up), RFA_E_UNSUPPORTED (FP64 state, the
- * potential-solve source, the tissue-state perfusion coupling, more than 8
- * labels), RFA_E_OOM (workspace).
+ * potential-solve source, the tissue-state perfusion coupling, a FIXED_TIP
+ * needle, more than 8 labels), RFA_E_OOM (workspace).
  */
 rfa_status rfa_backward(rfa_grid *g, const float *dLdT_final_dev, double *grads);
 
@@ -318,7 +347,8 @@ rfa_status rfa_set_perfusion_coupling(rfa_grid *g, int mode);
  *                   together), final FP64 ||b - A x||/||b|| (check it against
  *                   tol: reaching max_iters is not an error).
  * Synchronous.  rfa_set_tissue re-solves with the same settings.  rfa_backward
- * returns RFA_E_UNSUPPORTED while this source is in use.
+ * returns RFA_E_UNSUPPORTED while this source is in use.  A FIXED_TIP needle
+ * is not accepted here; one placed earlier is removed first.
  * Errors: RFA_E_STATE (no tissue), RFA_E_INVALID (needle, sigma, n_sigma,
  * max_iters, tol), RFA_E_UNSUPPORTED (more than 16 labels), RFA_E_OOM,
  * RFA_E_NONFINITE (the iteration diverged).
@@ -361,7 +391,8 @@ rfa_status rfa_set_potential_preconditioner(rfa_grid *g, int mode);
  * every face).  May be set before or after rfa_set_tissue; changing it after
  * recorded steps invalidates the recording.
  * Errors: RFA_E_INVALID (unknown mode), RFA_E_UNSUPPORTED (more than 16
- * labels), RFA_E_UNSTABLE (1 - deg * max_m w(l, m) - b_l < 0 for a free label).
+ * labels, or the harmonic form while a FIXED_TIP needle is placed),
+ * RFA_E_UNSTABLE (1 - deg * max_m w(l, m) - b_l < 0 for a free label).
  */
 enum { RFA_COND_CENTRE = 0, RFA_COND_HARMONIC = 1 };
 rfa_status rfa_set_conduction(rfa_grid *g, int mode);

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "librfa.so")
 STATE_F32, STATE_F32C, STATE_F64 = 0, 1, 2
 PARAM_BF16, PARAM_F32, PARAM_F64 = 0, 1, 2
 FACE_DIRICHLET, FACE_INSULATED = 0, 1
-NEEDLE_STRAIGHT, NEEDLE_UMBRELLA = 0, 1
+NEEDLE_STRAIGHT, NEEDLE_UMBRELLA, NEEDLE_FIXED_TIP = 0, 1, 2
 FIELD_THETA, FIELD_A, FIELD_B, FIELD_S, FIELD_LATCH, FIELD_OMEGA, FIELD_THETA_LO = range(7)
 
 STATUS = {0: "RFA_OK", 1: "RFA_E_INVALID", 2: "RFA_E_OOM", 3: "RFA_E_CUDA", 4: "RFA_E_UNSTABLE",
@@ -55,7 +55,8 @@ class rfa_needle(ctypes.Structure):
                 ("axis", ctypes.c_double * 3), ("active_len_m", ctypes.c_double),
                 ("tine_len_m", ctypes.c_double), ("tine_polar_deg", ctypes.c_double),
                 ("n_tines", ctypes.c_int), ("tine_axial", ctypes.c_int),
-                ("power_W", ctypes.c_double), ("r_clamp_m", ctypes.c_double)]
+                ("power_W", ctypes.c_double), ("r_clamp_m", ctypes.c_double),
+                ("T_tip_C", ctypes.c_double)]
 
 
 _lib = None
@@ -158,6 +159,7 @@ def make_needle(nd) -> rfa_needle:
     n.tine_axial = int(nd.tine_axial)
     n.power_W = nd.power
     n.r_clamp_m = nd.r_clamp
+    n.T_tip_C = float(getattr(nd, "T_tip_C", 90.0))
     return n
 
 

@@ -471,6 +471,10 @@ rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads)
         set_error("rfa_backward does not differentiate the tissue-state perfusion coupling");
         return RFA_E_UNSUPPORTED;
     }
+    if (g->tip_on) {
+        set_error("rfa_backward does not differentiate a FIXED_TIP needle (no RF source)");
+        return RFA_E_UNSUPPORTED;
+    }
     if (g->n_labels > kMaxGradLabels) {
         set_error("rfa_backward supports at most 8 labels");
         return RFA_E_UNSUPPORTED;

@@ -782,6 +782,10 @@ extern "C" rfa_status rfa_set_conduction(rfa_grid *g, int mode)
         set_error("unknown conduction mode");
         return RFA_E_INVALID;
     }
+    if (mode == RFA_COND_HARMONIC && g->tip_on) {
+        set_error("the conservative form does not run with a FIXED_TIP needle");
+        return RFA_E_UNSUPPORTED;
+    }
     if (mode == RFA_COND_HARMONIC && g->have_tissue) {
         const rfa_status st = cond_build_tables(g, g->table.data(), g->n_labels);
         if (st != RFA_OK) return st;

@@ -251,7 +251,96 @@ __global__ void __launch_bounds__(256) k_source_write(const uint8_t *__restrict_
     }
 }
 
+// The paper's hot tip (Sec. "Evaluation Methods"): a voxel hemisphere five
+// voxels across and three deep, held at a fixed temperature.  One thread per
+// candidate offset (u, v across the axis in -2..2, w = 0..2 along it); a voxel
+// belongs to the hemisphere when (u/2.5)^2 + (v/2.5)^2 + (w/3)^2 <= 1, tested
+// exactly as 36 u^2 + 36 v^2 + 25 w^2 <= 225.
+//   paint:   a = b = s = 0, theta = theta_tip (hi and the exact lo of a pair);
+//   restore: a, b as the set-up stores them for the voxel's label (0 for fixed
+//            labels and Dirichlet face voxels), theta of fixed voxels back to
+//            their held value; free voxels keep their current temperature
+//            (their source is rewritten by the next placement).
+struct TipGeom {
+    int c[3];
+    int ax, sgn;
+};
+
+template <int SP, int PP>
+__global__ void k_tip(TipGeom t, const uint8_t *__restrict__ label, const LabelCoef *__restrict__ tab, int nx,
+                      int ny, int nz, int pitch, int face, double T_a, double th_tip, bool paint, void *th,
+                      void *lo, void *ab, void *s)
+{
+    using T = typename std::conditional<SP == RFA_STATE_F64, double, float>::type;
+    using AB = typename std::conditional<PP == RFA_PARAM_BF16, uint32_t,
+                                         typename std::conditional<PP == RFA_PARAM_F32, float2, double2>::type>::type;
+    const int k = threadIdx.x;
+    if (k >= 75) return;
+    const int u = k % 5 - 2, v = (k / 5) % 5 - 2, w = k / 25;
+    if (36 * u * u + 36 * v * v + 25 * w * w > 225) return;
+    int p[3] = {t.c[0], t.c[1], t.c[2]};
+    p[t.ax] += t.sgn * w;
+    p[(t.ax + 1) % 3] += u;
+    p[(t.ax + 2) % 3] += v;
+    if (p[0] < 0 || p[1] < 0 || p[2] < 0 || p[0] >= nx || p[1] >= ny || p[2] >= nz) return;
+    const size_t i = ((size_t)p[2] * ny + p[1]) * pitch + p[0];
+    double a = 0.0, b = 0.0, thv = th_tip;
+    bool set_theta = paint;
+    if (paint) {
+        ((T *)s)[i] = T(0);
+    } else {
+        const LabelCoef c = tab[label[i]];
+        const bool face_vox = p[0] == 0 || p[1] == 0 || p[2] == 0 || p[0] == nx - 1 || p[1] == ny - 1 ||
+                              p[2] == nz - 1;
+        if (c.fixed) {
+            set_theta = true;
+            thv = c.T_fixed - T_a;
+        } else if (face == RFA_FACE_DIRICHLET && face_vox) {
+            set_theta = true;
+            thv = 0.0;
+        } else {
+            a = c.a;
+            b = c.b;
+        }
+    }
+    if (PP == RFA_PARAM_BF16)
+        ((uint32_t *)ab)[i] = (uint32_t)bf16_bits_rne(a) | ((uint32_t)bf16_bits_rne(b) << 16);
+    else if (PP == RFA_PARAM_F32)
+        ((float2 *)ab)[i] = make_float2((float)a, (float)b);
+    else
+        ((double2 *)ab)[i] = make_double2(a, b);
+    if (set_theta) {
+        ((T *)th)[i] = (T)thv;
+        if (SP == RFA_STATE_F32C) ((float *)lo)[i] = (float)(thv - (double)(float)thv);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_tip(rfa_grid *g, bool paint, double T_tip_C)
+{
+    TipGeom t;
+    for (int d = 0; d < 3; ++d) t.c[d] = g->tip_c[d];
+    t.ax = g->tip_ax;
+    t.sgn = g->tip_sgn;
+    const double th_tip = T_tip_C - g->T_a;
+    void *th = g->th[g->cur], *lo = g->lo[g->cur];
+#define TIP_CASE(SPV, PPV)                                                                                       \
+    if (g->sp == SPV && g->pp == PPV)                                                                           \
+        k_tip<SPV, PPV><<<1, 96, 0, g->stream>>>(t, g->label, g->d_table, g->nx, g->ny, g->nz, g->pitch, g->face, \
+                                                 g->T_a, th_tip, paint, th, lo, g->ab, g->s);
+    TIP_CASE(RFA_STATE_F32, RFA_PARAM_BF16)
+    TIP_CASE(RFA_STATE_F32, RFA_PARAM_F32)
+    TIP_CASE(RFA_STATE_F32, RFA_PARAM_F64)
+    TIP_CASE(RFA_STATE_F32C, RFA_PARAM_BF16)
+    TIP_CASE(RFA_STATE_F32C, RFA_PARAM_F32)
+    TIP_CASE(RFA_STATE_F32C, RFA_PARAM_F64)
+    TIP_CASE(RFA_STATE_F64, RFA_PARAM_BF16)
+    TIP_CASE(RFA_STATE_F64, RFA_PARAM_F32)
+    TIP_CASE(RFA_STATE_F64, RFA_PARAM_F64)
+#undef TIP_CASE
+    return cudaGetLastError();
+}
 
 cudaError_t launch_setup(rfa_grid *g, const uint8_t *labels_dense_dev, int n_labels)
 {

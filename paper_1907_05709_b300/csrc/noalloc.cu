@@ -26,6 +26,7 @@
 #include "rfa_internal.cuh"
 #include "necrosis.cuh"
 
+#include <cstdint>
 #include <mutex>
 
 namespace rfa {
@@ -127,6 +128,10 @@ extern "C" rfa_status rfa_necrosis_reduce_noalloc(rfa_grid *g, double smooth_wid
     }
     if (!(smooth_width_K > 0.0)) {
         set_error("smooth_width_K must be > 0");
+        return RFA_E_INVALID;
+    }
+    if (((uintptr_t)result_dev & 7u) != 0) {  // the kernel stores int64 and double words
+        set_error("result_dev must be 8-byte aligned");
         return RFA_E_INVALID;
     }
     const size_t nrec = (g->nvp + kNoAllocVoxelsPerRecord - 1) / kNoAllocVoxelsPerRecord;

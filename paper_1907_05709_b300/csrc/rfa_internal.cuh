@@ -154,6 +154,11 @@ struct rfa_grid {
     bool have_tissue = false, have_needle = false;
     rfa_needle needle{};
     rfa::NeedleGeom geom{};
+    // the hemisphere of a placed FIXED_TIP needle: voxel nearest the tip,
+    // axis index (0 x, 1 y, 2 z) and direction of the dome
+    bool tip_on = false;
+    int tip_c[3] = {0, 0, 0};
+    int tip_ax = 2, tip_sgn = 1;
     int dmg = 0;
     double A = 7.39e39, Ea = 2.577e5, R = 8.31, T_thr = 60.0;
     int64_t steps = 0;
@@ -206,6 +211,9 @@ __device__ inline double needle_dist2(const NeedleGeom &g, double px, double py,
 // setup / source (kernels_setup.cu)
 cudaError_t launch_setup(rfa_grid *g, const uint8_t *labels_dense_dev, int n_labels);
 cudaError_t launch_source(rfa_grid *g);
+// FIXED_TIP hemisphere (g->tip_*): paint holds its voxels at theta_tip with
+// a = b = s = 0; otherwise its voxels get back what their labels define
+cudaError_t launch_tip(rfa_grid *g, bool paint, double T_tip_C);
 // s from source weights already in g->stage (FP64 per padded voxel) and their
 // per-block partial sums over the free voxels
 cudaError_t launch_source_write(rfa_grid *g, const double *partial, int npartial);

@@ -2,6 +2,7 @@
 // argument checks, status codes, stepping schedule and state (de)serialisation.
 #include "rfa_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -45,12 +46,25 @@ static rfa_status build_geometry(const rfa_needle &nd, NeedleGeom &g)
     double n = std::sqrt(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2]);
     if (!(n > 0.0) || !std::isfinite(n)) return fail(RFA_E_INVALID, "needle axis must be non-zero");
     for (double &v : ax) v /= n;
+    g.nseg = 0;
+    const double *tip = nd.tip_m;
+    if (nd.kind == RFA_NEEDLE_FIXED_TIP) {
+        // no RF source: the tip is a voxel hemisphere held at T_tip_C (painted after
+        // the source is written)
+        int nonzero = 0;
+        for (double v : ax) nonzero += v != 0.0;
+        if (nonzero != 1) return fail(RFA_E_INVALID, "a FIXED_TIP needle needs a coordinate axis (+-x, +-y or +-z)");
+        if (!std::isfinite(nd.T_tip_C)) return fail(RFA_E_INVALID, "T_tip_C must be finite");
+        for (int d = 0; d < 3; ++d)
+            if (!std::isfinite(tip[d])) return fail(RFA_E_INVALID, "tip_m must be finite");
+        g.r0 = 1.0;
+        g.P = 0.0;
+        return RFA_OK;
+    }
     if (!(nd.r_clamp_m > 0.0)) return fail(RFA_E_INVALID, "needle r_clamp_m must be > 0");
     if (nd.power_W < 0.0) return fail(RFA_E_INVALID, "needle power_W must be >= 0");
     g.r0 = nd.r_clamp_m;
     g.P = nd.power_W;
-    g.nseg = 0;
-    const double *tip = nd.tip_m;
     if (nd.kind == RFA_NEEDLE_STRAIGHT) {
         if (nd.active_len_m < 0.0) return fail(RFA_E_INVALID, "active_len_m must be >= 0");
         for (int d = 0; d < 3; ++d) {
@@ -98,6 +112,34 @@ static rfa_status build_geometry(const rfa_needle &nd, NeedleGeom &g)
         g.seg[k].inv_uu = uu > 0.0 ? 1.0 / uu : 0.0;
     }
     return RFA_OK;
+}
+
+// Give the voxels of a painted FIXED_TIP hemisphere back what their labels define.
+static cudaError_t remove_tip(rfa_grid *g)
+{
+    if (!g->tip_on) return cudaSuccess;
+    g->tip_on = false;
+    return launch_tip(g, false, 0.0);
+}
+
+// Write the source of g->needle (g->geom built from it) and, for a FIXED_TIP
+// needle, paint its hemisphere: the voxel nearest the tip, the axis and its sign.
+static cudaError_t place_source(rfa_grid *g)
+{
+    cudaError_t e = remove_tip(g);
+    if (e != cudaSuccess) return e;
+    if ((e = launch_source(g)) != cudaSuccess) return e;
+    if (g->needle.kind != RFA_NEEDLE_FIXED_TIP) return cudaSuccess;
+    for (int d = 0; d < 3; ++d) {
+        const double c = std::nearbyint(g->needle.tip_m[d] / g->h);
+        g->tip_c[d] = (int)std::max(-1e6, std::min(1e6, c));  // far outside the grid: nothing is painted
+        if (g->needle.axis[d] != 0.0) {
+            g->tip_ax = d;
+            g->tip_sgn = g->needle.axis[d] > 0.0 ? 1 : -1;
+        }
+    }
+    g->tip_on = true;
+    return launch_tip(g, true, g->needle.T_tip_C);
 }
 
 rfa_status read_status(rfa_grid *g)
@@ -269,6 +311,7 @@ rfa_status rfa_set_tissue(rfa_grid *g, const uint8_t *labels, const rfa_tissue *
     RFA_CUDA(cudaMemcpyAsync(g->stage, labels, n, dev_labels ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));
     RFA_CUDA(cudaMemsetAsync(g->status, 0, 256, g->stream));
     RFA_CUDA(launch_setup(g, (const uint8_t *)g->stage, n_labels));
+    g->tip_on = false;  // the set-up rewrote every voxel
     g->table.assign(table, table + n_labels);
     g->n_labels = n_labels;
     g->cur = 0;
@@ -291,7 +334,7 @@ rfa_status rfa_set_tissue(rfa_grid *g, const uint8_t *labels, const rfa_tissue *
             const rfa_status st = potential_place(g);
             if (st != RFA_OK) return st;
         } else {
-            RFA_CUDA(launch_source(g));
+            RFA_CUDA(place_source(g));
             RFA_CUDA(cudaStreamSynchronize(g->stream));
         }
     }
@@ -302,13 +345,15 @@ rfa_status rfa_place_needle(rfa_grid *g, const rfa_needle *needle)
 {
     if (!g || !needle) return fail(RFA_E_INVALID, "null argument");
     if (!g->have_tissue) return fail(RFA_E_STATE, "rfa_set_tissue must come first");
+    if (needle->kind == RFA_NEEDLE_FIXED_TIP && g->cond != RFA_COND_CENTRE)
+        return fail(RFA_E_UNSUPPORTED, "a FIXED_TIP needle runs with the centre conduction form only");
     NeedleGeom geom{};
     rfa_status st = build_geometry(*needle, geom);
     if (st != RFA_OK) return st;
     g->geom = geom;
     g->needle = *needle;
     g->src_mode = 0;
-    RFA_CUDA(launch_source(g));
+    RFA_CUDA(place_source(g));
     RFA_CUDA(cudaStreamSynchronize(g->stream));
     g->have_needle = true;
     if (g->steps > 0) g->rec.valid = false;  // the recorded trajectory used another source
@@ -326,9 +371,12 @@ rfa_status rfa_place_needle_potential(rfa_grid *g, const rfa_needle *needle, con
     for (int l = 0; l < n_sigma; ++l)
         if (!(sigma_S_per_m[l] >= 0.0) || !std::isfinite(sigma_S_per_m[l]))
             return fail(RFA_E_INVALID, "sigma must be finite and >= 0");
+    if (needle->kind == RFA_NEEDLE_FIXED_TIP)
+        return fail(RFA_E_INVALID, "the potential-solve source needs a straight or umbrella needle");
     NeedleGeom geom{};
     rfa_status st = build_geometry(*needle, geom);
     if (st != RFA_OK) return st;
+    RFA_CUDA(remove_tip(g));
     g->geom = geom;
     g->needle = *needle;
     g->sigma.assign(sigma_S_per_m, sigma_S_per_m + n_sigma);
@@ -519,6 +567,9 @@ rfa_status rfa_set_state(rfa_grid *g, const void *blob, size_t n)
     std::memcpy(&hd, blob, sizeof hd);
     if (hd.magic != kStateMagic || hd.nx != g->nx || hd.ny != g->ny || hd.nz != g->nz || hd.sp != g->sp)
         return fail(RFA_E_INVALID, "blob does not match this grid");
+    // a corrupt counter would delay the FP64 fold of the FP32 damage carry indefinitely
+    if (hd.steps < 0 || hd.carry_steps < 0 || hd.carry_steps >= kCarrySteps || hd.carry_steps > hd.steps)
+        return fail(RFA_E_INVALID, "blob step counters out of range");
     const char *p = (const char *)blob + sizeof hd;
     RFA_CUDA(cudaMemcpyAsync(g->th[g->cur], p, nvp * g->state_elem(), cudaMemcpyHostToDevice, g->stream));
     p += nvp * g->state_elem();

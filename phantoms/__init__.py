@@ -372,6 +372,21 @@ def paper_tip_case(T_tip_C: float = 90.0, n: int = 64, nsteps: int = 1200) -> Ca
                 damage=Damage(enable=0, T_thr_C=42.5))
 
 
+def paper_tip_needle_case(T_tip_C: float = 90.0, n: int = 64, nsteps: int = 1200) -> Case:
+    """The same set-up as paper_tip_case, described as the library's FIXED_TIP
+    needle instead of a painted label: every voxel is liver (paper constants)
+    and the needle's tip sits on the voxel the hemisphere's flat face is
+    centred on, axis +z (the dome toward +z)."""
+    c = n // 2
+    h = 0.5e-3
+    base = paper_tip_case(T_tip_C, n, nsteps)
+    needle = Needle(kind=FIXED_TIP, tip=(c * h, c * h, c * h), axis=(0.0, 0.0, 1.0), power=0.0,
+                    T_tip_C=T_tip_C)
+    return Case(name=f"papertipneedle{int(T_tip_C)}", nx=n, ny=n, nz=n, h=h, dt=base.dt, nsteps=nsteps,
+                labels=np.zeros((n, n, n), dtype=np.uint8), table=[paper_liver()], needle=needle,
+                damage=base.damage)
+
+
 def paper_tip_probes(n: int = 64):
     """Voxel indices (z, y, x) 2.5 mm and 5 mm beyond the tip's outer x face."""
     c = n // 2

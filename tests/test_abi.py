@@ -39,15 +39,16 @@ def test_exports_every_declared_symbol():
 def test_struct_layout_matches_header(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "rfa.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(rfa_tissue), '
+                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(rfa_tissue), '
                    'sizeof(rfa_needle), offsetof(rfa_needle, power_W), '
-                   'offsetof(rfa_tissue, T_fixed_C));return 0;}\n')
+                   'offsetof(rfa_tissue, T_fixed_C), offsetof(rfa_needle, T_tip_C));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     import ctypes
     assert vals == [ctypes.sizeof(rfa.rfa_tissue), ctypes.sizeof(rfa.rfa_needle),
-                    rfa.rfa_needle.power_W.offset, rfa.rfa_tissue.T_fixed_C.offset]
+                    rfa.rfa_needle.power_W.offset, rfa.rfa_tissue.T_fixed_C.offset,
+                    rfa.rfa_needle.T_tip_C.offset]
 
 
 def test_invalid_arguments_rejected_without_gpu():

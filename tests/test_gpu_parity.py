@@ -126,3 +126,58 @@ def test_paper_fixed_tip_setup(T_tip):
     compare(case, gpu, orc, rfa.STATE_F32C, damage=False)
     gpu64 = run_gpu(case, rfa.STATE_F64, rfa.PARAM_BF16, 1200, damage=False)
     compare(case, gpu64, orc, rfa.STATE_F64, damage=False)
+
+
+@pytest.mark.parametrize("T_tip", [90.0, 60.0])
+def test_paper_fixed_tip_through_place_needle(T_tip):
+    """The same set-up through rfa_place_needle with a FIXED_TIP needle (all
+    voxels liver, no painted label): the library builds the hemisphere itself
+    and must match the oracle run on the painted-label case, with the blocked
+    kernel too (bit-identical to one step per launch)."""
+    case = ph.paper_tip_case(T_tip, nsteps=1200)
+    orc = run_oracle(case, rfa.PARAM_BF16, 1200, damage=False)
+    lib_case = ph.paper_tip_needle_case(T_tip, nsteps=1200)
+    for sp in (rfa.STATE_F32C, rfa.STATE_F64):
+        gpu = run_gpu(lib_case, sp, rfa.PARAM_BF16, 1200, damage=False)
+        compare(case, gpu, orc, sp, damage=False)
+        tip = ph.paper_tip_case(T_tip, nsteps=0).labels == 1
+        assert np.all(gpu["T"][tip] == T_tip) and np.all(gpu["a"][tip] == 0) and np.all(gpu["s"][tip] == 0)
+    blk = run_gpu(lib_case, rfa.STATE_F32C, rfa.PARAM_BF16, 1200, damage=False, schedule=(2, 0))
+    one = run_gpu(lib_case, rfa.STATE_F32C, rfa.PARAM_BF16, 1200, damage=False)
+    assert np.array_equal(blk["T"], one["T"])
+
+
+def test_fixed_tip_moves_and_is_removed():
+    """Placing another needle gives the old hemisphere's voxels back their label's
+    coefficients (free voxels keep their temperature); a moved tip paints the new
+    place only; rfa_set_tissue starts over and paints the placed tip again."""
+    lib_case = ph.paper_tip_needle_case(90.0, n=32, nsteps=0)
+    g = rfa.Grid.from_case(lib_case, rfa.STATE_F32C, rfa.PARAM_BF16, damage=False)
+    a_free = g.field(rfa.FIELD_A)[5, 5, 5]
+    old = ph.paper_tip_case(90.0, n=32, nsteps=0).labels == 1
+    assert np.all(g.field(rfa.FIELD_A)[old] == 0) and np.all(g.temperature()[old] == 90.0)
+    g.step(50)
+    T50 = g.temperature()
+    nd = lib_case.needle
+    moved = ph.Needle(kind=ph.FIXED_TIP, tip=(nd.tip[0] + 4 * lib_case.h, nd.tip[1], nd.tip[2]),
+                      axis=(-1.0, 0.0, 0.0), power=0.0, T_tip_C=60.0)
+    g.place_needle(moved)
+    a = g.field(rfa.FIELD_A)
+    T = g.temperature()
+    c = 16
+    new = np.zeros_like(old)
+    for w in range(3):
+        for u in range(-2, 3):
+            for v in range(-2, 3):
+                if 36 * u * u + 36 * v * v + 25 * w * w <= 225:
+                    new[c + v, c + u, c + 4 - w] = True    # (z, y, x): dome toward -x
+    assert np.all(a[new] == 0) and np.all(T[new] == 60.0)
+    freed = old & ~new
+    assert freed.any() and np.all(a[freed] == a_free) and np.array_equal(T[freed], T50[freed])
+    with pytest.raises(rfa.RfaError) as e:
+        rfa.rfa_set_conduction(g.handle, rfa.COND_HARMONIC)
+    assert e.value.status == 8
+    g.set_tissue(lib_case.labels, lib_case.table)        # starts over, the moved tip painted again
+    T = g.temperature()
+    assert np.all(T[new] == 60.0) and np.all(T[~new] == lib_case.T_a_C)
+    g.close()

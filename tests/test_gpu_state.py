@@ -55,3 +55,24 @@ def test_blob_from_another_grid_is_refused():
         rfa.rfa_set_state(f64.handle, blob)
     for x in (g, h, f64):
         x.close()
+
+
+def test_blob_with_counters_out_of_range_is_refused():
+    """A blob whose step counters are corrupt (negative, or a damage-carry count
+    at or beyond the fold interval) is refused: restoring it would postpone the
+    FP64 fold of the FP32 damage carry without bound."""
+    case = ph.random_small_case(33, 30, 20, 10)
+    g = rfa.Grid.from_case(case)
+    g.step(7)
+    blob = bytearray(rfa.rfa_get_state(g.handle))
+    steps, carry = np.frombuffer(bytes(blob[24:40]), np.int64)
+    assert steps == 7 and 0 <= carry < 256
+    for s_, c_ in ((7, 256), (7, 1 << 40), (7, -1), (-3, 0), (5, 6)):
+        bad = bytearray(blob)
+        bad[24:40] = np.array([s_, c_], np.int64).tobytes()
+        with pytest.raises(rfa.RfaError) as e:
+            rfa.rfa_set_state(g.handle, bytes(bad))
+        assert e.value.status == 1
+    rfa.rfa_set_state(g.handle, bytes(blob))          # the intact blob still restores
+    assert g.steps_done == 7
+    g.close()
