@@ -4,9 +4,12 @@
 One bench "step" is one pass of the whole hot path over one synthetic
 phantom: tissue set-up (labels -> coefficients), needle placement (RF
 source), N explicit time steps fused with the 60 C latch and the FP64
-Arrhenius integral, and the necrosis reduction.  Default workload: 256^3
-voxels, h = 0.5 mm, 1-3 tumours and 2-4 vessels, 4-tine umbrella at 30 W,
-dt = 0.05 s, 12000 steps, BF16 coefficient fields, compensated FP32 state.
+Arrhenius integral, and the necrosis reduction.  Default workload (large512):
+512^3 voxels, h = 0.25 mm, 1-3 tumours and 8 vessels, 9-tine umbrella at
+40 W, dt = 0.02 s, 5000 steps, BF16 coefficient fields, compensated FP32
+state.  The 256^3 single-needle workload (4-tine umbrella at 30 W, 12000
+steps) is timed beside it, with the one-step kernel too, as are the adjoint,
+the batch and the model options.
 
 The metric is voxel-steps per second (GVox-steps/s); ``value`` times the
 device-resident path (labels already in HBM), ``e2e`` the same work through
@@ -48,6 +51,8 @@ def workload(name: str, seed: int, sim_steps):
         c = ph.homogeneous_case()
     elif name == "adjoint128":
         c = ph.adjoint_case_128(seed=seed)
+    elif name == "adjoint256":
+        c = ph.adjoint_case_256(seed=seed)
     elif name == "large512":
         c = ph.large_case_512(seed=seed)
     else:
@@ -229,26 +234,29 @@ def run_reference(args):
         return 0
     case = workload(args.workload, 0, args.sim_steps)
     import oracle
-    # one step = oracle set-up + a bounded sample of time steps on the full grid
-    n, t_cal, t_setup, _ = oracle_sample(case, target_s=4.0, min_steps=2)
-    per_step_target = 12.0
-    n = max(2, int(n * per_step_target / max(4.0, 1e-9)))
+    # The oracle's set-up (S1, S2) runs once and is charged to every step pro rata:
+    # one bench step of the GPU runs the set-up and all case.nsteps time steps, one
+    # step here a bounded sample of n time steps on the full grid plus the necrosis
+    # read-out, with n / case.nsteps of the set-up time added.
+    n, t_cal, t_setup, m = oracle_sample(case, target_s=3.0, min_steps=2)
+    per_step_target = float(os.environ.get("RFA_REFERENCE_STEP_S", "5.0"))
+    n = max(2, int(n * per_step_target / 3.0))
     dmg = case.damage if case.damage.enable else None
+    st = oracle.initial_state(m)
     times = []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        m = oracle.setup(case, "bf16")
-        st = oracle.initial_state(m)
         oracle.run(m, st, n, damage=dmg)
         oracle.necrosis(m, st)
-        dt = time.perf_counter() - t0
+        dt = time.perf_counter() - t0 + t_setup * n / case.nsteps
         if k >= args.warmup:
             times.append(dt)
     tot = sum(times)
     value = case.nvox * n * len(times) / tot / 1e9
     sample = (f"FP64 oracle (C, OpenMP over z, {os.cpu_count()} threads) on the full "
-              f"{case.nx}x{case.ny}x{case.nz} phantom: set-up + {n} of {case.nsteps} time steps"
-              f"{' with Arrhenius' if case.damage.enable else ''} + necrosis per step")
+              f"{case.nx}x{case.ny}x{case.nz} phantom: {n} of {case.nsteps} time steps"
+              f"{' with Arrhenius' if case.damage.enable else ''} + necrosis per step, plus "
+              f"{n}/{case.nsteps} of the set-up's {t_setup:.1f} s")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
@@ -274,13 +282,15 @@ def _ms_between(torch, stream, fn):
     return e0.elapsed_time(e1)
 
 
-def measure_adjoint(rfa, stream, conduction="centre", cpu_baseline_on: bool = False):
-    """128^3, h = 0.75 mm, straight 20 W needle, 2000 steps: recorded forward
-    (sqrt(N) checkpoints) vs rfa_backward (recompute + adjoint + contractions),
-    seed = the C3 loss gradient of an arbitrary target.  conduction="harmonic"
-    runs the conservative form (its own forward and adjoint kernels)."""
+def measure_adjoint(rfa, stream, conduction="centre", cpu_baseline_on: bool = False, name="adjoint128"):
+    """adjoint128: 128^3, h = 0.75 mm, straight 20 W needle, 2000 steps (its
+    fields sit in L2); adjoint256: the same at 256^3, h = 0.5 mm (~0.8 GB of
+    fields, HBM-bound).  Recorded forward (sqrt(N) checkpoints) vs rfa_backward
+    (recompute + adjoint + contractions), seed = a uniform dL/dT.
+    conduction="harmonic" runs the conservative form (its own forward and
+    adjoint kernels)."""
     import torch
-    case = ph.adjoint_case_128()
+    case = workload(name, 0, None)
     case.conduction = conduction
     g = rfa.Grid.from_case(case, damage=False, cuda_stream=stream.cuda_stream)
     rfa.rfa_autotune(g.handle, None)      # the forward runs with the tuned schedule
@@ -301,11 +311,11 @@ def measure_adjoint(rfa, stream, conduction="centre", cpu_baseline_on: bool = Fa
     sched = rfa.rfa_get_schedule(g.handle)
     t_plain = _ms_between(torch, stream, lambda: g.step(case.nsteps))
     g.close()
-    res = {"workload": "adjoint128", "grid": [case.nx, case.ny, case.nz], "time_steps": case.nsteps,
+    res = {"workload": name, "grid": [case.nx, case.ny, case.nz], "time_steps": case.nsteps,
            "forward_recorded_ms": t_f, "backward_ms": t_b, "forward_unrecorded_ms": t_plain,
            "backward_over_forward": t_b / t_f, "schedule": sched}
     if cpu_baseline_on:
-        # the oracle's discrete adjoint beside it: 20 reverse steps of the same 128^3 case
+        # the oracle's discrete adjoint beside it: 20 reverse steps of the same case
         import oracle
         mo = oracle.setup(case, "f64")
         seed_np = np.full((case.nz, case.ny, case.nx), 1e-6)
@@ -314,8 +324,37 @@ def measure_adjoint(rfa, stream, conduction="centre", cpu_baseline_on: bool = Fa
         t = time.perf_counter() - t0
         res["cpu_baseline"] = {"value": case.nvox * 20 / t / 1e9, "unit": "GVox-steps/s (backward)",
                                "cores": os.cpu_count(), "kind": "oracle",
-                               "sample": "128^3, 20 steps of the FP64 oracle's adjoint (recompute and reverse)"}
+                               "sample": f"{case.nx}^3, 20 steps of the FP64 oracle's adjoint (recompute and reverse)"}
     return res
+
+
+def measure_single_grid(rfa, stream, name="umbrella256", schedule="auto", nsteps=None):
+    """One grid of ``name`` stepped alone with the given schedule ("auto": the
+    autotuner's pick, "plain": one step per launch): GVox-steps/s and the step
+    kernel's fraction of HBM on its algorithmic bytes (per launch, averaged over
+    the run, CUDA events on the launching stream).  Set-up outside the timing."""
+    import torch
+    case = workload(name, 0, nsteps)
+    g = rfa.Grid.from_case(case, cuda_stream=stream.cuda_stream)
+    if schedule == "auto":
+        rfa.rfa_autotune(g.handle, os.environ.get("RFA_AUTOTUNE_CACHE") or None)
+    elif schedule == "plain":
+        g.set_schedule(1, 0)
+    depth, variant = rfa.rfa_get_schedule(g.handle)
+    g.step(min(case.nsteps, 200))                 # warm-up
+    g.set_tissue(case.labels, case.table)
+    ms = _ms_between(torch, stream, lambda: g.step(case.nsteps))
+    g.close()
+    launches = case.nsteps // depth + case.nsteps % depth
+    peak, _ = measured_peak_hbm()
+    nbytes = algorithmic_bytes_per_voxel(bool(case.damage.enable), depth) * case.nvox
+    achieved = nbytes * launches / (ms * 1e-3) / 1e9
+    return {"workload": name, "grid": [case.nx, case.ny, case.nz], "time_steps": case.nsteps,
+            "schedule": {"tb_depth": depth, "tile_variant": variant},
+            "kernel": "k_step_tb" if depth > 1 else "k_step_plain",
+            "gvox_steps_s": case.nvox * case.nsteps / (ms * 1e-3) / 1e9, "ms": ms,
+            "avg_launch_us": 1e3 * ms / launches, "bytes_per_voxel_per_launch": nbytes / case.nvox,
+            "achieved_GBs": achieved, "peak_GBs": peak, "frac": achieved / peak}
 
 
 def measure_next_rows(rfa, stream, case, g, cpu_baseline_on: bool):
@@ -616,14 +655,17 @@ def run_ours(args):
     # end to end from host buffers (labels in, temperature field out)
     e2e = None
     if not args.no_e2e:
+        # at most 5 bench steps (each is a whole simulation), wall clock around them
+        n_e2e = max(2, min(args.steps, 5))
         one_step(True)
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(n_e2e):
             one_step(True)
         barrier()
         wall = time.perf_counter() - t0
-        e2e = {"value": vox_steps / reduce_max(wall, dist, dev) / 1e9, "unit": UNIT,
+        e2e = {"value": case.nvox * case.nsteps * n_e2e * world / reduce_max(wall, dist, dev) / 1e9,
+               "unit": UNIT, "steps": n_e2e,
                "h2d_bytes_per_step": int(case.nvox + 256 * 9 * 8 + 104),
                "d2h_bytes_per_step": int(case.nvox * 4 + 32 + 4)}
 
@@ -644,10 +686,29 @@ def run_ours(args):
     kernels_per_step = 2 + 3 + launches_per_step + 2   # setup (2), source (3), steps, necrosis (2)
     secondary = None
     if rank == 0 and not args.no_secondary:
-        secondary = {"adjoint": measure_adjoint(rfa, stream, cpu_baseline_on=not args.no_cpu_baseline),
-                     "batched": measure_batched(rfa, stream, args),
-                     "next_rows": measure_next_rows(rfa, stream, case, g, not args.no_cpu_baseline)}
+        secondary = {}
+        if args.workload != "umbrella256":
+            secondary["umbrella256"] = measure_single_grid(rfa, stream, "umbrella256", "auto")
+        secondary["umbrella256_plain"] = measure_single_grid(rfa, stream, "umbrella256", "plain", 2000)
+        secondary["adjoint"] = measure_adjoint(rfa, stream, cpu_baseline_on=not args.no_cpu_baseline)
+        secondary["adjoint256"] = measure_adjoint(rfa, stream, name="adjoint256")
+        secondary["batched"] = measure_batched(rfa, stream, args)
+        secondary["next_rows"] = measure_next_rows(rfa, stream, case, g, not args.no_cpu_baseline)
         secondary["path_rows"] = measure_path_rows(rfa, stream, case, g, labels_dev, not args.no_cpu_baseline)
+        # the ratios the targets name, last in the line (a log tail keeps them)
+        summ = {"headline_frac": roof["frac"]}
+        if "umbrella256" in secondary:
+            summ["umbrella256_gvox_steps_s"] = secondary["umbrella256"]["gvox_steps_s"]
+            summ["umbrella256_frac"] = secondary["umbrella256"]["frac"]
+        summ["plain_step_frac_256"] = secondary["umbrella256_plain"]["frac"]
+        summ["adjoint128_backward_over_forward"] = secondary["adjoint"]["backward_over_forward"]
+        summ["adjoint256_backward_over_forward"] = secondary["adjoint256"]["backward_over_forward"]
+        summ["conservative_adjoint128_backward_over_forward"] = \
+            secondary["next_rows"]["conservative_adjoint"]["backward_over_forward"]
+        summ["batched_over_plain_loop"] = secondary["batched"]["batched_over_plain_loop"]
+        summ["batched_over_tuned_loop"] = secondary["batched"]["batched_over_tuned_loop"]
+        summ["batched_gvox_steps_s"] = secondary["batched"]["batched_gvox_steps_s"]
+        secondary["summary"] = summ
     if dist is not None:
         dist.barrier()
     if rank == 0:
@@ -736,7 +797,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="umbrella256")
+    ap.add_argument("--workload", default="large512")
     ap.add_argument("--sim-steps", type=int, default=None, help="override time steps per bench step")
     ap.add_argument("--schedule", default="auto", help="auto | plain | tbN | tbNvV")
     ap.add_argument("--no-e2e", action="store_true")

@@ -424,6 +424,20 @@ rfa_status rfa_warp_temperature(rfa_grid *g, const float *u_inv_dev, void *dst_d
  * usable.  Uses the current device and the legacy default stream; synchronous. */
 rfa_status rfa_selftest_wait_timeout(long long spin_limit_cycles);
 
+/* Diagnostic (the paper has no counterpart): spin limits, in SM clock cycles,
+ * of the library's real device-side waits -- the TMA (mbarrier) waits of the
+ * blocked and batched step kernels, and the batch's grid barrier between time
+ * blocks -- for kernels launched afterwards on the current device, by any grid
+ * of this process.  Defaults 2^32 each (about 2 s at 2 GHz).  A wait that runs
+ * out records a timeout; the next synchronising call of the grid (of the
+ * batch's first member) returns RFA_E_TIMEOUT and names the wait; the kernel's
+ * outputs are then undefined until rfa_set_tissue or rfa_set_state.  A CTA that
+ * gives up first waits, with the full limit, for its own copies in flight, so
+ * short limits never leave a copy landing in released shared memory.  Limits
+ * below 2^20 cycles poll without suspending the waiting thread.  Synchronous.
+ * Errors: RFA_E_INVALID (a limit outside 1..2^32), RFA_E_CUDA. */
+rfa_status rfa_set_wait_limits(long long mbarrier_cycles, long long grid_barrier_cycles);
+
 /* Wait for the grid's stream and report deferred device errors. */
 rfa_status rfa_synchronize(rfa_grid *g);
 

@@ -35,7 +35,7 @@ EXPORTED = ("rfa_create_grid", "rfa_destroy_grid", "rfa_set_tissue", "rfa_place_
             "rfa_last_error", "rfa_necrosis_reduce_noalloc", "rfa_batch_autotune",
             "rfa_batch_get_schedule", "rfa_selftest_wait_timeout", "rfa_warp_temperature",
             "rfa_set_conduction", "rfa_place_needle_potential", "rfa_set_perfusion_coupling",
-            "rfa_set_potential_preconditioner")
+            "rfa_set_potential_preconditioner", "rfa_set_wait_limits")
 
 
 class RfaError(RuntimeError):
@@ -98,6 +98,7 @@ def lib():
         "rfa_batch_autotune": [P, ctypes.c_char_p],
         "rfa_batch_get_schedule": [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)],
         "rfa_selftest_wait_timeout": [ctypes.c_longlong],
+        "rfa_set_wait_limits": [ctypes.c_longlong, ctypes.c_longlong],
         "rfa_warp_temperature": [P, P, P, I],
         "rfa_set_conduction": [P, I],
         "rfa_set_perfusion_coupling": [P, I],
@@ -333,6 +334,13 @@ def rfa_batch_get_schedule(b):
 
 def rfa_selftest_wait_timeout(spin_limit_cycles: int):
     _check(lib().rfa_selftest_wait_timeout(int(spin_limit_cycles)), "rfa_selftest_wait_timeout")
+
+
+WAIT_LIMIT_DEFAULT = 1 << 32
+
+
+def rfa_set_wait_limits(mbarrier_cycles: int = WAIT_LIMIT_DEFAULT, grid_barrier_cycles: int = WAIT_LIMIT_DEFAULT):
+    _check(lib().rfa_set_wait_limits(int(mbarrier_cycles), int(grid_barrier_cycles)), "rfa_set_wait_limits")
 
 
 def rfa_synchronize(g):

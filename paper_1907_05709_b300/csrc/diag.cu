@@ -4,7 +4,8 @@
 // barrier) spins with a clock64 limit and, when the limit passes, records
 // kStatusTimeout instead of hanging.  rfa_selftest_wait_timeout exercises the
 // same pattern on a flag that nothing sets, so the host-side reporting can be
-// tested without faulting or hanging a GPU.
+// tested without faulting or hanging a GPU; rfa_set_wait_limits shortens the
+// limits of the real waits so that a test can make them run out.
 #include "rfa_internal.cuh"
 
 namespace rfa {
@@ -48,5 +49,16 @@ extern "C" rfa_status rfa_selftest_wait_timeout(long long spin_limit_cycles)
         set_error("device-side wait gave up after its limit (self-test)");
         return RFA_E_TIMEOUT;
     }
+    return RFA_OK;
+}
+
+extern "C" rfa_status rfa_set_wait_limits(long long mbarrier_cycles, long long grid_barrier_cycles)
+{
+    if (mbarrier_cycles < 1 || mbarrier_cycles > (1ll << 32) || grid_barrier_cycles < 1 ||
+        grid_barrier_cycles > (1ll << 32)) {
+        set_error("wait limits must be in 1..2^32 cycles");
+        return RFA_E_INVALID;
+    }
+    RFA_CUDA(tb_set_wait_limits(mbarrier_cycles, grid_barrier_cycles));
     return RFA_OK;
 }

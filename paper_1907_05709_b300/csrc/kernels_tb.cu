@@ -105,24 +105,46 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+// Spin limits of the bounded waits in SM clock cycles: the TMA (mbarrier) waits
+// and the batch's grid barrier.  2^32 cycles (about 2 s at 2 GHz) unless a test
+// shortens them through rfa_set_wait_limits; kernels read them at start.
+__device__ long long g_wait_limit_mbar = 1ll << 32;
+__device__ long long g_wait_limit_grid = 1ll << 32;
+// the wait for a CTA's own copies in flight before it leaves after a timeout
+// keeps the full limit whatever the limits above are
+constexpr long long kDrainLimit = 1ll << 32;
+
 // bounded wait for the phase with the given parity; false on timeout.  Each
 // try_wait may suspend the thread for up to kSuspendNs (it resumes as soon as
 // the phase completes), so waiting warps do not spin on the issue slots.
+// Limits below kSuspendMin poll with the non-blocking test_wait instead, so a
+// short limit is not hidden inside one suspended try_wait.
 constexpr uint32_t kSuspendNs = 100000;
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+constexpr long long kSuspendMin = 1ll << 20;
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit)
 {
     const long long t0 = clock64();
+    const bool suspend = limit >= kSuspendMin;
     while (true) {
         uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity), "r"(kSuspendNs)
-            : "memory");
+        if (suspend)
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(done)
+                : "r"(bar), "r"(parity), "r"(kSuspendNs)
+                : "memory");
+        else
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(done)
+                : "r"(bar), "r"(parity)
+                : "memory");
         if (done) return true;
-        if (clock64() - t0 > (1ll << 32)) return false;  // ~2 s at 2 GHz
+        if (clock64() - t0 > limit) return false;
     }
 }
 
@@ -145,7 +167,9 @@ __device__ __forceinline__ float4 ld4(const float *sm, int off)
 struct TBPipe {
     float *sm;
     uint32_t sm_base, bar_base;
-    long long nload;  // stage-0 planes loaded so far (ring slot and mbarrier phase)
+    long long nload;   // stage-0 planes consumed so far (ring slot and mbarrier phase)
+    long long issued;  // stage-0 planes requested so far (thread 0 only)
+    long long limit;   // spin limit of the mbarrier waits
 };
 
 template <int M, int V>
@@ -161,9 +185,10 @@ __device__ __forceinline__ void tb_item_geom(const TBTile &T, int item, int &X0,
 
 // stage-0 plane z of the tile at (X0, Y0) into ring slot j
 template <int M, int V>
-__device__ __forceinline__ void tb_issue(const TBPipe &P, int j, const CUtensorMap *maps, int X0, int Y0, int z)
+__device__ __forceinline__ void tb_issue(TBPipe &P, int j, const CUtensorMap *maps, int X0, int Y0, int z)
 {
     using C = Cfg<M, V>;
+    ++P.issued;
     const uint32_t dst = P.sm_base + 4u * (uint32_t)(j * C::SLOT0);
     const uint32_t bar = P.bar_base + 8u * j;
     mbar_expect_tx(bar, (uint32_t)(4 * C::BOX * 4));   // four boxes of 4-byte elements
@@ -317,7 +342,7 @@ __device__ bool tb_run(TBPipe &P, const Items &items, int nitems, const Get &get
                     om23 = reinterpret_cast<const double2 *>(A.omega + gio)[1];
                 }
             }
-            const bool ok = mbar_wait(bar_base + 8u * s0_cur, phase);
+            const bool ok = mbar_wait(bar_base + 8u * s0_cur, phase, P.limit);
             // the last stage's coefficients (plane p0 - M) go to registers before the
             // last barrier: its ring-0 slot is then refilled right after that barrier
             uint4 wM = make_uint4(0u, 0u, 0u, 0u);
@@ -474,9 +499,13 @@ __device__ bool tb_run(TBPipe &P, const Items &items, int nitems, const Get &get
                     // the stage-1 barrier also agrees on the stage-0 wait: a CTA whose
                     // wait timed out leaves (stage 1 only wrote shared memory)
                     if (__syncthreads_or(!ok)) {
-                        if (tid == 0) {  // let the request in flight land first (bounded)
+                        if (tid == 0) {
+                            // let every request in flight land before the CTA's shared
+                            // memory is released: planes nload .. issued-1 (bounded)
                             atomicOr(status, kStatusTimeout);
-                            mbar_wait(bar_base + 8u * s0_next, s0_next == 0 ? phase ^ 1u : phase);
+                            for (long long q = P.nload; q < P.issued; ++q)
+                                mbar_wait(bar_base + 8u * (uint32_t)(q % S0), (uint32_t)((q / S0) & 1),
+                                          kDrainLimit);
                         }
                         return false;
                     }
@@ -533,6 +562,8 @@ __device__ __forceinline__ bool tb_setup(TBPipe &P, unsigned *status)
     P.sm_base = smem_u32(sm);
     P.bar_base = P.sm_base + 4u * C::BAR_OFF;
     P.nload = 0;
+    P.issued = 0;
+    P.limit = g_wait_limit_mbar;
     if (P.sm_base & 127u) {  // TMA destinations need 128-byte alignment
         if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
         return false;
@@ -583,9 +614,9 @@ struct TBMember {
     int item_begin, cur0;
 };
 
-// Software grid barrier for a cooperative (co-resident) grid; bounded spin.
-// bar[0] counts arrivals, bar[1] is the generation.
-__device__ bool grid_sync(unsigned *bar, unsigned nblocks)
+// Software grid barrier for a cooperative (co-resident) grid; bounded spin
+// (limit in SM cycles).  bar[0] counts arrivals, bar[1] is the generation.
+__device__ bool grid_sync(unsigned *bar, unsigned nblocks, long long limit)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -602,7 +633,7 @@ __device__ bool grid_sync(unsigned *bar, unsigned nblocks)
         } else {
             const long long t0 = clock64();
             while (*vgen == g) {
-                if (clock64() - t0 > (1ll << 32)) {
+                if (clock64() - t0 > limit) {
                     ok = 0;
                     break;
                 }
@@ -624,6 +655,7 @@ __global__ void __launch_bounds__(Cfg<M, V>::THREADS, Cfg<M, V>::MINB)
 {
     TBPipe P;
     if (!tb_setup<M, V>(P, status)) return;
+    const long long glimit = g_wait_limit_grid;
     bool bad = false;
     for (int t = 0; t < ntime; ++t) {
         auto get = [&](int item, int &local, const CUtensorMap *&mp) -> TBTile {
@@ -643,8 +675,8 @@ __global__ void __launch_bounds__(Cfg<M, V>::THREADS, Cfg<M, V>::MINB)
         const bool ok = fold ? tb_run<M, V, DMG, true, false>(P, items, nitems, get, status, bad)
                              : tb_run<M, V, DMG, false, false>(P, items, nitems, get, status, bad);
         if (!ok) break;
-        if (!grid_sync(gbar, gridDim.x)) {
-            if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+        if (!grid_sync(gbar, gridDim.x, glimit)) {
+            if (threadIdx.x == 0) atomicOr(status, kStatusTimeout | kStatusGridTimeout);
             break;
         }
         // the next block's TMA (async proxy) reads what other CTAs just stored
@@ -796,6 +828,13 @@ MapCache &map_cache()
 }
 
 }  // namespace
+
+cudaError_t tb_set_wait_limits(long long mbar_cycles, long long grid_cycles)
+{
+    cudaError_t e = cudaMemcpyToSymbol(g_wait_limit_mbar, &mbar_cycles, sizeof mbar_cycles);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(g_wait_limit_grid, &grid_cycles, sizeof grid_cycles);
+}
 
 bool tb_supported(const rfa_grid *g, int depth, int variant)
 {

@@ -31,6 +31,7 @@ namespace rfa {
 constexpr unsigned kStatusNonfinite = 1u;
 constexpr unsigned kStatusTimeout = 2u;
 constexpr unsigned kStatusBadLabel = 4u;
+constexpr unsigned kStatusGridTimeout = 8u;  // with kStatusTimeout: the batch's grid barrier ran out
 constexpr int kMaxSegments = 17;
 constexpr int kReduceBlocks = 592;  // 4 per SM on 148 SMs; fixed => deterministic reductions
 constexpr int kCarrySteps = 256;   // fold the FP32 damage carry into the FP64 integral every 256 steps
@@ -238,6 +239,9 @@ cudaError_t launch_adjoint_cond(rfa_grid *g, const float *lam_in, float *lam_out
                                 double *acc);
 // temporal-blocked TMA kernel (kernels_tb.cu)
 bool tb_supported(const rfa_grid *g, int depth, int variant);
+// spin limits (SM cycles) of the blocked kernels' mbarrier waits and of the
+// batch's grid barrier, for kernels launched afterwards on the current device
+cudaError_t tb_set_wait_limits(long long mbar_cycles, long long grid_cycles);
 void tb_forget_maps(const rfa_grid *g);
 cudaError_t launch_step_tb(rfa_grid *g, int depth, int variant, const void *th_in,
                            const void *lo_in, void *th_out, void *lo_out, bool damage, bool fold);

@@ -281,6 +281,14 @@ def adjoint_case_128(seed: int = 0, nsteps: int = 2000) -> Case:
                               kind=STRAIGHT, damage=Damage(enable=0), name="adjoint128")
 
 
+def adjoint_case_256(seed: int = 0, nsteps: int = 2000) -> Case:
+    """The adjoint workload at the single-needle size: 256^3, h = 0.5 mm, tumour +
+    vessel phantom, straight 15 mm needle at 20 W, dt = 0.05 s, 2000 steps
+    (damage off); its fields (~0.8 GB) do not fit in L2."""
+    return single_needle_case(seed=seed, n=256, h=0.5e-3, nsteps=nsteps, power=20.0,
+                              kind=STRAIGHT, damage=Damage(enable=0), name="adjoint256")
+
+
 def large_case_512(seed: int = 0, nsteps: int = 5000) -> Case:
     """512^3, h = 0.25 mm, 8 vessels, 9-tine umbrella (8 ring + 1 axial) at 40 W,
     dt = 0.02 s, 5000 steps, Arrhenius damage on."""

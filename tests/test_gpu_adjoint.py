@@ -81,6 +81,16 @@ def test_adjoint_128_cube_2000_steps():
     _compare_grads(g_gpu, g_orc, len(case.table))
 
 
+def test_adjoint_256_cube_bounded_steps():
+    """The HBM-bound size the bench times (256^3, h = 0.5 mm, straight needle at
+    20 W), recorded with the autotuned blocked schedule; the oracle's FP64
+    discrete adjoint is run for the first 150 of the bench's 2000 steps (about
+    ten seconds of CPU work) and every gradient compared."""
+    case = ph.adjoint_case_256(nsteps=150)
+    g_gpu, g_orc = _adjoint_case(case, 150, schedule=(2, 0))
+    _compare_grads(g_gpu, g_orc, len(case.table))
+
+
 def test_backward_needs_recorded_steps():
     import torch
     case = ph.random_small_case(3, 20, 20, 20)

@@ -72,3 +72,74 @@ def test_bounded_wait_times_out_and_context_survives():
     g.synchronize()
     assert np.all(np.isfinite(g.temperature()))
     g.close()
+
+
+def _restore_limits():
+    rfa.rfa_set_wait_limits(rfa.WAIT_LIMIT_DEFAULT, rfa.WAIT_LIMIT_DEFAULT)
+
+
+def test_tma_wait_of_the_blocked_step_runs_out_and_the_grid_recovers():
+    """The blocked step's own mbarrier waits with a 1-cycle limit: the first
+    wait of every CTA gives up before its TMA copy lands, the CTA waits (with the
+    full limit) for its copies in flight and leaves, and the grid reports
+    RFA_E_TIMEOUT.  With the limits restored, set-up and stepping give the same
+    bits as a grid that never timed out."""
+    case = ph.random_small_case(9, 70, 40, 30, kind=ph.UMBRELLA, power=6.0)
+    ref = rfa.Grid.from_case(case)
+    ref.set_schedule(2, 0)
+    ref.step(40)
+    want = ref.temperature()
+    ref.close()
+    g = rfa.Grid.from_case(case)
+    g.set_schedule(2, 0)
+    try:
+        rfa.rfa_set_wait_limits(1, rfa.WAIT_LIMIT_DEFAULT)
+        g.step(4)
+        with pytest.raises(rfa.RfaError) as e:
+            g.synchronize()
+        assert e.value.status == 7 and "mbarrier" in str(e.value)
+    finally:
+        _restore_limits()
+    g.set_tissue(case.labels, case.table)   # clears the status, state from the labels
+    g.step(40)
+    g.synchronize()
+    assert np.array_equal(g.temperature(), want)
+    g.close()
+
+
+def test_grid_barrier_of_the_batch_runs_out_and_the_batch_recovers():
+    """The batch's grid barrier between time blocks with a 1-cycle limit: CTAs
+    that arrive before the others give up, the launch reports RFA_E_TIMEOUT on
+    the first member, naming the grid barrier.  With the limits restored the
+    members, set up again, step to the same bits as stepped alone."""
+    cases = [ph.random_small_case(40 + k, 64 + 8 * k, 48, 40, kind=ph.UMBRELLA, power=5.0) for k in range(6)]
+    grids = [rfa.Grid.from_case(c) for c in cases]
+    b = rfa.rfa_batch_create([g.handle for g in grids])
+    try:
+        rfa.rfa_set_wait_limits(rfa.WAIT_LIMIT_DEFAULT, 1)
+        rfa.rfa_batch_step(b, 8)
+        with pytest.raises(rfa.RfaError) as e:
+            grids[0].synchronize()
+        assert e.value.status == 7 and "grid barrier" in str(e.value)
+    finally:
+        _restore_limits()
+    for g, c in zip(grids, cases):
+        g.set_tissue(c.labels, c.table)
+    rfa.rfa_batch_step(b, 8)
+    grids[0].synchronize()
+    got = [g.temperature() for g in grids]
+    rfa.rfa_batch_destroy(b)
+    for g, c, t in zip(grids, cases, got):
+        alone = rfa.Grid.from_case(c)
+        alone.set_schedule(2, 0)
+        alone.step(8)
+        assert np.array_equal(alone.temperature(), t)
+        alone.close()
+        g.close()
+
+
+def test_wait_limits_are_checked():
+    for bad in ((0, 1 << 32), (1, 0), ((1 << 32) + 1, 5)):
+        with pytest.raises(rfa.RfaError) as e:
+            rfa.rfa_set_wait_limits(*bad)
+        assert e.value.status == 1

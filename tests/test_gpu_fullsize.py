@@ -1,10 +1,12 @@
-"""Parity at the benchmark's full size and launch configuration (256^3 umbrella
-phantom, autotuned blocked schedule, compensated FP32 state, BF16 coefficients,
-Arrhenius damage):
-  - every voxel against the FP64 oracle after the first 300 of its 12000 steps
-    (the oracle finishes that in seconds);
-  - the whole 12000-step run against the FP64 GPU path on the same coefficients
-    (that path matches the oracle to 1e-9 K in the smaller parity tests)."""
+"""Parity at the single-needle workload's full size and launch configuration
+(256^3 umbrella phantom, autotuned blocked schedule, compensated FP32 state,
+BF16 coefficients, Arrhenius damage):
+  - every voxel against the FP64 oracle after the first 300 of its 12000 steps;
+  - the whole 12000-step run, every voxel, against the FP64 oracle on the same
+    coefficients (a few minutes of CPU work on the host cores) and against the
+    FP64 GPU path.
+The 512^3 workload is compared on a 128^3 crop and with the FP64 GPU path in
+test_gpu_precision_study.py."""
 import numpy as np
 import pytest
 
@@ -36,6 +38,21 @@ def test_umbrella256_first_300_steps_every_voxel():
     gpu = _gpu_run(case, rfa.STATE_F32C, 300, tune=True)
     assert gpu["schedule"][0] >= 1
     compare(case, gpu, orc, rfa.STATE_F32C)
+
+
+def test_umbrella256_12000_steps_every_voxel_against_the_oracle():
+    """Eq. CUDAbioheat3d stepped 12000 times with the 60 C latch and Eq.
+    eq-tissState: T within 1e-3 K, Omega within the relative tolerance, masks
+    equal outside the bands, counts and the smoothed volume as in every parity
+    test."""
+    case = ph.umbrella_case_256(seed=0)
+    gpu = _gpu_run(case, rfa.STATE_F32C, case.nsteps, tune=True)
+    orc = run_oracle(case, rfa.PARAM_BF16, case.nsteps)
+    res = compare(case, gpu, orc, rfa.STATE_F32C)
+    assert orc["counts"][0] > 1000 and orc["counts"][1] > 1000    # the case really ablates
+    print(f"256^3 x 12000 vs oracle: max|dT| = {res['err_T']:.3e} K, "
+          f"max rel dOmega = {res['err_omega_rel']:.3e}, band voxels {res['mask_band']}, "
+          f"schedule {gpu['schedule']}")
 
 
 def test_umbrella256_12000_steps_against_fp64_gpu():
