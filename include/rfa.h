@@ -53,7 +53,9 @@ typedef enum {
     RFA_E_STATE = 5,        /* call out of order (e.g. step before set_tissue) */
     RFA_E_NONFINITE = 6,    /* a step produced a non-finite temperature */
     RFA_E_TIMEOUT = 7,      /* a bounded device-side wait gave up */
-    RFA_E_UNSUPPORTED = 8   /* a valid request the library does not serve on this path */
+    RFA_E_UNSUPPORTED = 8,  /* a valid request the library does not serve on this path */
+    RFA_E_INTERNAL = 9      /* an internal consistency check failed (index checks of the
+                               checked build, librfa_check.so) */
 } rfa_status;
 
 /* State precision: FP32, FP32 hi + FP32 lo compensated pair, FP64. */

@@ -16,7 +16,9 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "librfa.so")
+# RFA_CHECKED_BUILD=1 loads the checked build (index checks in the kernels,
+# built by build.py --checked) instead of the ordinary one
+LIB_PATH = os.path.join(_HERE, "librfa_check.so" if os.environ.get("RFA_CHECKED_BUILD") == "1" else "librfa.so")
 
 STATE_F32, STATE_F32C, STATE_F64 = 0, 1, 2
 PARAM_BF16, PARAM_F32, PARAM_F64 = 0, 1, 2
@@ -25,7 +27,8 @@ NEEDLE_STRAIGHT, NEEDLE_UMBRELLA, NEEDLE_FIXED_TIP = 0, 1, 2
 FIELD_THETA, FIELD_A, FIELD_B, FIELD_S, FIELD_LATCH, FIELD_OMEGA, FIELD_THETA_LO = range(7)
 
 STATUS = {0: "RFA_OK", 1: "RFA_E_INVALID", 2: "RFA_E_OOM", 3: "RFA_E_CUDA", 4: "RFA_E_UNSTABLE",
-          5: "RFA_E_STATE", 6: "RFA_E_NONFINITE", 7: "RFA_E_TIMEOUT", 8: "RFA_E_UNSUPPORTED"}
+          5: "RFA_E_STATE", 6: "RFA_E_NONFINITE", 7: "RFA_E_TIMEOUT", 8: "RFA_E_UNSUPPORTED",
+          9: "RFA_E_INTERNAL"}
 
 EXPORTED = ("rfa_create_grid", "rfa_destroy_grid", "rfa_set_tissue", "rfa_place_needle",
             "rfa_set_damage", "rfa_step", "rfa_get_temperature", "rfa_get_field",
@@ -68,7 +71,7 @@ def lib():
     if _lib is not None:
         return _lib
     if not os.path.exists(LIB_PATH):
-        raise RuntimeError(f"librfa.so is not built ({LIB_PATH}); run "
+        raise RuntimeError(f"{os.path.basename(LIB_PATH)} is not built ({LIB_PATH}); run "
                            "python paper_1907_05709_b300/build.py")
     L = ctypes.CDLL(LIB_PATH)
     P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64

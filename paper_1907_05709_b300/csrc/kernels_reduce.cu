@@ -47,8 +47,9 @@ __global__ void __launch_bounds__(256) k_necrosis(const void *th, const float *l
                                                   const float *carry,
                                                   int nx, int ny, int nz, int pitch, double T_a,
                                                   double T_thr, double inv_width,
-                                                  uint8_t *mask_dense, NecroPartial *part)
+                                                  uint8_t *mask_dense, NecroPartial *part, unsigned *status)
 {
+    const size_t nvp = (size_t)pitch * ny * nz;
     unsigned n0 = 0, n1 = 0;
     double sm = 0.0;
     const double off = T_thr - T_a;
@@ -58,6 +59,7 @@ __global__ void __launch_bounds__(256) k_necrosis(const void *th, const float *l
         for (int x0 = 4 * (int)(threadIdx.x & 31); x0 < nx; x0 += 128) {
             const int nin = nx - x0 < 4 ? nx - x0 : 4;
             uint8_t m[4];
+            if (!RFA_CHECK_RANGE(rb + x0, rb + x0 + 4, nvp, rb + x0, 4, status)) continue;
             necro_quad<SP>(th, lo, latch, omega, carry, rb + x0, nin, off, inv_width, offf, iwf, n0, n1, sm, m);
             if (mask_dense)
                 for (int q = 0; q < nin; ++q) mask_dense[(size_t)row * nx + x0 + q] = m[q];
@@ -171,15 +173,15 @@ cudaError_t launch_necrosis(rfa_grid *g, uint8_t *mask_dense_dev, double width_K
     if (g->sp == RFA_STATE_F64)
         k_necrosis<RFA_STATE_F64><<<kReduceBlocks, 256, 0, g->stream>>>(
             th, lo, g->latch, g->omega, g->omega_c, g->nx, g->ny, g->nz, g->pitch, g->T_a, g->T_thr, iw,
-            mask_dense_dev, part);
+            mask_dense_dev, part, g->status);
     else if (g->sp == RFA_STATE_F32C)
         k_necrosis<RFA_STATE_F32C><<<kReduceBlocks, 256, 0, g->stream>>>(
             th, lo, g->latch, g->omega, g->omega_c, g->nx, g->ny, g->nz, g->pitch, g->T_a, g->T_thr, iw,
-            mask_dense_dev, part);
+            mask_dense_dev, part, g->status);
     else
         k_necrosis<RFA_STATE_F32><<<kReduceBlocks, 256, 0, g->stream>>>(
             th, lo, g->latch, g->omega, g->omega_c, g->nx, g->ny, g->nz, g->pitch, g->T_a, g->T_thr, iw,
-            mask_dense_dev, part);
+            mask_dense_dev, part, g->status);
     k_necrosis_final<<<1, 256, 0, g->stream>>>(part, kReduceBlocks, (NecroPartial *)result_dev);
     return cudaGetLastError();
 }

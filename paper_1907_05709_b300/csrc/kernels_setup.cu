@@ -80,6 +80,10 @@ __global__ void __launch_bounds__(256) k_setup(const uint8_t *__restrict__ label
             T th = T(0);
             float lo = 0.f;
             uint8_t l = 0;
+            if (!RFA_CHECK_RANGE(i, i + 1, (size_t)pitch * ny * nz, 0, 1, status) ||
+                (x < nx && !RFA_CHECK_RANGE((size_t)row * nx + x, (size_t)row * nx + x + 1, (size_t)nx * ny * nz, 0, 1,
+                                            status)))
+                continue;
             if (x < nx) {
                 l = labels[(size_t)row * nx + x];
                 if (l >= n_labels) {
@@ -169,7 +173,8 @@ __device__ __forceinline__ double needle_dist2_pruned(const NeedleGeom &g, const
 // pass 1: per-block sums of w over free voxels
 __global__ void k_source_sum(NeedleGeom geom, const uint8_t *__restrict__ label,
                              const LabelCoef *__restrict__ tab, int nx, int ny, int nz,
-                             int pitch, double h, int face, float margin, double *partial, double *wbuf)
+                             int pitch, double h, int face, float margin, double *partial, double *wbuf,
+                             unsigned *status)
 {
     __shared__ float s32[kMaxSegments][7];
     if (threadIdx.x < geom.nseg) {
@@ -193,6 +198,7 @@ __global__ void k_source_sum(NeedleGeom geom, const uint8_t *__restrict__ label,
         int z = (int)(r / ny);
         bool face_vox = (x == 0 || y == 0 || z == 0 || x == nx - 1 || y == ny - 1 || z == nz - 1);
         if (tab[label[i]].fixed || (face == RFA_FACE_DIRICHLET && face_vox)) continue;
+        if (!RFA_CHECK_RANGE(i, i + 1, nvp, 0, 1, status)) continue;
         const double w = needle_weight2(
             geom, needle_dist2_pruned(geom, s32, x * h, y * h, z * h, x * hf, y * hf, z * hf, margin));
         wbuf[i] = w;
@@ -221,7 +227,7 @@ template <int SP>
 __global__ void __launch_bounds__(256) k_source_write(const uint8_t *__restrict__ label,
                                                       const LabelCoef *__restrict__ tab, int n_labels, int nx,
                                                       int ny, int nz, int pitch, int face, const double *Wp,
-                                                      const double *wbuf, void *s)
+                                                      const double *wbuf, void *s, unsigned *status)
 {
     using T = typename std::conditional<SP == RFA_STATE_F64, double, float>::type;
     __shared__ double qm[256], dtrc[256];
@@ -239,6 +245,7 @@ __global__ void __launch_bounds__(256) k_source_write(const uint8_t *__restrict_
         const size_t rb = (size_t)row * pitch;
         for (int x = threadIdx.x & 31; x < pitch; x += 32) {
             const size_t i = rb + x;
+            if (!RFA_CHECK_RANGE(i, i + 1, (size_t)pitch * ny * nz, 0, 1, status)) continue;
             double v = 0.0;
             if (x < nx) {
                 const int l = label[i];
@@ -269,7 +276,7 @@ struct TipGeom {
 template <int SP, int PP>
 __global__ void k_tip(TipGeom t, const uint8_t *__restrict__ label, const LabelCoef *__restrict__ tab, int nx,
                       int ny, int nz, int pitch, int face, double T_a, double th_tip, bool paint, void *th,
-                      void *lo, void *ab, void *s)
+                      void *lo, void *ab, void *s, unsigned *status)
 {
     using T = typename std::conditional<SP == RFA_STATE_F64, double, float>::type;
     using AB = typename std::conditional<PP == RFA_PARAM_BF16, uint32_t,
@@ -284,6 +291,7 @@ __global__ void k_tip(TipGeom t, const uint8_t *__restrict__ label, const LabelC
     p[(t.ax + 2) % 3] += v;
     if (p[0] < 0 || p[1] < 0 || p[2] < 0 || p[0] >= nx || p[1] >= ny || p[2] >= nz) return;
     const size_t i = ((size_t)p[2] * ny + p[1]) * pitch + p[0];
+    if (!RFA_CHECK_RANGE(i, i + 1, (size_t)pitch * ny * nz, 0, 1, status)) return;
     double a = 0.0, b = 0.0, thv = th_tip;
     bool set_theta = paint;
     if (paint) {
@@ -328,7 +336,7 @@ cudaError_t launch_tip(rfa_grid *g, bool paint, double T_tip_C)
 #define TIP_CASE(SPV, PPV)                                                                                       \
     if (g->sp == SPV && g->pp == PPV)                                                                           \
         k_tip<SPV, PPV><<<1, 96, 0, g->stream>>>(t, g->label, g->d_table, g->nx, g->ny, g->nz, g->pitch, g->face, \
-                                                 g->T_a, th_tip, paint, th, lo, g->ab, g->s);
+                                                 g->T_a, th_tip, paint, th, lo, g->ab, g->s, g->status);
     TIP_CASE(RFA_STATE_F32, RFA_PARAM_BF16)
     TIP_CASE(RFA_STATE_F32, RFA_PARAM_F32)
     TIP_CASE(RFA_STATE_F32, RFA_PARAM_F64)
@@ -372,11 +380,11 @@ cudaError_t launch_source_write(rfa_grid *g, const double *partial, int npartial
     if (g->sp == RFA_STATE_F64)
         k_source_write<RFA_STATE_F64><<<148 * 8, 256, 0, g->stream>>>(
             g->label, g->d_table, g->n_labels, g->nx, g->ny, g->nz, g->pitch, g->face, W, (const double *)g->stage,
-            g->s);
+            g->s, g->status);
     else
         k_source_write<RFA_STATE_F32><<<148 * 8, 256, 0, g->stream>>>(
             g->label, g->d_table, g->n_labels, g->nx, g->ny, g->nz, g->pitch, g->face, W, (const double *)g->stage,
-            g->s);
+            g->s, g->status);
     return cudaGetLastError();
 }
 
@@ -395,7 +403,7 @@ cudaError_t launch_source(rfa_grid *g)
     const float margin = (float)(2e-4 * L * L);
     k_source_sum<<<kReduceBlocks, 256, 0, g->stream>>>(g->geom, g->label, g->d_table, g->nx,
                                                        g->ny, g->nz, g->pitch, g->h, g->face, margin,
-                                                       partial, (double *)g->stage);
+                                                       partial, (double *)g->stage, g->status);
     return launch_source_write(g, partial, kReduceBlocks);
 }
 

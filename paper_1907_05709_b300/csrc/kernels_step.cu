@@ -130,7 +130,8 @@ __global__ void __launch_bounds__(256) k_step_plain(const PlainArgs A)
 
     Q4<T> hm = zq<T>(), hc = zq<T>(), hp = zq<T>();
     Q4<float> lm = zq<float>(), lc = zq<float>(), lp = zq<float>();
-    if (inrow) {
+    if (inrow && RFA_CHECK_RANGE((long long)((size_t)zb * A.plane + rowoff) - (zb > 0 ? (long long)A.plane : 0),
+                                 (size_t)zb * A.plane + rowoff + 4, A.plane * A.nz, rowoff, 4, A.status)) {
         if (zb > 0) hm = ldq(hin + (size_t)(zb - 1) * A.plane + rowoff);
         hc = ldq(hin + (size_t)zb * A.plane + rowoff);
         if (COMP) {
@@ -142,12 +143,19 @@ __global__ void __launch_bounds__(256) k_step_plain(const PlainArgs A)
     for (int z = zb; z < ze; ++z) {
         const size_t i = (size_t)z * A.plane + rowoff;
         const bool hasZp = z + 1 < A.nz, hasZm = z > 0;
+        // checked build: every access of this iteration lies in [i - pitch - 1, i + plane + 5)
+        // of arrays of plane * nz elements, quads 4-aligned (inb == inrow otherwise)
+        const bool inb =
+            inrow && RFA_CHECK_RANGE((long long)i - (hasYm ? A.pitch : 0) - (lane == 0 && hasL ? 1 : 0),
+                                     i + (hasZp ? A.plane : hasYp ? (size_t)A.pitch : 0) +
+                                         (lane == 31 && hasR ? 5 : 4),
+                                     A.plane * A.nz, i, 4, A.status);
         Q4<T> hym = zq<T>(), hyp = zq<T>();
         Q4<float> lym = zq<float>(), lyp = zq<float>();
         T aq[4], bq[4], sq[4];
         T left = T(0), right = T(0);
         float lleft = 0.f, lright = 0.f;
-        if (inrow) {
+        if (inb) {
             if (hasZp) {
                 hp = ldq(hin + i + A.plane);
                 if (COMP) lp = ldq(lin + i + A.plane);
@@ -172,15 +180,15 @@ __global__ void __launch_bounds__(256) k_step_plain(const PlainArgs A)
             lleft = __shfl_up_sync(FULL, lc.v[3], 1);
             lright = __shfl_down_sync(FULL, lc.v[0], 1);
         }
-        if (inrow && lane == 0 && hasL) {
+        if (inb && lane == 0 && hasL) {
             left = hin[i - 1];
             if (COMP) lleft = lin[i - 1];
         }
-        if (inrow && lane == 31 && hasR) {
+        if (inb && lane == 31 && hasR) {
             right = hin[i + 4];
             if (COMP) lright = lin[i + 4];
         }
-        if (inrow) {
+        if (inb) {
             Q4<T> ho;
             Q4<float> lo;
             uint32_t latch_bits = 0;

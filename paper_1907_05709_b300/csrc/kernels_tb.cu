@@ -212,6 +212,43 @@ struct ClaimedItems {
     __device__ int after(int) const { return (int)atomicAdd(ctr, 1u); }
 };
 
+// Checked build: every shared-memory word stage k reads or writes for the quad at
+// plane offset id lies inside the rings (below the mbarriers).  The ordinary build
+// compiles this to true.
+template <int M, int V>
+__device__ __forceinline__ bool tb_stage_smem_ok(int k, const int *r0, const int *e, const int *f, int id,
+                                                 unsigned *status)
+{
+#ifdef RFA_CHECK
+    using C = Cfg<M, V>;
+    constexpr int PLANE = C::PLANE;
+    int lo = r0[k], hi = r0[k] + 4 * PLANE;  // coefficients (ab, s) of the stage's plane
+    if (k == 1) {
+        lo = min(lo, min(r0[0], min(r0[1], r0[2])));
+        hi = max(hi, max(r0[0], max(r0[1], r0[2])) + 2 * PLANE);
+    } else {
+        const int rk = C::ring_off(k - 1), sl = C::ring_planes(k - 1) * PLANE;
+        const int nsl = C::ring_slots(k - 1);
+        for (int d = 0; d < nsl; ++d) {
+            const int b = rk + (nsl == 4 ? f[d] : e[d % 3]) * sl;
+            lo = min(lo, b);
+            hi = max(hi, b + sl);
+        }
+    }
+    if (k < M) {
+        const int ro = C::ring_off(k), sl = C::ring_planes(k) * PLANE;
+        lo = min(lo, ro);
+        hi = max(hi, ro + C::ring_slots(k) * sl);
+    }
+    // words id - TB_EX - 1 .. id + TB_EX + 4 of every plane in [lo, hi)
+    return RFA_CHECK_RANGE((long long)lo + id - TB_EX - 1, (long long)hi - PLANE + id + TB_EX + 4, C::BAR_OFF, id,
+                           4, status) &&
+           RFA_CHECK_RANGE(lo, hi, C::BAR_OFF, 0, 1, status);
+#else
+    return true;
+#endif
+}
+
 // Advance the work items of `items` (< nitems) by M steps.
 // get(item, local, maps) returns the item's TBTile (a reference to kernel
 // parameters for one grid; a register copy for the batch), its index in that
@@ -329,8 +366,11 @@ __device__ bool tb_run(TBPipe &P, const Items &items, int nitems, const Get &get
             const int s0_next = s0_cur + 1 == S0 ? 0 : s0_cur + 1;
             // output-stage operands of plane p0 - M, loaded early to hide their latency
             const int qo = p0 - M;
-            const bool out_now = out_quad && it >= 2 * M && qo >= 0 && qo < A.nz;
-            const size_t gio = out_now ? (size_t)qo * A.plane + (size_t)yg * A.pitch + xg0 : 0;
+            const size_t gio_c = (size_t)(qo > 0 ? qo : 0) * A.plane + (size_t)yg * A.pitch + xg0;
+            // checked build: the output quad's global words lie in the grid's arrays
+            const bool out_now = out_quad && it >= 2 * M && qo >= 0 && qo < A.nz &&
+                                 RFA_CHECK_RANGE(gio_c, gio_c + 4, A.plane * A.nz, gio_c, 4, status);
+            const size_t gio = out_now ? gio_c : 0;
             float4 carry4 = make_float4(0.f, 0.f, 0.f, 0.f);
             uint32_t latch4 = 0;
             double2 om01 = make_double2(0.0, 0.0), om23 = om01;
@@ -353,7 +393,7 @@ __device__ bool tb_run(TBPipe &P, const Items &items, int nitems, const Get &get
             }
 #pragma unroll
             for (int k = 1; k <= M; ++k) {
-                if (it >= 2 * k && mact[k]) {
+                if (it >= 2 * k && mact[k] && tb_stage_smem_ok<M, V>(k, r0, e, f, mid[k], status)) {
                     const int id = mid[k];
                     const int cb = r0[k];                     // coefficients of plane q = p0 - k
                     int bc, bm, bp;                           // planes q, q - 1, q + 1 of stage k - 1
@@ -447,7 +487,10 @@ __device__ bool tb_run(TBPipe &P, const Items &items, int nitems, const Get &get
                         }
                         if (REC && mrec[k]) {
                             const int q = p0 - k, xr = X0 + mxo[k], yr = Y0 + myo[k];
-                            if (q >= zb && q < ze && yr < A.ny && xr < A.nx) {  // this item's planes only
+                            const size_t ro_ = (size_t)(k - 1) * A.rec_stride + (size_t)(q > 0 ? q : 0) * A.plane +
+                                               (size_t)yr * A.pitch + (xr > 0 ? xr : 0);
+                            if (q >= zb && q < ze && yr < A.ny && xr < A.nx &&  // this item's planes only
+                                RFA_CHECK_RANGE(ro_, ro_ + 4, (size_t)(M - 1) * A.rec_stride, ro_, 4, status)) {
                                 float *dst = A.rec_hi + (size_t)(k - 1) * A.rec_stride + (size_t)q * A.plane +
                                              (size_t)yr * A.pitch + xr;
                                 *reinterpret_cast<float4 *>(dst) = make_float4(H01.x, H01.y, H23.x, H23.y);

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256) k_na_partials(const void *th, const float
                                                      const uint8_t *latch, const double *omega,
                                                      const float *carry, int nx, int ny, int nz,
                                                      int pitch, double off, double inv_width,
-                                                     NaRecord *rec)
+                                                     NaRecord *rec, unsigned *status)
 {
     const unsigned nvp = (unsigned)((size_t)pitch * ny * nz);
     const unsigned begin = blockIdx.x * (unsigned)kNoAllocVoxelsPerRecord;
@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(256) k_na_partials(const void *th, const float
         if (x0 >= nx) continue;
         const int nin = nx - x0 < 4 ? nx - x0 : 4;
         uint8_t m[4];
+        if (!RFA_CHECK_RANGE(i, (size_t)i + 4, nvp, i, 4, status)) continue;
         necro_quad<SP>(th, lo, latch, omega, carry, i, nin, off, inv_width, offf, iwf, n0, n1, sm, m);
     }
     const unsigned long long c0 = na_block_sum((unsigned long long)n0), c1 = na_block_sum((unsigned long long)n1);
@@ -166,13 +167,13 @@ extern "C" rfa_status rfa_necrosis_reduce_noalloc(rfa_grid *g, double smooth_wid
     const unsigned nb = (unsigned)nrec;
     if (g->sp == RFA_STATE_F64)
         k_na_partials<RFA_STATE_F64><<<nb, 256, 0, g->stream>>>(th, lo, g->latch, g->omega, g->omega_c, g->nx,
-                                                                g->ny, g->nz, g->pitch, off, iw, rec);
+                                                                g->ny, g->nz, g->pitch, off, iw, rec, g->status);
     else if (g->sp == RFA_STATE_F32C)
         k_na_partials<RFA_STATE_F32C><<<nb, 256, 0, g->stream>>>(th, lo, g->latch, g->omega, g->omega_c, g->nx,
-                                                                 g->ny, g->nz, g->pitch, off, iw, rec);
+                                                                 g->ny, g->nz, g->pitch, off, iw, rec, g->status);
     else
         k_na_partials<RFA_STATE_F32><<<nb, 256, 0, g->stream>>>(th, lo, g->latch, g->omega, g->omega_c, g->nx,
-                                                                g->ny, g->nz, g->pitch, off, iw, rec);
+                                                                g->ny, g->nz, g->pitch, off, iw, rec, g->status);
     k_na_final<<<1, 256, 0, g->stream>>>(rec, (int)nrec, g->h * g->h * g->h, result_dev);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "rfa_necrosis_reduce_noalloc launch");

@@ -32,6 +32,26 @@ constexpr unsigned kStatusNonfinite = 1u;
 constexpr unsigned kStatusTimeout = 2u;
 constexpr unsigned kStatusBadLabel = 4u;
 constexpr unsigned kStatusGridTimeout = 8u;  // with kStatusTimeout: the batch's grid barrier ran out
+constexpr unsigned kStatusBadIndex = 16u;    // an index check of the checked build failed
+
+// Index checks of the checked build (compiled with -DRFA_CHECK, librfa_check.so):
+// an access range [lo, hi) outside [0, n), or a vector access whose first index
+// is not a multiple of `align`, records kStatusBadIndex in the grid's status
+// word and the access is skipped.  The ordinary build compiles every check to
+// `true`.  No check traps.
+#ifdef RFA_CHECK
+__device__ __forceinline__ bool check_range(long long lo, long long hi, long long n, long long first, int align,
+                                            unsigned *status)
+{
+    const bool ok = lo >= 0 && hi <= n && lo <= hi && (first % align) == 0;
+    if (!ok && status) atomicOr(status, kStatusBadIndex);
+    return ok;
+}
+#define RFA_CHECK_RANGE(lo, hi, n, first, align, status)                                                     \
+    ::rfa::check_range((long long)(lo), (long long)(hi), (long long)(n), (long long)(first), (align), (status))
+#else
+#define RFA_CHECK_RANGE(lo, hi, n, first, align, status) true
+#endif
 constexpr int kMaxSegments = 17;
 constexpr int kReduceBlocks = 592;  // 4 per SM on 148 SMs; fixed => deterministic reductions
 constexpr int kCarrySteps = 256;   // fold the FP32 damage carry into the FP64 integral every 256 steps

@@ -149,6 +149,8 @@ rfa_status read_status(rfa_grid *g)
     RFA_CUDA(cudaStreamSynchronize(g->stream));
     unsigned st = *g->status_host;
     if (st & kStatusNonfinite) return fail(RFA_E_NONFINITE, "a step produced a non-finite temperature");
+    if (st & kStatusBadIndex)
+        return fail(RFA_E_INTERNAL, "an index check of the checked build failed (an access outside its array)");
     if (st & kStatusGridTimeout) return fail(RFA_E_TIMEOUT, "a grid barrier wait of a batched launch exceeded its limit");
     if (st & kStatusTimeout) return fail(RFA_E_TIMEOUT, "a TMA (mbarrier) wait exceeded its limit");
     return RFA_OK;
