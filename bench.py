@@ -358,20 +358,21 @@ def measure_single_grid(rfa, stream, name="umbrella256", schedule="auto", nsteps
 
 
 def measure_next_rows(rfa, stream, case, g, cpu_baseline_on: bool):
-    """The model options at the bench's size, each against its compulsory bytes
-    (HBM roofline), and -- the CPU-baseline leg, unless disabled -- the FP64
-    oracle timed on a bounded sample beside it: breathing resample (Eq.
-    breathing), conservative conduction step, step with tissue-state perfusion,
-    potential-solve source (CG iterations)."""
+    """The model options, each against its compulsory bytes (HBM roofline), and
+    -- the CPU-baseline leg, unless disabled -- the FP64 oracle timed on a
+    bounded sample beside it: breathing resample (Eq. breathing) of the bench
+    grid; conservative conduction step, step with tissue-state perfusion and
+    potential-solve source (CG iterations) on the 256^3 single-needle phantom."""
     import torch
     peak, _ = measured_peak_hbm()
     out = {}
     n = case.nvox
     cores = os.cpu_count()
 
-    def roof(nbytes, ms):
+    def roof(nbytes, ms, nvox=None):
         gbs = nbytes / (ms * 1e-3) / 1e9
-        return {"achieved_GBs": gbs, "peak_GBs": peak, "frac": gbs / peak, "bytes_per_voxel": nbytes / n}
+        return {"achieved_GBs": gbs, "peak_GBs": peak, "frac": gbs / peak,
+                "bytes_per_voxel": nbytes / (nvox or n)}
 
     def cpu(value, unit, sample):
         return {"value": value, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample}
@@ -404,7 +405,9 @@ def measure_next_rows(rfa, stream, case, g, cpu_baseline_on: bool):
         g2.step(4)
         ms = _ms_between(torch, stream, lambda: g2.step(20)) / 20
         g2.close()
-        out[name] = dict(roof(bpv * n, ms), ms_per_step=ms, gvox_steps_s=n / (ms * 1e-3) / 1e9)
+        n2 = c2.nvox
+        out[name] = dict(roof(bpv * n2, ms, n2), workload="umbrella256", ms_per_step=ms,
+                         gvox_steps_s=n2 / (ms * 1e-3) / 1e9)
         if cpu_baseline_on:
             import oracle
             sm = ph.single_needle_case(seed=1, n=96, nsteps=4)
@@ -442,10 +445,12 @@ def measure_next_rows(rfa, stream, case, g, cpu_baseline_on: bool):
     adj = measure_adjoint(rfa, stream, conduction="harmonic")
     out["conservative_adjoint"] = {k: adj[k] for k in ("workload", "grid", "time_steps", "forward_recorded_ms",
                                                        "backward_ms", "backward_over_forward")}
-    out["potential_source"] = dict(roof(164.0 * n * it, ms), ms=ms, preconditioner="multigrid", cg_iterations=it,
+    n3 = c3.nvox
+    out["potential_source"] = dict(roof(164.0 * n3 * it, ms, n3), workload="umbrella256", ms=ms,
+                                   preconditioner="multigrid", cg_iterations=it,
                                    rel_residual=rel, ms_per_iteration=ms / max(it, 1),
                                    jacobi={"ms": ms_j, "cg_iterations": it_j, "rel_residual": rel_j,
-                                           "frac": roof(54.0 * n * it_j, ms_j)["frac"]},
+                                           "frac": roof(54.0 * n3 * it_j, ms_j, n3)["frac"]},
                                    multigrid_over_jacobi=ms_j / ms)
     if cpu_baseline_on:
         import oracle
