@@ -275,13 +275,13 @@ rfa_status rfa_batch_autotune(rfa_batch *b, const char *cache_path)
         const size_t pos = s.find(std::string("\"") + key + "\"");
         int d = 0, v = 0;
         if (pos != std::string::npos && std::sscanf(s.c_str() + s.find('[', pos) + 1, "%d , %d", &d, &v) == 2 &&
-            ((v == 0 && (d == 2 || d == 3)) || (v == 1 && d == 2))) {
+            ((v == 0 && (d == 2 || d == 3)) || ((v == 1 || v == 2) && d == 2))) {
             b->depth = d;
             b->variant = v;
             return build_plan(b);
         }
     }
-    const int cands[3][2] = {{2, 0}, {3, 0}, {2, 1}};
+    const int cands[4][2] = {{2, 0}, {3, 0}, {2, 1}, {2, 2}};
     // snapshot every member's evolving state; restored after each trial
     std::vector<MemberSnap> snaps(b->members.size());
     rfa_status st = RFA_OK;

@@ -284,6 +284,8 @@ struct TBTile {
     float c0, c1, TK0;
     float *rec_hi;  // replay: hi of the intermediate states (stage k at rec_hi + (k - 1) * rec_stride)
     size_t rec_stride;
+    const uint32_t *ab;  // packed BF16 coefficients and source (read directly by the
+    const float *s;      // split-barrier pipeline's last stage)
 };
 // a batch member on the host: tiles and tensor maps for both ping-pong parities
 struct TBMemberHost {

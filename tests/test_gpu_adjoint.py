@@ -65,11 +65,12 @@ def test_adjoint_matches_oracle_small(kind):
     assert g_gpu[4 + ph.VESSEL] == 0.0 and g_gpu[4 + 3 + ph.VESSEL] == 0.0
 
 
-def test_adjoint_recorded_in_chunks_and_blocked_forward():
+@pytest.mark.parametrize("sched", [(2, 0), (2, 2)])
+def test_adjoint_recorded_in_chunks_and_blocked_forward(sched):
     case = ph.random_small_case(32, 37, 30, 33, kind=ph.UMBRELLA, power=5.0)
     # forward by the 2-step blocked kernel; the recomputation replays the checkpoint
     # segments with the blocked kernel too (two steps per launch, Dirichlet faces)
-    g_gpu, g_orc = _adjoint_case(case, 123, chunks=[50, 1, 72], schedule=(2, 0))
+    g_gpu, g_orc = _adjoint_case(case, 123, chunks=[50, 1, 72], schedule=sched)
     _compare_grads(g_gpu, g_orc, len(case.table))
 
 

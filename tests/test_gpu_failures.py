@@ -79,12 +79,14 @@ def _restore_limits():
 
 
 def test_tma_wait_of_the_blocked_step_runs_out_and_the_grid_recovers():
-    """The blocked step's own mbarrier waits with a 1-cycle limit: the first
-    wait of every CTA gives up before its TMA copy lands, the CTA waits (with the
-    full limit) for its copies in flight and leaves, and the grid reports
-    RFA_E_TIMEOUT.  With the limits restored, set-up and stepping give the same
-    bits as a grid that never timed out."""
-    case = ph.random_small_case(9, 70, 40, 30, kind=ph.UMBRELLA, power=6.0)
+    """The blocked step's own mbarrier waits with a 1-cycle limit: a wait that
+    finds its TMA copy not yet landed gives up, its CTA waits (with the full
+    limit) for its copies in flight and leaves, and the grid reports
+    RFA_E_TIMEOUT.  The grid is large enough for a full wave of CTAs whose copies
+    compete for L2 and HBM, over 20 launches, so some wait finds its copy in
+    flight.  With the limits restored, set-up and stepping give the same bits
+    as a grid that never timed out."""
+    case = ph.random_small_case(9, 200, 160, 120, kind=ph.UMBRELLA, power=6.0)
     ref = rfa.Grid.from_case(case)
     ref.set_schedule(2, 0)
     ref.step(40)
@@ -94,7 +96,7 @@ def test_tma_wait_of_the_blocked_step_runs_out_and_the_grid_recovers():
     g.set_schedule(2, 0)
     try:
         rfa.rfa_set_wait_limits(1, rfa.WAIT_LIMIT_DEFAULT)
-        g.step(4)
+        g.step(40)
         with pytest.raises(rfa.RfaError) as e:
             g.synchronize()
         assert e.value.status == 7 and "mbarrier" in str(e.value)

@@ -1,5 +1,6 @@
-"""Temporally blocked step (several steps per launch, TMA-staged tiles):
-bit-identical states to the one-step kernel, and parity with the oracle."""
+"""Temporally blocked step (several steps per launch, TMA-staged tiles; tile
+variant 2 is the split-barrier pipeline): bit-identical states to the one-step
+kernel, and parity with the oracle."""
 import numpy as np
 import pytest
 
@@ -9,7 +10,7 @@ from tests.parity_util import compare, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
-SCHEDULES = [(2, 0), (3, 0), (2, 1)]
+SCHEDULES = [(2, 0), (3, 0), (2, 1), (2, 2)]
 
 
 @pytest.mark.parametrize("sched", SCHEDULES)
@@ -29,7 +30,7 @@ def test_blocked_equals_one_step(sched, dims):
     assert rel.max() <= 2e-5
 
 
-@pytest.mark.parametrize("sched", [(2, 0), (3, 0), (2, 1)])
+@pytest.mark.parametrize("sched", SCHEDULES)
 def test_blocked_parity_with_oracle(sched):
     case = ph.random_small_case(21, 71, 45, 38, kind=ph.UMBRELLA, power=6.0)
     n = 301
@@ -55,6 +56,13 @@ def test_schedule_rejected_where_unsupported():
     with pytest.raises(rfa.RfaError) as e:
         g.set_schedule(9, 0)
     assert e.value.status == 1
+    g.close()
+    # the split-barrier pipeline (tile variant 2) runs depth 2 only
+    g = rfa.Grid.from_case(case)
+    with pytest.raises(rfa.RfaError) as e:
+        g.set_schedule(3, 2)
+    assert e.value.status == 8
+    g.set_schedule(2, 2)
     g.close()
     # insulated faces: the blocked kernel needs Dirichlet faces (one step per launch)
     ins = ph.random_small_case(3, 20, 20, 20, face_bc=ph.INSULATED)
