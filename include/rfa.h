@@ -274,10 +274,8 @@ rfa_status rfa_set_state(rfa_grid *g, const void *blob, size_t n);
  * Temporal blocking: advance tb_depth steps per launch (1 = one step per
  * launch); tile_variant selects the xy tile of the blocked kernel (0: 64 x 12
  * output voxels per plane at depth 2, 64 x 10 at depth 3; 1: 64 x 28 at depth
- * 2; 2: the tile of 0 at depth 2 with a split-barrier pipeline -- warps meet at
- * an mbarrier one plane later instead of a CTA barrier every plane).  All
- * variants give bit-identical states.  The blocked kernel needs compensated
- * FP32 state, BF16 coefficients and Dirichlet faces; otherwise
+ * 2).  All variants give bit-identical states.  The blocked kernel needs
+ * compensated FP32 state, BF16 coefficients and Dirichlet faces; otherwise
  * rfa_set_schedule returns RFA_E_UNSUPPORTED and the autotuner keeps one step
  * per launch.
  * rfa_autotune times the candidates on a scratch copy of the grid's state and

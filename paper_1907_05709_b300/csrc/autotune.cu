@@ -133,7 +133,7 @@ extern "C" rfa_status rfa_autotune(rfa_grid *g, const char *cache_path)
         }
     }
     std::vector<std::pair<int, int>> cands = {{1, 0}};
-    for (int v = 0; v <= 2; ++v)
+    for (int v = 0; v <= 1; ++v)
         for (int d = 2; d <= 8; ++d)
             if (tb_supported(g, d, v)) cands.push_back({d, v});
     if (cands.size() == 1) {

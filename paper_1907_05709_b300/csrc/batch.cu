@@ -33,6 +33,7 @@ struct rfa_batch {
     unsigned *d_gbar = nullptr;
     void *h_members = nullptr;  // pinned staging of the member descriptors
     std::map<int64_t, cudaGraphExec_t> graphs;
+    bool graphs_lim = false;  // the graphs hold the instantiation for shortened wait limits
     bool use_graphs = true;
     int grid = 0;             // co-resident CTAs of the batch kernel
     std::string graph_error;  // why graph capture was given up, if it was
@@ -133,6 +134,11 @@ cudaError_t enqueue_blocks(rfa_batch *b, int64_t ntime)
 rfa_status run_blocks(rfa_batch *b, int64_t ntime)
 {
     if (ntime <= 0) return RFA_OK;
+    if (b->use_graphs && b->graphs_lim != tb_limits_set()) {  // wait limits changed: capture again
+        for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+        b->graphs.clear();
+        b->graphs_lim = tb_limits_set();
+    }
     if (b->use_graphs) {
         auto it = b->graphs.find(ntime);
         if (it == b->graphs.end()) {
@@ -275,13 +281,13 @@ rfa_status rfa_batch_autotune(rfa_batch *b, const char *cache_path)
         const size_t pos = s.find(std::string("\"") + key + "\"");
         int d = 0, v = 0;
         if (pos != std::string::npos && std::sscanf(s.c_str() + s.find('[', pos) + 1, "%d , %d", &d, &v) == 2 &&
-            ((v == 0 && (d == 2 || d == 3)) || ((v == 1 || v == 2) && d == 2))) {
+            ((v == 0 && (d == 2 || d == 3)) || (v == 1 && d == 2))) {
             b->depth = d;
             b->variant = v;
             return build_plan(b);
         }
     }
-    const int cands[4][2] = {{2, 0}, {3, 0}, {2, 1}, {2, 2}};
+    const int cands[3][2] = {{2, 0}, {3, 0}, {2, 1}};
     // snapshot every member's evolving state; restored after each trial
     std::vector<MemberSnap> snaps(b->members.size());
     rfa_status st = RFA_OK;

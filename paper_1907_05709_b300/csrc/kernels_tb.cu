@@ -39,6 +39,7 @@
 #include <cudaTypedefs.h>
 
 #include <array>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -56,9 +57,7 @@ constexpr int TB_QX = TB_EX / 4;  // quads (4 consecutive x voxels) per tile row
 // Tile variants (height EY of the loaded tile):
 //   0: EY = 16 (2 CTAs per SM at depth 2)
 //   1: EY = 32 (1 CTA per SM)
-//   2: EY = 16, depth 2 only, the split-barrier pipeline (tb_run_skew, CfgS)
 __host__ __device__ constexpr int tile_ey(int v) { return v == 1 ? 32 : 16; }
-constexpr int kSkewVariant = 2;
 
 template <int M, int V>
 struct Cfg {
@@ -92,11 +91,6 @@ struct Cfg {
     static_assert((PLANE * 4) % 128 == 0 && (SLOT0 * 4) % 128 == 0, "TMA destinations must be 128-byte aligned");
 };
 
-// the tile geometry (launch shape, tiles, tensor-map boxes) of a variant: the
-// split-barrier pipeline uses that of variant 0
-template <int M, int V>
-using CfgL = Cfg<M, V == kSkewVariant ? 0 : V>;
-
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -113,27 +107,39 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
 }
 
 // Spin limits of the bounded waits in SM clock cycles: the TMA (mbarrier) waits
-// and the batch's grid barrier.  2^32 cycles (about 2 s at 2 GHz) unless a test
-// shortens them through rfa_set_wait_limits; kernels read them at start.
-__device__ long long g_wait_limit_mbar = 1ll << 32;
-__device__ long long g_wait_limit_grid = 1ll << 32;
+// and the batch's grid barrier.  kDefaultLimit (2^32 cycles, about 2 s at
+// 2 GHz) is compiled into the kernels; while a test has set other limits through
+// rfa_set_wait_limits, the host launches the instantiations with LIM = true,
+// which read them from these globals at start.
+constexpr long long kDefaultLimit = 1ll << 32;
+__device__ long long g_wait_limit_mbar = kDefaultLimit;
+__device__ long long g_wait_limit_grid = kDefaultLimit;
 // the wait for a CTA's own copies in flight before it leaves after a timeout
 // keeps the full limit whatever the limits above are
 constexpr long long kDrainLimit = 1ll << 32;
 
 // bounded wait for the phase with the given parity; false on timeout.  Each
-// try_wait may suspend the thread for up to kSuspendNs (it resumes as soon as
-// the phase completes), so waiting warps do not spin on the issue slots.
-// Limits below kSuspendMin (set only by tests) poll with the non-blocking
-// test_wait instead (mbar_poll), so a short limit is not hidden inside one
-// suspended try_wait; the check sits outside the wait loop.
+// try_wait may suspend the thread for up to `hint` ns (it resumes as soon as
+// the phase completes), so waiting warps do not spin on the issue slots.  The
+// kernels pass kSuspendNs, or 0 for limits below kSuspendMin (set only by
+// tests), which polls with test_wait, so that a short limit is not hidden
+// inside one suspended try_wait.
 constexpr uint32_t kSuspendNs = 100000;
 constexpr long long kSuspendMin = 1ll << 20;
-__device__ __noinline__ bool mbar_poll(uint32_t bar, uint32_t parity, long long limit)
+__device__ __forceinline__ uint32_t suspend_hint(long long limit) { return limit >= kSuspendMin ? kSuspendNs : 0u; }
+// mbarrier phase test: a suspending try_wait, or with hint 0 the non-blocking test_wait
+__device__ __forceinline__ uint32_t mbar_test(uint32_t bar, uint32_t parity, uint32_t hint)
 {
-    const long long t0 = clock64();
-    while (true) {
-        uint32_t done;
+    uint32_t done;
+    if (hint)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity), "r"(hint)
+            : "memory");
+    else
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -141,24 +147,13 @@ __device__ __noinline__ bool mbar_poll(uint32_t bar, uint32_t parity, long long 
             : "=r"(done)
             : "r"(bar), "r"(parity)
             : "memory");
-        if (done) return true;
-        if (clock64() - t0 > limit) return false;
-    }
+    return done;
 }
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit, uint32_t hint)
 {
-    if (limit < kSuspendMin) return mbar_poll(bar, parity, limit);
     const long long t0 = clock64();
     while (true) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity), "r"(kSuspendNs)
-            : "memory");
-        if (done) return true;
+        if (mbar_test(bar, parity, hint)) return true;
         if (clock64() - t0 > limit) return false;
     }
 }
@@ -183,9 +178,8 @@ struct TBPipe {
     float *sm;
     uint32_t sm_base, bar_base;
     long long nload;   // stage-0 planes consumed so far (ring slot and mbarrier phase)
-    long long issued;  // stage-0 planes requested so far (by the requesting thread only)
-    long long limit;   // spin limit of the mbarrier waits
-    long long niter;   // iterations of the split-barrier pipeline (phases of its done barriers)
+    long long limit;   // spin limit of the mbarrier waits (kernels instantiated with LIM)
+    uint32_t hint;     // suspend-time hint of their try_wait (ns)
 };
 
 template <int M, int V>
@@ -204,7 +198,6 @@ template <int M, int V>
 __device__ __forceinline__ void tb_issue(TBPipe &P, int j, const CUtensorMap *maps, int X0, int Y0, int z)
 {
     using C = Cfg<M, V>;
-    ++P.issued;
     const uint32_t dst = P.sm_base + 4u * (uint32_t)(j * C::SLOT0);
     const uint32_t bar = P.bar_base + 8u * j;
     mbar_expect_tx(bar, (uint32_t)(4 * C::BOX * 4));   // four boxes of 4-byte elements
@@ -289,7 +282,7 @@ __device__ __forceinline__ bool tb_stage_smem_ok(int k, const int *r0, const int
 // nothing is carried between planes; for M = 3 the running sum and maximum
 // travel with the values through the stage-2 ring.  The sums keep the order
 // ((inc_1 + inc_2) + ...) of the per-step evaluation.
-template <int M, int V, bool DMG, bool FOLD, bool REC, class Items, class Get>
+template <int M, int V, bool DMG, bool FOLD, bool REC, bool LIM, class Items, class Get>
 __device__ bool tb_run(TBPipe &P, const Items &items, int nitems, const Get &get, unsigned *status, bool &bad)
 {
     static_assert(!(REC && DMG), "the replay has no damage integral");
@@ -400,7 +393,8 @@ __device__ bool tb_run(TBPipe &P, const Items &items, int nitems, const Get &get
                     om23 = reinterpret_cast<const double2 *>(A.omega + gio)[1];
                 }
             }
-            const bool ok = mbar_wait(bar_base + 8u * s0_cur, phase, P.limit);
+            const bool ok = mbar_wait(bar_base + 8u * s0_cur, phase, LIM ? P.limit : kDefaultLimit,
+                                      LIM ? P.hint : kSuspendNs);
             // the last stage's coefficients (plane p0 - M) go to registers before the
             // last barrier: its ring-0 slot is then refilled right after that barrier
             uint4 wM = make_uint4(0u, 0u, 0u, 0u);
@@ -562,11 +556,13 @@ __device__ bool tb_run(TBPipe &P, const Items &items, int nitems, const Get &get
                     if (__syncthreads_or(!ok)) {
                         if (tid == 0) {
                             // let every request in flight land before the CTA's shared
-                            // memory is released: planes nload .. issued-1 (bounded)
+                            // memory is released (bounded): this plane, and the next one,
+                            // requested one iteration ago if it exists
                             atomicOr(status, kStatusTimeout);
-                            for (long long q = P.nload; q < P.issued; ++q)
+                            const long long last = P.nload + ((it + 1 < L || nxt < nitems) ? 1 : 0);
+                            for (long long q = P.nload; q <= last; ++q)
                                 mbar_wait(bar_base + 8u * (uint32_t)(q % S0), (uint32_t)((q / S0) & 1),
-                                          kDrainLimit);
+                                          kDrainLimit, kSuspendNs);
                         }
                         return false;
                     }
@@ -614,372 +610,6 @@ __device__ bool tb_run(TBPipe &P, const Items &items, int nitems, const Get &get
     return true;
 }
 
-// ------------------------------------------------------------------ split-barrier pipeline
-// Depth 2 with the tile of variant 0 (72 x 16 loaded, 64 x 12 out), but with
-// no CTA barrier per plane.  Stage 2 runs one plane later than in tb_run: at
-// the iteration that receives stage-0 plane p0 it computes stage 1 on plane
-// p0 - 1 and stage 2 on plane p0 - 3, so stage 2 reads only stage-1 planes
-// written in earlier iterations.  Every warp arrives on an mbarrier at the end
-// of each iteration and waits, before its stage 2, for the previous
-// iteration's phase: warps may drift by up to one stage 1 instead of meeting at
-// a barrier.  That drift is what the ring depths are sized for:
-//   - stage-1 ring: 5 slots (planes p0-5 .. p0-1 may be in use), 14 rows each
-//     (rows 1..14 of the tile, the rows stage 1 computes);
-//   - stage-0 ring: 4 slots (hi, lo, ab, s) as in tb_run; plane p0+2 goes into
-//     the slot of p0-2 once the previous iteration's phase has completed,
-//     because stage 1 reads a stage-0 plane last as its centre one iteration
-//     after it arrived (its z- neighbour comes from registers, preloaded for
-//     the first planes of an item) and stage 2 takes its coefficients from
-//     global memory (L2) rather than from the ring.
-// The producer of the TMA requests is lane 0 of the last warp (the one with the
-// least work: 28 stage-1 quads, no stage-2 quads).
-// Timeouts: a wait that gives up sets a shared abort flag that every other wait
-// polls; all threads then meet at one CTA barrier, and the producer waits (with
-// the full limit) for its copies in flight before the function returns false.
-struct CfgS {
-    static constexpr int EY = 16, TY = 12;
-    static constexpr int NQ1 = (EY - 2) * TB_QX;  // 252 stage-1 quads
-    static constexpr int NQO = TY * (TB_QX - 2);  // 192 stage-2 quads
-    static constexpr int THREADS = 256, NWARPS = 8;
-    static constexpr int PRODUCER = 32 * (NWARPS - 1);
-    static constexpr int S0 = 4;
-    static constexpr int BOX = TB_EX * EY;
-    static constexpr int PLANE = (BOX + 31) / 32 * 32;
-    static constexpr int SLOT0 = 4 * PLANE;
-    static constexpr int R1 = 5;
-    static constexpr int P1 = TB_EX * (EY - 2);    // a stage-1 plane: rows 1 .. EY-2
-    static constexpr int SLOT1 = 2 * P1;           // hi, lo
-    static constexpr int RING1 = S0 * SLOT0;
-    static constexpr int BAR_OFF = RING1 + R1 * SLOT1;
-    static constexpr int NBAR = S0 + 2;            // full[S0], done[2]
-    static constexpr int SMEM = BAR_OFF * 4 + 8 * NBAR;
-    static_assert(NQ1 <= THREADS && NQO <= 32 * (NWARPS - 2), "thread maps");
-    static_assert(SMEM <= 113 * 1024, "two CTAs per SM");
-    static_assert((PLANE * 4) % 128 == 0 && (SLOT0 * 4) % 128 == 0 && (RING1 * 4) % 16 == 0 &&
-                      (P1 * 4) % 16 == 0 && (BAR_OFF * 4) % 8 == 0,
-                  "alignment");
-};
-
-// One quad of Eq. CUDAbioheat3d from its loaded operands, in the operation order
-// of the one-step kernel (so the states are bit-identical): centre pair (ch, cl),
-// x neighbours (lh, ll), (rh, rl), y (ymh, yml), (yph, ypl), z (zmh, zml),
-// (zph, zpl), packed BF16 a/b w4, source s4 -> new pairs (H, N) and the old value
-// T (the centre rounded to FP32) of voxel pairs (0,1) and (2,3).
-__device__ __forceinline__ void quad_update(const float4 &ch, const float4 &cl, float lh, float ll, float rh,
-                                            float rl, const float4 &ymh, const float4 &yml, const float4 &yph,
-                                            const float4 &ypl, const float4 &zmh, const float4 &zml,
-                                            const float4 &zph, const float4 &zpl, const uint4 &w4, const float4 &s4,
-                                            float2 &H01, float2 &N01, float2 &T01, float2 &H23, float2 &N23,
-                                            float2 &T23)
-{
-    const float2 C01 = make_float2(ch.x, ch.y), C23 = make_float2(ch.z, ch.w);
-    const float2 L01 = make_float2(cl.x, cl.y), L23 = make_float2(cl.z, cl.w);
-    const float xh[6] = {lh, ch.x, ch.y, ch.z, ch.w, rh}, xl[6] = {ll, cl.x, cl.y, cl.z, cl.w, rl};
-    float dm[4], dp[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        dm[j] = cdiff(xh[j], xl[j], xh[j + 1], xl[j + 1]);
-        dp[j] = cdiff(xh[j + 2], xl[j + 2], xh[j + 1], xl[j + 1]);
-    }
-    float2 S01 = add2(make_float2(dm[0], dm[1]), make_float2(dp[0], dp[1]));
-    float2 S23 = add2(make_float2(dm[2], dm[3]), make_float2(dp[2], dp[3]));
-    S01 = add2(S01, cdiff2(make_float2(ymh.x, ymh.y), make_float2(yml.x, yml.y), C01, L01));
-    S23 = add2(S23, cdiff2(make_float2(ymh.z, ymh.w), make_float2(yml.z, yml.w), C23, L23));
-    S01 = add2(S01, cdiff2(make_float2(yph.x, yph.y), make_float2(ypl.x, ypl.y), C01, L01));
-    S23 = add2(S23, cdiff2(make_float2(yph.z, yph.w), make_float2(ypl.z, ypl.w), C23, L23));
-    S01 = add2(S01, cdiff2(make_float2(zmh.x, zmh.y), make_float2(zml.x, zml.y), C01, L01));
-    S23 = add2(S23, cdiff2(make_float2(zmh.z, zmh.w), make_float2(zml.z, zml.w), C23, L23));
-    S01 = add2(S01, cdiff2(make_float2(zph.x, zph.y), make_float2(zpl.x, zpl.y), C01, L01));
-    S23 = add2(S23, cdiff2(make_float2(zph.z, zph.w), make_float2(zpl.z, zpl.w), C23, L23));
-    const float2 a01 = make_float2(bf16_to_float(w4.x & 0xffffu), bf16_to_float(w4.y & 0xffffu));
-    const float2 a23 = make_float2(bf16_to_float(w4.z & 0xffffu), bf16_to_float(w4.w & 0xffffu));
-    const float2 b01 = make_float2(bf16_to_float(w4.x >> 16), bf16_to_float(w4.y >> 16));
-    const float2 b23 = make_float2(bf16_to_float(w4.z >> 16), bf16_to_float(w4.w >> 16));
-    cupdate2(C01, L01, S01, a01, b01, make_float2(s4.x, s4.y), H01, N01, T01);
-    cupdate2(C23, L23, S23, a23, b23, make_float2(s4.z, s4.w), H23, N23, T23);
-}
-
-// bounded wait that also gives up as soon as another warp has aborted
-__device__ __forceinline__ bool mbar_wait_abort(uint32_t bar, uint32_t parity, long long limit,
-                                                const volatile int *abort)
-{
-    const long long t0 = clock64();
-    const bool suspend = limit >= kSuspendMin;
-    while (true) {
-        uint32_t done;
-        if (suspend)
-            asm volatile(
-                "{\n\t.reg .pred p;\n\t"
-                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-                "selp.u32 %0, 1, 0, p;\n\t}"
-                : "=r"(done)
-                : "r"(bar), "r"(parity), "r"(kSuspendNs / 10)
-                : "memory");
-        else
-            asm volatile(
-                "{\n\t.reg .pred p;\n\t"
-                "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                "selp.u32 %0, 1, 0, p;\n\t}"
-                : "=r"(done)
-                : "r"(bar), "r"(parity)
-                : "memory");
-        if (done) return true;
-        if (*abort || clock64() - t0 > limit) return false;
-    }
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-// Advance the work items of `items` by two steps with the split-barrier
-// pipeline (see CfgS).  Item geometry, tile descriptors, latch, damage, replay
-// records and results are those of tb_run<2, 0>; the states are bit-identical.
-// P.niter counts this CTA's iterations (mbarrier phases of done[]).  Returns
-// false, uniformly over the CTA, if a wait ran out.
-template <bool DMG, bool FOLD, bool REC, class Items, class Get>
-__device__ bool tb_run_skew(TBPipe &P, const Items &items, int nitems, const Get &get, unsigned *status, bool &bad)
-{
-    static_assert(!(REC && DMG), "the replay has no damage integral");
-    using C = CfgS;
-    constexpr int S0 = C::S0, PLANE = C::PLANE, P1 = C::P1, PD = 2;
-    float *sm = P.sm;
-    const uint32_t bar_base = P.bar_base, done_base = P.bar_base + 8u * S0;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const bool producer = tid == C::PRODUCER;
-    __shared__ int s_q[2];
-    __shared__ volatile int s_abort;
-
-    // stage 1: thread t -> tile row y1 = 1 + t / 18, quad qx1 = t % 18 (rows 1 .. 14)
-    const bool a1 = tid < C::NQ1;
-    const int y1 = 1 + tid / TB_QX, qx1 = tid % TB_QX;
-    const int id1 = y1 * TB_EX + 4 * qx1;  // offset in a stage-0 plane
-    const int o1 = id1 - TB_EX;            // offset in a stage-1 plane (rows from 1)
-    const int xl1 = qx1 > 0 ? -1 : 0, xh1 = qx1 < TB_QX - 1 ? 4 : 3;  // the outer columns read themselves
-    const bool rec1 = REC && a1 && y1 >= 2 && y1 < C::EY - 2 && qx1 >= 1 && qx1 < TB_QX - 1;
-    // stage 2: thread t < 192 -> tile row y2 = 2 + t / 16, quad qx2 = 1 + t % 16 (the output tile)
-    const bool a2 = tid < C::NQO;
-    const int y2 = 2 + tid / 16, qx2 = 1 + tid % 16;
-    const int o2 = (y2 - 1) * TB_EX + 4 * qx2;
-
-    if (tid == 0) {
-        s_abort = 0;
-        const int i0 = items.start();
-        s_q[0] = i0;
-        s_q[1] = i0 < nitems ? items.after(i0) : nitems;
-    }
-    __syncthreads();
-    int qk = 0;
-    int item = s_q[0], nxt = s_q[1];
-    if (producer && item < nitems) {  // the first PD planes of the first item
-        int local;
-        const CUtensorMap *mp;
-        decltype(auto) T = get(item, local, mp);
-        int X0, Y0, zb, ze;
-        tb_item_geom<2, 0>(T, local, X0, Y0, zb, ze);
-#pragma unroll
-        for (int j = 0; j < PD; ++j) tb_issue<2, 0>(P, (int)((P.nload + j) % S0), mp, X0, Y0, zb - 2 + j);
-    }
-    // stage-1 ring slots of planes p0-1 (written this iteration) .. p0-5
-    int g1[C::R1];
-#pragma unroll
-    for (int d = 0; d < C::R1; ++d) g1[d] = C::RING1 + (int)((P.niter + C::R1 - d) % C::R1) * C::SLOT1;
-    bool ok = true;
-    while (ok && item < nitems) {
-        int local;
-        const CUtensorMap *maps;
-        decltype(auto) A = get(item, local, maps);
-        int X0, Y0, zb, ze;
-        tb_item_geom<2, 0>(A, local, X0, Y0, zb, ze);
-        const int L = ze - zb + 4;  // stage-0 planes zb-2 .. ze+1
-        const int xg0 = X0 + 4 * (qx2 - 1), yg = Y0 + (y2 - 2);
-        const bool out_quad = a2 && yg < A.ny && xg0 < A.nx;
-        const int nin = A.nx - xg0;
-        int s0_cur = (int)(P.nload % S0);
-        uint32_t phase = (uint32_t)((P.nload / S0) & 1);
-        int r0[S0];  // ring-0 slot offsets of planes p0 - d
-#pragma unroll
-        for (int d = 0; d < S0; ++d) r0[d] = ((s0_cur - d + S0) % S0) * C::SLOT0;
-        float4 k1ch = make_float4(0.f, 0.f, 0.f, 0.f), k1cl = k1ch, k1mh = k1ch, k1ml = k1ch;
-
-        for (int it = 0; it <= L; ++it) {
-            const int p0 = zb - 2 + it;
-            const bool cons = it < L;  // this iteration receives stage-0 plane p0
-            // the last stage's operands of plane q2 = p0 - 3 from global memory, early
-            const int q2 = p0 - 3;
-            const bool out_now =
-                out_quad && it >= 5 && q2 >= 0 && q2 < A.nz &&
-                RFA_CHECK_RANGE((size_t)q2 * A.plane + (size_t)yg * A.pitch + xg0,
-                                (size_t)q2 * A.plane + (size_t)yg * A.pitch + xg0 + 4, A.plane * A.nz, xg0, 4, status);
-            const size_t gio = out_now ? (size_t)q2 * A.plane + (size_t)yg * A.pitch + xg0 : 0;
-            float4 carry4 = make_float4(0.f, 0.f, 0.f, 0.f), s2 = carry4;
-            uint4 w2 = make_uint4(0u, 0u, 0u, 0u);
-            uint32_t latch4 = 0;
-            double2 om01 = make_double2(0.0, 0.0), om23 = om01;
-            if (out_now) {
-                w2 = __ldg(reinterpret_cast<const uint4 *>(A.ab + gio));
-                s2 = __ldg(reinterpret_cast<const float4 *>(A.s + gio));
-                if (!REC) {
-                    latch4 = *reinterpret_cast<const uint32_t *>(A.latch + gio);
-                    if (DMG) carry4 = *reinterpret_cast<const float4 *>(A.omega_c + gio);
-                    if (DMG && FOLD) {
-                        om01 = reinterpret_cast<const double2 *>(A.omega + gio)[0];
-                        om23 = reinterpret_cast<const double2 *>(A.omega + gio)[1];
-                    }
-                }
-            }
-            if (cons && !mbar_wait_abort(bar_base + 8u * s0_cur, phase, P.limit, &s_abort)) {
-                s_abort = 1;
-                atomicOr(status, kStatusTimeout);
-                ok = false;
-                break;
-            }
-            // stage 1 on plane p0 - 1 (centre slot r0[1], z+ slot r0[0], z- and the centre's
-            // own values from registers)
-            if (cons && a1 && it == 1) {  // the item's first two planes, for its first stage-1 plane
-                k1mh = ld4(sm, r0[1] + id1);
-                k1ml = ld4(sm, r0[1] + PLANE + id1);
-                k1ch = ld4(sm, r0[0] + id1);
-                k1cl = ld4(sm, r0[0] + PLANE + id1);
-            }
-            if (cons && a1 && it >= 2) {
-                const int cb = r0[1], bp = r0[0];
-                const float4 ymh = ld4(sm, cb + id1 - TB_EX), yml = ld4(sm, cb + PLANE + id1 - TB_EX);
-                const float4 yph = ld4(sm, cb + id1 + TB_EX), ypl = ld4(sm, cb + PLANE + id1 + TB_EX);
-                const float4 zph = ld4(sm, bp + id1), zpl = ld4(sm, bp + PLANE + id1);
-                const float lh = sm[cb + id1 + xl1], ll = sm[cb + PLANE + id1 + xl1];
-                const float rh = sm[cb + id1 + xh1], rl = sm[cb + PLANE + id1 + xh1];
-                const uint4 w4 = *reinterpret_cast<const uint4 *>(sm + cb + 2 * PLANE + id1);
-                const float4 s4 = ld4(sm, cb + 3 * PLANE + id1);
-                float2 H01, N01, T01, H23, N23, T23;
-                quad_update(k1ch, k1cl, lh, ll, rh, rl, ymh, yml, yph, ypl, k1mh, k1ml, zph, zpl, w4, s4, H01, N01,
-                            T01, H23, N23, T23);
-                k1mh = k1ch;
-                k1ml = k1cl;
-                k1ch = zph;
-                k1cl = zpl;
-                *reinterpret_cast<float4 *>(sm + g1[0] + o1) = make_float4(H01.x, H01.y, H23.x, H23.y);
-                *reinterpret_cast<float4 *>(sm + g1[0] + P1 + o1) = make_float4(N01.x, N01.y, N23.x, N23.y);
-                if (rec1) {
-                    const int q = p0 - 1, xr = X0 + 4 * qx1 - TB_HX, yr = Y0 + y1 - 2;
-                    const size_t ro_ = (size_t)(q > 0 ? q : 0) * A.plane + (size_t)yr * A.pitch + (xr > 0 ? xr : 0);
-                    if (q >= zb && q < ze && yr < A.ny && xr < A.nx &&  // this item's planes only
-                        RFA_CHECK_RANGE(ro_, ro_ + 4, A.rec_stride, ro_, 4, status))
-                        *reinterpret_cast<float4 *>(A.rec_hi + (size_t)q * A.plane + (size_t)yr * A.pitch + xr) =
-                            make_float4(H01.x, H01.y, H23.x, H23.y);
-                }
-            }
-            // every warp has finished the previous iteration: its stage-1 plane is
-            // written, its reads of older planes and of the ring-0 slot refilled next are done
-            if (P.niter >= 1) {
-                const long long n = P.niter - 1;
-                if (!mbar_wait_abort(done_base + 8u * (uint32_t)(n & 1), (uint32_t)((n >> 1) & 1), P.limit,
-                                     &s_abort)) {
-                    s_abort = 1;
-                    atomicOr(status, kStatusTimeout);
-                    ok = false;
-                    break;
-                }
-            }
-            if (producer) {
-                if (cons) {  // plane p0 + PD (of this item, else of the next one) into the slot of p0 - 2
-                    const int s0_pd = s0_cur + PD >= S0 ? s0_cur + PD - S0 : s0_cur + PD;
-                    if (it + PD < L) {
-                        tb_issue<2, 0>(P, s0_pd, maps, X0, Y0, p0 + PD);
-                    } else if (nxt < nitems) {
-                        int local1;
-                        const CUtensorMap *maps1;
-                        decltype(auto) T1 = get(nxt, local1, maps1);
-                        int X1, Y1, zb1, ze1;
-                        tb_item_geom<2, 0>(T1, local1, X1, Y1, zb1, ze1);
-                        tb_issue<2, 0>(P, s0_pd, maps1, X1, Y1, zb1 - 2 + (it + PD - L));
-                    }
-                }
-                // the item after next: every thread read this entry at the end of the item
-                // before last, long before the previous iteration's phase completed
-                if (it == 3) s_q[qk] = nxt < nitems ? items.after(nxt) : nitems;
-            }
-            // stage 2 on plane p0 - 3 from stage-1 planes p0 - 2 (g1[1]), p0 - 3 (g1[2]), p0 - 4 (g1[3])
-            if (out_now) {
-                const int bc = g1[2], bp = g1[1], bm = g1[3];
-                const float4 ch = ld4(sm, bc + o2), cl = ld4(sm, bc + P1 + o2);
-                const float4 ymh = ld4(sm, bc + o2 - TB_EX), yml = ld4(sm, bc + P1 + o2 - TB_EX);
-                const float4 yph = ld4(sm, bc + o2 + TB_EX), ypl = ld4(sm, bc + P1 + o2 + TB_EX);
-                const float4 zmh = ld4(sm, bm + o2), zml = ld4(sm, bm + P1 + o2);
-                const float4 zph = ld4(sm, bp + o2), zpl = ld4(sm, bp + P1 + o2);
-                const float lh = sm[bc + o2 - 1], ll = sm[bc + P1 + o2 - 1];
-                const float rh = sm[bc + o2 + 4], rl = sm[bc + P1 + o2 + 4];
-                float2 H01, N01, T01, H23, N23, T23;
-                quad_update(ch, cl, lh, ll, rh, rl, ymh, yml, yph, ypl, zmh, zml, zph, zpl, w2, s2, H01, N01, T01,
-                            H23, N23, T23);
-                *reinterpret_cast<float4 *>(A.hi_out + gio) = make_float4(H01.x, H01.y, H23.x, H23.y);
-                *reinterpret_cast<float4 *>(A.lo_out + gio) = make_float4(N01.x, N01.y, N23.x, N23.y);
-                bad |= !(isfinite(H01.x) && isfinite(H01.y) && isfinite(H23.x) && isfinite(H23.y));
-                if (!REC) {  // latch and damage of both steps (the replay leaves them alone)
-                    const float2 V01 = add2(H01, N01), V23 = add2(H23, N23);
-                    const float mx[4] = {fmaxf(T01.x, V01.x), fmaxf(T01.y, V01.y), fmaxf(T23.x, V23.x),
-                                         fmaxf(T23.y, V23.y)};
-                    uint32_t lbits = 0;
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (j < nin && mx[j] >= A.thr) lbits |= 1u << (8 * j);
-                    if ((latch4 | lbits) != latch4) *reinterpret_cast<uint32_t *>(A.latch + gio) = latch4 | lbits;
-                    if (DMG) {
-                        const float2 P01 = add2(arrhenius_inc2(T01, A.c0, A.c1, A.TK0),
-                                                arrhenius_inc2(V01, A.c0, A.c1, A.TK0));
-                        const float2 P23 = add2(arrhenius_inc2(T23, A.c0, A.c1, A.TK0),
-                                                arrhenius_inc2(V23, A.c0, A.c1, A.TK0));
-                        const float part[4] = {P01.x, P01.y, P23.x, P23.y};
-                        float Pc[4] = {carry4.x, carry4.y, carry4.z, carry4.w};
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if (j < nin) Pc[j] = __fadd_rn(Pc[j], part[j]);
-                        if (FOLD) {
-                            double om[4] = {om01.x, om01.y, om23.x, om23.y};
-#pragma unroll
-                            for (int j = 0; j < 4; ++j)
-                                if (j < nin) carry_fold(om[j], Pc[j]);
-                            double2 *op = reinterpret_cast<double2 *>(A.omega + gio);
-                            op[0] = make_double2(om[0], om[1]);
-                            op[1] = make_double2(om[2], om[3]);
-                        }
-                        *reinterpret_cast<float4 *>(A.omega_c + gio) = make_float4(Pc[0], Pc[1], Pc[2], Pc[3]);
-                    }
-                }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(done_base + 8u * (uint32_t)(P.niter & 1));
-            ++P.niter;
-            if (cons) {  // rotate the ring-0 slots by one plane
-                ++P.nload;
-                const int t0 = r0[S0 - 1];
-#pragma unroll
-                for (int d = S0 - 1; d > 0; --d) r0[d] = r0[d - 1];
-                r0[0] = t0;
-                const int s0_next = s0_cur + 1 == S0 ? 0 : s0_cur + 1;
-                if (s0_next == 0) phase ^= 1u;
-                s0_cur = s0_next;
-            }
-            const int t1 = g1[C::R1 - 1];  // the stage-1 ring turns every iteration
-#pragma unroll
-            for (int d = C::R1 - 1; d > 0; --d) g1[d] = g1[d - 1];
-            g1[0] = t1;
-        }
-        item = nxt;
-        nxt = s_q[qk];
-        qk ^= 1;
-    }
-    // all threads agree; after a timeout the producer lets its copies in flight land
-    if (__syncthreads_or(s_abort)) {
-        if (producer)
-            for (long long q = P.nload; q < P.issued; ++q)
-                mbar_wait(bar_base + 8u * (uint32_t)(q % S0), (uint32_t)((q / S0) & 1), kDrainLimit);
-        return false;
-    }
-    return true;
-}
-
 template <int M, int V>
 __device__ __forceinline__ bool tb_setup(TBPipe &P, unsigned *status)
 {
@@ -989,42 +619,14 @@ __device__ __forceinline__ bool tb_setup(TBPipe &P, unsigned *status)
     P.sm_base = smem_u32(sm);
     P.bar_base = P.sm_base + 4u * C::BAR_OFF;
     P.nload = 0;
-    P.issued = 0;
-    P.niter = 0;
     P.limit = g_wait_limit_mbar;
+    P.hint = suspend_hint(P.limit);
     if (P.sm_base & 127u) {  // TMA destinations need 128-byte alignment
         if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
         return false;
     }
     if (threadIdx.x == 0) {
         for (int j = 0; j < C::S0; ++j) mbar_init(P.bar_base + 8u * j, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-    return true;
-}
-
-// set-up of the split-barrier pipeline: full[S0] (one arrival: the TMA producer)
-// and done[2] (one arrival per warp and iteration)
-__device__ __forceinline__ bool tb_setup_skew(TBPipe &P, unsigned *status)
-{
-    using C = CfgS;
-    extern __shared__ __align__(128) float sm[];
-    P.sm = sm;
-    P.sm_base = smem_u32(sm);
-    P.bar_base = P.sm_base + 4u * C::BAR_OFF;
-    P.nload = 0;
-    P.issued = 0;
-    P.niter = 0;
-    P.limit = g_wait_limit_mbar;
-    if (P.sm_base & 127u) {  // TMA destinations need 128-byte alignment
-        if (threadIdx.x == 0) atomicOr(status, kStatusTimeout);
-        return false;
-    }
-    if (threadIdx.x == 0) {
-        for (int j = 0; j < C::S0; ++j) mbar_init(P.bar_base + 8u * j, 1);
-        for (int j = 0; j < 2; ++j) mbar_init(P.bar_base + 8u * (C::S0 + j), C::NWARPS);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -1037,16 +639,12 @@ struct TBMaps {
 };
 
 // one grid, M steps
-template <int M, int V, bool DMG, bool FOLD, bool REC>
-__global__ void __launch_bounds__(CfgL<M, V>::THREADS, CfgL<M, V>::MINB)
+template <int M, int V, bool DMG, bool FOLD, bool REC, bool LIM>
+__global__ void __launch_bounds__(Cfg<M, V>::THREADS, Cfg<M, V>::MINB)
     k_step_tb(const __grid_constant__ TBMaps maps, const TBTile T0, unsigned *status)
 {
     TBPipe P;
-    if constexpr (V == kSkewVariant) {
-        if (!tb_setup_skew(P, status)) return;
-    } else {
-        if (!tb_setup<M, V>(P, status)) return;
-    }
+    if (!tb_setup<M, V>(P, status)) return;
     // the descriptor stays in kernel-parameter space (constant-bank operands).
     // The reference returned is to the kernel's own parameter, which outlives
     // every call of the lambda; the compiler's "reference to local" note does
@@ -1060,12 +658,8 @@ __global__ void __launch_bounds__(CfgL<M, V>::THREADS, CfgL<M, V>::MINB)
     };
 #pragma nv_diag_default 836
     bool bad = false;
-    if constexpr (V == kSkewVariant)
-        tb_run_skew<DMG, FOLD, REC>(P, StrideItems{(int)blockIdx.x, (int)gridDim.x}, T0.xt * T0.yt * T0.zc, get,
-                                    status, bad);
-    else
-        tb_run<M, V, DMG, FOLD, REC>(P, StrideItems{(int)blockIdx.x, (int)gridDim.x}, T0.xt * T0.yt * T0.zc, get,
-                                     status, bad);
+    tb_run<M, V, DMG, FOLD, REC, LIM>(P, StrideItems{(int)blockIdx.x, (int)gridDim.x}, T0.xt * T0.yt * T0.zc, get,
+                                      status, bad);
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusNonfinite);
 }
 
@@ -1111,18 +705,14 @@ __device__ bool grid_sync(unsigned *bar, unsigned nblocks, long long limit)
 }
 
 // every member, ntime blocks of M steps, one persistent launch
-template <int M, int V, bool DMG>
-__global__ void __launch_bounds__(CfgL<M, V>::THREADS, CfgL<M, V>::MINB)
+template <int M, int V, bool DMG, bool LIM>
+__global__ void __launch_bounds__(Cfg<M, V>::THREADS, Cfg<M, V>::MINB)
     k_batch_tb(const TBMember *mem, int nmem, int nitems, int ntime, int fold_every, unsigned *gbar,
                unsigned *status)
 {
     TBPipe P;
-    if constexpr (V == kSkewVariant) {
-        if (!tb_setup_skew(P, status)) return;
-    } else {
-        if (!tb_setup<M, V>(P, status)) return;
-    }
-    const long long glimit = g_wait_limit_grid;
+    if (!tb_setup<M, V>(P, status)) return;
+    const long long glimit = LIM ? g_wait_limit_grid : kDefaultLimit;
     bool bad = false;
     for (int t = 0; t < ntime; ++t) {
         auto get = [&](int item, int &local, const CUtensorMap *&mp) -> TBTile {
@@ -1139,13 +729,8 @@ __global__ void __launch_bounds__(CfgL<M, V>::THREADS, CfgL<M, V>::MINB)
         };
         const bool fold = DMG && ((t + 1) % fold_every == 0 || t == ntime - 1);
         const ClaimedItems items{gbar + 2 + t};  // one counter per time block, zeroed before the launch
-        bool ok;
-        if constexpr (V == kSkewVariant)
-            ok = fold ? tb_run_skew<DMG, true, false>(P, items, nitems, get, status, bad)
-                      : tb_run_skew<DMG, false, false>(P, items, nitems, get, status, bad);
-        else
-            ok = fold ? tb_run<M, V, DMG, true, false>(P, items, nitems, get, status, bad)
-                      : tb_run<M, V, DMG, false, false>(P, items, nitems, get, status, bad);
+        const bool ok = fold ? tb_run<M, V, DMG, true, false, LIM>(P, items, nitems, get, status, bad)
+                             : tb_run<M, V, DMG, false, false, LIM>(P, items, nitems, get, status, bad);
         if (!ok) break;
         if (!grid_sync(gbar, gridDim.x, glimit)) {
             if (threadIdx.x == 0) atomicOr(status, kStatusTimeout | kStatusGridTimeout);
@@ -1158,11 +743,6 @@ __global__ void __launch_bounds__(CfgL<M, V>::THREADS, CfgL<M, V>::MINB)
 }
 
 // ------------------------------------------------------------------ host side
-template <int M, int V>
-constexpr int kernel_smem()
-{
-    return V == kSkewVariant ? CfgS::SMEM : CfgL<M, V>::SMEM;
-}
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
@@ -1200,7 +780,7 @@ int variant_ey(int variant) { return tile_ey(variant); }
 template <int M, int V>
 void tile_plan(const rfa_grid *g, int resident, int max_chunk, TBTile &T)
 {
-    using C = CfgL<M, V>;
+    using C = Cfg<M, V>;
     T.xt = (g->nx + TB_TX - 1) / TB_TX;
     T.yt = (g->ny + C::TY - 1) / C::TY;
     const long long tiles = (long long)T.xt * T.yt;
@@ -1239,23 +819,31 @@ void fill_tile(const rfa_grid *g, int parity, TBTile &T)
     T.TK0 = dc.TK0;
     T.rec_hi = nullptr;
     T.rec_stride = g->nvp;
-    T.ab = (const uint32_t *)g->ab;
-    T.s = (const float *)g->s;
 }
 
-template <int M, int V, bool DMG, bool FOLD, bool REC = false>
-cudaError_t launch_inst(rfa_grid *g, const TBMaps &maps, TBTile T)
+// set while rfa_set_wait_limits has set limits other than the default (process-wide)
+std::atomic<bool> g_limits_set{false};
+
+template <int M, int V, bool DMG, bool FOLD, bool REC, bool LIM>
+cudaError_t launch_inst_lim(rfa_grid *g, const TBMaps &maps, TBTile T)
 {
-    using C = CfgL<M, V>;
-    cudaError_t e = cudaFuncSetAttribute(k_step_tb<M, V, DMG, FOLD, REC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (kernel_smem<M, V>()));
+    using C = Cfg<M, V>;
+    cudaError_t e = cudaFuncSetAttribute(k_step_tb<M, V, DMG, FOLD, REC, LIM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     const int resident = 148 * C::MINB;
     tile_plan<M, V>(g, resident, 1 << 30, T);
     const long long items = (long long)T.xt * T.yt * T.zc;
     const unsigned grid = (unsigned)(items < resident ? items : resident);
-    k_step_tb<M, V, DMG, FOLD, REC><<<grid, C::THREADS, (kernel_smem<M, V>()), g->stream>>>(maps, T, g->status);
+    k_step_tb<M, V, DMG, FOLD, REC, LIM><<<grid, C::THREADS, C::SMEM, g->stream>>>(maps, T, g->status);
     return cudaGetLastError();
+}
+
+template <int M, int V, bool DMG, bool FOLD, bool REC = false>
+cudaError_t launch_inst(rfa_grid *g, const TBMaps &maps, TBTile T)
+{
+    return g_limits_set.load() ? launch_inst_lim<M, V, DMG, FOLD, REC, true>(g, maps, T)
+                               : launch_inst_lim<M, V, DMG, FOLD, REC, false>(g, maps, T);
 }
 
 // shared-memory opt-in and the co-resident grid size of the batch kernel
@@ -1263,15 +851,24 @@ cudaError_t launch_inst(rfa_grid *g, const TBMaps &maps, TBTile T)
 template <int M, int V, bool DMG>
 cudaError_t prepare_batch_inst(int nitems, int *grid)
 {
-    using C = CfgL<M, V>;
-    cudaError_t e = cudaFuncSetAttribute(k_batch_tb<M, V, DMG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (kernel_smem<M, V>()));
+    using C = Cfg<M, V>;
+    // both instantiations (default and test wait limits): shared-memory opt-in, and the
+    // co-resident grid of the one with the lower occupancy
+    cudaError_t e = cudaFuncSetAttribute(k_batch_tb<M, V, DMG, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         C::SMEM);
     if (e != cudaSuccess) return e;
-    int dev = 0, nsm = 0, per_sm = 0;
+    e = cudaFuncSetAttribute(k_batch_tb<M, V, DMG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             C::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0, per_sm = 0, per_sm_lim = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_tb<M, V, DMG>, C::THREADS, (kernel_smem<M, V>()));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_tb<M, V, DMG, false>, C::THREADS, C::SMEM);
     if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_lim, k_batch_tb<M, V, DMG, true>, C::THREADS,
+                                                      C::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm_lim < per_sm) per_sm = per_sm_lim;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     *grid = nsm * per_sm < nitems ? nsm * per_sm : nitems;
     return cudaSuccess;
@@ -1281,19 +878,21 @@ template <int M, int V, bool DMG>
 cudaError_t launch_batch_inst(const TBMember *mem, int nmem, int nitems, int ntime, int fold_every,
                               unsigned *gbar, unsigned *status, cudaStream_t stream, int grid)
 {
-    using C = CfgL<M, V>;
+    using C = Cfg<M, V>;
     // cooperative launch: every CTA is resident at once, which the grid barrier needs
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3((unsigned)C::THREADS);
-    cfg.dynamicSmemBytes = (kernel_smem<M, V>());
+    cfg.dynamicSmemBytes = C::SMEM;
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_batch_tb<M, V, DMG>, mem, nmem, nitems, ntime, fold_every, gbar, status);
+    if (g_limits_set.load())
+        return cudaLaunchKernelEx(&cfg, k_batch_tb<M, V, DMG, true>, mem, nmem, nitems, ntime, fold_every, gbar, status);
+    return cudaLaunchKernelEx(&cfg, k_batch_tb<M, V, DMG, false>, mem, nmem, nitems, ntime, fold_every, gbar, status);
 }
 
 // tensor maps per (grid, input buffers, tile height); erased when the grid is destroyed
@@ -1313,17 +912,22 @@ cudaError_t tb_set_wait_limits(long long mbar_cycles, long long grid_cycles)
 {
     cudaError_t e = cudaMemcpyToSymbol(g_wait_limit_mbar, &mbar_cycles, sizeof mbar_cycles);
     if (e != cudaSuccess) return e;
-    return cudaMemcpyToSymbol(g_wait_limit_grid, &grid_cycles, sizeof grid_cycles);
+    e = cudaMemcpyToSymbol(g_wait_limit_grid, &grid_cycles, sizeof grid_cycles);
+    if (e != cudaSuccess) return e;
+    g_limits_set.store(mbar_cycles != kDefaultLimit || grid_cycles != kDefaultLimit);
+    return cudaSuccess;
 }
+
+bool tb_limits_set() { return g_limits_set.load(); }
 
 bool tb_supported(const rfa_grid *g, int depth, int variant)
 {
     if (g->sp != RFA_STATE_F32C || g->pp != RFA_PARAM_BF16) return false;
-    if (variant < 0 || variant > kSkewVariant) return false;
+    if (variant < 0 || variant > 1) return false;
     if (g->face != RFA_FACE_DIRICHLET) return false;  // insulated faces: one-step kernel
     if (g->cond != RFA_COND_CENTRE || g->alpha_perf) return false;  // model options: their own kernel
     if (variant == 0 && (depth < 2 || depth > 3)) return false;
-    if (variant >= 1 && depth != 2) return false;  // tile 1 and the split-barrier pipeline: depth 2
+    if (variant >= 1 && depth != 2) return false;
     return encode_fn() != nullptr;
 }
 
@@ -1374,7 +978,6 @@ cudaError_t launch_step_tb(rfa_grid *g, int depth, int variant, const void *th_i
     TB_CASE(2, 0)
     TB_CASE(3, 0)
     TB_CASE(2, 1)
-    TB_CASE(2, 2)
 #undef TB_CASE
     return cudaErrorInvalidValue;
 }
@@ -1392,7 +995,6 @@ cudaError_t launch_step_tb_rec(rfa_grid *g, int depth, int variant, const void *
     if (depth == 2 && variant == 0) return launch_inst<2, 0, false, false, true>(g, maps, T);
     if (depth == 3 && variant == 0) return launch_inst<3, 0, false, false, true>(g, maps, T);
     if (depth == 2 && variant == 1) return launch_inst<2, 1, false, false, true>(g, maps, T);
-    if (depth == 2 && variant == 2) return launch_inst<2, 2, false, false, true>(g, maps, T);
     return cudaErrorInvalidValue;
 }
 
@@ -1443,7 +1045,6 @@ cudaError_t prepare_batch_tb(int depth, int variant, bool damage, int nitems, in
     PREP_CASE(2, 0)
     PREP_CASE(3, 0)
     PREP_CASE(2, 1)
-    PREP_CASE(2, 2)
 #undef PREP_CASE
     return cudaErrorInvalidValue;
 }
@@ -1454,7 +1055,7 @@ template <int M, int V, bool DMG>
 cudaError_t graph_batch_inst(const TBMember *mem, int nmem, int nitems, int ntime, int fold_every,
                              unsigned *gbar, unsigned *status, int grid, cudaGraphExec_t *exec)
 {
-    using C = CfgL<M, V>;
+    using C = Cfg<M, V>;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaGraphCreate(&graph, 0);
     if (e != cudaSuccess) return e;
@@ -1471,10 +1072,10 @@ cudaError_t graph_batch_inst(const TBMember *mem, int nmem, int nitems, int ntim
                     (void *)&gbar, (void *)&status};
     if (e == cudaSuccess) {
         cudaKernelNodeParams kp = {};
-        kp.func = (void *)k_batch_tb<M, V, DMG>;
+        kp.func = g_limits_set.load() ? (void *)k_batch_tb<M, V, DMG, true> : (void *)k_batch_tb<M, V, DMG, false>;
         kp.gridDim = dim3((unsigned)grid);
         kp.blockDim = dim3((unsigned)C::THREADS);
-        kp.sharedMemBytes = (kernel_smem<M, V>());
+        kp.sharedMemBytes = C::SMEM;
         kp.kernelParams = args;
         e = cudaGraphAddKernelNode(&nkernel, graph, &nmemset, 1, &kp);
     }
@@ -1500,7 +1101,6 @@ cudaError_t graph_batch_tb(int depth, int variant, bool damage, const void *memb
     GRAPH_CASE(2, 0)
     GRAPH_CASE(3, 0)
     GRAPH_CASE(2, 1)
-    GRAPH_CASE(2, 2)
 #undef GRAPH_CASE
     return cudaErrorInvalidValue;
 }
@@ -1517,7 +1117,6 @@ cudaError_t launch_batch_tb(int depth, int variant, bool damage, const void *mem
     BATCH_CASE(2, 0)
     BATCH_CASE(3, 0)
     BATCH_CASE(2, 1)
-    BATCH_CASE(2, 2)
 #undef BATCH_CASE
     return cudaErrorInvalidValue;
 }

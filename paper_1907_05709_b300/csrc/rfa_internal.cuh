@@ -262,6 +262,8 @@ bool tb_supported(const rfa_grid *g, int depth, int variant);
 // spin limits (SM cycles) of the blocked kernels' mbarrier waits and of the
 // batch's grid barrier, for kernels launched afterwards on the current device
 cudaError_t tb_set_wait_limits(long long mbar_cycles, long long grid_cycles);
+// true while limits other than the default are set (kernels then read them at start)
+bool tb_limits_set();
 void tb_forget_maps(const rfa_grid *g);
 cudaError_t launch_step_tb(rfa_grid *g, int depth, int variant, const void *th_in,
                            const void *lo_in, void *th_out, void *lo_out, bool damage, bool fold);
@@ -284,8 +286,6 @@ struct TBTile {
     float c0, c1, TK0;
     float *rec_hi;  // replay: hi of the intermediate states (stage k at rec_hi + (k - 1) * rec_stride)
     size_t rec_stride;
-    const uint32_t *ab;  // packed BF16 coefficients and source (read directly by the
-    const float *s;      // split-barrier pipeline's last stage)
 };
 // a batch member on the host: tiles and tensor maps for both ping-pong parities
 struct TBMemberHost {

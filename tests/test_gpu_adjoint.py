@@ -65,7 +65,7 @@ def test_adjoint_matches_oracle_small(kind):
     assert g_gpu[4 + ph.VESSEL] == 0.0 and g_gpu[4 + 3 + ph.VESSEL] == 0.0
 
 
-@pytest.mark.parametrize("sched", [(2, 0), (2, 2)])
+@pytest.mark.parametrize("sched", [(2, 0), (2, 1)])
 def test_adjoint_recorded_in_chunks_and_blocked_forward(sched):
     case = ph.random_small_case(32, 37, 30, 33, kind=ph.UMBRELLA, power=5.0)
     # forward by the 2-step blocked kernel; the recomputation replays the checkpoint

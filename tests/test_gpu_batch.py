@@ -25,7 +25,7 @@ def _state(g):
 
 
 @pytest.mark.parametrize("damage", [False, True])
-@pytest.mark.parametrize("sched", [None, (2, 0), (3, 0), (2, 1), (2, 2)])
+@pytest.mark.parametrize("sched", [None, (2, 0), (3, 0), (2, 1)])
 def test_batch_equals_members_stepped_alone(damage, sched):
     cases, alone = _members(damage)
     _, grids = _members(damage)
@@ -88,7 +88,7 @@ def test_batch_autotune_restores_states(tmp_path):
     b = rfa.rfa_batch_create([g.handle for g in grids])
     rfa.rfa_batch_autotune(b, str(tmp_path / "t.txt"))
     d, v, graphs = rfa.rfa_batch_get_schedule(b)
-    assert (d, v) in [(2, 0), (3, 0), (2, 1), (2, 2)]
+    assert (d, v) in [(2, 0), (3, 0), (2, 1)]
     for g, st in zip(grids, before):
         now = _state(g)
         assert all(np.array_equal(x, y) for x, y in zip(st, now))

@@ -1,6 +1,5 @@
-"""Temporally blocked step (several steps per launch, TMA-staged tiles; tile
-variant 2 is the split-barrier pipeline): bit-identical states to the one-step
-kernel, and parity with the oracle."""
+"""Temporally blocked step (several steps per launch, TMA-staged tiles):
+bit-identical states to the one-step kernel, and parity with the oracle."""
 import numpy as np
 import pytest
 
@@ -10,7 +9,7 @@ from tests.parity_util import compare, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
-SCHEDULES = [(2, 0), (3, 0), (2, 1), (2, 2)]
+SCHEDULES = [(2, 0), (3, 0), (2, 1)]
 
 
 @pytest.mark.parametrize("sched", SCHEDULES)
@@ -57,12 +56,12 @@ def test_schedule_rejected_where_unsupported():
         g.set_schedule(9, 0)
     assert e.value.status == 1
     g.close()
-    # the split-barrier pipeline (tile variant 2) runs depth 2 only
+    # tile variant 1 runs depth 2 only; there is no variant 2
     g = rfa.Grid.from_case(case)
-    with pytest.raises(rfa.RfaError) as e:
-        g.set_schedule(3, 2)
-    assert e.value.status == 8
-    g.set_schedule(2, 2)
+    for bad in ((3, 1), (2, 2)):
+        with pytest.raises(rfa.RfaError) as e:
+            g.set_schedule(*bad)
+        assert e.value.status == 8
     g.close()
     # insulated faces: the blocked kernel needs Dirichlet faces (one step per launch)
     ins = ph.random_small_case(3, 20, 20, 20, face_bc=ph.INSULATED)
