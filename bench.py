@@ -508,11 +508,12 @@ def measure_path_rows(rfa, stream, case, g, labels_dev, cpu_baseline_on: bool = 
 
 def measure_batched(rfa, stream, args):
     """64 needle configurations on {96,128,160,192}^3 grids, 4000 steps (or
-    --batch-steps): one batched persistent launch per call vs the per-needle loop
-    of one-step launches, and vs the per-needle loop with the tuned schedule."""
+    --batch-steps), with the latch and the Arrhenius integral as in the headline:
+    one batched persistent launch per call vs the per-needle loop of one-step
+    launches, and vs the per-needle loop with the tuned schedule."""
     import torch
     cases = ph.batch_members(0, 64, args.batch_steps)
-    grids = [rfa.Grid.from_case(c, damage=False, cuda_stream=stream.cuda_stream) for c in cases]
+    grids = [rfa.Grid.from_case(c, damage=True, cuda_stream=stream.cuda_stream) for c in cases]
     vox = sum(c.nvox for c in cases)
     n = args.batch_steps
     b = rfa.rfa_batch_create([g.handle for g in grids])
@@ -532,7 +533,7 @@ def measure_batched(rfa, stream, args):
     t_tuned = _ms_between(torch, stream, lambda: loop(d, v))
     for g in grids:
         g.close()
-    return {"workload": "batch64", "members": len(cases), "voxels": vox, "time_steps": n,
+    return {"workload": "batch64", "members": len(cases), "voxels": vox, "time_steps": n, "arrhenius": True,
             "batched_ms": t_batch, "batched_gvox_steps_s": vox * n / t_batch / 1e6,
             "plain_loop_ms": t_plain, "plain_loop_gvox_steps_s": vox * n / t_plain / 1e6,
             "tuned_loop_ms": t_tuned, "batched_over_plain_loop": t_plain / t_batch,

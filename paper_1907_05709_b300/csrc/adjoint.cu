@@ -14,6 +14,10 @@
 // with dw_i/dtip = 4 d_i^-6 (x_i - p*_i) outside the clamp radius (every
 // segment moves rigidly with the tip) and W = sum_free w, dW = sum_free dw.
 //
+// Lambda is accumulated once per pair of reverse steps (the second step of a
+// pair adds both inputs; the first input is still in its ping-pong buffer when
+// the second step reads it), which halves its read-modify-write traffic.
+//
 // Trajectory: checkpoints (hi, lo) every ceil(sqrt(N)) steps are taken while
 // rfa_step records; the backward pass replays each segment -- two steps per
 // launch with the blocked kernel in replay mode, which also stores the
@@ -93,6 +97,10 @@ struct AdjArgs {
     const uint8_t *label;
     const LabelCoef *tab;
     int nx, ny, nz, pitch, zchunk, face;
+    // Lambda update of this step: 0 none, 1 Lambda += lambda_in + lambda_prev (the
+    // previous step's input, still in lam_out until this step overwrites it), 2
+    // Lambda += lambda_in.  Pairing the steps halves Lambda's read-modify-write.
+    int lam_mode;
     size_t plane;
     float fk[kMaxGradLabels], gw[kMaxGradLabels];
     double *acc;  // [2 * kMaxGradLabels]: sum lambda f L(theta), -sum lambda g theta
@@ -170,7 +178,7 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_step(const AdjArgs A)
             float4 lym = make_float4(0, 0, 0, 0), lyp = lym, tym = lym, typ = lym;
             float aym[4] = {0, 0, 0, 0}, ayp[4] = {0, 0, 0, 0};
             uint32_t lab4 = 0;
-            float4 Lc = make_float4(0, 0, 0, 0);
+            float4 Lc = make_float4(0, 0, 0, 0), Lp = Lc;
             if (inrow) {
                 if (hasZp) {
                     lp = ld4g(A.lam_in + i + A.plane);
@@ -193,7 +201,8 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_step(const AdjArgs A)
                     adj_load_ab<PP>(A.ab, i + A.pitch, ayp, bdum);
                 }
                 lab4 = __ldg(reinterpret_cast<const uint32_t *>(A.label + i));
-                Lc = ld4g(A.Lam + i);
+                if (A.lam_mode != 0) Lc = *reinterpret_cast<const float4 *>(A.Lam + i);
+                if (A.lam_mode == 1) Lp = *reinterpret_cast<const float4 *>(A.lam_out + i);
             }
             const float lcv[4] = {lc.x, lc.y, lc.z, lc.w}, tcv[4] = {tc.x, tc.y, tc.z, tc.w};
             const float lmv[4] = {lm.x, lm.y, lm.z, lm.w}, tmv[4] = {tm.x, tm.y, tm.z, tm.w};
@@ -236,7 +245,7 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_step(const AdjArgs A)
             }
             if (inrow) {
                 float lo_[4], Lo_[4], vk4[4], vw4[4];
-                const float Lcv[4] = {Lc.x, Lc.y, Lc.z, Lc.w};
+                const float Lcv[4] = {Lc.x, Lc.y, Lc.z, Lc.w}, Lpv[4] = {Lp.x, Lp.y, Lp.z, Lp.w};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int x = x0 + q;
@@ -252,7 +261,7 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_step(const AdjArgs A)
                     if (hasZp) { smu += ap[q] * lpv[q] - m; lt += tpv[q] - t; }
                     const bool valid = x < A.nx;
                     lo_[q] = valid ? l + smu - bc[q] * l : 0.f;
-                    Lo_[q] = valid ? Lcv[q] + l : 0.f;
+                    Lo_[q] = valid ? Lcv[q] + (A.lam_mode == 1 ? Lpv[q] + l : l) : 0.f;
                     // free voxels are exactly those with a > 0 (fixed labels and Dirichlet
                     // faces carry a = 0; every tissue has K > 0)
                     const bool free_vox = valid && ac[q] > 0.f;
@@ -289,7 +298,8 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_step(const AdjArgs A)
                     }
                 }
                 *reinterpret_cast<float4 *>(A.lam_out + i) = make_float4(lo_[0], lo_[1], lo_[2], lo_[3]);
-                *reinterpret_cast<float4 *>(A.Lam + i) = make_float4(Lo_[0], Lo_[1], Lo_[2], Lo_[3]);
+                if (A.lam_mode != 0)
+                    *reinterpret_cast<float4 *>(A.Lam + i) = make_float4(Lo_[0], Lo_[1], Lo_[2], Lo_[3]);
             }
             lm = lc; lc = lp; tm = tc; tc = tp;
 #pragma unroll
@@ -421,12 +431,13 @@ __global__ void k_src_grad_final(const double *part, int nblocks, double *out)
 }
 
 cudaError_t launch_adjoint_step(rfa_grid *g, const AdjArgs &A0, const float *lam_in, float *lam_out,
-                                const float *th)
+                                const float *th, int lam_mode)
 {
     AdjArgs A = A0;
     A.lam_in = lam_in;
     A.lam_out = lam_out;
     A.th = th;
+    A.lam_mode = lam_mode;
     dim3 blk(32, 8);
     dim3 grd = plain_grid_dims(g, A.zchunk);
     const bool few = g->n_labels <= 4;
@@ -523,6 +534,7 @@ rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads)
     if (g->sched.tb_depth == 2 && tb_supported(g, 2, g->sched.tile_variant)) replay_variant = g->sched.tile_variant;
     else if (tb_supported(g, 2, 0)) replay_variant = 0;
     int lcur = 0;  // lambda ping-pong index holding lambda^{n+1}
+    int64_t kadj = 0;  // adjoint steps done (the centre form pairs their Lambda updates)
     const int64_t nck = (int64_t)g->rec.used;
     for (int64_t c = nck - 1; c >= 0; --c) {
         const int64_t s0 = c * seg, s1 = (s0 + seg < N) ? s0 + seg : N;
@@ -559,8 +571,10 @@ rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads)
                 RFA_CUDA(launch_adjoint_cond(g, lam2 + (size_t)lcur * nvp, lam2 + (size_t)(lcur ^ 1) * nvp,
                                              (float *)Lam.p, th, accd));
             else
-                RFA_CUDA(launch_adjoint_step(g, A, lam2 + (size_t)lcur * nvp, lam2 + (size_t)(lcur ^ 1) * nvp, th));
+                RFA_CUDA(launch_adjoint_step(g, A, lam2 + (size_t)lcur * nvp, lam2 + (size_t)(lcur ^ 1) * nvp, th,
+                                             (kadj & 1) ? 1 : (kadj == N - 1 ? 2 : 0)));
             lcur ^= 1;
+            ++kadj;
         }
     }
     // source contractions
