@@ -103,16 +103,37 @@ __device__ __forceinline__ size_t pot_at(const PotGrid &G, int x, int y, int z)
     return (size_t)z * G.plane + (size_t)y * G.pitch + x;
 }
 
-__global__ void k_pot_class(NeedleGeom geom, PotGrid G, double h, uint8_t *cls)
+// Electrode: the voxels whose FP64 squared distance to the needle is at most
+// r0^2.  The FP32 distance decides where it lies more than the margin from r0^2
+// (the FP64 value is within the margin of it); the voxels near r0^2 take the
+// FP64 value (needle_dist2_pruned equals needle_dist2), so the classes are those
+// of the FP64 test everywhere.  A warp per grid row, lanes along x (padding
+// included).
+__global__ void __launch_bounds__(256) k_pot_class(NeedleGeom geom, PotGrid G, double h, float margin, uint8_t *cls)
 {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < G.nvp; i += (size_t)gridDim.x * blockDim.x) {
-        int x, y, z;
-        pot_xyz(G, i, x, y, z);
-        uint8_t c = CLS_FREE;
-        if (x >= G.nx) c = CLS_PAD;
-        else if (x == 0 || y == 0 || z == 0 || x == G.nx - 1 || y == G.ny - 1 || z == G.nz - 1) c = CLS_GROUND;
-        else if (needle_dist2(geom, x * h, y * h, z * h) <= geom.r0 * geom.r0) c = CLS_ELECTRODE;
-        cls[i] = c;
+    __shared__ float s32[kMaxSegments][7];
+    load_seg32(geom, s32);
+    __syncthreads();
+    const double r02 = geom.r0 * geom.r0;
+    const float r02f = (float)r02, hf = (float)h;
+    for (int row = blockIdx.x * 8 + (int)(threadIdx.x >> 5); row < G.ny * G.nz; row += gridDim.x * 8) {
+        const int y = row % G.ny, z = row / G.ny;
+        for (int x = threadIdx.x & 31; x < G.pitch; x += 32) {
+            uint8_t c = CLS_FREE;
+            if (x >= G.nx) {
+                c = CLS_PAD;
+            } else if (x == 0 || y == 0 || z == 0 || x == G.nx - 1 || y == G.ny - 1 || z == G.nz - 1) {
+                c = CLS_GROUND;
+            } else {
+                const float d32 = needle_dist2_f32(geom, s32, x * hf, y * hf, z * hf);
+                bool el;
+                if (d32 > r02f + margin) el = false;
+                else if (d32 + margin < r02f) el = true;
+                else el = needle_dist2_pruned(geom, s32, x * h, y * h, z * h, x * hf, y * hf, z * hf, margin) <= r02;
+                if (el) c = CLS_ELECTRODE;
+            }
+            cls[pot_at(G, x, y, z)] = c;
+        }
     }
 }
 
@@ -1148,7 +1169,7 @@ rfa_status potential_place(rfa_grid *g)
     uint8_t *quni = (uint8_t *)B.p[10];
     PotGrid G{cls, g->label, quni, dS, g->nx, g->ny, g->nz, g->pitch, g->plane, nvp};
     const unsigned nb = kReduceBlocks;
-    k_pot_class<<<nb, 256, 0, g->stream>>>(g->geom, G, g->h, cls);
+    k_pot_class<<<nb, 256, 0, g->stream>>>(g->geom, G, g->h, needle_margin(g), cls);
     k_pot_quni<<<nb, 256, 0, g->stream>>>(G, quni);
     k_pot_init<<<nb, 256, 0, g->stream>>>(G, xv, r, zv, p, Dv, iDv, part);
     k_pot_scalars<<<1, 1024, 0, g->stream>>>(part, nb, SCW_START, sc);

@@ -136,40 +136,6 @@ __device__ double block_sum(double v)
     return v;
 }
 
-// needle_dist2 with the same FP64 value, evaluating in FP64 only the segments
-// that can be the nearest.  An FP32 pass over all segments gives each squared
-// distance to within e (bounded by the coordinates' magnitude); the nearest
-// segment's FP32 value is then within 2e of the FP32 minimum, so every segment
-// within margin >= 2e of it is evaluated with needle_dist2's FP64 expression
-// and the minimum of those is needle_dist2's minimum.  s32 holds the segments
-// in FP32: p0 (3), p1 - p0 (3), 1 / |p1 - p0|^2.
-__device__ __forceinline__ double needle_dist2_pruned(const NeedleGeom &g, const float (*s32)[7], double px,
-                                                      double py, double pz, float pxf, float pyf, float pzf,
-                                                      float margin)
-{
-    auto d32 = [&](int k) {
-        const float *q = s32[k];
-        const float wx = pxf - q[0], wy = pyf - q[1], wz = pzf - q[2];
-        const float t = fminf(fmaxf((wx * q[3] + wy * q[4] + wz * q[5]) * q[6], 0.f), 1.f);
-        const float ex = wx - t * q[3], ey = wy - t * q[4], ez = wz - t * q[5];
-        return ex * ex + ey * ey + ez * ez;
-    };
-    float m32 = 3.0e38f;
-    for (int k = 0; k < g.nseg; ++k) m32 = fminf(m32, d32(k));
-    double best = 1e300;
-    for (int k = 0; k < g.nseg; ++k) {
-        if (!(d32(k) <= m32 + margin)) continue;
-        const Segment &sg = g.seg[k];
-        double ux = sg.p1[0] - sg.p0[0], uy = sg.p1[1] - sg.p0[1], uz = sg.p1[2] - sg.p0[2];
-        double wx = px - sg.p0[0], wy = py - sg.p0[1], wz = pz - sg.p0[2];
-        double t = (wx * ux + wy * uy + wz * uz) * sg.inv_uu;
-        t = fmin(fmax(t, 0.0), 1.0);
-        double ex = wx - t * ux, ey = wy - t * uy, ez = wz - t * uz;
-        best = fmin(best, ex * ex + ey * ey + ez * ez);
-    }
-    return best;
-}
-
 // pass 1: per-block sums of w over free voxels
 __global__ void k_source_sum(NeedleGeom geom, const uint8_t *__restrict__ label,
                              const LabelCoef *__restrict__ tab, int nx, int ny, int nz,
@@ -177,14 +143,7 @@ __global__ void k_source_sum(NeedleGeom geom, const uint8_t *__restrict__ label,
                              unsigned *status)
 {
     __shared__ float s32[kMaxSegments][7];
-    if (threadIdx.x < geom.nseg) {
-        const Segment &sg = geom.seg[threadIdx.x];
-        for (int c = 0; c < 3; ++c) {
-            s32[threadIdx.x][c] = (float)sg.p0[c];
-            s32[threadIdx.x][3 + c] = (float)(sg.p1[c] - sg.p0[c]);
-        }
-        s32[threadIdx.x][6] = (float)sg.inv_uu;
-    }
+    load_seg32(geom, s32);
     __syncthreads();
     const float hf = (float)h;
     size_t nvp = (size_t)pitch * ny * nz;
@@ -391,16 +350,7 @@ cudaError_t launch_source_write(rfa_grid *g, const double *partial, int npartial
 cudaError_t launch_source(rfa_grid *g)
 {
     double *partial = (double *)g->red;
-    // With coordinates of magnitude at most L, the FP32 squared distance is off
-    // by at most ~110 u L d + 3 u d^2 <= 2.3e-5 L^2 (u = 2^-24, d <= 2 sqrt(3) L:
-    // roundings of the coordinates, the projection t and the difference e).  The
-    // nearest segment is then within 2e <= 4.6e-5 L^2 of the FP32 minimum; the
-    // margin is 2e-4 L^2.
-    double L = std::max({g->nx, g->ny, g->nz}) * g->h;
-    for (int k = 0; k < g->geom.nseg; ++k)
-        for (int c = 0; c < 3; ++c)
-            L = std::max({L, std::fabs(g->geom.seg[k].p0[c]), std::fabs(g->geom.seg[k].p1[c])});
-    const float margin = (float)(2e-4 * L * L);
+    const float margin = needle_margin(g);
     k_source_sum<<<kReduceBlocks, 256, 0, g->stream>>>(g->geom, g->label, g->d_table, g->nx,
                                                        g->ny, g->nz, g->pitch, g->h, g->face, margin,
                                                        partial, (double *)g->stage, g->status);

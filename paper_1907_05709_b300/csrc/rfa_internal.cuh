@@ -20,6 +20,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -226,6 +228,85 @@ __device__ inline double needle_dist2(const NeedleGeom &g, double px, double py,
         best = fmin(best, ex * ex + ey * ey + ez * ez);
     }
     return best;
+}
+
+// The segments in FP32 for the pruned distance below, one per thread of the
+// block's first nseg threads (the caller synchronises): p0 (3), p1 - p0 (3),
+// 1 / |p1 - p0|^2.
+__device__ __forceinline__ void load_seg32(const NeedleGeom &g, float (*s32)[7])
+{
+    if (threadIdx.x < (unsigned)g.nseg) {
+        const Segment &sg = g.seg[threadIdx.x];
+        for (int c = 0; c < 3; ++c) {
+            s32[threadIdx.x][c] = (float)sg.p0[c];
+            s32[threadIdx.x][3 + c] = (float)(sg.p1[c] - sg.p0[c]);
+        }
+        s32[threadIdx.x][6] = (float)sg.inv_uu;
+    }
+}
+
+// squared distance to the nearest segment in FP32 (within e of the FP64 value,
+// see needle_margin)
+__device__ __forceinline__ float needle_dist2_f32(const NeedleGeom &g, const float (*s32)[7], float pxf, float pyf,
+                                                  float pzf)
+{
+    float m32 = 3.0e38f;
+    for (int k = 0; k < g.nseg; ++k) {
+        const float *q = s32[k];
+        const float wx = pxf - q[0], wy = pyf - q[1], wz = pzf - q[2];
+        const float t = fminf(fmaxf((wx * q[3] + wy * q[4] + wz * q[5]) * q[6], 0.f), 1.f);
+        const float ex = wx - t * q[3], ey = wy - t * q[4], ez = wz - t * q[5];
+        m32 = fminf(m32, ex * ex + ey * ey + ez * ez);
+    }
+    return m32;
+}
+
+// needle_dist2 with the same FP64 value, evaluating in FP64 only the segments
+// that can be the nearest.  An FP32 pass over all segments gives each squared
+// distance to within e (bounded by the coordinates' magnitude); the nearest
+// segment's FP32 value is then within 2e of the FP32 minimum, so every segment
+// within margin >= 2e of it is evaluated with needle_dist2's FP64 expression
+// and the minimum of those is needle_dist2's minimum.  s32 holds the segments
+// in FP32: p0 (3), p1 - p0 (3), 1 / |p1 - p0|^2.
+__device__ __forceinline__ double needle_dist2_pruned(const NeedleGeom &g, const float (*s32)[7], double px,
+                                                      double py, double pz, float pxf, float pyf, float pzf,
+                                                      float margin)
+{
+    auto d32 = [&](int k) {
+        const float *q = s32[k];
+        const float wx = pxf - q[0], wy = pyf - q[1], wz = pzf - q[2];
+        const float t = fminf(fmaxf((wx * q[3] + wy * q[4] + wz * q[5]) * q[6], 0.f), 1.f);
+        const float ex = wx - t * q[3], ey = wy - t * q[4], ez = wz - t * q[5];
+        return ex * ex + ey * ey + ez * ez;
+    };
+    float m32 = 3.0e38f;
+    for (int k = 0; k < g.nseg; ++k) m32 = fminf(m32, d32(k));
+    double best = 1e300;
+    for (int k = 0; k < g.nseg; ++k) {
+        if (!(d32(k) <= m32 + margin)) continue;
+        const Segment &sg = g.seg[k];
+        double ux = sg.p1[0] - sg.p0[0], uy = sg.p1[1] - sg.p0[1], uz = sg.p1[2] - sg.p0[2];
+        double wx = px - sg.p0[0], wy = py - sg.p0[1], wz = pz - sg.p0[2];
+        double t = (wx * ux + wy * uy + wz * uz) * sg.inv_uu;
+        t = fmin(fmax(t, 0.0), 1.0);
+        double ex = wx - t * ux, ey = wy - t * uy, ez = wz - t * uz;
+        best = fmin(best, ex * ex + ey * ey + ez * ez);
+    }
+    return best;
+}
+
+// With coordinates of magnitude at most L, the FP32 squared distance is off by
+// at most e = ~110 u L d + 3 u d^2 <= 2.3e-5 L^2 (u = 2^-24, d <= 2 sqrt(3) L:
+// roundings of the coordinates, the projection t and the difference e).  The
+// nearest segment is then within 2e <= 4.6e-5 L^2 of the FP32 minimum, and the
+// FP64 minimum within e of it; the margin is 2e-4 L^2.
+inline float needle_margin(const rfa_grid *g)
+{
+    double L = std::max({g->nx, g->ny, g->nz}) * g->h;
+    for (int k = 0; k < g->geom.nseg; ++k)
+        for (int c = 0; c < 3; ++c)
+            L = std::max({L, std::fabs(g->geom.seg[k].p0[c]), std::fabs(g->geom.seg[k].p1[c])});
+    return (float)(2e-4 * L * L);
 }
 
 // ---------------------------------------------------------------- launchers
