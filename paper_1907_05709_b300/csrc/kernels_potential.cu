@@ -663,30 +663,6 @@ __global__ void __launch_bounds__(256) k_mg0_first(PotGrid G, const float *iD32,
     }
 }
 
-// fine level: out = in + omega (b - A in) / D (RESID: out = b - A in)
-template <bool RESID>
-__global__ void __launch_bounds__(256) k_mg0_sweep(PotGrid G, const float *D32, const float *iD32, const float *b,
-                                                  const float *in, float *out)
-{
-    __shared__ float S[kCondLabels * kCondLabels];
-    pot_table32(G, S);
-    POT_QUADS(G)
-    {
-        const size_t i = pot_at(G, x0, y, z);
-        float4 v4;
-        const float4 a4 = pot_av4(G, S, in, D32, i, x0, y, z, v4);
-        const float4 b4 = ld4(b + i);
-        const float4 r4 = make_float4(b4.x - a4.x, b4.y - a4.y, b4.z - a4.z, b4.w - a4.w);
-        if (RESID) {
-            st4(out + i, r4);
-        } else {
-            const float4 d4 = ld4(iD32 + i);
-            st4(out + i, make_float4(fmaf(kMgOmega * d4.x, r4.x, v4.x), fmaf(kMgOmega * d4.y, r4.y, v4.y),
-                                     fmaf(kMgOmega * d4.z, r4.z, v4.z), fmaf(kMgOmega * d4.w, r4.w, v4.w)));
-        }
-    }
-}
-
 // fine level: coarse right side bc = P^T r (sum of the up to 8 fine children)
 __global__ void __launch_bounds__(256) k_mg0_restrict(PotGrid G, const float *r, MgLevel C, float *bc)
 {
@@ -748,6 +724,97 @@ __global__ void __launch_bounds__(256) k_mg_first(MgLevel L, const float *b, flo
 }
 
 // coarse level: out = in + omega (b - A in) / D (RESID: out = b - A in)
+// fine level: out = in + omega (b - A in) / D (RESID: out = b - A in), streaming
+// z: a thread per quad of 4 x voxels of one row walks a chunk of planes with the
+// quad's values of planes z-1, z, z+1 in registers; the x neighbours come from
+// the adjacent lanes (a row's outer lanes load theirs).  Per voxel the
+// operations of pot_av4 in its order.  Blocks of 32 x 8 quads (plain_grid_dims).
+template <bool RESID>
+__global__ void __launch_bounds__(256) k_mg0_sweep_z(PotGrid G, const float *D32, const float *iD32, const float *b,
+                                                    const float *in, float *out, int zchunk)
+{
+    __shared__ float S[kCondLabels * kCondLabels];
+    for (int k = threadIdx.y * 32 + threadIdx.x; k < kCondLabels * kCondLabels; k += 256) S[k] = (float)G.S[k];
+    __syncthreads();
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x;
+    const int y = blockIdx.y * 8 + threadIdx.y;
+    if (y >= G.ny) return;  // whole warp
+    const int x0 = 4 * (blockIdx.x * 32 + lane);
+    const bool inrow = x0 < G.nx;
+    const int zb = blockIdx.z * zchunk, ze = min(G.nz, zb + zchunk);
+    const size_t oy = G.pitch, oz = G.plane;
+    const bool hasL = x0 > 0, hasR = x0 + 4 < G.pitch, hasYm = y > 0, hasYp = y + 1 < G.ny;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const uchar4 bz = make_uchar4(0, 0, 0, 0);
+    size_t i = (size_t)zb * oz + (size_t)y * oy + x0;
+    float4 vm = zero, vc = zero, vp = zero;
+    if (inrow) {
+        vc = ld4(in + i);
+        if (zb > 0) vm = ld4(in + i - oz);
+    }
+    for (int z = zb; z < ze; ++z, i += oz) {
+        const bool hasZm = z > 0, hasZp = z + 1 < G.nz;
+        vp = inrow && hasZp ? ld4(in + i + oz) : zero;
+        // x neighbours: lanes hold consecutive quads of the row; a quad past nx
+        // holds zeros, as the padding does
+        float pL = __shfl_up_sync(FULL, vc.w, 1), pR = __shfl_down_sync(FULL, vc.x, 1);
+        if (lane == 0) pL = inrow && hasL ? in[i - 1] : 0.f;
+        if (lane == 31) pR = inrow && hasR ? in[i + 4] : 0.f;
+        if (!inrow) continue;
+        const uchar4 c4 = ldb4(G.cls + i);
+        const int fl = G.quni[i >> 2];
+        const float4 D4 = ld4(D32 + i);
+        const float4 pym = hasYm ? ld4(in + i - oy) : zero, pyp = hasYp ? ld4(in + i + oy) : zero;
+        uchar4 l4 = bz, lym = bz, lyp = bz, lzm = bz, lzp = bz;
+        int lL = 0, lR = 0;
+        if (fl == 0) {
+            l4 = ldb4(G.label + i);
+            lL = hasL ? G.label[i - 1] : 0;
+            lR = hasR ? G.label[i + 4] : 0;
+            if (hasYm) lym = ldb4(G.label + i - oy);
+            if (hasYp) lyp = ldb4(G.label + i + oy);
+            if (hasZm) lzm = ldb4(G.label + i - oz);
+            if (hasZp) lzp = ldb4(G.label + i + oz);
+        }
+        const bool uni = fl != 0;
+        const float su = uni ? S[(fl - 1) * (kCondLabels + 1)] : 0.f;
+        float a4[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float pq = f4at(vc, q);
+            const float nb[6] = {q == 0 ? pL : f4at(vc, q - 1), q == 3 ? pR : f4at(vc, q + 1), f4at(pym, q),
+                                 f4at(pyp, q), f4at(vm, q), f4at(vp, q)};
+            float w[6];
+            if (uni) {
+#pragma unroll
+                for (int d = 0; d < 6; ++d) w[d] = su;
+            } else {
+                const int l = b4at(l4, q);
+                const int ln[6] = {q == 0 ? lL : b4at(l4, q - 1), q == 3 ? lR : b4at(l4, q + 1), b4at(lym, q),
+                                   b4at(lyp, q), b4at(lzm, q), b4at(lzp, q)};
+#pragma unroll
+                for (int d = 0; d < 6; ++d) w[d] = S[l * kCondLabels + ln[d]];
+            }
+            float a = f4at(D4, q) * pq;
+#pragma unroll
+            for (int d = 0; d < 6; ++d) a = fmaf(-w[d], nb[d], a);
+            a4[q] = b4at(c4, q) == CLS_FREE ? a : 0.f;
+        }
+        const float4 b4 = ld4(b + i);
+        const float4 r4 = make_float4(b4.x - a4[0], b4.y - a4[1], b4.z - a4[2], b4.w - a4[3]);
+        if (RESID) {
+            st4(out + i, r4);
+        } else {
+            const float4 d4 = ld4(iD32 + i);
+            st4(out + i, make_float4(fmaf(kMgOmega * d4.x, r4.x, vc.x), fmaf(kMgOmega * d4.y, r4.y, vc.y),
+                                     fmaf(kMgOmega * d4.z, r4.z, vc.z), fmaf(kMgOmega * d4.w, r4.w, vc.w)));
+        }
+        vm = vc;
+        vc = vp;
+    }
+}
+
 template <bool RESID>
 __global__ void __launch_bounds__(256) k_mg_sweep(MgLevel L, const float *b, const float *in, float *out)
 {
@@ -1196,14 +1263,17 @@ rfa_status potential_place(rfa_grid *g)
         if (rfa_status st = mg_setup(g, G, H, use_mg)) return st;
     const int nl = (int)H.L.size() - 1;
     // z = M b: one V-cycle (the fine iterates alternate between z32 and zB)
+    // the fine-level sweeps stream z in chunks (32 x 8 quads a block)
+    const int zc0 = choose_zchunk(g, 3);
+    const dim3 sblk(32, 8), sgrd = plain_grid_dims(g, zc0);
     auto vcycle = [&](const float *b0) -> float * {
         float *cur0 = z32, *oth0 = zB;
         k_mg0_first<<<nb, 256, 0, g->stream>>>(G, iD32, b0, cur0);
         for (int s = 1; s < kMgNu; ++s) {
-            k_mg0_sweep<false><<<nb, 256, 0, g->stream>>>(G, D32, iD32, b0, cur0, oth0);
+            k_mg0_sweep_z<false><<<sgrd, sblk, 0, g->stream>>>(G, D32, iD32, b0, cur0, oth0, zc0);
             std::swap(cur0, oth0);
         }
-        k_mg0_sweep<true><<<nb, 256, 0, g->stream>>>(G, D32, iD32, b0, cur0, rt);
+        k_mg0_sweep_z<true><<<sgrd, sblk, 0, g->stream>>>(G, D32, iD32, b0, cur0, rt, zc0);
         k_mg0_restrict<<<mg_blocks(H.L[1].n), 256, 0, g->stream>>>(G, rt, H.L[1], H.L[1].b);
         std::vector<float *> cur(nl + 1), oth(nl + 1);
         for (int l = 1; l < nl; ++l) {
@@ -1232,7 +1302,7 @@ rfa_status potential_place(rfa_grid *g)
         }
         k_mg0_prolong<<<nb, 256, 0, g->stream>>>(G, iD32, H.L[1], cur[1], cur0);
         for (int s = 0; s < kMgNu; ++s) {
-            k_mg0_sweep<false><<<nb, 256, 0, g->stream>>>(G, D32, iD32, b0, cur0, oth0);
+            k_mg0_sweep_z<false><<<sgrd, sblk, 0, g->stream>>>(G, D32, iD32, b0, cur0, oth0, zc0);
             std::swap(cur0, oth0);
         }
         return cur0;
