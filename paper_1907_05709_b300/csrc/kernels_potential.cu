@@ -597,60 +597,6 @@ struct MgLevel {
     float *b, *x, *t, *r;              // right side, two iterates, residual
 };
 
-// A v on a quad of the fine grid (0 off the free set; v is 0 there)
-__device__ __forceinline__ float4 pot_av4(const PotGrid &G, const float *S, const float *v, const float *D32,
-                                          size_t i, int x0, int y, int z, float4 &v4)
-{
-    const uchar4 c4 = ldb4(G.cls + i);
-    const int fl = G.quni[i >> 2];
-    v4 = ld4(v + i);
-    const float4 D4 = ld4(D32 + i);
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    const uchar4 bz = make_uchar4(0, 0, 0, 0);
-    const bool hasL = x0 > 0, hasR = x0 + 4 < G.pitch, hasYm = y > 0, hasYp = y + 1 < G.ny, hasZm = z > 0,
-               hasZp = z + 1 < G.nz;
-    const size_t oy = G.pitch, oz = G.plane;
-    const float pL = hasL ? v[i - 1] : 0.f, pR = hasR ? v[i + 4] : 0.f;
-    const float4 pym = hasYm ? ld4(v + i - oy) : zero, pyp = hasYp ? ld4(v + i + oy) : zero;
-    const float4 pzm = hasZm ? ld4(v + i - oz) : zero, pzp = hasZp ? ld4(v + i + oz) : zero;
-    uchar4 l4 = bz, lym = bz, lyp = bz, lzm = bz, lzp = bz;
-    int lL = 0, lR = 0;
-    if (fl == 0) {
-        l4 = ldb4(G.label + i);
-        lL = hasL ? G.label[i - 1] : 0;
-        lR = hasR ? G.label[i + 4] : 0;
-        if (hasYm) lym = ldb4(G.label + i - oy);
-        if (hasYp) lyp = ldb4(G.label + i + oy);
-        if (hasZm) lzm = ldb4(G.label + i - oz);
-        if (hasZp) lzp = ldb4(G.label + i + oz);
-    }
-    const bool uni = fl != 0;
-    const float su = uni ? S[(fl - 1) * (kCondLabels + 1)] : 0.f;
-    float out[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float pq = f4at(v4, q);
-        const float nb[6] = {q == 0 ? pL : f4at(v4, q - 1), q == 3 ? pR : f4at(v4, q + 1), f4at(pym, q),
-                             f4at(pyp, q), f4at(pzm, q), f4at(pzp, q)};
-        float w[6];
-        if (uni) {
-#pragma unroll
-            for (int d = 0; d < 6; ++d) w[d] = su;
-        } else {
-            const int l = b4at(l4, q);
-            const int ln[6] = {q == 0 ? lL : b4at(l4, q - 1), q == 3 ? lR : b4at(l4, q + 1), b4at(lym, q),
-                               b4at(lyp, q), b4at(lzm, q), b4at(lzp, q)};
-#pragma unroll
-            for (int d = 0; d < 6; ++d) w[d] = S[l * kCondLabels + ln[d]];
-        }
-        float a = f4at(D4, q) * pq;
-#pragma unroll
-        for (int d = 0; d < 6; ++d) a = fmaf(-w[d], nb[d], a);
-        out[q] = b4at(c4, q) == CLS_FREE ? a : 0.f;
-    }
-    return make_float4(out[0], out[1], out[2], out[3]);
-}
-
 // fine level: x = omega b / D (the first sweep, from zero)
 __global__ void __launch_bounds__(256) k_mg0_first(PotGrid G, const float *iD32, const float *b, float *x)
 {
@@ -716,19 +662,75 @@ __device__ __forceinline__ float mg_av(const MgLevel &L, const float *v, int c, 
     for (int c = blockIdx.x * blockDim.x + threadIdx.x, X, Y, Z; c < (L).n; c += gridDim.x * blockDim.x)     \
         if ((X = c % (L).nx), (Y = (c / (L).nx) % (L).ny), (Z = c / ((L).nx * (L).ny)), true)
 
+// Coarse-level passes, each over the cells c of a level that this thread takes
+// in its grid (grid-stride): the per-level kernels below and the one-block tail
+// of the V-cycle run the same code.
 // coarse level: x = omega b / D
-__global__ void __launch_bounds__(256) k_mg_first(MgLevel L, const float *b, float *x)
+__device__ __forceinline__ void mg_first_cells(const MgLevel &L, const float *b, float *x)
 {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < L.n; c += gridDim.x * blockDim.x)
         x[c] = kMgOmega * L.iD[c] * b[c];
 }
 
 // coarse level: out = in + omega (b - A in) / D (RESID: out = b - A in)
+template <bool RESID>
+__device__ __forceinline__ void mg_sweep_cells(const MgLevel &L, const float *b, const float *in, float *out)
+{
+    MG_CELLS(L)
+    {
+        const float r = b[c] - mg_av(L, in, c, X, Y, Z);
+        out[c] = RESID ? r : fmaf(kMgOmega * L.iD[c], r, in[c]);
+    }
+}
+
+// coarse level l -> l+1: bc = P^T r
+__device__ __forceinline__ void mg_restrict_cells(const MgLevel &F, const float *r, const MgLevel &C, float *bc)
+{
+    MG_CELLS(C)
+    {
+        float s = 0.f;
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int x = 2 * X + dx, y = 2 * Y + dy, z = 2 * Z + dz;
+                    if (x < F.nx && y < F.ny && z < F.nz) s += r[(z * F.ny + y) * F.nx + x];
+                }
+        bc[c] = s;
+    }
+}
+
+// coarse level l+1 -> l: x += gamma P xc on the cells with free children
+__device__ __forceinline__ void mg_prolong_cells(const MgLevel &F, const MgLevel &C, const float *xc, float *x)
+{
+    MG_CELLS(F)
+    {
+        if (F.iD[c] > 0.f) x[c] = fmaf(kMgGamma, xc[((Z >> 1) * C.ny + (Y >> 1)) * C.nx + (X >> 1)], x[c]);
+    }
+}
+
+// coarsest level: x = A^-1 b with the dense inverse (n <= kMgCoarsest, one block;
+// sb: kMgCoarsest floats of shared memory)
+__device__ __forceinline__ void mg_coarsest_cells(int n, const float *Ainv, const float *b, float *x, float *sb)
+{
+    for (int k = threadIdx.x; k < n; k += blockDim.x) sb[k] = b[k];
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        float s = 0.f;
+        for (int k = 0; k < n; ++k) s = fmaf(Ainv[(size_t)k * n + t], sb[k], s);
+        x[t] = s;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mg_first(MgLevel L, const float *b, float *x) { mg_first_cells(L, b, x); }
+
 // fine level: out = in + omega (b - A in) / D (RESID: out = b - A in), streaming
 // z: a thread per quad of 4 x voxels of one row walks a chunk of planes with the
 // quad's values of planes z-1, z, z+1 in registers; the x neighbours come from
-// the adjacent lanes (a row's outer lanes load theirs).  Per voxel the
-// operations of pot_av4 in its order.  Blocks of 32 x 8 quads (plain_grid_dims).
+// the adjacent lanes (a row's outer lanes load theirs).  Per voxel, A v = D v -
+// sum over the faces x-, x+, y-, y+, z-, z+ (in that order) of the face
+// conductance times the neighbour's v, 0 off the free set (v is 0 there; the
+// labels are read only where the quad's neighbourhood has more than one).
+// Blocks of 32 x 8 quads (plain_grid_dims).
 template <bool RESID>
 __global__ void __launch_bounds__(256) k_mg0_sweep_z(PotGrid G, const float *D32, const float *iD32, const float *b,
                                                     const float *in, float *out, int zchunk)
@@ -818,48 +820,69 @@ __global__ void __launch_bounds__(256) k_mg0_sweep_z(PotGrid G, const float *D32
 template <bool RESID>
 __global__ void __launch_bounds__(256) k_mg_sweep(MgLevel L, const float *b, const float *in, float *out)
 {
-    MG_CELLS(L)
-    {
-        const float r = b[c] - mg_av(L, in, c, X, Y, Z);
-        out[c] = RESID ? r : fmaf(kMgOmega * L.iD[c], r, in[c]);
-    }
+    mg_sweep_cells<RESID>(L, b, in, out);
 }
 
-// coarse level l -> l+1: bc = P^T r
 __global__ void __launch_bounds__(256) k_mg_restrict(MgLevel F, const float *r, MgLevel C, float *bc)
 {
-    MG_CELLS(C)
-    {
-        float s = 0.f;
-        for (int dz = 0; dz < 2; ++dz)
-            for (int dy = 0; dy < 2; ++dy)
-                for (int dx = 0; dx < 2; ++dx) {
-                    const int x = 2 * X + dx, y = 2 * Y + dy, z = 2 * Z + dz;
-                    if (x < F.nx && y < F.ny && z < F.nz) s += r[(z * F.ny + y) * F.nx + x];
-                }
-        bc[c] = s;
-    }
+    mg_restrict_cells(F, r, C, bc);
 }
 
-// coarse level l+1 -> l: x += gamma P xc on the cells with free children
 __global__ void __launch_bounds__(256) k_mg_prolong(MgLevel F, MgLevel C, const float *xc, float *x)
 {
-    MG_CELLS(F)
-    {
-        if (F.iD[c] > 0.f) x[c] = fmaf(kMgGamma, xc[((Z >> 1) * C.ny + (Y >> 1)) * C.nx + (X >> 1)], x[c]);
-    }
+    mg_prolong_cells(F, C, xc, x);
 }
 
-// coarsest level: x = A^-1 b with the dense inverse (n <= kMgCoarsest, one block)
-__global__ void __launch_bounds__(kMgCoarsest) k_mg_coarsest(int n, const float *Ainv, const float *b, float *x)
+// The V-cycle on the smallest levels in one block: every level of at most
+// kMgTailCells cells, the coarsest included, where a launch per pass would cost
+// more than the pass.  Down: first sweep, kMgNu - 1 sweeps, residual and
+// restriction per level; the coarsest level's dense inverse; up: prolongation
+// and kMgNu sweeps per level; a block barrier after every pass (the next pass
+// reads what other threads wrote).  The iterates alternate between x and t as
+// in the per-level launches, so the same buffer ends up with the result.
+constexpr int kMgTailCells = 4096;
+constexpr int kMgTailMax = 8;
+struct MgTail {
+    MgLevel L[kMgTailMax];  // L[n - 1] is the coarsest level
+    int n;
+    const float *Ainv;
+};
+__global__ void __launch_bounds__(1024) k_mg_tail(const MgTail T)
 {
     __shared__ float sb[kMgCoarsest];
-    for (int k = threadIdx.x; k < n; k += blockDim.x) sb[k] = b[k];
+    float *cur[kMgTailMax], *oth[kMgTailMax];
+    for (int l = 0; l + 1 < T.n; ++l) {
+        const MgLevel &L = T.L[l];
+        cur[l] = L.x;
+        oth[l] = L.t;
+        mg_first_cells(L, L.b, cur[l]);
+        __syncthreads();
+        for (int s = 1; s < kMgNu; ++s) {
+            mg_sweep_cells<false>(L, L.b, cur[l], oth[l]);
+            __syncthreads();
+            float *t = cur[l];
+            cur[l] = oth[l];
+            oth[l] = t;
+        }
+        mg_sweep_cells<true>(L, L.b, cur[l], L.r);
+        __syncthreads();
+        mg_restrict_cells(L, L.r, T.L[l + 1], T.L[l + 1].b);
+        __syncthreads();
+    }
+    cur[T.n - 1] = T.L[T.n - 1].x;
+    mg_coarsest_cells(T.L[T.n - 1].n, T.Ainv, T.L[T.n - 1].b, cur[T.n - 1], sb);
     __syncthreads();
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        float s = 0.f;
-        for (int k = 0; k < n; ++k) s = fmaf(Ainv[(size_t)k * n + t], sb[k], s);
-        x[t] = s;
+    for (int l = T.n - 2; l >= 0; --l) {
+        const MgLevel &L = T.L[l];
+        mg_prolong_cells(L, T.L[l + 1], cur[l + 1], cur[l]);
+        __syncthreads();
+        for (int s = 0; s < kMgNu; ++s) {
+            mg_sweep_cells<false>(L, L.b, cur[l], oth[l]);
+            __syncthreads();
+            float *t = cur[l];
+            cur[l] = oth[l];
+            oth[l] = t;
+        }
     }
 }
 
@@ -1262,6 +1285,15 @@ rfa_status potential_place(rfa_grid *g)
     if (g->pot_precond == RFA_PRECOND_MULTIGRID)
         if (rfa_status st = mg_setup(g, G, H, use_mg)) return st;
     const int nl = (int)H.L.size() - 1;
+    // the levels of at most kMgTailCells cells (and the coarsest) run in one block
+    int lt = nl;
+    MgTail tail{};
+    if (use_mg) {
+        while (lt > 1 && H.L[lt - 1].n <= kMgTailCells && nl - lt + 2 <= kMgTailMax) --lt;
+        tail.n = nl - lt + 1;
+        tail.Ainv = H.Ainv;
+        for (int l = lt; l <= nl; ++l) tail.L[l - lt] = H.L[l];
+    }
     // z = M b: one V-cycle (the fine iterates alternate between z32 and zB)
     // the fine-level sweeps stream z in chunks (32 x 8 quads a block)
     const int zc0 = choose_zchunk(g, 3);
@@ -1276,7 +1308,7 @@ rfa_status potential_place(rfa_grid *g)
         k_mg0_sweep_z<true><<<sgrd, sblk, 0, g->stream>>>(G, D32, iD32, b0, cur0, rt, zc0);
         k_mg0_restrict<<<mg_blocks(H.L[1].n), 256, 0, g->stream>>>(G, rt, H.L[1], H.L[1].b);
         std::vector<float *> cur(nl + 1), oth(nl + 1);
-        for (int l = 1; l < nl; ++l) {
+        for (int l = 1; l < lt; ++l) {
             const MgLevel &L = H.L[l];
             const unsigned bl = mg_blocks(L.n);
             cur[l] = L.x;
@@ -1289,9 +1321,15 @@ rfa_status potential_place(rfa_grid *g)
             k_mg_sweep<true><<<bl, 256, 0, g->stream>>>(L, L.b, cur[l], L.r);
             k_mg_restrict<<<mg_blocks(H.L[l + 1].n), 256, 0, g->stream>>>(L, L.r, H.L[l + 1], H.L[l + 1].b);
         }
+        // levels lt .. nl in one block; their iterates alternate as in k_mg_tail
+        k_mg_tail<<<1, 1024, 0, g->stream>>>(tail);
+        for (int l = lt; l < nl; ++l) {
+            cur[l] = H.L[l].x;
+            oth[l] = H.L[l].t;
+            for (int s = 1; s < 2 * kMgNu; ++s) std::swap(cur[l], oth[l]);
+        }
         cur[nl] = H.L[nl].x;
-        k_mg_coarsest<<<1, kMgCoarsest, 0, g->stream>>>(H.L[nl].n, H.Ainv, H.L[nl].b, cur[nl]);
-        for (int l = nl - 1; l >= 1; --l) {
+        for (int l = lt - 1; l >= 1; --l) {
             const MgLevel &L = H.L[l];
             const unsigned bl = mg_blocks(L.n);
             k_mg_prolong<<<bl, 256, 0, g->stream>>>(L, H.L[l + 1], cur[l + 1], cur[l]);
