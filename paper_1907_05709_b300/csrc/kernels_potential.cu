@@ -597,18 +597,6 @@ struct MgLevel {
     float *b, *x, *t, *r;              // right side, two iterates, residual
 };
 
-// fine level: x = omega b / D (the first sweep, from zero)
-__global__ void __launch_bounds__(256) k_mg0_first(PotGrid G, const float *iD32, const float *b, float *x)
-{
-    POT_QUADS(G)
-    {
-        const size_t i = pot_at(G, x0, y, z);
-        const float4 b4 = ld4(b + i), d4 = ld4(iD32 + i);
-        st4(x + i, make_float4(kMgOmega * d4.x * b4.x, kMgOmega * d4.y * b4.y, kMgOmega * d4.z * b4.z,
-                               kMgOmega * d4.w * b4.w));
-    }
-}
-
 // fine level: coarse right side bc = P^T r (sum of the up to 8 fine children)
 __global__ void __launch_bounds__(256) k_mg0_restrict(PotGrid G, const float *r, MgLevel C, float *bc)
 {
@@ -622,25 +610,6 @@ __global__ void __launch_bounds__(256) k_mg0_restrict(PotGrid G, const float *r,
                     if (x < G.nx && y < G.ny && z < G.nz) s += r[pot_at(G, x, y, z)];
                 }
         bc[c] = s;
-    }
-}
-
-// fine level: x += gamma P xc on the free voxels (those with a nonzero diagonal)
-__global__ void __launch_bounds__(256) k_mg0_prolong(PotGrid G, const float *iD32, MgLevel C, const float *xc,
-                                                    float *x)
-{
-    POT_QUADS(G)
-    {
-        const size_t i = pot_at(G, x0, y, z);
-        const float4 d4 = ld4(iD32 + i);
-        float4 x4 = ld4(x + i);
-        const size_t cb = ((size_t)(z >> 1) * C.ny + (y >> 1)) * C.nx;
-        const int X0 = x0 >> 1;  // children x0, x0+1 of cell X0; x0+2, x0+3 of X0+1
-        if (d4.x > 0.f) x4.x = fmaf(kMgGamma, xc[cb + X0], x4.x);
-        if (d4.y > 0.f) x4.y = fmaf(kMgGamma, xc[cb + X0], x4.y);
-        if (d4.z > 0.f) x4.z = fmaf(kMgGamma, xc[cb + X0 + 1], x4.z);
-        if (d4.w > 0.f) x4.w = fmaf(kMgGamma, xc[cb + X0 + 1], x4.w);
-        st4(x + i, x4);
     }
 }
 
@@ -661,6 +630,25 @@ __device__ __forceinline__ float mg_av(const MgLevel &L, const float *v, int c, 
 #define MG_CELLS(L)                                                                                           \
     for (int c = blockIdx.x * blockDim.x + threadIdx.x, X, Y, Z; c < (L).n; c += gridDim.x * blockDim.x)     \
         if ((X = c % (L).nx), (Y = (c / (L).nx) % (L).ny), (Z = c / ((L).nx * (L).ny)), true)
+
+// fine level: x += gamma P xc on the free voxels (those with a nonzero diagonal)
+__global__ void __launch_bounds__(256) k_mg0_prolong(PotGrid G, const float *iD32, MgLevel C, const float *xc,
+                                                    float *x)
+{
+    POT_QUADS(G)
+    {
+        const size_t i = pot_at(G, x0, y, z);
+        const float4 d4 = ld4(iD32 + i);
+        float4 x4 = ld4(x + i);
+        const size_t cb = ((size_t)(z >> 1) * C.ny + (y >> 1)) * C.nx;
+        const int X0 = x0 >> 1;  // children x0, x0+1 of cell X0; x0+2, x0+3 of X0+1
+        if (d4.x > 0.f) x4.x = fmaf(kMgGamma, xc[cb + X0], x4.x);
+        if (d4.y > 0.f) x4.y = fmaf(kMgGamma, xc[cb + X0], x4.y);
+        if (d4.z > 0.f) x4.z = fmaf(kMgGamma, xc[cb + X0 + 1], x4.z);
+        if (d4.w > 0.f) x4.w = fmaf(kMgGamma, xc[cb + X0 + 1], x4.w);
+        st4(x + i, x4);
+    }
+}
 
 // Coarse-level passes, each over the cells c of a level that this thread takes
 // in its grid (grid-stride): the per-level kernels below and the one-block tail
@@ -731,7 +719,11 @@ __global__ void __launch_bounds__(256) k_mg_first(MgLevel L, const float *b, flo
 // conductance times the neighbour's v, 0 off the free set (v is 0 there; the
 // labels are read only where the quad's neighbourhood has more than one).
 // Blocks of 32 x 8 quads (plain_grid_dims).
-template <bool RESID>
+// FIRST: the first sweep, from zero: the iterate v = omega b / D is formed where
+// it is read (no pass stores it; in is not read).  Fusing the prolongation into
+// the first post-sweep the same way was measured slower (every neighbour read
+// then also loads 1/D and the coarse value): 143 us against 40 + 93 us at 256^3.
+template <bool RESID, bool FIRST>
 __global__ void __launch_bounds__(256) k_mg0_sweep_z(PotGrid G, const float *D32, const float *iD32, const float *b,
                                                     const float *in, float *out, int zchunk)
 {
@@ -749,25 +741,35 @@ __global__ void __launch_bounds__(256) k_mg0_sweep_z(PotGrid G, const float *D32
     const bool hasL = x0 > 0, hasR = x0 + 4 < G.pitch, hasYm = y > 0, hasYp = y + 1 < G.ny;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     const uchar4 bz = make_uchar4(0, 0, 0, 0);
+    // v of the voxel j and of the quad at j
+    auto v1 = [&](size_t j) -> float { return FIRST ? kMgOmega * iD32[j] * b[j] : in[j]; };
+    auto v4 = [&](size_t j) -> float4 {
+        if (FIRST) {
+            const float4 b4 = ld4(b + j), d4 = ld4(iD32 + j);
+            return make_float4(kMgOmega * d4.x * b4.x, kMgOmega * d4.y * b4.y, kMgOmega * d4.z * b4.z,
+                               kMgOmega * d4.w * b4.w);
+        }
+        return ld4(in + j);
+    };
     size_t i = (size_t)zb * oz + (size_t)y * oy + x0;
     float4 vm = zero, vc = zero, vp = zero;
     if (inrow) {
-        vc = ld4(in + i);
-        if (zb > 0) vm = ld4(in + i - oz);
+        vc = v4(i);
+        if (zb > 0) vm = v4(i - oz);
     }
     for (int z = zb; z < ze; ++z, i += oz) {
         const bool hasZm = z > 0, hasZp = z + 1 < G.nz;
-        vp = inrow && hasZp ? ld4(in + i + oz) : zero;
+        vp = inrow && hasZp ? v4(i + oz) : zero;
         // x neighbours: lanes hold consecutive quads of the row; a quad past nx
         // holds zeros, as the padding does
         float pL = __shfl_up_sync(FULL, vc.w, 1), pR = __shfl_down_sync(FULL, vc.x, 1);
-        if (lane == 0) pL = inrow && hasL ? in[i - 1] : 0.f;
-        if (lane == 31) pR = inrow && hasR ? in[i + 4] : 0.f;
+        if (lane == 0) pL = inrow && hasL ? v1(i - 1) : 0.f;
+        if (lane == 31) pR = inrow && hasR ? v1(i + 4) : 0.f;
         if (!inrow) continue;
         const uchar4 c4 = ldb4(G.cls + i);
         const int fl = G.quni[i >> 2];
         const float4 D4 = ld4(D32 + i);
-        const float4 pym = hasYm ? ld4(in + i - oy) : zero, pyp = hasYp ? ld4(in + i + oy) : zero;
+        const float4 pym = hasYm ? v4(i - oy) : zero, pyp = hasYp ? v4(i + oy) : zero;
         uchar4 l4 = bz, lym = bz, lyp = bz, lzm = bz, lzp = bz;
         int lL = 0, lR = 0;
         if (fl == 0) {
@@ -1298,14 +1300,17 @@ rfa_status potential_place(rfa_grid *g)
     // the fine-level sweeps stream z in chunks (32 x 8 quads a block)
     const int zc0 = choose_zchunk(g, 3);
     const dim3 sblk(32, 8), sgrd = plain_grid_dims(g, zc0);
+    static_assert(kMgNu >= 2, "the first pre-sweep is the fused pass from zero");
     auto vcycle = [&](const float *b0) -> float * {
         float *cur0 = z32, *oth0 = zB;
-        k_mg0_first<<<nb, 256, 0, g->stream>>>(G, iD32, b0, cur0);
-        for (int s = 1; s < kMgNu; ++s) {
-            k_mg0_sweep_z<false><<<sgrd, sblk, 0, g->stream>>>(G, D32, iD32, b0, cur0, oth0, zc0);
+        // the first sweep from zero (v = omega b / D formed where it is read), written to zB
+        k_mg0_sweep_z<false, true><<<sgrd, sblk, 0, g->stream>>>(G, D32, iD32, b0, nullptr, oth0, zc0);
+        std::swap(cur0, oth0);
+        for (int s = 2; s < kMgNu; ++s) {
+            k_mg0_sweep_z<false, false><<<sgrd, sblk, 0, g->stream>>>(G, D32, iD32, b0, cur0, oth0, zc0);
             std::swap(cur0, oth0);
         }
-        k_mg0_sweep_z<true><<<sgrd, sblk, 0, g->stream>>>(G, D32, iD32, b0, cur0, rt, zc0);
+        k_mg0_sweep_z<true, false><<<sgrd, sblk, 0, g->stream>>>(G, D32, iD32, b0, cur0, rt, zc0);
         k_mg0_restrict<<<mg_blocks(H.L[1].n), 256, 0, g->stream>>>(G, rt, H.L[1], H.L[1].b);
         std::vector<float *> cur(nl + 1), oth(nl + 1);
         for (int l = 1; l < lt; ++l) {
@@ -1340,7 +1345,7 @@ rfa_status potential_place(rfa_grid *g)
         }
         k_mg0_prolong<<<nb, 256, 0, g->stream>>>(G, iD32, H.L[1], cur[1], cur0);
         for (int s = 0; s < kMgNu; ++s) {
-            k_mg0_sweep_z<false><<<sgrd, sblk, 0, g->stream>>>(G, D32, iD32, b0, cur0, oth0, zc0);
+            k_mg0_sweep_z<false, false><<<sgrd, sblk, 0, g->stream>>>(G, D32, iD32, b0, cur0, oth0, zc0);
             std::swap(cur0, oth0);
         }
         return cur0;
