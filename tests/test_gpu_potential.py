@@ -102,3 +102,21 @@ def test_grid_without_coarse_level_falls_back_to_jacobi():
     s = g.field(rfa.FIELD_S)
     assert np.max(np.abs(s - m.s)) <= 1e-7 * max(np.max(np.abs(m.s)), 1e-300)
     g.close()
+
+
+@pytest.mark.parametrize("dims", [(10, 9, 8), (96, 40, 6)])
+def test_multigrid_level_layouts_match_direct_solve(dims):
+    # 10 x 9 x 8: one coarse level of 100 cells, the coarsest (the V-cycle's one-block
+    # tail is the dense solve alone); 96 x 40 x 6: every coarse level has at most 4096
+    # cells (2880, 480 and the 60-cell coarsest), so the whole coarse hierarchy runs in
+    # the one-block tail
+    case = _case(85, dims, kind=ph.STRAIGHT)
+    m = oracle.setup(case, "bf16")
+    g = rfa.Grid(case.nx, case.ny, case.nz, case.h, case.dt, state_prec=rfa.STATE_F64)
+    g.set_tissue(case.labels, case.table)
+    rfa.rfa_set_potential_preconditioner(g.handle, rfa.PRECOND_MULTIGRID)
+    it, res = rfa.rfa_place_needle_potential(g.handle, case.needle, [t.sigma for t in case.table], 20000, 1e-12)
+    assert 0 < it < 20000 and res <= 1e-12
+    s = g.field(rfa.FIELD_S)
+    assert np.max(np.abs(s - m.s)) <= 1e-7 * np.max(np.abs(m.s))
+    g.close()
