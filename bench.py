@@ -68,7 +68,9 @@ def workload_config(c, name, oracle_arm: bool = False):
     gb = 46.0 * c.nvox / 1e9
     return {"workload": name, "grid": [c.nx, c.ny, c.nz], "h_mm": c.h * 1e3, "dt_s": c.dt,
             "time_steps": c.nsteps, "needle": {0: "straight", 1: "umbrella", 2: "fixed tip"}[c.needle.kind],
-            "n_tines": c.needle.n_tines if c.needle.kind == 1 else 0,
+            # every tine: the ring's and the axial one (the 9-tine umbrella: 8 + 1)
+            "n_tines": c.needle.n_tines + c.needle.tine_axial if c.needle.kind == 1 else 0,
+            "axial_tine": bool(c.needle.tine_axial) if c.needle.kind == 1 else False,
             "power_W": c.needle.power, "arrhenius": bool(c.damage.enable),
             "state": "fp64 (oracle)" if oracle_arm else "fp32 hi+lo compensated",
             "coefficients": "bf16 (rounded, fed to the FP64 oracle)" if oracle_arm else "bf16",
