@@ -118,17 +118,31 @@ __device__ __forceinline__ void mld_ab(const void *ab, size_t i, W a[4], W b[4])
     }
 }
 
+__device__ __forceinline__ int byte_at(uint32_t w, int q) { return (int)((w >> (8 * q)) & 0xffu); }
+
+// (hi, lo) + delta of two voxels at once with the paired FP32 instructions:
+// every lane performs cadd's operations in cadd's order (bit-identical)
+__device__ __forceinline__ void cadd2(float2 c, float2 cl, float2 delta, float2 &nh, float2 &nl)
+{
+    const float2 s1 = add2(c, delta);
+    const float2 bb = sub2(s1, c);
+    const float2 e1 = add2(sub2(c, sub2(s1, bb)), sub2(delta, bb));
+    const float2 l1 = add2(cl, e1);
+    const float2 s2 = add2(s1, l1);
+    nl = sub2(l1, sub2(s2, s1));
+    nh = s2;
+}
+
 // One step of the model options, a thread per quad of 4 consecutive x voxels
 // streaming z (planes z-1, z, z+1 and their labels in registers); x neighbours
 // and their labels by warp shuffles, y neighbours through L1.  Per voxel the
 // centre form performs the one-step kernel's operations; the harmonic form
 // weighs every neighbour difference with its face weight from the label-pair
 // table; with the tissue-state coupling b is divided by max(1, Omega).
-// The conservative form alone (FP32 states) runs faster at 3 CTAs/SM (a few spilled
-// registers, more warps to hide its load latency); the tissue-state forms run
-// faster at 2 (measured at 256^3).
+// Every form runs at 2 CTAs/SM: at 3 (80 registers) the conservative form spills
+// and reloads its parameters, and was 13 % slower (measured at 256^3).
 template <int SP, int PP, bool COND, bool ALPHA>
-__global__ void __launch_bounds__(256, (COND && !ALPHA && SP != RFA_STATE_F64) ? 3 : 2) k_step_model(const CondArgs A)
+__global__ void __launch_bounds__(256, 2) k_step_model(const CondArgs A)
 {
     using T = typename std::conditional<SP == RFA_STATE_F64, double, float>::type;
     using W = typename std::conditional<PP == RFA_PARAM_F64, double, float>::type;
@@ -146,53 +160,64 @@ __global__ void __launch_bounds__(256, (COND && !ALPHA && SP != RFA_STATE_F64) ?
     if (y >= A.ny) return;  // whole warp (blockDim.x == 32), after the only barrier
     const int x0 = 4 * (blockIdx.x * 32 + lane);
     const bool inrow = x0 < A.pitch;
+    // Every lane takes part in every load and shuffle, with no branch and no zero
+    // fill: a lane past the row's end reads the row's last quad and stores nothing,
+    // and a neighbour outside the grid is read at the voxel's own place (its
+    // difference is then dropped by the in-grid flags; a label read there equals
+    // the voxel's own, so the one-label test still covers the in-grid faces alone).
+    const int xq = inrow ? x0 : A.pitch - 4;
     const int zb = blockIdx.z * A.zchunk, ze = min(A.nz, zb + A.zchunk);
     const T *hin = (const T *)A.th_in;
     T *hout = (T *)A.th_out;
     const T thr = (T)A.thr;
-    const size_t rowoff = (size_t)y * A.pitch + x0;
+    const size_t rowoff = (size_t)y * A.pitch + xq;
     const bool hasYm = y > 0, hasYp = y < A.ny - 1, hasL = x0 > 0, hasR = x0 + 4 < A.nx;
-    MQ<T> hm = mzq<T>(), hc = mzq<T>(), hp = mzq<T>();
+    const size_t dym = hasYm ? (size_t)A.pitch : 0, dyp = hasYp ? (size_t)A.pitch : 0;
+    // lane 0 reads the voxel left of its quad and lane 31 the one right of it; the
+    // other lanes take theirs from the neighbouring lanes by shuffles
+    const ptrdiff_t dxe = lane == 0 ? (hasL && xq > 0 ? -1 : 0) : (lane == 31 && hasR ? 4 : 0);
+    MQ<T> hm, hc, hp;
     MQ<float> lm = mzq<float>(), lc = mzq<float>(), lp = mzq<float>();
-    uint32_t labm = 0, labc = 0, labp = 0;
-    if (inrow) {
-        const size_t ic = (size_t)zb * A.plane + rowoff;
+    uint32_t labm, labc, labp;
+    {
+        const size_t ic = (size_t)zb * A.plane + rowoff, im = zb > 0 ? ic - A.plane : ic;
         hc = mldq(hin + ic);
-        if (COMP) lc = mldq(A.lo_in + ic);
-        labc = *reinterpret_cast<const uint32_t *>(A.label + ic);
-        if (zb > 0) {
-            hm = mldq(hin + ic - A.plane);
-            if (COMP) lm = mldq(A.lo_in + ic - A.plane);
-            labm = *reinterpret_cast<const uint32_t *>(A.label + ic - A.plane);
+        hm = mldq(hin + im);
+        if (COMP) {
+            lc = mldq(A.lo_in + ic);
+            lm = mldq(A.lo_in + im);
         }
+        labc = *reinterpret_cast<const uint32_t *>(A.label + ic);
+        labm = *reinterpret_cast<const uint32_t *>(A.label + im);
     }
     bool bad = false;
     for (int z = zb; z < ze; ++z) {
         const size_t i = (size_t)z * A.plane + rowoff;
         const bool hasZp = z + 1 < A.nz, hasZm = z > 0;
-        MQ<T> hym = mzq<T>(), hyp = mzq<T>();
+        const size_t ip = hasZp ? i + A.plane : i;
+        hp = mldq(hin + ip);
+        const MQ<T> hym = mldq(hin + i - dym), hyp = mldq(hin + i + dyp);
         MQ<float> lym = mzq<float>(), lyp = mzq<float>();
-        uint32_t labym = 0, labyp = 0;
-        W aq[4] = {0, 0, 0, 0}, bq[4] = {0, 0, 0, 0};
-        MQ<T> sq = mzq<T>();
-        if (inrow) {
-            if (hasZp) {
-                hp = mldq(hin + i + A.plane);
-                if (COMP) lp = mldq(A.lo_in + i + A.plane);
-                labp = *reinterpret_cast<const uint32_t *>(A.label + i + A.plane);
-            }
-            if (hasYm) {
-                hym = mldq(hin + i - A.pitch);
-                if (COMP) lym = mldq(A.lo_in + i - A.pitch);
-                labym = *reinterpret_cast<const uint32_t *>(A.label + i - A.pitch);
-            }
-            if (hasYp) {
-                hyp = mldq(hin + i + A.pitch);
-                if (COMP) lyp = mldq(A.lo_in + i + A.pitch);
-                labyp = *reinterpret_cast<const uint32_t *>(A.label + i + A.pitch);
-            }
-            mld_ab<PP, W>(A.ab, i, aq, bq);
-            sq = mldq((const T *)A.s + i);
+        float le = 0.f;
+        if (COMP) {
+            lp = mldq(A.lo_in + ip);
+            lym = mldq(A.lo_in + i - dym);
+            lyp = mldq(A.lo_in + i + dyp);
+            le = A.lo_in[i + dxe];
+        }
+        labp = *reinterpret_cast<const uint32_t *>(A.label + ip);
+        const uint32_t labym = *reinterpret_cast<const uint32_t *>(A.label + i - dym);
+        const uint32_t labyp = *reinterpret_cast<const uint32_t *>(A.label + i + dyp);
+        const T he = hin[i + dxe];
+        const uint32_t lbe = A.label[i + dxe];
+        W aq[4], bq[4];
+        mld_ab<PP, W>(A.ab, i, aq, bq);
+        const MQ<T> sq = mldq((const T *)A.s + i);
+        MQ<double> om4 = mzq<double>();
+        float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (A.damage || ALPHA) {
+            cc = *reinterpret_cast<const float4 *>(A.omega_c + i);
+            if (ALPHA || A.fold || SP == RFA_STATE_F64) om4 = mldq(A.omega + i);
         }
         // x neighbours across quads (value, lo part, label)
         T left = __shfl_up_sync(FULL, hc.v[3], 1), right = __shfl_down_sync(FULL, hc.v[0], 1);
@@ -202,15 +227,15 @@ __global__ void __launch_bounds__(256, (COND && !ALPHA && SP != RFA_STATE_F64) ?
             lright = __shfl_down_sync(FULL, lc.v[0], 1);
         }
         uint32_t labl = __shfl_up_sync(FULL, labc >> 24, 1), labr = __shfl_down_sync(FULL, labc & 0xffu, 1);
-        if (inrow && lane == 0 && hasL) {
-            left = hin[i - 1];
-            if (COMP) lleft = A.lo_in[i - 1];
-            labl = A.label[i - 1];
+        if (lane == 0) {
+            left = he;
+            lleft = le;
+            labl = lbe;
         }
-        if (inrow && lane == 31 && hasR) {
-            right = hin[i + 4];
-            if (COMP) lright = A.lo_in[i + 4];
-            labr = A.label[i + 4];
+        if (lane == 31) {
+            right = he;
+            lright = le;
+            labr = lbe;
         }
         // the quad, its x neighbours and its y/z neighbour quads all of one label
         const uint32_t l0 = labc & 0xffu;
@@ -218,85 +243,149 @@ __global__ void __launch_bounds__(256, (COND && !ALPHA && SP != RFA_STATE_F64) ?
                          labp == labc && labl == l0 && labr == l0;
         W wuni = W(0);
         if (COND && uni) wuni = wt[l0 * (kCondLabels + 1)];
-        if (inrow) {
-            MQ<double> om4 = mzq<double>();
-            float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (A.damage || ALPHA) {
-                cc = *reinterpret_cast<const float4 *>(A.omega_c + i);
-                if (ALPHA || A.fold || SP == RFA_STATE_F64) om4 = mldq(A.omega + i);
+        const float ccv[4] = {cc.x, cc.y, cc.z, cc.w};
+        MQ<T> ho;
+        MQ<float> lo;
+        uint32_t latch_bits = 0;
+        IT inc[4] = {0, 0, 0, 0};
+        // b of a free voxel: with the tissue state, b / max(1, Omega) with Omega at the
+        // start of the step.  Omega below 0.5 (the high word of the double) and a carry
+        // below 0.5 give an FP64 sum below 1 exactly, so the FP64 sum and the division
+        // are skipped there.
+        auto bfree = [&](int q) -> BT {
+            BT bd = (BT)bq[q];
+            if (ALPHA && !(__double2hiint(om4.v[q]) < 0x3FE00000 && ccv[q] < 0.5f)) {
+                const double om = om4.v[q] + (double)ccv[q];
+                if (om > 1.0) bd = (BT)((double)bq[q] / om);
             }
-            const float ccv[4] = {cc.x, cc.y, cc.z, cc.w};
-            MQ<T> ho;
-            MQ<float> lo;
-            uint32_t latch_bits = 0;
-            IT inc[4] = {0, 0, 0, 0};
+            return bd;
+        };
+        if (COMP) {
+            // compensated FP32 state: the voxels (0, 1) and (2, 3) of the quad at once with
+            // the paired FP32 instructions; every lane performs the operations of cdiff,
+            // cupdate and cadd in their order, so the results are bit-identical to the
+            // one-voxel forms (the centre form's to the one-step kernel's)
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const int qa = 2 * p, qb = qa + 1;
+                const int xa = x0 + qa, xb = x0 + qb;
+                const float2 c2 = make_float2((float)hc.v[qa], (float)hc.v[qb]);
+                const float2 cl2 = make_float2(lc.v[qa], lc.v[qb]);
+                float2 nh2 = c2, nl2 = cl2;
+                const bool ua = aq[qa] != W(0) && xa < A.nx, ub = aq[qb] != W(0) && xb < A.nx;
+                if (ua || ub) {
+                    const float2 b2 = make_float2((float)bfree(qa), (float)bfree(qb));
+                    const float2 s2 = make_float2((float)sq.v[qa], (float)sq.v[qb]);
+                    // neighbour pairs in the fixed order x-, x+, y-, y+, z-, z+
+                    const float2 nb[6] = {
+                        make_float2(qa == 0 ? (float)left : (float)hc.v[qa - 1], (float)hc.v[qa]),
+                        make_float2((float)hc.v[qb], qb == 3 ? (float)right : (float)hc.v[qb + 1]),
+                        make_float2((float)hym.v[qa], (float)hym.v[qb]),
+                        make_float2((float)hyp.v[qa], (float)hyp.v[qb]),
+                        make_float2((float)hm.v[qa], (float)hm.v[qb]),
+                        make_float2((float)hp.v[qa], (float)hp.v[qb])};
+                    const float2 nbl[6] = {make_float2(qa == 0 ? lleft : lc.v[qa - 1], lc.v[qa]),
+                                           make_float2(lc.v[qb], qb == 3 ? lright : lc.v[qb + 1]),
+                                           make_float2(lym.v[qa], lym.v[qb]),
+                                           make_float2(lyp.v[qa], lyp.v[qb]),
+                                           make_float2(lm.v[qa], lm.v[qb]),
+                                           make_float2(lp.v[qa], lp.v[qb])};
+                    const bool ina[6] = {xa > 0, xa + 1 < A.nx, hasYm, hasYp, hasZm, hasZp};
+                    const bool inb[6] = {true, xb + 1 < A.nx, hasYm, hasYp, hasZm, hasZp};
+                    float2 h2, l2;
+                    if (!COND) {
+                        float2 S = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int d = 0; d < 6; ++d) {
+                            const float2 dd = cdiff2(nb[d], nbl[d], c2, cl2);
+                            S = add2(S, make_float2(ina[d] ? dd.x : 0.f, inb[d] ? dd.y : 0.f));
+                        }
+                        float2 th;
+                        cupdate2(c2, cl2, S, make_float2((float)aq[qa], (float)aq[qb]), b2, s2, h2, l2, th);
+                    } else {
+                        // face weights: one table entry where the quad and all its
+                        // neighbours share a label, else one look-up per face and voxel
+                        float2 w2[6];
+                        if (uni) {
+#pragma unroll
+                            for (int d = 0; d < 6; ++d) w2[d] = make_float2((float)wuni, (float)wuni);
+                        } else {
+                            const int la = byte_at(labc, qa), lb = byte_at(labc, qb);
+                            const int nla[6] = {qa == 0 ? (int)labl : byte_at(labc, qa - 1), byte_at(labc, qb),
+                                                byte_at(labym, qa), byte_at(labyp, qa),
+                                                byte_at(labm, qa), byte_at(labp, qa)};
+                            const int nlb[6] = {byte_at(labc, qa), qb == 3 ? (int)labr : byte_at(labc, qb + 1),
+                                                byte_at(labym, qb), byte_at(labyp, qb),
+                                                byte_at(labm, qb), byte_at(labp, qb)};
+#pragma unroll
+                            for (int d = 0; d < 6; ++d)
+                                w2[d] = make_float2((float)wt[la * kCondLabels + nla[d]],
+                                                    (float)wt[lb * kCondLabels + nlb[d]]);
+                        }
+                        const float2 th = add2(c2, cl2);
+                        float2 delta = __ffma2_rn(neg2(b2), th, s2);
+#pragma unroll
+                        for (int d = 0; d < 6; ++d) {
+                            const float2 r = __ffma2_rn(w2[d], cdiff2(nb[d], nbl[d], c2, cl2), delta);
+                            delta = make_float2(ina[d] ? r.x : delta.x, inb[d] ? r.y : delta.y);
+                        }
+                        cadd2(c2, cl2, delta, h2, l2);
+                    }
+                    nh2 = make_float2(ua ? h2.x : c2.x, ub ? h2.y : c2.y);
+                    nl2 = make_float2(ua ? l2.x : cl2.x, ub ? l2.y : cl2.y);
+                }
+                if (xa >= A.nx) nh2.x = nl2.x = 0.f;
+                if (xb >= A.nx) nh2.y = nl2.y = 0.f;
+                bad |= (xa < A.nx && !isfinite(nh2.x)) || (xb < A.nx && !isfinite(nh2.y));
+                ho.v[qa] = (T)nh2.x;
+                ho.v[qb] = (T)nh2.y;
+                lo.v[qa] = nl2.x;
+                lo.v[qb] = nl2.y;
+                if (A.latch_on) {
+                    if (xa < A.nx && nh2.x + nl2.x >= (float)thr) latch_bits |= 1u << (8 * qa);
+                    if (xb < A.nx && nh2.y + nl2.y >= (float)thr) latch_bits |= 1u << (8 * qb);
+                }
+                if (A.damage) {
+                    const float2 e2 = arrhenius_inc2(add2(nh2, nl2), A.dc.c0, A.dc.c1, A.dc.TK0);
+                    inc[qa] = (IT)e2.x;
+                    inc[qb] = (IT)e2.y;
+                }
+            }
+        }
+        if (!COMP) {
+            // plain FP32 or FP64 state, one voxel at a time
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int x = x0 + q;
                 const T c = hc.v[q];
-                const float cl = COMP ? lc.v[q] : 0.f;
                 T nh = c;
-                float nl = cl;
                 if (aq[q] != W(0) && x < A.nx) {
-                    BT bd = (BT)bq[q];
-                    // tissue state: b / max(1, Omega) with Omega at the start of the step.  Omega
-                    // below 0.5 (the high word of the double) and a carry below 0.5 give an FP64
-                    // sum below 1 exactly, so the FP64 sum and the division are skipped there.
-                    if (ALPHA && !(__double2hiint(om4.v[q]) < 0x3FE00000 && ccv[q] < 0.5f)) {
-                        const double om = om4.v[q] + (double)ccv[q];
-                        if (om > 1.0) bd = (BT)((double)bq[q] / om);
-                    }
+                    const BT bd = bfree(q);
                     // neighbours in the fixed order x-, x+, y-, y+, z-, z+
                     const bool in[6] = {x > 0, x + 1 < A.nx, hasYm, hasYp, hasZm, hasZp};
-                    const T nbh[6] = {q == 0 ? left : hc.v[q - 1], q == 3 ? right : hc.v[q + 1], hym.v[q], hyp.v[q],
-                                      hm.v[q], hp.v[q]};
-                    const float nbl[6] = {COMP ? (q == 0 ? lleft : lc.v[q - 1]) : 0.f,
-                                          COMP ? (q == 3 ? lright : lc.v[q + 1]) : 0.f, lym.v[q], lyp.v[q], lm.v[q],
-                                          lp.v[q]};
-                    // face weights w(l, m): one table entry where the quad and all its
-                    // neighbours share a label, else one look-up per face
-                    W wv[6];
-                    if (COND) {
-                        if (uni) {
-#pragma unroll
-                            for (int d = 0; d < 6; ++d) wv[d] = wuni;
-                        } else {
-                            const int l = (labc >> (8 * q)) & 0xff;
-                            const int nbl_lab[6] = {q == 0 ? (int)labl : (int)((labc >> (8 * (q - 1))) & 0xff),
-                                                    q == 3 ? (int)labr : (int)((labc >> (8 * (q + 1))) & 0xff),
-                                                    (int)((labym >> (8 * q)) & 0xff),
-                                                    (int)((labyp >> (8 * q)) & 0xff),
-                                                    (int)((labm >> (8 * q)) & 0xff),
-                                                    (int)((labp >> (8 * q)) & 0xff)};
-#pragma unroll
-                            for (int d = 0; d < 6; ++d) wv[d] = wt[l * kCondLabels + nbl_lab[d]];
-                        }
-                    }
-                    if (COMP) {
-                        float h2, l2;
-                        if (!COND) {
-                            float S = 0.f;
-#pragma unroll
-                            for (int d = 0; d < 6; ++d)
-                                S = acc(S, in[d] ? cdiff((float)nbh[d], nbl[d], (float)c, cl) : 0.f);
-                            cupdate((float)c, cl, S, (float)aq[q], (float)bd, (float)sq.v[q], h2, l2);
-                        } else {
-                            const float th = __fadd_rn((float)c, cl);
-                            float delta = __fmaf_rn(-(float)bd, th, (float)sq.v[q]);
-#pragma unroll
-                            for (int d = 0; d < 6; ++d)
-                                if (in[d])
-                                    delta = __fmaf_rn((float)wv[d], cdiff((float)nbh[d], nbl[d], (float)c, cl), delta);
-                            cadd((float)c, cl, delta, h2, l2);
-                        }
-                        nh = (T)h2;
-                        nl = l2;
-                    } else if (!COND) {
+                    const T nbh[6] = {q == 0 ? left : hc.v[q - 1], q == 3 ? right : hc.v[q + 1], hym.v[q],
+                                      hyp.v[q], hm.v[q], hp.v[q]};
+                    if (!COND) {
                         T S = T(0);
 #pragma unroll
                         for (int d = 0; d < 6; ++d) S = acc(S, in[d] ? pdiff(nbh[d], c) : T(0));
                         nh = pupdate(c, S, (T)aq[q], (T)bd, sq.v[q]);
                     } else {
+                        // face weights w(l, m): one table entry where the quad and all its
+                        // neighbours share a label, else one look-up per face
+                        W wv[6];
+                        if (uni) {
+#pragma unroll
+                            for (int d = 0; d < 6; ++d) wv[d] = wuni;
+                        } else {
+                            const int l = byte_at(labc, q);
+                            const int nbl_lab[6] = {q == 0 ? (int)labl : byte_at(labc, q - 1),
+                                                    q == 3 ? (int)labr : byte_at(labc, q + 1),
+                                                    byte_at(labym, q), byte_at(labyp, q),
+                                                    byte_at(labm, q), byte_at(labp, q)};
+#pragma unroll
+                            for (int d = 0; d < 6; ++d) wv[d] = wt[l * kCondLabels + nbl_lab[d]];
+                        }
                         T delta;
                         if (SP == RFA_STATE_F64) delta = (T)__fma_rn(-bd, (double)c, (double)sq.v[q]);
                         else delta = (T)__fmaf_rn(-(float)bd, (float)c, (float)sq.v[q]);
@@ -313,19 +402,18 @@ __global__ void __launch_bounds__(256, (COND && !ALPHA && SP != RFA_STATE_F64) ?
                                                  : (T)__fadd_rn((float)c, (float)delta);
                     }
                 }
-                if (x >= A.nx) {
-                    nh = T(0);
-                    nl = 0.f;
-                }
+                if (x >= A.nx) nh = T(0);
                 bad |= x < A.nx && !isfinite(nh);
                 ho.v[q] = nh;
-                lo.v[q] = nl;
-                if (A.latch_on && x < A.nx && nh + (T)nl >= thr) latch_bits |= 1u << (8 * q);
+                lo.v[q] = 0.f;
+                if (A.latch_on && x < A.nx && nh >= thr) latch_bits |= 1u << (8 * q);
                 if (A.damage && x < A.nx) {
                     if (SP == RFA_STATE_F64) inc[q] = exp2(A.dc.c0d - A.dc.c1d / ((double)nh + A.dc.TK0d));
-                    else inc[q] = arrhenius_inc(__fadd_rn((float)nh, nl), A.dc.c0, A.dc.c1, A.dc.TK0);
+                    else inc[q] = arrhenius_inc(__fadd_rn((float)nh, 0.f), A.dc.c0, A.dc.c1, A.dc.TK0);
                 }
             }
+        }
+        if (inrow) {
             if (SP == RFA_STATE_F64) {
                 reinterpret_cast<double2 *>(hout + i)[0] = make_double2((double)ho.v[0], (double)ho.v[1]);
                 reinterpret_cast<double2 *>(hout + i)[1] = make_double2((double)ho.v[2], (double)ho.v[3]);
@@ -393,8 +481,6 @@ struct CondAdjArgs {
     size_t plane;
     double *acc;                   // [0..7] dL/dK, [8..15] dL/dw_b
 };
-
-__device__ __forceinline__ int byte_at(uint32_t w, int q) { return (int)((w >> (8 * q)) & 0xffu); }
 
 // One adjoint step of the conservative form: lam_out = A^T lam_in, Lam +=
 // lam_in, and the contractions dL/dK (through both labels of every face of a
