@@ -135,7 +135,20 @@ __device__ __forceinline__ void adj_load_ab(const void *ab, size_t i, float a[4]
 
 __device__ __forceinline__ float4 ld4g(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
 
-// one adjoint step: lam_out = A^T lam_in, Lam += lam_in, per-label contractions
+// the coefficient a of one voxel
+template <int PP>
+__device__ __forceinline__ float adj_load_a1(const void *ab, size_t i)
+{
+    if (PP == RFA_PARAM_BF16) return bf16_to_float(__ldg((const uint32_t *)ab + i) & 0xffffu);
+    if (PP == RFA_PARAM_F32) return __ldg((const float2 *)ab + i).x;
+    return (float)__ldg((const double2 *)ab + i).x;
+}
+
+// one adjoint step: lam_out = A^T lam_in, Lam += lam_in, per-label contractions.
+// Every lane of a row takes part in every load, with no branch and no zero fill:
+// a lane past the row's end reads the row's last quad and stores nothing, and a
+// neighbour outside the grid is read at the voxel's own place and dropped by the
+// in-grid flags.
 template <int PP, int NL>
 __global__ void __launch_bounds__(256, 2) k_adjoint_step(const AdjArgs A)
 {
@@ -150,60 +163,46 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_step(const AdjArgs A)
     const bool wvalid = y < A.ny;  // warp-uniform (blockDim.x == 32)
     const int x0 = 4 * (blockIdx.x * 32 + lane);
     const bool inrow = wvalid && x0 < A.pitch;
+    const int xq = x0 < A.pitch ? x0 : A.pitch - 4;
     const int zb = blockIdx.z * A.zchunk;
     const int ze = min(A.nz, zb + A.zchunk);
-    const size_t rowoff = (size_t)(wvalid ? y : 0) * A.pitch + x0;
+    const size_t rowoff = (size_t)(wvalid ? y : 0) * A.pitch + xq;
     const bool hasYm = y > 0, hasYp = y < A.ny - 1;
+    const size_t dym = hasYm ? (size_t)A.pitch : 0, dyp = hasYp ? (size_t)A.pitch : 0;
+    // lane 0 reads the voxel left of its quad and lane 31 the one right of it; the
+    // other lanes take theirs from the neighbouring lanes by shuffles
+    const ptrdiff_t dxe = lane == 0 ? (x0 > 0 && xq > 0 ? -1 : 0) : (lane == 31 && x0 + 4 < A.nx ? 4 : 0);
 
     if (wvalid) {
-        float4 lm = make_float4(0, 0, 0, 0), lc = lm, lp = lm;   // lambda at z-1, z, z+1
-        float4 tm = lm, tc = lm, tp = lm;                         // theta
-        float am[4] = {0, 0, 0, 0}, ac[4] = {0, 0, 0, 0}, ap[4] = {0, 0, 0, 0};
-        float bc[4] = {0, 0, 0, 0}, bp[4] = {0, 0, 0, 0}, bdum[4];
-        if (inrow) {
-            if (zb > 0) {
-                const size_t i = (size_t)(zb - 1) * A.plane + rowoff;
-                lm = ld4g(A.lam_in + i);
-                tm = ld4g(A.th + i);
-                adj_load_ab<PP>(A.ab, i, am, bdum);
-            }
-            const size_t i = (size_t)zb * A.plane + rowoff;
-            lc = ld4g(A.lam_in + i);
-            tc = ld4g(A.th + i);
-            adj_load_ab<PP>(A.ab, i, ac, bc);
+        float4 lm, lc, lp, tm, tc, tp;                            // lambda and theta at z-1, z, z+1
+        float am[4], ac[4], ap[4], bc[4], bp[4], bdum[4];
+        {
+            const size_t ic = (size_t)zb * A.plane + rowoff, im = zb > 0 ? ic - A.plane : ic;
+            lm = ld4g(A.lam_in + im);
+            tm = ld4g(A.th + im);
+            adj_load_ab<PP>(A.ab, im, am, bdum);
+            lc = ld4g(A.lam_in + ic);
+            tc = ld4g(A.th + ic);
+            adj_load_ab<PP>(A.ab, ic, ac, bc);
         }
         for (int z = zb; z < ze; ++z) {
             const size_t i = (size_t)z * A.plane + rowoff;
             const bool hasZp = z + 1 < A.nz, hasZm = z > 0;
-            float4 lym = make_float4(0, 0, 0, 0), lyp = lym, tym = lym, typ = lym;
-            float aym[4] = {0, 0, 0, 0}, ayp[4] = {0, 0, 0, 0};
-            uint32_t lab4 = 0;
+            const size_t ip = hasZp ? i + A.plane : i;
+            lp = ld4g(A.lam_in + ip);
+            tp = ld4g(A.th + ip);
+            adj_load_ab<PP>(A.ab, ip, ap, bp);
+            const float4 lym = ld4g(A.lam_in + i - dym), tym = ld4g(A.th + i - dym);
+            const float4 lyp = ld4g(A.lam_in + i + dyp), typ = ld4g(A.th + i + dyp);
+            float aym[4], ayp[4];
+            adj_load_ab<PP>(A.ab, i - dym, aym, bdum);
+            adj_load_ab<PP>(A.ab, i + dyp, ayp, bdum);
+            const uint32_t lab4 = __ldg(reinterpret_cast<const uint32_t *>(A.label + i));
             float4 Lc = make_float4(0, 0, 0, 0), Lp = Lc;
-            if (inrow) {
-                if (hasZp) {
-                    lp = ld4g(A.lam_in + i + A.plane);
-                    tp = ld4g(A.th + i + A.plane);
-                    adj_load_ab<PP>(A.ab, i + A.plane, ap, bp);
-                } else {
-                    lp = make_float4(0, 0, 0, 0);
-                    tp = lp;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) ap[q] = bp[q] = 0.f;
-                }
-                if (hasYm) {
-                    lym = ld4g(A.lam_in + i - A.pitch);
-                    tym = ld4g(A.th + i - A.pitch);
-                    adj_load_ab<PP>(A.ab, i - A.pitch, aym, bdum);
-                }
-                if (hasYp) {
-                    lyp = ld4g(A.lam_in + i + A.pitch);
-                    typ = ld4g(A.th + i + A.pitch);
-                    adj_load_ab<PP>(A.ab, i + A.pitch, ayp, bdum);
-                }
-                lab4 = __ldg(reinterpret_cast<const uint32_t *>(A.label + i));
-                if (A.lam_mode != 0) Lc = *reinterpret_cast<const float4 *>(A.Lam + i);
-                if (A.lam_mode == 1) Lp = *reinterpret_cast<const float4 *>(A.lam_out + i);
-            }
+            if (A.lam_mode != 0) Lc = *reinterpret_cast<const float4 *>(A.Lam + i);
+            if (A.lam_mode == 1) Lp = *reinterpret_cast<const float4 *>(A.lam_out + i);
+            const float ae = adj_load_a1<PP>(A.ab, i + dxe);
+            const float le = __ldg(A.lam_in + i + dxe), te = __ldg(A.th + i + dxe);
             const float lcv[4] = {lc.x, lc.y, lc.z, lc.w}, tcv[4] = {tc.x, tc.y, tc.z, tc.w};
             const float lmv[4] = {lm.x, lm.y, lm.z, lm.w}, tmv[4] = {tm.x, tm.y, tm.z, tm.w};
             const float lpv[4] = {lp.x, lp.y, lp.z, lp.w}, tpv[4] = {tp.x, tp.y, tp.z, tp.w};
@@ -215,33 +214,13 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_step(const AdjArgs A)
             // x neighbours across quads: mu and theta
             float muL = __shfl_up_sync(FULL, mu[3], 1), muR = __shfl_down_sync(FULL, mu[0], 1);
             float thL = __shfl_up_sync(FULL, tcv[3], 1), thR = __shfl_down_sync(FULL, tcv[0], 1);
-            if (inrow && lane == 0 && x0 > 0) {
-                float a1[1], b1[1];
-                (void)b1;
-                // scalar neighbour at x0 - 1 (coefficient and lambda)
-                if (PP == RFA_PARAM_BF16) {
-                    uint32_t w = __ldg((const uint32_t *)A.ab + i - 1);
-                    a1[0] = bf16_to_float(w & 0xffffu);
-                } else if (PP == RFA_PARAM_F32) {
-                    a1[0] = __ldg((const float2 *)A.ab + i - 1).x;
-                } else {
-                    a1[0] = (float)__ldg((const double2 *)A.ab + i - 1).x;
-                }
-                muL = a1[0] * __ldg(A.lam_in + i - 1);
-                thL = __ldg(A.th + i - 1);
+            if (lane == 0) {
+                muL = ae * le;
+                thL = te;
             }
-            if (inrow && lane == 31 && x0 + 4 < A.nx) {
-                float a1;
-                if (PP == RFA_PARAM_BF16) {
-                    uint32_t w = __ldg((const uint32_t *)A.ab + i + 4);
-                    a1 = bf16_to_float(w & 0xffffu);
-                } else if (PP == RFA_PARAM_F32) {
-                    a1 = __ldg((const float2 *)A.ab + i + 4).x;
-                } else {
-                    a1 = (float)__ldg((const double2 *)A.ab + i + 4).x;
-                }
-                muR = a1 * __ldg(A.lam_in + i + 4);
-                thR = __ldg(A.th + i + 4);
+            if (lane == 31) {
+                muR = ae * le;
+                thR = te;
             }
             if (inrow) {
                 float lo_[4], Lo_[4], vk4[4], vw4[4];
