@@ -134,6 +134,10 @@ __device__ __forceinline__ void adj_load_ab(const void *ab, size_t i, float a[4]
 }
 
 __device__ __forceinline__ float4 ld4g(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+// the cache line holding p into L2 (no register is written): a thread streaming z
+// asks for its fields two planes ahead, so their HBM latency overlaps the planes
+// in between
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 // the coefficient a of one voxel
 template <int PP>
@@ -189,6 +193,14 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_step(const AdjArgs A)
             const size_t i = (size_t)z * A.plane + rowoff;
             const bool hasZp = z + 1 < A.nz, hasZm = z > 0;
             const size_t ip = hasZp ? i + A.plane : i;
+            if (z + 2 < A.nz) {  // the streamed fields two planes ahead into L2
+                const size_t iq = i + 2 * A.plane;
+                prefetch_l2(A.lam_in + iq);
+                prefetch_l2(A.th + iq);
+                prefetch_l2((const char *)A.ab + iq * (PP == RFA_PARAM_BF16 ? 4 : PP == RFA_PARAM_F32 ? 8 : 16));
+                if (A.lam_mode != 0) prefetch_l2(A.Lam + iq);
+                if (A.lam_mode == 1) prefetch_l2(A.lam_out + iq);
+            }
             lp = ld4g(A.lam_in + ip);
             tp = ld4g(A.th + ip);
             adj_load_ab<PP>(A.ab, ip, ap, bp);
