@@ -760,11 +760,15 @@ def profile_case(name):
         seed = torch.full(case.labels.shape, 1e-6, dtype=torch.float32, device="cuda")
         for _ in range(2):
             g.backward(seed)
-    elif name == "adjoint256":
-        # the same at 256^3 (fields beyond L2): 200 recorded steps, two backward passes
+    elif name in ("adjoint256", "adjoint256h"):
+        # the same at 256^3 (fields beyond L2): 200 recorded steps, two backward passes;
+        # adjoint256h with the conservative (harmonic-mean face) conduction
         case = ph.adjoint_case_256(nsteps=200)
+        if name == "adjoint256h":
+            case.conduction = "harmonic"
         g = rfa.Grid.from_case(case, damage=False, cuda_stream=stream.cuda_stream)
-        g.set_schedule(2, 0)
+        if name == "adjoint256":
+            g.set_schedule(2, 0)
         g.step(case.nsteps, record=True)
         seed = torch.full(case.labels.shape, 1e-6, dtype=torch.float32, device="cuda")
         for _ in range(2):
@@ -822,7 +826,7 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-secondary", action="store_true", help="skip the adjoint and batched measurements")
     ap.add_argument("--batch-steps", type=int, default=4000)
-    ap.add_argument("--profile-case", default=None, help="batch16 | adjoint128 | adjoint256 | model256 | potential256: short case for ncu")
+    ap.add_argument("--profile-case", default=None, help="batch16 | adjoint128 | adjoint256 | adjoint256h | model256 | potential256: short case for ncu")
     args = ap.parse_args(argv)
     if args.schedule == "plain":
         args.schedule = "tb1"
