@@ -77,3 +77,38 @@ def test_noalloc_rejects_grids_above_its_scratch():
         rfa.rfa_necrosis_reduce_noalloc(g.handle, out, 1.0)
     assert e.value.status == 1 and "268435456" in str(e.value)
     g.close()
+
+
+def test_noalloc_reduction_captures_in_a_cuda_graph():
+    """After its first call on a device the entry point neither allocates nor
+    synchronises: a second call is captured into a CUDA graph on the grid's
+    stream (an allocating or synchronising call would end the capture with an
+    error), and replays of the graph read the state at replay time and give the
+    results of rfa_necrosis_mask."""
+    import torch
+    case = ph.random_small_case(17, 48, 40, 32, kind=ph.UMBRELLA, power=8.0)
+    s = torch.cuda.Stream()
+    g = rfa.Grid.from_case(case, cuda_stream=s.cuda_stream)
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(s):
+        g.step(40)
+        rfa.rfa_necrosis_reduce_noalloc(g.handle, out, 1.0)   # the first call looks up the scratch
+    s.synchronize()
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cg, stream=s):
+        rfa.rfa_necrosis_reduce_noalloc(g.handle, out, 1.0)
+    seen = 0
+    for nsteps in (60, 120):
+        with torch.cuda.stream(s):
+            g.step(nsteps)
+            out.fill_(-1.0)
+            cg.replay()
+        s.synchronize()
+        res = out.cpu()
+        _, counts, _, sv = g.necrosis(want_mask=False)
+        assert np.array_equal(res.view(torch.int64)[:2].numpy(), counts)
+        assert abs(float(res[2]) - sv) <= 1e-12 * max(sv, 1e-30)
+        seen = max(seen, int(counts[0]))
+    assert seen > 0
+    del cg
+    g.close()
