@@ -104,6 +104,7 @@ struct AdjArgs {
     size_t plane;
     float fk[kMaxGradLabels], gw[kMaxGradLabels];
     double *acc;  // [2 * kMaxGradLabels]: sum lambda f L(theta), -sum lambda g theta
+    unsigned *status;  // the grid's status word (index checks of the checked build)
 };
 
 template <int PP>
@@ -180,19 +181,35 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_step(const AdjArgs A)
     if (wvalid) {
         float4 lm, lc, lp, tm, tc, tp;                            // lambda and theta at z-1, z, z+1
         float am[4], ac[4], ap[4], bc[4], bp[4], bdum[4];
+        bool run = true;
         {
             const size_t ic = (size_t)zb * A.plane + rowoff, im = zb > 0 ? ic - A.plane : ic;
-            lm = ld4g(A.lam_in + im);
-            tm = ld4g(A.th + im);
-            adj_load_ab<PP>(A.ab, im, am, bdum);
-            lc = ld4g(A.lam_in + ic);
-            tc = ld4g(A.th + ic);
-            adj_load_ab<PP>(A.ab, ic, ac, bc);
+#ifdef RFA_CHECK
+            // checked build: the warp skips its chunk when any lane's range falls outside
+            run = __all_sync(FULL, RFA_CHECK_RANGE(im, ic + 4, A.plane * A.nz, ic, 4, A.status));
+#endif
+            if (run) {
+                lm = ld4g(A.lam_in + im);
+                tm = ld4g(A.th + im);
+                adj_load_ab<PP>(A.ab, im, am, bdum);
+                lc = ld4g(A.lam_in + ic);
+                tc = ld4g(A.th + ic);
+                adj_load_ab<PP>(A.ab, ic, ac, bc);
+            }
         }
-        for (int z = zb; z < ze; ++z) {
+        for (int z = zb; run && z < ze; ++z) {
             const size_t i = (size_t)z * A.plane + rowoff;
             const bool hasZp = z + 1 < A.nz, hasZm = z > 0;
             const size_t ip = hasZp ? i + A.plane : i;
+#ifdef RFA_CHECK
+            // checked build: every access of this iteration lies in [lo, hi) of arrays of
+            // plane * nz elements, the quads 4-aligned; the warp stops at the first miss
+            {
+                const long long lo = std::min((long long)(i - dym), (long long)i + dxe);
+                const long long hi = std::max((long long)std::max(ip, i + dyp) + 4, (long long)i + dxe + 1);
+                if (!__all_sync(FULL, RFA_CHECK_RANGE(lo, hi, A.plane * A.nz, i, 4, A.status))) break;
+            }
+#endif
             if (z + 2 < A.nz) {  // the streamed fields two planes ahead into L2
                 const size_t iq = i + 2 * A.plane;
                 prefetch_l2(A.lam_in + iq);
@@ -455,6 +472,8 @@ struct DevBuf {
 
 }  // namespace
 
+rfa_status read_status(rfa_grid *g);  // runtime.cu: the grid's status word, after a synchronize
+
 rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads)
 {
     if (g->sp == RFA_STATE_F64) {
@@ -512,6 +531,7 @@ rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads)
     A.zchunk = choose_zchunk_waves(g, 2);
     A.face = g->face;
     A.acc = accd;
+    A.status = g->status;
     for (int l = 0; l < kMaxGradLabels; ++l) {
         A.fk[l] = A.gw[l] = 0.f;
         if (l < g->n_labels && !g->table[l].fixed) {
@@ -578,6 +598,10 @@ rfa_status backward_impl(rfa_grid *g, const float *dLdT, double *grads)
     RFA_CUDA(cudaMemcpyAsync(host, accd, sizeof host, cudaMemcpyDeviceToHost, g->stream));
     RFA_CUDA(cudaStreamSynchronize(g->stream));
     tb_forget_maps(g);  // tensor maps of the segment buffers, freed on return
+    // a replay or reverse step that recorded a fault (a non-finite value, a timed-out
+    // wait, an index check of the checked build) fails the call
+    const rfa_status st = read_status(g);
+    if (st != RFA_OK) return st;
     const double W = host[32], A1 = host[36];
     const double *dW = host + 33, *A2 = host + 37;
     const double P = g->geom.P;

@@ -187,6 +187,10 @@ __global__ void __launch_bounds__(256, 2) k_step_model(const CondArgs A)
     uint32_t labm, labc, labp;
     {
         const size_t ic = (size_t)zb * A.plane + rowoff, im = zb > 0 ? ic - A.plane : ic;
+#ifdef RFA_CHECK
+        // checked build: the warp leaves when any lane's range falls outside the arrays
+        if (!__all_sync(FULL, RFA_CHECK_RANGE(im, ic + 4, A.plane * A.nz, ic, 4, A.status))) return;
+#endif
         hc = mldq(hin + ic);
         hm = mldq(hin + im);
         if (COMP) {
@@ -201,6 +205,15 @@ __global__ void __launch_bounds__(256, 2) k_step_model(const CondArgs A)
         const size_t i = (size_t)z * A.plane + rowoff;
         const bool hasZp = z + 1 < A.nz, hasZm = z > 0;
         const size_t ip = hasZp ? i + A.plane : i;
+#ifdef RFA_CHECK
+        // checked build: every access of this iteration lies in [lo, hi) of arrays of
+        // plane * nz elements, the quads 4-aligned; the warp stops at the first miss
+        {
+            const long long lo = std::min((long long)(i - dym), (long long)i + dxe);
+            const long long hi = std::max((long long)std::max(ip, i + dyp) + 4, (long long)i + dxe + 1);
+            if (!__all_sync(FULL, RFA_CHECK_RANGE(lo, hi, A.plane * A.nz, i, 4, A.status))) break;
+        }
+#endif
         if (z + 2 < A.nz) {  // the streamed fields two planes ahead into L2
             const size_t iq = i + 2 * A.plane;
             prefetch_l2(hin + iq);

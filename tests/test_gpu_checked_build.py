@@ -28,6 +28,12 @@ CASES = [
     "tests/test_gpu_tb.py::test_blocked_parity_with_oracle",
     "tests/test_gpu_batch.py::test_batch_equals_members_stepped_alone",
     "tests/test_zz_no_alloc.py::test_noalloc_reduction_matches_necrosis_mask_and_oracle_on_two_calls",
+    # the model-option step and the adjoint step read every neighbour at a clamped
+    # address (no branch): ragged grids, both face kinds, both state precisions
+    "tests/test_gpu_cond.py::test_conservative_step_matches_oracle",
+    "tests/test_gpu_alpha.py::test_coupled_perfusion_matches_oracle",
+    "tests/test_gpu_adjoint.py::test_adjoint_matches_oracle_small",
+    "tests/test_gpu_adjoint.py::test_adjoint_recorded_in_chunks_and_blocked_forward",
 ]
 
 
