@@ -529,15 +529,16 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_cond(const CondAdjArgs A)
     constexpr int NL = 8;  // the backward pass admits at most 8 labels
     const unsigned FULL = 0xffffffffu;
     // per label pair (l, m) of a voxel and its neighbour, the four weights a face
-    // uses, in one 16-byte entry: w(l, m), dw(l, m)/dK_l, w(m, l), dw(m, l)/dK_l
+    // uses, in one 16-byte entry: w(l, m), dw(l, m)/dK_l, and w(m, l), dw(m, l)/dK_l
+    // where label m is updated by the step (0 where it is fixed, so that a fixed
+    // neighbour's terms vanish without a test)
     __shared__ float4 pair[kCondLabels * kCondLabels];
-    __shared__ uint8_t afree[kCondLabels];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     for (int k = tid; k < kCondLabels * kCondLabels; k += blockDim.x * blockDim.y) {
         const int l = k / kCondLabels, m = k % kCondLabels, km = m * kCondLabels + l;
-        pair[k] = make_float4(A.wpair[k], A.dA[k], A.wpair[km], A.dB[km]);
+        const bool mfree = m < A.n_labels && A.tab[m].a != 0.0;
+        pair[k] = make_float4(A.wpair[k], A.dA[k], mfree ? A.wpair[km] : 0.f, mfree ? A.dB[km] : 0.f);
     }
-    if (tid < kCondLabels) afree[tid] = tid < A.n_labels && A.tab[tid].a != 0.0;
     __syncthreads();
     float accK[NL], accW[NL];
 #pragma unroll
@@ -650,21 +651,23 @@ __global__ void __launch_bounds__(256, 2) k_adjoint_cond(const CondAdjArgs A)
                     // theta_i) to label l_i and db[l_i][l_j] lam_i (theta_j - theta_i) to label
                     // l_j; the second is collected here by the receiving voxel, so every term
                     // lands on this voxel's own label
-                    float diag = fr ? 1.f - bq[q] : 1.f, nsum = 0.f, gk = 0.f;
+                    // (the two dL/dK terms in separate sums: shorter dependent chains)
+                    float diag = fr ? 1.f - bq[q] : 1.f, nsum = 0.f, g_in = 0.f, g_out = 0.f;
 #pragma unroll
                     for (int d = 0; d < 6; ++d) {
                         if (!in[d]) continue;
                         const int m = nlab[d];
                         const float4 c = pair[l * kCondLabels + m];
-                        if (afree[m] && !nface[d]) {
+                        if (!nface[d]) {  // (a fixed neighbour's entry holds zeros)
                             nsum += c.z * nl[d];
-                            gk += c.w * (nl[d] * (t - nt[d]));
+                            g_in += c.w * (nl[d] * (t - nt[d]));
                         }
                         if (fr) {
                             diag -= c.x;
-                            gk += c.y * (lam * (nt[d] - t));
+                            g_out += c.y * (nt[d] - t);
                         }
                     }
+                    const float gk = g_in + lam * g_out;
                     lo_[q] = valid ? diag * lam + nsum : 0.f;
                     Lo_[q] = valid ? Lcv[q] + lam : 0.f;
                     gkq[q] = valid ? gk : 0.f;
