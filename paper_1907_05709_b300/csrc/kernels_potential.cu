@@ -723,6 +723,11 @@ __global__ void __launch_bounds__(256) k_mg_first(MgLevel L, const float *b, flo
 // it is read (no pass stores it; in is not read).  Fusing the prolongation into
 // the first post-sweep the same way was measured slower (every neighbour read
 // then also loads 1/D and the coarse value): 143 us against 40 + 93 us at 256^3.
+// the cache line holding p into L2 (no register is written): a thread streaming z
+// asks for its fields two planes ahead, so their HBM latency overlaps the planes
+// in between (the fine-grid sweeps: 4 % of the solve, the same iterates)
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 template <bool RESID, bool FIRST>
 __global__ void __launch_bounds__(256) k_mg0_sweep_z(PotGrid G, const float *D32, const float *iD32, const float *b,
                                                     const float *in, float *out, int zchunk)
@@ -759,6 +764,14 @@ __global__ void __launch_bounds__(256) k_mg0_sweep_z(PotGrid G, const float *D32
     }
     for (int z = zb; z < ze; ++z, i += oz) {
         const bool hasZm = z > 0, hasZp = z + 1 < G.nz;
+        if (inrow && z + 2 < G.nz) {  // the streamed fields two planes ahead into L2
+            const size_t iq = i + 2 * oz;
+            prefetch_l2(b + iq);
+            prefetch_l2(FIRST ? iD32 + iq : in + iq);
+            prefetch_l2(D32 + iq);
+            if (!RESID && !FIRST) prefetch_l2(iD32 + iq);
+            prefetch_l2(G.cls + iq);
+        }
         vp = inrow && hasZp ? v4(i + oz) : zero;
         // x neighbours: lanes hold consecutive quads of the row; a quad past nx
         // holds zeros, as the padding does
