@@ -31,24 +31,6 @@ namespace rfa {
 
 namespace {
 
-template <int PP>
-__device__ __forceinline__ void cond_ab(const void *ab, size_t i, double &a, double &b)
-{
-    if (PP == RFA_PARAM_BF16) {
-        const uint32_t w = ((const uint32_t *)ab)[i];
-        a = bf16_to_float(w & 0xffffu);
-        b = bf16_to_float(w >> 16);
-    } else if (PP == RFA_PARAM_F32) {
-        const float2 v = ((const float2 *)ab)[i];
-        a = v.x;
-        b = v.y;
-    } else {
-        const double2 v = ((const double2 *)ab)[i];
-        a = v.x;
-        b = v.y;
-    }
-}
-
 struct CondArgs {
     const void *th_in;
     const float *lo_in;
