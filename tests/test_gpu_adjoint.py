@@ -123,3 +123,12 @@ def test_autograd_function_matches_rfa_backward():
     assert np.allclose(params.grad.numpy(), direct, rtol=1e-5, atol=0)
     assert params.grad[0].item() != 0.0
     g.close()
+
+
+def test_adjoint_rows_across_thread_blocks():
+    """Rows of 150 voxels span two blocks of 32 quads, the second ragged: the
+    reverse step's x neighbours across the block edge and the clamped lanes past
+    the row's end."""
+    case = ph.random_small_case(33, 150, 24, 20, kind=ph.UMBRELLA, power=6.0)
+    g_gpu, g_orc = _adjoint_case(case, 80)
+    _compare_grads(g_gpu, g_orc, len(case.table))

@@ -34,6 +34,8 @@ CASES = [
     "tests/test_gpu_alpha.py::test_coupled_perfusion_matches_oracle",
     "tests/test_gpu_adjoint.py::test_adjoint_matches_oracle_small",
     "tests/test_gpu_adjoint.py::test_adjoint_recorded_in_chunks_and_blocked_forward",
+    "tests/test_gpu_cond.py::test_model_step_rows_across_thread_blocks",
+    "tests/test_gpu_adjoint.py::test_adjoint_rows_across_thread_blocks",
 ]
 
 

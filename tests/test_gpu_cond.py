@@ -84,3 +84,39 @@ def test_conservative_mode_refusals():
         g.set_tissue(bad.labels, bad.table)
     assert e.value.status == 4
     g.close()
+
+
+@pytest.mark.parametrize("cond,perf", [("harmonic", "constant"), ("centre", "tissue_state"),
+                                       ("harmonic", "tissue_state")])
+@pytest.mark.parametrize("face", [ph.DIRICHLET, ph.INSULATED])
+def test_model_step_rows_across_thread_blocks(cond, perf, face):
+    """Rows of 150 voxels span two blocks of 32 quads, the second one ragged: the
+    x neighbours are read across the block edge (lane 31 of the first block, lane
+    0 of the second), and the lanes past the row's end read a clamped quad and
+    store nothing."""
+    case = _case(73, (150, 22, 16), face_bc=face, power=8.0)
+    case.conduction, case.perfusion = cond, perf
+    n = 160
+    orc = run_oracle(case, rfa.PARAM_BF16, n)
+    gpu = run_gpu(case, rfa.STATE_F32C, rfa.PARAM_BF16, n)
+    compare(case, gpu, orc, rfa.STATE_F32C)
+
+
+def test_conservative_adjoint_rows_across_thread_blocks():
+    import torch
+    case = _case(74, (150, 24, 20), kind=ph.STRAIGHT, power=5.0)
+    nsteps = 90
+    m = oracle.setup(case, "bf16")
+    st = oracle.initial_state(m)
+    oracle.run(m, st, nsteps)
+    rng = np.random.default_rng(1)
+    sel = rng.random(m.a.shape) < 0.1
+    target = st.theta + case.T_a_C + rng.normal(0, 2.0, size=m.a.shape)
+    seed = c3_loss_seed(st.theta, case.T_a_C, target, sel)
+    _, _, gk, gw, gP, gtip = oracle.adjoint(m, nsteps, seed)
+    g_orc = np.concatenate([[gP], gtip, gk, gw])
+    g = rfa.Grid.from_case(case, damage=False)
+    g.step(nsteps, record=True)
+    g_gpu = g.backward(torch.from_numpy(seed.astype(np.float32)).cuda())
+    g.close()
+    _compare_grads(g_gpu, g_orc, len(case.table))
