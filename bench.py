@@ -444,9 +444,11 @@ def measure_next_rows(rfa, stream, case, g, cpu_baseline_on: bool):
     g3.close()
     it, rel = res["r"]
     it_j, rel_j = res["j"]
+    keys = ("workload", "grid", "time_steps", "forward_recorded_ms", "backward_ms", "backward_over_forward")
     adj = measure_adjoint(rfa, stream, conduction="harmonic")
-    out["conservative_adjoint"] = {k: adj[k] for k in ("workload", "grid", "time_steps", "forward_recorded_ms",
-                                                       "backward_ms", "backward_over_forward")}
+    out["conservative_adjoint"] = {k: adj[k] for k in keys}
+    adj = measure_adjoint(rfa, stream, conduction="harmonic", name="adjoint256")   # fields beyond L2
+    out["conservative_adjoint256"] = {k: adj[k] for k in keys}
     n3 = c3.nvox
     out["potential_source"] = dict(roof(164.0 * n3 * it, ms, n3), workload="umbrella256", ms=ms,
                                    preconditioner="multigrid", cg_iterations=it,
@@ -713,6 +715,8 @@ def run_ours(args):
         summ["adjoint256_backward_over_forward"] = secondary["adjoint256"]["backward_over_forward"]
         summ["conservative_adjoint128_backward_over_forward"] = \
             secondary["next_rows"]["conservative_adjoint"]["backward_over_forward"]
+        summ["conservative_adjoint256_backward_over_forward"] = \
+            secondary["next_rows"]["conservative_adjoint256"]["backward_over_forward"]
         summ["batched_over_plain_loop"] = secondary["batched"]["batched_over_plain_loop"]
         summ["batched_over_tuned_loop"] = secondary["batched"]["batched_over_tuned_loop"]
         summ["batched_gvox_steps_s"] = secondary["batched"]["batched_gvox_steps_s"]
