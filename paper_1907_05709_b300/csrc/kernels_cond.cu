@@ -148,8 +148,8 @@ __global__ void __launch_bounds__(256, 2) k_step_model(const CondArgs A)
     if (y >= A.ny) return;  // whole warp (blockDim.x == 32), after the only barrier
     const int x0 = 4 * (blockIdx.x * 32 + lane);
     const bool inrow = x0 < A.pitch;
-    // Every lane takes part in every load and shuffle, with no branch and no zero
-    // fill: a lane past the row's end reads the row's last quad and stores nothing,
+    // Every lane takes part in every quad load and shuffle, with no branch and no
+    // zero fill: a lane past the row's end reads the row's last quad and stores nothing,
     // and a neighbour outside the grid is read at the voxel's own place (its
     // difference is then dropped by the in-grid flags; a label read there equals
     // the voxel's own, so the one-label test still covers the in-grid faces alone).
@@ -161,8 +161,9 @@ __global__ void __launch_bounds__(256, 2) k_step_model(const CondArgs A)
     const size_t rowoff = (size_t)y * A.pitch + xq;
     const bool hasYm = y > 0, hasYp = y < A.ny - 1, hasL = x0 > 0, hasR = x0 + 4 < A.nx;
     const size_t dym = hasYm ? (size_t)A.pitch : 0, dyp = hasYp ? (size_t)A.pitch : 0;
-    // lane 0 reads the voxel left of its quad and lane 31 the one right of it; the
-    // other lanes take theirs from the neighbouring lanes by shuffles
+    // lane 0 reads the voxel left of its quad and lane 31 the one right of it (those
+    // two lanes alone: the same load from every lane made the one-step kernel 3 %
+    // slower at 256^3); the other lanes take theirs from their neighbours by shuffles
     const ptrdiff_t dxe = lane == 0 ? (hasL && xq > 0 ? -1 : 0) : (lane == 31 && hasR ? 4 : 0);
     MQ<T> hm, hc, hp;
     MQ<float> lm = mzq<float>(), lc = mzq<float>(), lp = mzq<float>();
@@ -210,17 +211,22 @@ __global__ void __launch_bounds__(256, 2) k_step_model(const CondArgs A)
         const MQ<T> hym = mldq(hin + i - dym), hyp = mldq(hin + i + dyp);
         MQ<float> lym = mzq<float>(), lyp = mzq<float>();
         float le = 0.f;
+        T he = T(0);
+        uint32_t lbe = 0;
+        const bool edge = lane == 0 || lane == 31;
         if (COMP) {
             lp = mldq(A.lo_in + ip);
             lym = mldq(A.lo_in + i - dym);
             lyp = mldq(A.lo_in + i + dyp);
-            le = A.lo_in[i + dxe];
+            if (edge) le = A.lo_in[i + dxe];
         }
         labp = *reinterpret_cast<const uint32_t *>(A.label + ip);
         const uint32_t labym = *reinterpret_cast<const uint32_t *>(A.label + i - dym);
         const uint32_t labyp = *reinterpret_cast<const uint32_t *>(A.label + i + dyp);
-        const T he = hin[i + dxe];
-        const uint32_t lbe = A.label[i + dxe];
+        if (edge) {
+            he = hin[i + dxe];
+            lbe = A.label[i + dxe];
+        }
         W aq[4], bq[4];
         mld_ab<PP, W>(A.ab, i, aq, bq);
         const MQ<T> sq = mldq((const T *)A.s + i);

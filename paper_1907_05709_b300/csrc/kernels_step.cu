@@ -129,26 +129,50 @@ __global__ void __launch_bounds__(256) k_step_plain(const PlainArgs A)
     const float *lin = (const float *)A.lo_in;
     T *hout = (T *)A.th_out;
     float *lout = (float *)A.lo_out;
-    const size_t rowoff = (size_t)y * A.pitch + x0;
     const bool hasYm = y > 0, hasYp = y < A.ny - 1;
     const bool hasL = x0 > 0, hasR = x0 + 4 < A.nx;
     const T thr = (T)A.thr;
+    // Every lane takes part in every quad load and shuffle, with no branch and no
+    // zero fill: a lane past the row's end reads the row's last quad and stores nothing,
+    // and a neighbour outside the grid is read at the voxel's own place (its
+    // difference is then dropped by the in-grid flags).
+    const int xq = inrow ? x0 : A.pitch - 4;
+    const size_t rowoff = (size_t)y * A.pitch + xq;
+    const size_t dym = hasYm ? (size_t)A.pitch : 0, dyp = hasYp ? (size_t)A.pitch : 0;
+    // lane 0 reads the voxel left of its quad and lane 31 the one right of it (those
+    // two lanes alone: the same load from every lane made the one-step kernel 3 %
+    // slower at 256^3); the other lanes take theirs from their neighbours by shuffles
+    const ptrdiff_t dxe = lane == 0 ? (hasL && xq > 0 ? -1 : 0) : (lane == 31 && hasR ? 4 : 0);
 
-    Q4<T> hm = zq<T>(), hc = zq<T>(), hp = zq<T>();
+    Q4<T> hm, hc, hp;
     Q4<float> lm = zq<float>(), lc = zq<float>(), lp = zq<float>();
-    if (inrow && RFA_CHECK_RANGE((long long)((size_t)zb * A.plane + rowoff) - (zb > 0 ? (long long)A.plane : 0),
-                                 (size_t)zb * A.plane + rowoff + 4, A.plane * A.nz, rowoff, 4, A.status)) {
-        if (zb > 0) hm = ldq(hin + (size_t)(zb - 1) * A.plane + rowoff);
-        hc = ldq(hin + (size_t)zb * A.plane + rowoff);
+    {
+        const size_t ic = (size_t)zb * A.plane + rowoff, im = zb > 0 ? ic - A.plane : ic;
+#ifdef RFA_CHECK
+        // checked build: the warp leaves when any lane's range falls outside the arrays
+        if (!__all_sync(FULL, RFA_CHECK_RANGE(im, ic + 4, A.plane * A.nz, ic, 4, A.status))) return;
+#endif
+        hc = ldq(hin + ic);
+        hm = ldq(hin + im);
         if (COMP) {
-            if (zb > 0) lm = ldq(lin + (size_t)(zb - 1) * A.plane + rowoff);
-            lc = ldq(lin + (size_t)zb * A.plane + rowoff);
+            lc = ldq(lin + ic);
+            lm = ldq(lin + im);
         }
     }
     bool bad = false;
     for (int z = zb; z < ze; ++z) {
         const size_t i = (size_t)z * A.plane + rowoff;
         const bool hasZp = z + 1 < A.nz, hasZm = z > 0;
+        const size_t ip = hasZp ? i + A.plane : i;
+#ifdef RFA_CHECK
+        // checked build: every access of this iteration lies in [lo, hi) of arrays of
+        // plane * nz elements, the quads 4-aligned; the warp stops at the first miss
+        {
+            const long long lo = std::min((long long)(i - dym), (long long)i + dxe);
+            const long long hi = std::max((long long)std::max(ip, i + dyp) + 4, (long long)i + dxe + 1);
+            if (!__all_sync(FULL, RFA_CHECK_RANGE(lo, hi, A.plane * A.nz, i, 4, A.status))) break;
+        }
+#endif
         if (inrow && z + 2 < A.nz) {  // the streamed fields two planes ahead into L2
             const size_t iq = i + 2 * A.plane;
             prefetch_l2(hin + iq);
@@ -159,107 +183,126 @@ __global__ void __launch_bounds__(256) k_step_plain(const PlainArgs A)
             if (DMG) prefetch_l2(A.omega_c + iq);
             if (DMG && FOLD) prefetch_l2(A.omega + iq);
         }
-        // checked build: every access of this iteration lies in [i - pitch - 1, i + plane + 5)
-        // of arrays of plane * nz elements, quads 4-aligned (inb == inrow otherwise)
-        const bool inb =
-            inrow && RFA_CHECK_RANGE((long long)i - (hasYm ? A.pitch : 0) - (lane == 0 && hasL ? 1 : 0),
-                                     i + (hasZp ? A.plane : hasYp ? (size_t)A.pitch : 0) +
-                                         (lane == 31 && hasR ? 5 : 4),
-                                     A.plane * A.nz, i, 4, A.status);
-        Q4<T> hym = zq<T>(), hyp = zq<T>();
+        hp = ldq(hin + ip);
+        const Q4<T> hym = ldq(hin + i - dym), hyp = ldq(hin + i + dyp);
         Q4<float> lym = zq<float>(), lyp = zq<float>();
-        T aq[4], bq[4], sq[4];
-        T left = T(0), right = T(0);
-        float lleft = 0.f, lright = 0.f;
-        if (inb) {
-            if (hasZp) {
-                hp = ldq(hin + i + A.plane);
-                if (COMP) lp = ldq(lin + i + A.plane);
-            }
-            if (hasYm) {
-                hym = ldq(hin + i - A.pitch);
-                if (COMP) lym = ldq(lin + i - A.pitch);
-            }
-            if (hasYp) {
-                hyp = ldq(hin + i + A.pitch);
-                if (COMP) lyp = ldq(lin + i + A.pitch);
-            }
-            load_ab<PP, T>(A.ab, i, aq, bq);
-            Q4<T> sv = ldq((const T *)A.s + i);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) sq[q] = sv.v[q];
+        float le = 0.f;
+        T he = T(0);
+        const bool edge = lane == 0 || lane == 31;
+        if (COMP) {
+            lp = ldq(lin + ip);
+            lym = ldq(lin + i - dym);
+            lyp = ldq(lin + i + dyp);
+            if (edge) le = lin[i + dxe];
         }
+        if (edge) he = hin[i + dxe];
+        T aq[4], bq[4];
+        load_ab<PP, T>(A.ab, i, aq, bq);
+        const Q4<T> sv = ldq((const T *)A.s + i);
         // x neighbours across quads
-        left = __shfl_up_sync(FULL, hc.v[3], 1);
-        right = __shfl_down_sync(FULL, hc.v[0], 1);
+        T left = __shfl_up_sync(FULL, hc.v[3], 1), right = __shfl_down_sync(FULL, hc.v[0], 1);
+        float lleft = 0.f, lright = 0.f;
         if (COMP) {
             lleft = __shfl_up_sync(FULL, lc.v[3], 1);
             lright = __shfl_down_sync(FULL, lc.v[0], 1);
         }
-        if (inb && lane == 0 && hasL) {
-            left = hin[i - 1];
-            if (COMP) lleft = lin[i - 1];
+        if (lane == 0) {
+            left = he;
+            lleft = le;
         }
-        if (inb && lane == 31 && hasR) {
-            right = hin[i + 4];
-            if (COMP) lright = lin[i + 4];
+        if (lane == 31) {
+            right = he;
+            lright = le;
         }
-        if (inb) {
-            Q4<T> ho;
-            Q4<float> lo;
-            uint32_t latch_bits = 0;
-            double Sd[4];
+        Q4<T> ho;
+        Q4<float> lo;
+        uint32_t latch_bits = 0;
+        double Sd[4];
+        if (COMP) {
+            // the voxels (0, 1) and (2, 3) of the quad at once with the paired FP32
+            // instructions: every lane performs the operations of cdiff and cupdate in
+            // their order, bit-identical to the one-voxel forms
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const int qa = 2 * p, qb = qa + 1;
+                const int xa = x0 + qa, xb = x0 + qb;
+                const float2 c2 = make_float2((float)hc.v[qa], (float)hc.v[qb]);
+                const float2 cl2 = make_float2(lc.v[qa], lc.v[qb]);
+                // neighbour pairs in the fixed order x-, x+, y-, y+, z-, z+ (Eq. 2675-eq3)
+                const float2 nb[6] = {
+                    make_float2(qa == 0 ? (float)left : (float)hc.v[qa - 1], (float)hc.v[qa]),
+                    make_float2((float)hc.v[qb], qb == 3 ? (float)right : (float)hc.v[qb + 1]),
+                    make_float2((float)hym.v[qa], (float)hym.v[qb]),
+                    make_float2((float)hyp.v[qa], (float)hyp.v[qb]),
+                    make_float2((float)hm.v[qa], (float)hm.v[qb]),
+                    make_float2((float)hp.v[qa], (float)hp.v[qb])};
+                const float2 nbl[6] = {make_float2(qa == 0 ? lleft : lc.v[qa - 1], lc.v[qa]),
+                                       make_float2(lc.v[qb], qb == 3 ? lright : lc.v[qb + 1]),
+                                       make_float2(lym.v[qa], lym.v[qb]),
+                                       make_float2(lyp.v[qa], lyp.v[qb]),
+                                       make_float2(lm.v[qa], lm.v[qb]),
+                                       make_float2(lp.v[qa], lp.v[qb])};
+                const bool ina[6] = {xa > 0, xa + 1 < A.nx, hasYm, hasYp, hasZm, hasZp};
+                const bool inb[6] = {true, xb + 1 < A.nx, hasYm, hasYp, hasZm, hasZp};
+                float2 S = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int d = 0; d < 6; ++d) {
+                    const float2 dd = cdiff2(nb[d], nbl[d], c2, cl2);
+                    S = add2(S, make_float2(ina[d] ? dd.x : 0.f, inb[d] ? dd.y : 0.f));
+                }
+                float2 h2, l2, th;
+                cupdate2(c2, cl2, S, make_float2((float)aq[qa], (float)aq[qb]),
+                         make_float2((float)bq[qa], (float)bq[qb]), make_float2((float)sv.v[qa], (float)sv.v[qb]),
+                         h2, l2, th);
+                if (xa >= A.nx) h2.x = l2.x = 0.f;
+                if (xb >= A.nx) h2.y = l2.y = 0.f;
+                bad |= (xa < A.nx && !isfinite(h2.x)) || (xb < A.nx && !isfinite(h2.y));
+                ho.v[qa] = (T)h2.x;
+                ho.v[qb] = (T)h2.y;
+                lo.v[qa] = l2.x;
+                lo.v[qb] = l2.y;
+                if (LATCH) {
+                    if (xa < A.nx && h2.x + l2.x >= (float)thr) latch_bits |= 1u << (8 * qa);
+                    if (xb < A.nx && h2.y + l2.y >= (float)thr) latch_bits |= 1u << (8 * qb);
+                }
+                if (DMG) {
+                    const float2 e2 = arrhenius_inc2(add2(h2, l2), A.dc.c0, A.dc.c1, A.dc.TK0);
+                    Sd[qa] = (double)e2.x;
+                    Sd[qb] = (double)e2.y;
+                }
+            }
+        } else {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int x = x0 + q;
                 const T c = hc.v[q];
                 const T xm = q == 0 ? left : hc.v[q - 1];
                 const T xp = q == 3 ? right : hc.v[q + 1];
-                T nh;
-                float nl = 0.f;
-                if (COMP) {
-                    const float cl = lc.v[q];
-                    const float lxm = q == 0 ? lleft : lc.v[q - 1];
-                    const float lxp = q == 3 ? lright : lc.v[q + 1];
-                    // sum of neighbour differences (Eq. 2675-eq3 in x, y, z), fixed order
-                    float S = 0.f;
-                    S = acc(S, x > 0 ? cdiff((float)xm, lxm, (float)c, cl) : 0.f);
-                    S = acc(S, x + 1 < A.nx ? cdiff((float)xp, lxp, (float)c, cl) : 0.f);
-                    S = acc(S, hasYm ? cdiff((float)hym.v[q], lym.v[q], (float)c, cl) : 0.f);
-                    S = acc(S, hasYp ? cdiff((float)hyp.v[q], lyp.v[q], (float)c, cl) : 0.f);
-                    S = acc(S, hasZm ? cdiff((float)hm.v[q], lm.v[q], (float)c, cl) : 0.f);
-                    S = acc(S, hasZp ? cdiff((float)hp.v[q], lp.v[q], (float)c, cl) : 0.f);
-                    float h2;
-                    cupdate((float)c, cl, S, (float)aq[q], (float)bq[q], (float)sq[q], h2, nl);
-                    nh = (T)h2;
-                } else {
-                    T S = T(0);
-                    S = acc(S, x > 0 ? pdiff(xm, c) : T(0));
-                    S = acc(S, x + 1 < A.nx ? pdiff(xp, c) : T(0));
-                    S = acc(S, hasYm ? pdiff(hym.v[q], c) : T(0));
-                    S = acc(S, hasYp ? pdiff(hyp.v[q], c) : T(0));
-                    S = acc(S, hasZm ? pdiff(hm.v[q], c) : T(0));
-                    S = acc(S, hasZp ? pdiff(hp.v[q], c) : T(0));
-                    nh = pupdate(c, S, aq[q], bq[q], sq[q]);
-                }
-                if (x >= A.nx) {
-                    nh = T(0);
-                    nl = 0.f;
-                }
+                // sum of neighbour differences (Eq. 2675-eq3 in x, y, z), fixed order
+                T S = T(0);
+                S = acc(S, x > 0 ? pdiff(xm, c) : T(0));
+                S = acc(S, x + 1 < A.nx ? pdiff(xp, c) : T(0));
+                S = acc(S, hasYm ? pdiff(hym.v[q], c) : T(0));
+                S = acc(S, hasYp ? pdiff(hyp.v[q], c) : T(0));
+                S = acc(S, hasZm ? pdiff(hm.v[q], c) : T(0));
+                S = acc(S, hasZp ? pdiff(hp.v[q], c) : T(0));
+                T nh = pupdate(c, S, aq[q], bq[q], sv.v[q]);
+                if (x >= A.nx) nh = T(0);
                 bad |= (x < A.nx) && !isfinite((double)nh);
                 ho.v[q] = nh;
-                lo.v[q] = nl;
-                if (LATCH && x < A.nx && nh + (T)nl >= thr) latch_bits |= 1u << (8 * q);
+                lo.v[q] = 0.f;
+                if (LATCH && x < A.nx && nh + T(0) >= thr) latch_bits |= 1u << (8 * q);
                 if (DMG) {
                     if (SP == RFA_STATE_F64) {
                         double tk = (double)nh + A.dc.TK0d;
                         Sd[q] = exp2(A.dc.c0d - A.dc.c1d / tk);
                     } else {
-                        Sd[q] = (double)arrhenius_inc(__fadd_rn((float)nh, nl), A.dc.c0, A.dc.c1,
-                                                      A.dc.TK0);
+                        Sd[q] = (double)arrhenius_inc(__fadd_rn((float)nh, 0.f), A.dc.c0, A.dc.c1, A.dc.TK0);
                     }
                 }
             }
+        }
+        if (inrow) {
             stq(hout + i, ho);
             if (COMP) stq(lout + i, lo);
             if (LATCH && latch_bits) {
